@@ -1,0 +1,182 @@
+"""FP64 CPU oracle for the efunc O^{+Delta} representation (arXiv 2505.21319).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product path (the
+CUDA library and its Python binding) never imports this package.
+
+The arithmetic lives in ``efunc_oracle.c`` (plain C, FP64, single thread),
+which this module compiles with gcc on first use and wraps with ctypes.  Every
+function states the passage of the paper it follows; see the C file's header
+for the readings it fixes (domain, slot order, log-scale storage, window).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "efunc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libefunc_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NSLOT = 13
+L1, MSE = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/libefunc_oracle.so``.
+
+    ``-ffp-contract=off`` keeps the FP32 window decision free of fused
+    multiply-adds on every host (aarch64 gcc contracts by default)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            dp = ctypes.POINTER(ctypes.c_double)
+            i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            lib.ora_window_base.argtypes = [ctypes.c_float, i32]
+            lib.ora_window_base.restype = i32
+            lib.ora_forward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
+            lib.ora_backward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
+            lib.ora_forward_global.argtypes = [i32, f64, dp, dp, i64, i32, dp, dp]
+            lib.ora_loss_grad.argtypes = [i32, dp, dp, i64, dp, dp, dp]
+            lib.ora_adam.argtypes = [i64, dp, dp, dp, dp, i64, f64, f64, f64, f64, f64, i32]
+            for fn in ("ora_forward", "ora_backward", "ora_forward_global", "ora_loss_grad", "ora_adam"):
+                getattr(lib, fn).restype = None
+            _lib = lib
+    return _lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def default_log_beta0(R: int) -> float:
+    """log(beta) at initialisation.  Sec. 4.3 initialises every scale to exp(7)
+    (stated for the 32^3 grid); keeping beta*h^2 fixed across resolutions gives
+    7 + 2 ln(R/32)."""
+    return 7.0 + 2.0 * float(np.log(R / 32.0))
+
+
+def window_base(q: float, R: int) -> int:
+    """FP32 window base index along one axis (C function ``ora_window_base``)."""
+    return int(_load().ora_window_base(ctypes.c_float(float(np.float32(q))), R))
+
+
+def _check(params, q, R):
+    params = _f64(params).reshape(-1)
+    if params.size != R ** 3 * NSLOT:
+        raise ValueError(f"params must hold R^3*13 = {R**3*NSLOT} values, got {params.size}")
+    q = _f64(q)
+    if q.ndim != 2 or q.shape[1] < 3:
+        raise ValueError("q must be (J, >=3)")
+    return params, q
+
+
+def forward(params, q, R: int, W: int = 2, log_beta0: float | None = None, want_dq: bool = False):
+    """O(q_j), lse_j (and dO/dq_j) for the windowed O^{+Delta} model.
+
+    Sec. 3.3 Eq. func-offset evaluated by Algorithm 1 (Sec. 3.5) with the
+    log-sum-exp shift; dO/dq from Eq. func-normal.  ``q`` is (J, >=3); only the
+    first three columns are read.  W >= R is the paper's global support."""
+    lb = default_log_beta0(R) if log_beta0 is None else float(log_beta0)
+    params, q = _check(params, q, R)
+    J = q.shape[0]
+    O = np.zeros(J)
+    lse = np.zeros(J)
+    dq = np.zeros((J, 3)) if want_dq else None
+    _load().ora_forward(R, W, lb, _ptr(params), _ptr(q), J, q.shape[1], _ptr(O), _ptr(lse), _ptr(dq))
+    return (O, lse, dq) if want_dq else (O, lse)
+
+
+def backward(params, q, gO, R: int, W: int = 2, log_beta0: float | None = None, want_gq: bool = False):
+    """dL/dtheta (R^3, 13) and optionally dL/dq (J, 3) for upstream dL/dO = gO.
+
+    Algorithm 2 (Sec. 3.6) with the closed-form dO/dk, dO/dbeta, dO/dphi;
+    chain rule to the stored log-scale b and to the offset Delta."""
+    lb = default_log_beta0(R) if log_beta0 is None else float(log_beta0)
+    params, q = _check(params, q, R)
+    J = q.shape[0]
+    gO = _f64(gO).reshape(-1)
+    if gO.size != J:
+        raise ValueError("gO must have J entries")
+    grad = np.zeros(R ** 3 * NSLOT)
+    gq = np.zeros((J, 3)) if want_gq else None
+    _load().ora_backward(R, W, lb, _ptr(params), _ptr(q), J, q.shape[1], _ptr(gO), _ptr(grad), _ptr(gq))
+    grad = grad.reshape(R ** 3, NSLOT)
+    return (grad, gq) if want_gq else grad
+
+
+def forward_global(params, q, R: int, log_beta0: float | None = None):
+    """Brute force: the paper's global model over all 2I keys (no window)."""
+    lb = default_log_beta0(R) if log_beta0 is None else float(log_beta0)
+    params, q = _check(params, q, R)
+    J = q.shape[0]
+    O = np.zeros(J)
+    scratch = np.zeros(4 * R ** 3)
+    _load().ora_forward_global(R, lb, _ptr(params), _ptr(q), J, q.shape[1], _ptr(O), _ptr(scratch))
+    return O
+
+
+def loss_grad(O, target, loss: int = L1):
+    """Upstream gradient dL/dO_j, loss value and mean absolute error.
+
+    Eq. loss (Sec. 3.4) for MSE; L1 = mean |O - o| with sign(0) = 0."""
+    O = _f64(O).reshape(-1)
+    target = _f64(target).reshape(-1)
+    J = O.size
+    gO = np.zeros(J)
+    L = ctypes.c_double(0.0)
+    mae = ctypes.c_double(0.0)
+    _load().ora_loss_grad(int(loss), _ptr(O), _ptr(target), J, _ptr(gO), ctypes.byref(L), ctypes.byref(mae))
+    return gO, L.value, mae.value
+
+
+def adam(p, g, m, v, step: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+         eps: float = 1e-8, weight_decay: float = 0.0, decoupled: bool = False):
+    """One Adam (or AdamW, ``decoupled=True``) step, torch.optim semantics,
+    Sec. 3.4 / Sec. 4.2.  Returns new (p, m, v) as FP64 copies."""
+    p = _f64(p).reshape(-1).copy()
+    g = _f64(g).reshape(-1)
+    m = _f64(m).reshape(-1).copy()
+    v = _f64(v).reshape(-1).copy()
+    _load().ora_adam(p.size, _ptr(p), _ptr(g), _ptr(m), _ptr(v), int(step), lr, beta1, beta2, eps,
+                     weight_decay, int(bool(decoupled)))
+    return p, m, v
+
+
+def fit_step(params, m, v, step: int, qo, R: int, loss: int = L1, lr: float = 1e-3, W: int = 2,
+             log_beta0: float | None = None, **adam_kw):
+    """One fitting iteration (Sec. 3.4): forward, loss gradient, backward,
+    Adam.  ``qo`` is (J, 4) with the target SDF in column 3.  Returns
+    (params, m, v, loss, mae) as FP64 arrays / floats."""
+    qo = _f64(qo)
+    O, _ = forward(params, qo, R, W, log_beta0)
+    gO, L, mae = loss_grad(O, qo[:, 3], loss)
+    grad = backward(params, qo, gO, R, W, log_beta0)
+    p, m, v = adam(params, grad, m, v, step, lr=lr, **adam_kw)
+    return p.reshape(-1, NSLOT), m.reshape(-1, NSLOT), v.reshape(-1, NSLOT), L, mae

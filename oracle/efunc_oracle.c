@@ -1,0 +1,330 @@
+/*
+ * efunc_oracle.c -- plain, slow FP64 CPU oracle for the O^{+Delta} representation
+ * of "efunc: An Efficient Function Representation without Neural Networks"
+ * (arXiv 2505.21319).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this file.  It shares no code, header,
+ * table or constant with the CUDA library; the two meet only through the seeded
+ * input generators.
+ *
+ * What it computes (paper notation):
+ *   Keys      (Sec. 3.3, Eq. func-offset): every grid centre k_i carries a fixed
+ *             grid key k_i and a learnable offset key k_i + Delta_i; both key sets
+ *             enter ONE softmax (the union in Eq. func-offset).
+ *   Weights   (Sec. 3.1, Eq. nrbf): softmax over -beta ||q - key||^2.
+ *   Values    (Sec. 3.2, Eq. func-interp, Eq. poly-func, first order f^1):
+ *             f(q - key; phi) = o + dot(d, q - key), shift-invariant.
+ *   Forward   (Sec. 3.5, Algorithm 1): e_j = sum_i l, m_j = sum_i l f, O = m/e.
+ *   Backward  (Sec. 3.6, Algorithm 2 and the closed-form dO/dk, dO/dbeta,
+ *             dO/dphi that follow it).
+ *   dO/dq     (Sec. 3.2, Eq. func-normal).
+ *   Loss      (Sec. 3.4, Eq. loss: MSE) and the L1 variant.
+ *   Adam      (Sec. 3.4 / Sec. 4.2 name Adam / AdamW; torch.optim semantics).
+ *
+ * Readings of the paper that this file fixes (the paper is silent on them):
+ *   - Domain [-1,1]^3, R centres per axis, spacing h = 2/R, centre of index
+ *     (a,b,c) at k = -1 + ((a,b,c) + 0.5) h.  Parameters are stored as
+ *     params[((a*R + b)*R + c)*13 + slot].
+ *   - Slot order follows the parameter tuple of Eq. func-offset
+ *     {k_i, Delta_i, beta_i, beta'_i, phi_i, phi'_i} with k_i implicit:
+ *       0..2  Delta       3  b  (grid key log-scale)   4  b' (offset key log-scale)
+ *       5     o  (grid value constant)     6..8   d  (grid value linear term)
+ *       9     o' (offset value constant)   10..12 d' (offset value linear term)
+ *   - Scales are stored as log offsets: beta = exp(log_beta0 + b).  Sec. 4.3
+ *     initialises every scale to exp(7); log_beta0 carries that constant.
+ *   - Support: the paper's sum is global (Algorithm 1 loops over all I keys).
+ *     The hot path truncates it to a window of (2W)^3 centres around the query;
+ *     W >= R gives the paper's global model exactly.  The window base index per
+ *     axis is c = clamp(floor((q + 1) * (R/2) - 0.5), -1, R-1), evaluated in
+ *     FP32 on the FP32 query with no fused multiply-add (this file must be built
+ *     with -ffp-contract=off); the window holds the centres with index in
+ *     [c - W + 1, c + W], dropping indices outside [0, R-1].
+ *   - Softmax is evaluated with the maximum exponent subtracted (log-sum-exp);
+ *     mathematically identical to Algorithm 1, which has no shift.
+ *   - L1 loss uses sign(0) = 0.
+ *
+ * All arithmetic after the window choice is FP64.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <string.h>
+
+#define NSLOT 13
+
+/* ---------------------------------------------------------------- window */
+
+/* Window base index along one axis (see header).  FP32 on purpose: the CUDA
+ * path takes the same integer decision in the same precision. */
+int ora_window_base(float q, int R)
+{
+    float scale = (float)R * 0.5f;
+    float t = (q + 1.0f) * scale;
+    float u = t - 0.5f;
+    float lo = -1.0f, hi = (float)(R - 1);
+    if (!(u >= lo)) u = lo; /* also maps NaN to the first window */
+    if (u > hi) u = hi;
+    return (int)floorf(u);
+}
+
+static void window_range(const double *q, int R, int W, int lo[3], int hi[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        int c = ora_window_base((float)q[a], R);
+        int l = c - W + 1, h = c + W;
+        lo[a] = l < 0 ? 0 : l;
+        hi[a] = h > R - 1 ? R - 1 : h;
+    }
+}
+
+/* ------------------------------------------------------------- the keys */
+
+/* One key of the union in Eq. func-offset: position, scale beta and the
+ * first-order value f(x) = o + dot(d, x) with x = q - position. */
+typedef struct {
+    double p[3];
+    double beta;
+    double o;
+    double d[3];
+} key_t_;
+
+static double centre_coord(int idx, int R) { return -1.0 + ((double)idx + 0.5) * (2.0 / (double)R); }
+
+/* which = 0: grid key k_i; which = 1: offset key k_i + Delta_i. */
+static key_t_ make_key(const double *params, int R, double log_beta0, int a, int b, int c, int which)
+{
+    const double *th = params + ((size_t)((size_t)a * R + b) * R + c) * NSLOT;
+    key_t_ k;
+    k.p[0] = centre_coord(a, R);
+    k.p[1] = centre_coord(b, R);
+    k.p[2] = centre_coord(c, R);
+    if (which == 0) {
+        k.beta = exp(log_beta0 + th[3]);
+        k.o = th[5];
+        k.d[0] = th[6]; k.d[1] = th[7]; k.d[2] = th[8];
+    } else {
+        k.p[0] += th[0]; k.p[1] += th[1]; k.p[2] += th[2];
+        k.beta = exp(log_beta0 + th[4]);
+        k.o = th[9];
+        k.d[0] = th[10]; k.d[1] = th[11]; k.d[2] = th[12];
+    }
+    return k;
+}
+
+/* exponent -beta ||q - p||^2 (Eq. nrbf) and value f(q - p) (Eq. poly-func, f^1) */
+static void eval_key(const key_t_ *k, const double *q, double r[3], double *d2, double *expo, double *f)
+{
+    r[0] = q[0] - k->p[0];
+    r[1] = q[1] - k->p[1];
+    r[2] = q[2] - k->p[2];
+    *d2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    *expo = -k->beta * (*d2);
+    *f = k->o + k->d[0] * r[0] + k->d[1] * r[1] + k->d[2] * r[2];
+}
+
+/* --------------------------------------------------------------- forward */
+
+/* Algorithm 1 for one query over the windowed key set.  Returns O, the
+ * log-normaliser lse = log(sum exp(expo)) and, if dq != NULL, dO/dq from
+ * Eq. func-normal. */
+static void forward_one(const double *params, int R, int W, double log_beta0, const double *q,
+                        double *O_out, double *lse_out, double *dq)
+{
+    int lo[3], hi[3];
+    window_range(q, R, W, lo, hi);
+    double r[3], d2, expo, f;
+
+    /* maximum exponent (the stabilising shift) */
+    double M = -INFINITY;
+    for (int a = lo[0]; a <= hi[0]; ++a)
+        for (int b = lo[1]; b <= hi[1]; ++b)
+            for (int c = lo[2]; c <= hi[2]; ++c)
+                for (int s = 0; s < 2; ++s) {
+                    key_t_ k = make_key(params, R, log_beta0, a, b, c, s);
+                    eval_key(&k, q, r, &d2, &expo, &f);
+                    if (expo > M) M = expo;
+                }
+
+    /* e_j = sum l, m_j = sum l f  (Algorithm 1, with l scaled by exp(-M)) */
+    double e = 0.0, m = 0.0;
+    for (int a = lo[0]; a <= hi[0]; ++a)
+        for (int b = lo[1]; b <= hi[1]; ++b)
+            for (int c = lo[2]; c <= hi[2]; ++c)
+                for (int s = 0; s < 2; ++s) {
+                    key_t_ k = make_key(params, R, log_beta0, a, b, c, s);
+                    eval_key(&k, q, r, &d2, &expo, &f);
+                    double l = exp(expo - M);
+                    e += l;
+                    m += l * f;
+                }
+    double O = m / e;
+    *O_out = O;
+    if (lse_out) *lse_out = M + log(e);
+
+    if (dq) {
+        /* Eq. func-normal: dO/dq = sum softmax * (df/dq + 2 beta (q - p)(O - f)),
+         * df/dq = d for the first-order value. */
+        double g[3] = {0.0, 0.0, 0.0};
+        for (int a = lo[0]; a <= hi[0]; ++a)
+            for (int b = lo[1]; b <= hi[1]; ++b)
+                for (int c = lo[2]; c <= hi[2]; ++c)
+                    for (int s = 0; s < 2; ++s) {
+                        key_t_ k = make_key(params, R, log_beta0, a, b, c, s);
+                        eval_key(&k, q, r, &d2, &expo, &f);
+                        double w = exp(expo - M) / e;
+                        for (int x = 0; x < 3; ++x)
+                            g[x] += w * (k.d[x] + 2.0 * k.beta * r[x] * (O - f));
+                    }
+        dq[0] = g[0]; dq[1] = g[1]; dq[2] = g[2];
+    }
+}
+
+/* Forward over J queries.  q: J rows of q_stride doubles (x, y, z first).
+ * O, lse: J doubles each (lse may be NULL).  dq: J*3 doubles or NULL. */
+void ora_forward(int R, int W, double log_beta0, const double *params, const double *q, int64_t J,
+                 int q_stride, double *O, double *lse, double *dq)
+{
+    for (int64_t j = 0; j < J; ++j)
+        forward_one(params, R, W, log_beta0, q + j * q_stride, &O[j], lse ? &lse[j] : NULL,
+                    dq ? dq + 3 * j : NULL);
+}
+
+/* -------------------------------------------------------------- backward */
+
+/* Algorithm 2 with the closed-form gradients of Sec. 3.6.  For every query j
+ * and every key of its window:
+ *   l            = exp(-beta ||q - p||^2) / e_j                     (softmax)
+ *   dO/dphi      = l * df/dphi        (df/do = 1, df/dd = q - p)
+ *   dO/dbeta     = l * ( -||q - p||^2 (f - O) )
+ *   dO/dkey      = l * ( df/dkey + 2 beta (q - p)(f - O) ),  df/dkey = -d
+ * and dL/dtheta += dL/dO_j * dO_j/dtheta.  The stored scale is the log offset
+ * b (beta = exp(log_beta0 + b)), so dO/db = beta dO/dbeta; the offset key is
+ * k_i + Delta_i with k_i fixed, so dO/dDelta = dO/dkey of the offset key.
+ * Grid keys are fixed (configuration Full-4 of the ablation table): no
+ * gradient for k_i.
+ * grad: R^3*13 doubles, ACCUMULATED into.  gq: J*3 doubles or NULL, set to
+ * dL/dO_j * dO_j/dq. */
+void ora_backward(int R, int W, double log_beta0, const double *params, const double *q, int64_t J,
+                  int q_stride, const double *gO, double *grad, double *gq)
+{
+    for (int64_t j = 0; j < J; ++j) {
+        const double *qj = q + j * q_stride;
+        double O, lse, dq[3];
+        forward_one(params, R, W, log_beta0, qj, &O, &lse, gq ? dq : NULL);
+        if (gq) {
+            gq[3 * j + 0] = gO[j] * dq[0];
+            gq[3 * j + 1] = gO[j] * dq[1];
+            gq[3 * j + 2] = gO[j] * dq[2];
+        }
+        int lo[3], hi[3];
+        window_range(qj, R, W, lo, hi);
+        double r[3], d2, expo, f;
+        for (int a = lo[0]; a <= hi[0]; ++a)
+            for (int b = lo[1]; b <= hi[1]; ++b)
+                for (int c = lo[2]; c <= hi[2]; ++c)
+                    for (int s = 0; s < 2; ++s) {
+                        key_t_ k = make_key(params, R, log_beta0, a, b, c, s);
+                        eval_key(&k, qj, r, &d2, &expo, &f);
+                        double l = exp(expo - lse);
+                        double gl = gO[j] * l;
+                        double *gr = grad + ((size_t)((size_t)a * R + b) * R + c) * NSLOT;
+                        double dbeta = gl * (-d2 * (f - O));
+                        if (s == 0) {
+                            gr[5] += gl;
+                            gr[6] += gl * r[0];
+                            gr[7] += gl * r[1];
+                            gr[8] += gl * r[2];
+                            gr[3] += k.beta * dbeta;
+                        } else {
+                            gr[9] += gl;
+                            gr[10] += gl * r[0];
+                            gr[11] += gl * r[1];
+                            gr[12] += gl * r[2];
+                            gr[4] += k.beta * dbeta;
+                            for (int x = 0; x < 3; ++x)
+                                gr[x] += gl * (-k.d[x] + 2.0 * k.beta * r[x] * (f - O));
+                        }
+                    }
+    }
+}
+
+/* ------------------------------------------------ global-support brute force */
+
+/* The paper's global model (Algorithm 1 over ALL I centres, both key sets),
+ * written as an explicit table of the 2I key exponents and values followed by
+ * a two-pass softmax.  No window is involved; it pins the windowed oracle.
+ * scratch: 4*R^3 doubles. */
+void ora_forward_global(int R, double log_beta0, const double *params, const double *q, int64_t J,
+                        int q_stride, double *O, double *scratch)
+{
+    int64_t I = (int64_t)R * R * R;
+    double *ex = scratch, *fv = scratch + 2 * I;
+    for (int64_t j = 0; j < J; ++j) {
+        const double *qj = q + j * q_stride;
+        double M = -INFINITY;
+        for (int64_t i = 0; i < I; ++i) {
+            int a = (int)(i / ((int64_t)R * R)), b = (int)((i / R) % R), c = (int)(i % R);
+            for (int s = 0; s < 2; ++s) {
+                key_t_ k = make_key(params, R, log_beta0, a, b, c, s);
+                double r[3], d2;
+                eval_key(&k, qj, r, &d2, &ex[2 * i + s], &fv[2 * i + s]);
+                if (ex[2 * i + s] > M) M = ex[2 * i + s];
+            }
+        }
+        double e = 0.0, m = 0.0;
+        for (int64_t t = 0; t < 2 * I; ++t) {
+            double l = exp(ex[t] - M);
+            e += l;
+            m += l * fv[t];
+        }
+        O[j] = m / e;
+    }
+}
+
+/* ------------------------------------------------------------------ loss */
+
+/* Eq. loss (MSE) and the L1 variant: the upstream gradient dL/dO_j and the
+ * loss value.  loss_kind 0 = L1 (sign(0) = 0), 1 = MSE.  target: J doubles. */
+void ora_loss_grad(int loss_kind, const double *O, const double *target, int64_t J, double *gO,
+                   double *loss_out, double *mae_out)
+{
+    double L = 0.0, mae = 0.0;
+    for (int64_t j = 0; j < J; ++j) {
+        double diff = O[j] - target[j];
+        mae += fabs(diff);
+        if (loss_kind == 0) {
+            L += fabs(diff);
+            gO[j] = (diff > 0.0 ? 1.0 : (diff < 0.0 ? -1.0 : 0.0)) / (double)J;
+        } else {
+            L += diff * diff;
+            gO[j] = 2.0 * diff / (double)J;
+        }
+    }
+    if (loss_out) *loss_out = J > 0 ? L / (double)J : 0.0;
+    if (mae_out) *mae_out = J > 0 ? mae / (double)J : 0.0;
+}
+
+/* ------------------------------------------------------------------ Adam */
+
+/* One Adam / AdamW step with torch.optim semantics (Adam: L2 penalty added to
+ * the gradient; AdamW: decoupled decay p *= 1 - lr*wd).  step is 1-based.  The
+ * gradient is left untouched. */
+void ora_adam(int64_t n, double *p, const double *g, double *m, double *v, int64_t step, double lr,
+              double beta1, double beta2, double eps, double wd, int decoupled)
+{
+    double bc1 = 1.0 - pow(beta1, (double)step);
+    double bc2 = 1.0 - pow(beta2, (double)step);
+    for (int64_t i = 0; i < n; ++i) {
+        double gi = g[i];
+        if (decoupled)
+            p[i] *= 1.0 - lr * wd;
+        else
+            gi += wd * p[i];
+        m[i] = beta1 * m[i] + (1.0 - beta1) * gi;
+        v[i] = beta2 * v[i] + (1.0 - beta2) * gi * gi;
+        double mhat = m[i] / bc1;
+        double vhat = v[i] / bc2;
+        p[i] -= lr * mhat / (sqrt(vhat) + eps);
+    }
+}

@@ -1,0 +1,177 @@
+"""Seeded synthetic inputs: analytic SDF shapes, query samplers, parameter init.
+
+This module holds input generation only (none of the representation's
+arithmetic), so both the CUDA path and the FP64 oracle's tests may use it.
+
+The paper fits real meshes (Thingi10k and others, Sec. 4.2), which are not
+available; analytic shapes stand in for them, sampled with the paper's
+per-iteration structure: half the points uniform in the bounding volume, half
+near the surface (Sec. 4.2).
+
+Shapes: unions (min) of spheres, axis-aligned boxes and z-axis tori.
+  sphere  centre c, radius s                      |q - c| - s
+  box     centre c, half-extents e (3 values)     exact box distance
+  torus   centre c, major radius s, minor s/3     exact torus distance
+Surface samples: a primitive is chosen with probability proportional to its
+area, a point is drawn uniformly on its surface, kept only if it lies on the
+union's boundary (union SDF >= -1e-6), then displaced by N(0, sigma^2 I).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SPHERE, BOX, TORUS = 0, 1, 2
+
+
+def rng(seed: int) -> np.random.Generator:
+    """Counter-based Philox generator for a seed (same stream on every host)."""
+    return np.random.Generator(np.random.Philox(int(seed)))
+
+
+@dataclass
+class Shape:
+    kind: np.ndarray                       # (P,) int
+    centre: np.ndarray                     # (P, 3)
+    size: np.ndarray                       # (P, 3): sphere radius / box half-extents / torus (major, minor, 0)
+    meta: dict = field(default_factory=dict)
+
+    def sdf(self, q: np.ndarray) -> np.ndarray:
+        """Union SDF (FP64) at points q (N, 3)."""
+        q = np.asarray(q, dtype=np.float64)
+        out = np.full(q.shape[0], np.inf)
+        for k, c, s in zip(self.kind, self.centre, self.size):
+            out = np.minimum(out, _prim_sdf(k, c, s, q))
+        return out
+
+
+def _prim_sdf(kind, c, s, q):
+    p = q - c
+    if kind == SPHERE:
+        return np.linalg.norm(p, axis=1) - s[0]
+    if kind == BOX:
+        d = np.abs(p) - s
+        outside = np.linalg.norm(np.maximum(d, 0.0), axis=1)
+        inside = np.minimum(np.max(d, axis=1), 0.0)
+        return outside + inside
+    if kind == TORUS:
+        ring = np.sqrt(p[:, 0] ** 2 + p[:, 1] ** 2) - s[0]
+        return np.sqrt(ring ** 2 + p[:, 2] ** 2) - s[1]
+    raise ValueError(kind)
+
+
+def _prim_area(kind, s):
+    if kind == SPHERE:
+        return 4.0 * np.pi * s[0] ** 2
+    if kind == BOX:
+        return 8.0 * (s[0] * s[1] + s[1] * s[2] + s[0] * s[2])
+    if kind == TORUS:
+        return 4.0 * np.pi ** 2 * s[0] * s[1]
+    raise ValueError(kind)
+
+
+def _prim_surface(kind, c, s, n, g: np.random.Generator):
+    if kind == SPHERE:
+        v = g.standard_normal((n, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        return c + s[0] * v
+    if kind == BOX:
+        areas = np.array([s[1] * s[2], s[1] * s[2], s[0] * s[2], s[0] * s[2], s[0] * s[1], s[0] * s[1]])
+        face = g.choice(6, size=n, p=areas / areas.sum())
+        u = g.uniform(-1.0, 1.0, size=(n, 3)) * s
+        axis = face // 2
+        sign = np.where(face % 2 == 0, -1.0, 1.0)
+        u[np.arange(n), axis] = sign * s[axis]
+        return c + u
+    if kind == TORUS:
+        R, r = s[0], s[1]
+        out = np.empty((0, 3))
+        while out.shape[0] < n:   # rejection on the area element (R + r cos v)
+            m = 2 * (n - out.shape[0]) + 16
+            uu = g.uniform(0, 2 * np.pi, m)
+            vv = g.uniform(0, 2 * np.pi, m)
+            keep = g.uniform(0, 1, m) * (R + r) <= R + r * np.cos(vv)
+            uu, vv = uu[keep], vv[keep]
+            pts = np.stack([(R + r * np.cos(vv)) * np.cos(uu), (R + r * np.cos(vv)) * np.sin(uu), r * np.sin(vv)], 1)
+            out = np.concatenate([out, pts])
+        return c + out[:n]
+    raise ValueError(kind)
+
+
+def sphere(radius: float = 0.5, centre=(0.0, 0.0, 0.0)) -> Shape:
+    return Shape(np.array([SPHERE]), np.array([centre], dtype=np.float64),
+                 np.array([[radius, 0.0, 0.0]]), {"name": f"sphere r={radius}"})
+
+
+def random_union(seed: int, n_prims: int = 8, centre_range: float = 0.6, size_range=(0.1, 0.3)) -> Shape:
+    """Union of ``n_prims`` primitives, kind uniform over {sphere, box, torus},
+    centres U[-centre_range, centre_range]^3, size U[size_range]: sphere radius,
+    box half-extent per axis, torus major radius (minor = major / 3)."""
+    g = rng(seed)
+    kind = g.integers(0, 3, size=n_prims)
+    centre = g.uniform(-centre_range, centre_range, size=(n_prims, 3))
+    size = np.zeros((n_prims, 3))
+    for i, k in enumerate(kind):
+        if k == SPHERE:
+            size[i, 0] = g.uniform(*size_range)
+        elif k == BOX:
+            size[i] = g.uniform(*size_range, size=3)
+        else:
+            size[i, 0] = g.uniform(*size_range)
+            size[i, 1] = size[i, 0] / 3.0
+    return Shape(kind, centre, size, {"name": f"union{n_prims} seed={seed}"})
+
+
+def surface_points(shape: Shape, n: int, g: np.random.Generator) -> np.ndarray:
+    """n points uniformly distributed (by area) on the union's boundary."""
+    areas = np.array([_prim_area(k, s) for k, s in zip(shape.kind, shape.size)])
+    out = np.empty((0, 3))
+    while out.shape[0] < n:
+        m = 2 * (n - out.shape[0]) + 64
+        which = g.choice(len(areas), size=m, p=areas / areas.sum())
+        pts = np.empty((m, 3))
+        for i in range(len(areas)):
+            sel = which == i
+            if sel.any():
+                pts[sel] = _prim_surface(shape.kind[i], shape.centre[i], shape.size[i], int(sel.sum()), g)
+        pts = pts[shape.sdf(pts) >= -1e-6]
+        out = np.concatenate([out, pts])
+    return out[:n]
+
+
+def sample_batch(shape: Shape, J: int, seed: int, sigma: float = 0.01, near_frac: float = 0.5) -> np.ndarray:
+    """(J, 4) float32 rows (x, y, z, target SDF): ``J - n_near`` uniform points
+    in [-1,1]^3 and ``n_near = round(near_frac*J)`` surface points displaced by
+    N(0, sigma^2 I).  The target is the FP64 SDF at the FP32-rounded point."""
+    g = rng(seed)
+    n_near = int(round(near_frac * J))
+    n_vol = J - n_near
+    vol = g.uniform(-1.0, 1.0, size=(n_vol, 3))
+    near = surface_points(shape, n_near, g) + sigma * g.standard_normal((n_near, 3)) if n_near else np.empty((0, 3))
+    q = np.concatenate([vol, near]).astype(np.float32)
+    perm = g.permutation(J)
+    q = q[perm]
+    out = np.empty((J, 4), dtype=np.float32)
+    out[:, :3] = q
+    out[:, 3] = shape.sdf(q.astype(np.float64)).astype(np.float32)
+    return out
+
+
+def init_params(R: int, seed: int, std: float = 1e-3) -> np.ndarray:
+    """(R^3, 13) float32 parameters, every slot N(0, std^2)."""
+    return (rng(seed).standard_normal((R ** 3, 13)) * std).astype(np.float32)
+
+
+def random_params(R: int, seed: int, delta_scale: float = 0.3, b_scale: float = 0.3, value_scale: float = 0.5) -> np.ndarray:
+    """(R^3, 13) float32 parameters with every slot far from zero, for parity
+    tests: offsets up to ``delta_scale`` grid spacings, log-scales N(0, b_scale^2),
+    values N(0, value_scale^2)."""
+    g = rng(seed)
+    h = 2.0 / R
+    p = np.empty((R ** 3, 13))
+    p[:, 0:3] = g.uniform(-delta_scale, delta_scale, size=(R ** 3, 3)) * h
+    p[:, 3:5] = g.standard_normal((R ** 3, 2)) * b_scale
+    p[:, 5:13] = g.standard_normal((R ** 3, 8)) * value_scale
+    return p.astype(np.float32)
+

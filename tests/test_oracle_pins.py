@@ -1,0 +1,376 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each check uses an invariant,
+a closed-form special case, a library routine that the special case reduces
+to, brute force, or finite differences.  A dropped term, a flipped sign, a
+transposed index or a wrong key position in the oracle fails at least one.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.special
+import scipy.spatial.distance
+import torch
+
+import oracle
+from paper_2505_21319_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def centres(R):
+    """Centre positions from the stated reading: -1 + (idx + 0.5) * 2/R, x slowest."""
+    c = -1.0 + (np.arange(R) + 0.5) * (2.0 / R)
+    a, b, d = np.meshgrid(c, c, c, indexing="ij")
+    return np.stack([a.ravel(), b.ravel(), d.ravel()], 1)
+
+
+def queries(seed, J, spread=1.1):
+    return synth.rng(seed).uniform(-spread, spread, size=(J, 3)).astype(np.float32).astype(np.float64)
+
+
+def keys_of(params, R, log_beta0):
+    """Explicit key list (positions, beta, o, d) for the whole grid."""
+    p = np.asarray(params, dtype=np.float64).reshape(R ** 3, 13)
+    k = centres(R)
+    pos = np.concatenate([k, k + p[:, 0:3]])
+    beta = np.exp(log_beta0 + np.concatenate([p[:, 3], p[:, 4]]))
+    o = np.concatenate([p[:, 5], p[:, 9]])
+    d = np.concatenate([p[:, 6:9], p[:, 10:13]])
+    return pos, beta, o, d
+
+
+# --------------------------------------------------------------- layout pins
+
+def test_parameter_counts_match_paper():
+    """Table tab:main / tab:ablation / Fig. comp-trilinear print the float
+    counts of the representation; 13 floats per centre and I = R^3."""
+    g = json.load(open(os.path.join(GOLDEN, "param_counts.json")))
+    for row in g["table_main_ours"]:
+        n = row["R"] ** 3 * oracle.NSLOT
+        if "value" in row:
+            assert n == row["value"]
+        else:
+            assert abs(n - row["approx"]) <= row["rel_tol"] * row["approx"]
+    full = [r for r in g["table_ablation"] if r["floats_per_centre"] == 13]
+    assert full and all(r["R"] ** 3 * oracle.NSLOT == r["value"] for r in full)
+    for r in g["table_ablation"]:
+        assert r["R"] ** 3 * r["floats_per_centre"] == r["value"]
+    # Eq. func-offset: 5 + |phi| + |phi'| with first-order phi (1 + 3 floats)
+    assert 5 + 4 + 4 == oracle.NSLOT
+
+
+# --------------------------------------------------------------- value pins
+
+@pytest.mark.parametrize("R,W", [(1, 1), (2, 2), (3, 1), (8, 2), (5, 5)])
+def test_partition_of_unity(R, W):
+    """Eq. nrbf: the normalised weights form a convex combination, so equal
+    constant values reproduce that constant for any keys, scales, offsets."""
+    p = synth.random_params(R, seed=R, delta_scale=0.8, b_scale=1.0).astype(np.float64)
+    p[:, 5] = 0.375
+    p[:, 9] = 0.375
+    p[:, 6:9] = 0.0
+    p[:, 10:13] = 0.0
+    q = queries(11, 200)
+    O, lse, dq = oracle.forward(p, q, R, W, want_dq=True)
+    np.testing.assert_allclose(O, 0.375, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(dq, 0.0, atol=1e-9)
+
+
+@pytest.mark.parametrize("R,W", [(1, 1), (2, 2), (4, 2), (8, 2), (3, 3)])
+def test_affine_reproduction(R, W):
+    """Shift-invariance of f (Sec. 3.2): if every key holds the same global
+    affine function P(x) = a + b.x expressed about its own position, the blend
+    is P(q) exactly and dO/dq = b (Eq. func-normal), whatever the weights."""
+    rng = synth.rng(100 + R)
+    a = 0.3
+    b = np.array([0.7, -1.3, 0.45])
+    p = synth.random_params(R, seed=7 * R, delta_scale=0.9, b_scale=1.0).astype(np.float64)
+    k = centres(R)
+    p[:, 5] = a + k @ b
+    p[:, 6:9] = b
+    p[:, 9] = a + (k + p[:, 0:3]) @ b
+    p[:, 10:13] = b
+    q = queries(12 + R, 300)
+    O, _, dq = oracle.forward(p, q, R, W, want_dq=True)
+    np.testing.assert_allclose(O, a + q @ b, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(dq, np.broadcast_to(b, dq.shape), rtol=0, atol=1e-10)
+    # dO/d(log-scales) vanish because f - O == 0 for every key; dO/dDelta = -d' w + 0
+    gO = rng.standard_normal(q.shape[0])
+    g = oracle.backward(p, q, gO, R, W)
+    np.testing.assert_allclose(g[:, 3:5], 0.0, atol=1e-10)
+
+
+def test_two_key_logistic_closed_form():
+    """R = 1: one centre, two keys (grid key at the origin, offset key at
+    Delta).  With constant values the softmax over two keys is the logistic
+    function of the exponent difference (Eq. nrbf):
+        O = o' + (o - o') * expit(beta'|q - Delta|^2 - beta|q|^2)."""
+    rng = synth.rng(5)
+    for _ in range(20):
+        th = np.zeros((1, 13))
+        th[0, 0:3] = rng.uniform(-0.5, 0.5, 3)
+        th[0, 3:5] = rng.uniform(-2, 2, 2)
+        th[0, 5] = rng.uniform(-1, 1)
+        th[0, 9] = rng.uniform(-1, 1)
+        lb = rng.uniform(0, 3)
+        q = rng.uniform(-1, 1, (5, 3)).astype(np.float32).astype(np.float64)
+        beta, betap = math.exp(lb + th[0, 3]), math.exp(lb + th[0, 4])
+        z = betap * ((q - th[0, 0:3]) ** 2).sum(1) - beta * (q ** 2).sum(1)
+        want = th[0, 9] + (th[0, 5] - th[0, 9]) * scipy.special.expit(z)
+        O, _ = oracle.forward(th, q, 1, 1, log_beta0=lb)
+        np.testing.assert_allclose(O, want, rtol=1e-13, atol=1e-14)
+
+
+def test_symmetric_midpoint_and_nearest_key_limit():
+    """Two keys with equal scale: a query at their midpoint weighs them 1/2
+    each.  With a very large scale the blend tends to the nearest key's value
+    (the weight of every other key vanishes)."""
+    th = np.zeros((1, 13))
+    th[0, 0:3] = [0.4, -0.2, 0.1]
+    th[0, 5], th[0, 9] = 2.0, -1.0
+    mid = np.array([[0.2, -0.1, 0.05]])
+    O, _ = oracle.forward(th, mid, 1, 1, log_beta0=1.0)
+    assert abs(O[0] - 0.5) < 1e-15
+    # the grid key sits at the origin: a query next to it, huge beta -> o
+    O, _ = oracle.forward(th, np.array([[0.01, 0.0, 0.0]]), 1, 1, log_beta0=12.0)
+    assert abs(O[0] - 2.0) < 1e-12
+    O, _ = oracle.forward(th, np.array([[0.39, -0.2, 0.1]]), 1, 1, log_beta0=12.0)
+    assert abs(O[0] + 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("R", [2, 3, 4])
+def test_f0_reduces_to_nrbf_library_softmax(R):
+    """Sec. 3.2: with zero linear terms (f^0) the model is the normalised RBF of
+    Eq. nrbf.  Global support (W >= R) against scipy's softmax over the
+    pairwise squared distances of all 2I keys."""
+    lb = 2.5
+    p = synth.random_params(R, seed=31 + R, delta_scale=0.7, b_scale=0.8).astype(np.float64)
+    p[:, 6:9] = 0.0
+    p[:, 10:13] = 0.0
+    q = queries(3 + R, 64)
+    pos, beta, o, _ = keys_of(p, R, lb)
+    D2 = scipy.spatial.distance.cdist(q, pos, "sqeuclidean")
+    want = scipy.special.softmax(-beta[None, :] * D2, axis=1) @ o
+    O, lse = oracle.forward(p, q, R, W=R, log_beta0=lb)
+    np.testing.assert_allclose(O, want, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(lse, scipy.special.logsumexp(-beta[None, :] * D2, axis=1), rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------- window pins
+
+@pytest.mark.parametrize("R", [2, 3, 4, 5])
+def test_window_at_least_R_equals_global_brute_force(R):
+    """Brute force over all 2I keys (the paper's global Algorithm 1) equals the
+    windowed oracle once the window covers the grid (W >= R)."""
+    p = synth.random_params(R, seed=R, delta_scale=0.9, b_scale=0.7).astype(np.float64)
+    q = queries(40 + R, 100, spread=1.3)
+    O, _ = oracle.forward(p, q, R, W=R)
+    G = oracle.forward_global(p, q, R)
+    np.testing.assert_allclose(O, G, rtol=1e-12, atol=1e-13)
+
+
+def test_window_truncation_error_bound():
+    """W = 2 drops keys at least 2h away along some axis; with the initial scale
+    (beta h^2 = 4e^7/1024) and no offsets every dropped key weighs at most
+    exp(-beta h^2 (4 - 3/4)) of the nearest one, so |O_W - O_global| is bounded
+    by 2I times that, times the spread of values."""
+    R = 8
+    p = synth.random_params(R, seed=9, delta_scale=0.0, b_scale=0.0).astype(np.float64)
+    q = queries(77, 300, spread=1.0)
+    O, _ = oracle.forward(p, q, R, W=2)
+    G = oracle.forward_global(p, q, R)
+    h = 2.0 / R
+    bh2 = math.exp(oracle.default_log_beta0(R)) * h * h
+    spread = np.abs(p[:, 5:13]).max() * 4.0
+    bound = 2 * R ** 3 * math.exp(-bh2 * (4 - 0.75)) * spread
+    assert np.abs(O - G).max() <= bound
+    assert np.abs(O - G).max() > 0  # the window really truncates
+
+
+def test_window_base_fp32_formula():
+    """Window base c = clamp(floor((q+1)*R/2 - 1/2), -1, R-1): against exact
+    rational arithmetic wherever FP32 rounding cannot move the floor, against
+    numpy FP32 arithmetic everywhere (ties included), and its clamping."""
+    from fractions import Fraction
+    rng = synth.rng(3)
+    for R in (1, 2, 7, 16, 32, 64):
+        qs = list(rng.uniform(-1.2, 1.2, 400).astype(np.float32))
+        # exact ties: cell-centre positions and grid faces
+        qs += [np.float32(-1 + i / R) for i in range(0, 2 * R + 1)]
+        qs += [np.nextafter(np.float32(-1 + i / R), np.float32(2)) for i in range(0, 2 * R + 1)]
+        for q in qs:
+            q = np.float32(q)
+            c = oracle.window_base(float(q), R)
+            u = (q + np.float32(1)) * np.float32(R * 0.5) - np.float32(0.5)
+            c32 = int(np.floor(np.clip(u, np.float32(-1), np.float32(R - 1))))
+            assert c == c32
+            exact = Fraction(float(q)) * 0 + (Fraction(float(q)) + 1) * Fraction(R, 2) - Fraction(1, 2)
+            fl = math.floor(exact)
+            if abs(exact - fl) > Fraction(1, 1 << 18) and abs(exact - fl - 1) > Fraction(1, 1 << 18):
+                assert c == max(-1, min(R - 1, fl))
+    assert oracle.window_base(float("nan"), 8) == -1
+    assert oracle.window_base(1e30, 8) == 7 and oracle.window_base(-1e30, 8) == -1
+
+
+def test_window_contents_brute_force():
+    """The window is the set of (2W)^3 centres whose index lies in
+    [c - W + 1, c + W] per axis; verified by enumerating every centre on a tiny
+    grid and zeroing the values of all centres outside that set: the output
+    must not change, while changing a centre inside it must."""
+    R, W = 6, 2
+    p = synth.random_params(R, seed=4).astype(np.float64)
+    q = queries(9, 30, spread=1.0)
+    O, _ = oracle.forward(p, q, R, W)
+    for j in range(q.shape[0]):
+        c = [oracle.window_base(q[j, a], R) for a in range(3)]
+        idx = np.arange(R ** 3)
+        ia, ib, ic = idx // (R * R), (idx // R) % R, idx % R
+        inside = np.ones(R ** 3, bool)
+        for a, ii in enumerate((ia, ib, ic)):
+            inside &= (ii >= c[a] - W + 1) & (ii <= c[a] + W)
+        p2 = p.copy()
+        p2[~inside, 5:13] = 123.0
+        O2, _ = oracle.forward(p2, q[j:j + 1], R, W)
+        assert O2[0] == O[j]
+        ins = np.flatnonzero(inside)
+        k = ins[np.argmin(((centres(R)[ins] - q[j]) ** 2).sum(1))]
+        p3 = p.copy()
+        p3[k, 5] += 1.0
+        O3, _ = oracle.forward(p3, q[j:j + 1], R, W)
+        assert O3[0] != O[j]
+
+
+# --------------------------------------------------------- gradient pins
+
+def _fd_params(p, q, gO, R, W, lb, entries, eps=1e-6):
+    out = []
+    for (i, s) in entries:
+        hstep = eps * max(1.0, abs(p[i, s]))
+        pp, pm = p.copy(), p.copy()
+        pp[i, s] += hstep
+        pm[i, s] -= hstep
+        Op, _ = oracle.forward(pp, q, R, W, lb)
+        Om, _ = oracle.forward(pm, q, R, W, lb)
+        out.append(float(gO @ (Op - Om)) / (2 * hstep))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("R,W", [(3, 3), (6, 2)])
+def test_param_gradients_match_central_differences(R, W):
+    """Algorithm 2 / Sec. 3.6 closed forms against FP64 central differences of
+    L = sum_j gO_j O(q_j), for all 13 slots of the centres the queries touch.
+    With W < R the queries stay 1e-3 h away from window switches, where the
+    windowed model is smooth."""
+    lb = oracle.default_log_beta0(R) - 1.0
+    p = synth.random_params(R, seed=50 + R, delta_scale=0.6, b_scale=0.5).astype(np.float64)
+    rng = synth.rng(60 + R)
+    q = rng.uniform(-0.95, 0.95, (6, 3))
+    if W < R:
+        t = (q + 1) * R / 2 - 0.5
+        frac = t - np.floor(t)
+        q = np.where(np.minimum(frac, 1 - frac) < 1e-3, q + 0.01, q)
+    q = q.astype(np.float32).astype(np.float64)
+    gO = rng.standard_normal(q.shape[0])
+    grad = oracle.backward(p, q, gO, R, W, lb)
+    touched = np.flatnonzero(np.abs(grad).sum(1) > 0)
+    assert touched.size > 0
+    sel = rng.choice(touched, size=min(10, touched.size), replace=False)
+    entries = [(i, s) for i in sel for s in range(13)]
+    fd = _fd_params(p, q, gO, R, W, lb, entries)
+    an = np.array([grad[i, s] for (i, s) in entries])
+    scale = np.abs(an).max()
+    np.testing.assert_allclose(an, fd, rtol=1e-6, atol=1e-7 * scale)
+    # untouched centres get exactly zero
+    assert np.all(grad[np.setdiff1d(np.arange(R ** 3), touched)] == 0.0)
+
+
+@pytest.mark.parametrize("R,W", [(3, 3), (5, 2)])
+def test_query_gradient_matches_central_differences(R, W):
+    """Eq. func-normal against FP64 central differences in q (away from window
+    switches), and dL/dq = gO * dO/dq from the backward."""
+    lb = oracle.default_log_beta0(R) - 0.5
+    p = synth.random_params(R, seed=70 + R, delta_scale=0.6, b_scale=0.5).astype(np.float64)
+    rng = synth.rng(80 + R)
+    q = rng.uniform(-0.9, 0.9, (8, 3))
+    t = (q + 1) * R / 2 - 0.5
+    frac = t - np.floor(t)
+    q = np.where(np.minimum(frac, 1 - frac) < 1e-3, q + 0.01, q)
+    _, _, dq = oracle.forward(p, q, R, W, lb, want_dq=True)
+    eps = 1e-6
+    for a in range(3):
+        qp, qm = q.copy(), q.copy()
+        qp[:, a] += eps
+        qm[:, a] -= eps
+        fd = (oracle.forward(p, qp, R, W, lb)[0] - oracle.forward(p, qm, R, W, lb)[0]) / (2 * eps)
+        np.testing.assert_allclose(dq[:, a], fd, rtol=1e-6, atol=1e-7 * np.abs(fd).max())
+    gO = rng.standard_normal(q.shape[0])
+    _, gq = oracle.backward(p, q, gO, R, W, lb, want_gq=True)
+    np.testing.assert_allclose(gq, gO[:, None] * dq, rtol=1e-14, atol=0)
+
+
+def test_value_gradient_sums_to_one():
+    """Partition of unity for the gradient: dO/do summed over all keys is
+    sum_i softmax_i = 1 for every query, so with gO = 1 for one query the
+    o and o' slots of the gradient sum to 1."""
+    R = 5
+    p = synth.random_params(R, seed=2).astype(np.float64)
+    q = queries(4, 7, spread=1.0)
+    for j in range(q.shape[0]):
+        g = oracle.backward(p, q[j:j + 1], np.ones(1), R, 2)
+        assert abs(g[:, 5].sum() + g[:, 9].sum() - 1.0) < 1e-13
+        assert np.all(g[:, 5] >= 0) and np.all(g[:, 9] >= 0)
+
+
+# ------------------------------------------------------ loss / Adam pins
+
+def test_loss_gradients_match_torch():
+    """Eq. loss (MSE) and L1 against torch's mean-reduced losses and autograd."""
+    rng = synth.rng(8)
+    O = rng.standard_normal(257)
+    t = rng.standard_normal(257)
+    t[:5] = O[:5]  # exact ties: sign(0) = 0
+    for kind, fn in ((oracle.L1, torch.nn.functional.l1_loss), (oracle.MSE, torch.nn.functional.mse_loss)):
+        Ot = torch.tensor(O, requires_grad=True)
+        L = fn(Ot, torch.tensor(t))
+        L.backward()
+        gO, Lv, mae = oracle.loss_grad(O, t, kind)
+        np.testing.assert_allclose(gO, Ot.grad.numpy(), rtol=1e-14, atol=1e-17)
+        assert abs(Lv - L.item()) < 1e-13
+        assert abs(mae - np.abs(O - t).mean()) < 1e-14
+
+
+@pytest.mark.parametrize("decoupled,wd", [(False, 0.0), (False, 0.01), (True, 0.01)])
+def test_adam_matches_torch_optim(decoupled, wd):
+    """Adam / AdamW (Sec. 3.4, Sec. 4.2) against torch.optim in FP64, 5 steps."""
+    rng = synth.rng(21)
+    p0 = rng.standard_normal(103)
+    pt = torch.tensor(p0.copy(), requires_grad=True)
+    opt = (torch.optim.AdamW if decoupled else torch.optim.Adam)([pt], lr=1e-2, betas=(0.9, 0.999), eps=1e-8,
+                                                                 weight_decay=wd)
+    p, m, v = p0.copy(), np.zeros(103), np.zeros(103)
+    for step in range(1, 6):
+        g = rng.standard_normal(103)
+        pt.grad = torch.tensor(g.copy())
+        opt.step()
+        p, m, v = oracle.adam(p, g, m, v, step, lr=1e-2, weight_decay=wd, decoupled=decoupled)
+        np.testing.assert_allclose(p, pt.detach().numpy(), rtol=1e-13, atol=1e-15)
+
+
+def test_fit_decreases_mae_on_sphere():
+    """Sec. 3.4: a few Adam iterations on the sphere SDF lower the error."""
+    R = 8
+    shape = synth.sphere(0.5)
+    qo = synth.sample_batch(shape, 2048, seed=1).astype(np.float64)
+    p = synth.init_params(R, seed=0).astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    maes = []
+    for step in range(1, 9):
+        p, m, v, L, mae = oracle.fit_step(p, m, v, step, qo, R, loss=oracle.L1, lr=2e-2)
+        maes.append(mae)
+    assert all(b < a for a, b in zip(maes, maes[1:]))
+    assert maes[-1] < 0.75 * maes[0]
