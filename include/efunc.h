@@ -1,0 +1,188 @@
+/*
+ * efunc.h -- C ABI of the GB300 (sm_103a) library for the O^{+Delta}
+ * representation of "efunc: An Efficient Function Representation without
+ * Neural Networks" (arXiv 2505.21319).
+ *
+ * Representation (Sec. 3.3, Eq. func-offset, first-order values of Sec. 3.2):
+ *   an R x R x R grid of centres k_i = -1 + (idx + 0.5) * 2/R on [-1,1]^3, each
+ *   holding 13 FP32 parameters, stored row-major as
+ *       params[((a*R + b)*R + c)*13 + slot]      (a = x index, slowest)
+ *   slot  0..2  Delta       offset of the second key, k_i + Delta_i
+ *         3     b           grid-key log-scale,   beta  = exp(log_beta0 + b)
+ *         4     b'          offset-key log-scale, beta' = exp(log_beta0 + b')
+ *         5     o           grid-key value constant
+ *         6..8  d           grid-key value linear term, f = o + d.(q - k)
+ *         9     o'          offset-key value constant
+ *         10..12 d'         offset-key value linear term, f' = o' + d'.(q - k - Delta)
+ *   O(q) = sum over keys of softmax(-beta ||q - key||^2) * f(q - key), one
+ *   softmax over the union of grid keys and offset keys (Eq. func-offset).
+ *
+ * Support: each query blends the (2W)^3 centres whose index lies in
+ * [c - W + 1, c + W] per axis, with c = clamp(floor((q+1)*R/2 - 1/2), -1, R-1)
+ * evaluated in FP32 without fused multiply-add; indices outside [0, R-1] are
+ * dropped.  W = 2 (64 centres, 128 keys) is the implemented width.  The
+ * paper's own sum is global (Algorithm 1); at the initial scale a truncated
+ * key weighs at most exp(-3.25 * beta h^2) ~ 1e-6 of the nearest one.
+ *
+ * Conventions for every call:
+ *   - Pointers marked [device] are device pointers owned by the caller; the
+ *     library never frees or keeps them.  [host|device] accepts either.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) unless stated otherwise.
+ *   - Work memory comes from the caller: `workspace` [device] of at least
+ *     efunc_workspace_bytes(grid, J) bytes, 256-byte aligned.  Concurrent calls
+ *     must not share a workspace.  The library allocates no device memory.
+ *   - Arguments are validated on the host before anything is launched; an
+ *     invalid argument returns EFUNC_ERR_ARG (or _WORKSPACE / _NONFINITE /
+ *     _UNSUPPORTED) and enqueues nothing.  A failing CUDA call returns
+ *     EFUNC_ERR_CUDA.  Nothing aborts the process.
+ *   - Queries: q holds J rows of q_stride floats (q_stride 3 or 4), x,y,z
+ *     first.  Outputs indexed by query are in the caller's query order.
+ *   - Non-finite parameters or queries give non-finite outputs; they are not
+ *     checked.
+ */
+#ifndef EFUNC_H
+#define EFUNC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *efunc_stream_t; /* same handle as cudaStream_t */
+
+typedef enum {
+    EFUNC_OK = 0,
+    EFUNC_ERR_ARG = 1,         /* invalid argument, nothing enqueued */
+    EFUNC_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    EFUNC_ERR_WORKSPACE = 3,   /* workspace NULL, misaligned or too small */
+    EFUNC_ERR_NONFINITE = 4,   /* a hyper-parameter is NaN or infinite */
+    EFUNC_ERR_UNSUPPORTED = 5  /* valid request outside the implemented set */
+} efunc_status;
+
+/* Grid description.  R in [1, 256]; W must be 2; log_beta0 is the log-scale
+ * that b = 0 stands for (Sec. 4.3 initialises scales to exp(7) at R = 32;
+ * efunc_default_log_beta0 keeps beta*h^2 fixed across R). */
+typedef struct {
+    int32_t R;
+    int32_t W;
+    float log_beta0;
+} efunc_grid;
+
+typedef enum { EFUNC_LOSS_L1 = 0, EFUNC_LOSS_MSE = 1 } efunc_loss;
+
+/* Adam (decoupled = 0: weight_decay added to the gradient) or AdamW
+ * (decoupled = 1: p *= 1 - lr*weight_decay), torch.optim semantics.
+ * Sec. 3.4 fits with Adam; Sec. 4.2 uses AdamW with lr 6e-4. */
+typedef struct {
+    float lr, beta1, beta2, eps, weight_decay;
+    int32_t decoupled;
+} efunc_adam;
+
+/* ---------------------------------------------------------------- helpers */
+
+/* Number of floats in the parameter grid, R^3 * 13 (Sec. 3.3: theta in
+ * R^{R^3 x (5 + |phi| + |phi'|)}).  -1 if R is outside [1, 256]. */
+int64_t efunc_param_count(int32_t R);
+
+/* 7 + 2 ln(R/32): exp(7) at R = 32 (Sec. 4.3), beta*h^2 constant in R. */
+float efunc_default_log_beta0(int32_t R);
+
+/* Static description of a status code.  Never NULL. */
+const char *efunc_status_str(efunc_status s);
+
+/* Bytes of workspace every call below needs for J queries on this grid
+ * (the maximum over all calls).  0 if the grid is invalid. */
+size_t efunc_workspace_bytes(const efunc_grid *grid, int64_t J);
+
+/* ------------------------------------------------------------ entry points */
+
+/* Cell sort (hot-path step a1; not in the paper, whose Algorithm 1 visits
+ * every key): groups the J queries by window base cell, cells in 4x4x4 bricks,
+ * Morton order inside a brick.
+ *   q        [device] J rows of q_stride floats
+ *   q_sorted [device] J x 4 floats, 16-byte aligned: (x, y, z, w) with w the
+ *            4th input column when q_stride == 4, else 0
+ *   perm     [device] J int32: q_sorted row i is input row perm[i]
+ * The order of queries inside a cell is unspecified (atomic arrival order). */
+efunc_status efunc_cell_sort(const efunc_grid *grid, const float *q, int64_t J, int32_t q_stride,
+                             float *q_sorted, int32_t *perm, void *workspace, size_t workspace_bytes,
+                             efunc_stream_t stream);
+
+/* Forward (Sec. 3.5, Algorithm 1; Eq. func-offset): O(q_j) for J queries.
+ *   params   [device] R^3*13 floats (layout above)
+ *   q        [device] J rows of q_stride floats
+ *   O        [device] J floats, written
+ *   lse      [device] J floats or NULL: natural log of the softmax
+ *            normaliser, log(sum_keys exp(-beta ||q - key||^2)) (the e_j of
+ *            Algorithm 1, in log form)
+ *   dOdq     [device] J*3 floats or NULL: dO/dq (Eq. func-normal) */
+efunc_status efunc_forward(const efunc_grid *grid, const float *params, const float *q, int64_t J,
+                           int32_t q_stride, float *O, float *lse, float *dOdq, void *workspace,
+                           size_t workspace_bytes, efunc_stream_t stream);
+
+/* Backward (Sec. 3.6, Algorithm 2 and the closed-form dO/dk, dO/dbeta,
+ * dO/dphi): recomputes the weights from params (no per-query state is kept
+ * between forward and backward) and ACCUMULATES
+ *   grad[i*13 + s] += sum_j gO_j * dO(q_j)/dtheta_{i,s}
+ * with the chain rule to the stored log-scales (dO/db = beta dO/dbeta) and to
+ * Delta (the offset key's dO/dk).  Grid keys are fixed.
+ *   gO       [device] J floats: dL/dO_j
+ *   grad     [device] R^3*13 floats, accumulated into (FP32 atomics: the
+ *            summation order is not deterministic)
+ *   gq       [device] J*3 floats or NULL: written with gO_j * dO/dq_j */
+efunc_status efunc_backward(const efunc_grid *grid, const float *params, const float *q, int64_t J,
+                            int32_t q_stride, const float *gO, float *grad, float *gq, void *workspace,
+                            size_t workspace_bytes, efunc_stream_t stream);
+
+/* One Adam/AdamW step over n floats (Sec. 3.4), step is 1-based (bias
+ * correction).  params, m, v are updated in place; grad is read and then
+ * zeroed.  All four [device], n >= 0. */
+efunc_status efunc_adam_step(const efunc_adam *adam, int64_t n, float *params, float *grad, float *m,
+                             float *v, int64_t step, efunc_stream_t stream);
+
+/* Fitting loop (Sec. 3.4): for s in [0, steps): take batch (s mod n_batches)
+ * of J rows (x, y, z, target SDF) from qo, cell-sort it, run the fused
+ * forward + loss gradient + backward, then one Adam step with step number
+ * step0 + s + 1.
+ *   loss     EFUNC_LOSS_L1 (dL/dO = sign(O - o)/J, sign(0) = 0) or
+ *            EFUNC_LOSS_MSE (Eq. loss, 2(O - o)/J)
+ *   params, m, v  [device] R^3*13 floats each, updated
+ *   qo       [host|device] n_batches*J*4 floats.  Host memory (pinned for
+ *            overlap) is copied to the device inside every step.
+ *   stats    [host|device] steps*2 floats or NULL: (loss, mean |O - o|) of
+ *            every step, evaluated at the parameters before that step's
+ *            update.  If stats is host memory the call synchronises the
+ *            stream before returning. */
+efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t loss, float *params,
+                       float *m, float *v, const float *qo, int64_t J, int32_t n_batches, int32_t steps,
+                       int64_t step0, float *stats, void *workspace, size_t workspace_bytes,
+                       efunc_stream_t stream);
+
+/* ------------------------------------------------------------ measurement */
+
+/* When enabled, every kernel launch of the library is bracketed by CUDA
+ * events recorded on its launch stream.  Events are created lazily (this is
+ * the one place the library asks the runtime for resources). */
+void efunc_profile_enable(int32_t enable);
+
+/* Waits for the recorded events and folds them into per-kernel totals.
+ * Writes the total milliseconds and launch count of kernel `name` (one of
+ * "bin", "scan_reduce", "scan_top", "scan_emit", "scatter", "forward",
+ * "fused_backward", "fused_fit", "adam").  Returns 0 on success, -1 for an
+ * unknown name or a CUDA error. */
+int32_t efunc_profile_read(const char *name, double *total_ms, int64_t *launches);
+
+/* Clears the per-kernel totals (pending events are discarded). */
+void efunc_profile_reset(void);
+
+/* Kernels launched by this library since it was loaded. */
+int64_t efunc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EFUNC_H */

@@ -1,0 +1,86 @@
+"""ctypes binding of ``libefunc.so`` (include/efunc.h): argument marshalling only.
+
+Every entry point of the header is declared here with its C signature.  The
+library is built in-tree on first use (nvcc) and fails loudly if it cannot be
+built or loaded: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+c_int32, c_int64, c_float, c_double = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
+c_size_t, c_void_p, c_char_p = ctypes.c_size_t, ctypes.c_void_p, ctypes.c_char_p
+P_float = ctypes.POINTER(ctypes.c_float)
+
+STATUS = {0: "EFUNC_OK", 1: "EFUNC_ERR_ARG", 2: "EFUNC_ERR_CUDA", 3: "EFUNC_ERR_WORKSPACE",
+          4: "EFUNC_ERR_NONFINITE", 5: "EFUNC_ERR_UNSUPPORTED"}
+LOSS_L1, LOSS_MSE = 0, 1
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("R", c_int32), ("W", c_int32), ("log_beta0", c_float)]
+
+
+class Adam(ctypes.Structure):
+    _fields_ = [("lr", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float),
+                ("weight_decay", c_float), ("decoupled", c_int32)]
+
+
+# name -> (restype, argtypes); the order follows include/efunc.h
+SIGNATURES = {
+    "efunc_param_count": (c_int64, [c_int32]),
+    "efunc_default_log_beta0": (c_float, [c_int32]),
+    "efunc_status_str": (c_char_p, [c_int32]),
+    "efunc_workspace_bytes": (c_size_t, [ctypes.POINTER(Grid), c_int64]),
+    "efunc_cell_sort": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_int64, c_int32, c_void_p, c_void_p,
+                                  c_void_p, c_size_t, c_void_p]),
+    "efunc_forward": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p,
+                                c_void_p, c_void_p, c_size_t, c_void_p]),
+    "efunc_backward": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p,
+                                 c_void_p, c_void_p, c_size_t, c_void_p]),
+    "efunc_adam_step": (c_int32, [ctypes.POINTER(Adam), c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,
+                                  c_void_p]),
+    "efunc_fit": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Adam), c_int32, c_void_p, c_void_p, c_void_p,
+                            c_void_p, c_int64, c_int32, c_int32, c_int64, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "efunc_profile_enable": (None, [c_int32]),
+    "efunc_profile_read": (c_int32, [c_char_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
+    "efunc_profile_reset": (None, []),
+    "efunc_launch_count": (c_int64, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(build: bool = True) -> ctypes.CDLL:
+    """Build (if needed) and load the library; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build and not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"CUDA library {_build.LIB} is missing and could not be built")
+            lib = ctypes.CDLL(_build.LIB)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class EfuncError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        msg = load().efunc_status_str(code).decode()
+        super().__init__(f"{fn} failed: {STATUS.get(code, code)} ({msg})")
+        self.code = code
+
+
+def check(fn: str, code: int) -> None:
+    if code != 0:
+        raise EfuncError(fn, code)

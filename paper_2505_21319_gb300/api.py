@@ -1,0 +1,223 @@
+"""PyTorch-facing wrappers of the C ABI (same names as include/efunc.h).
+
+PyTorch supplies device memory and the current CUDA stream; every step of the
+computation runs in the library's kernels.  Tensors must be CUDA float32 and
+contiguous; nothing is copied or converted implicitly.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import torch
+
+from . import _binding as B
+
+NSLOT = 13
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _need(t: torch.Tensor, name: str, numel: int | None = None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+
+
+def resolution_of(params: torch.Tensor) -> int:
+    n = params.numel() // NSLOT
+    R = int(round(n ** (1.0 / 3.0)))
+    if R ** 3 * NSLOT != params.numel():
+        raise ValueError("params must hold R^3 * 13 floats")
+    return R
+
+
+def default_log_beta0(R: int) -> float:
+    return float(B.load().efunc_default_log_beta0(R))
+
+
+def make_grid(R: int, log_beta0: float | None = None, W: int = 2) -> B.Grid:
+    return B.Grid(R, W, default_log_beta0(R) if log_beta0 is None else float(log_beta0))
+
+
+class Workspace:
+    """Grow-only device scratch buffer for one stream's calls."""
+
+    def __init__(self, device=None):
+        self.device = torch.device(device or "cuda")
+        self.buf = None
+
+    def get(self, grid: B.Grid, J: int) -> tuple[torch.Tensor, int]:
+        n = int(B.load().efunc_workspace_bytes(ctypes.byref(grid), int(J)))
+        if n == 0:
+            raise ValueError("invalid grid or query count")
+        if self.buf is None or self.buf.numel() < n:
+            self.buf = torch.empty(n, dtype=torch.uint8, device=self.device)
+        return self.buf, n
+
+
+_default_ws: dict = {}
+
+
+def _workspace(device, ws: Workspace | None) -> Workspace:
+    if ws is not None:
+        return ws
+    key = torch.device(device).index if torch.device(device).index is not None else torch.cuda.current_device()
+    if key not in _default_ws:
+        _default_ws[key] = Workspace(torch.device("cuda", key))
+    return _default_ws[key]
+
+
+def _queries(q: torch.Tensor):
+    _need(q, "q")
+    if q.dim() != 2 or q.shape[1] not in (3, 4):
+        raise ValueError("q must be (J, 3) or (J, 4)")
+    return q.shape[0], q.shape[1]
+
+
+def efunc_cell_sort(q: torch.Tensor, R: int, ws: Workspace | None = None):
+    """Cell-sorted copy of the queries (J, 4) and the permutation (J,) int32."""
+    J, stride = _queries(q)
+    grid = make_grid(R)
+    out = torch.empty((J, 4), dtype=torch.float32, device=q.device)
+    perm = torch.empty(J, dtype=torch.int32, device=q.device)
+    buf, n = _workspace(q.device, ws).get(grid, J)
+    B.check("efunc_cell_sort", B.load().efunc_cell_sort(ctypes.byref(grid), _ptr(q), J, stride, _ptr(out),
+                                                        _ptr(perm), _ptr(buf), n, _stream(q.device)))
+    return out, perm
+
+
+def efunc_forward(params: torch.Tensor, q: torch.Tensor, log_beta0: float | None = None, want_lse: bool = False,
+                  want_dq: bool = False, ws: Workspace | None = None):
+    """O(q) (Algorithm 1, Eq. func-offset); optionally lse and dO/dq (Eq. func-normal)."""
+    R = resolution_of(params)
+    _need(params, "params")
+    J, stride = _queries(q)
+    grid = make_grid(R, log_beta0)
+    O = torch.empty(J, dtype=torch.float32, device=q.device)
+    lse = torch.empty(J, dtype=torch.float32, device=q.device) if want_lse else None
+    dq = torch.empty((J, 3), dtype=torch.float32, device=q.device) if want_dq else None
+    buf, n = _workspace(q.device, ws).get(grid, J)
+    B.check("efunc_forward", B.load().efunc_forward(ctypes.byref(grid), _ptr(params), _ptr(q), J, stride, _ptr(O),
+                                                    _ptr(lse), _ptr(dq), _ptr(buf), n, _stream(q.device)))
+    out = [O]
+    if want_lse:
+        out.append(lse)
+    if want_dq:
+        out.append(dq)
+    return out[0] if len(out) == 1 else tuple(out)
+
+
+def efunc_backward(params: torch.Tensor, q: torch.Tensor, gO: torch.Tensor, grad: torch.Tensor | None = None,
+                   want_gq: bool = False, log_beta0: float | None = None, ws: Workspace | None = None):
+    """Accumulate dL/dparams into ``grad`` (Algorithm 2); optionally dL/dq."""
+    R = resolution_of(params)
+    _need(params, "params")
+    J, stride = _queries(q)
+    _need(gO, "gO", J)
+    if grad is None:
+        grad = torch.zeros_like(params)
+    _need(grad, "grad", params.numel())
+    gq = torch.empty((J, 3), dtype=torch.float32, device=q.device) if want_gq else None
+    grid = make_grid(R, log_beta0)
+    buf, n = _workspace(q.device, ws).get(grid, J)
+    B.check("efunc_backward", B.load().efunc_backward(ctypes.byref(grid), _ptr(params), _ptr(q), J, stride,
+                                                      _ptr(gO), _ptr(grad), _ptr(gq), _ptr(buf), n,
+                                                      _stream(q.device)))
+    return (grad, gq) if want_gq else grad
+
+
+def make_adam(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, decoupled=False) -> B.Adam:
+    return B.Adam(lr, beta1, beta2, eps, weight_decay, int(bool(decoupled)))
+
+
+def efunc_adam_step(params, grad, m, v, step: int, **adam_kw):
+    """One Adam/AdamW step in place; grad is zeroed."""
+    for t, nm in ((params, "params"), (grad, "grad"), (m, "m"), (v, "v")):
+        _need(t, nm, params.numel())
+    ad = make_adam(**adam_kw)
+    B.check("efunc_adam_step", B.load().efunc_adam_step(ctypes.byref(ad), params.numel(), _ptr(params), _ptr(grad),
+                                                        _ptr(m), _ptr(v), int(step), _stream(params.device)))
+
+
+def efunc_fit(params, m, v, qo, steps: int, J: int | None = None, n_batches: int = 1, step0: int = 0,
+              loss: str = "l1", stats=None, log_beta0: float | None = None, ws: Workspace | None = None,
+              **adam_kw):
+    """Fitting loop (Sec. 3.4) on batches of (x, y, z, target) rows.
+
+    ``qo`` is a CUDA tensor or a (pinned) CPU tensor of n_batches*J rows of 4
+    floats; ``stats`` (optional, CUDA or CPU float32 tensor of steps*2) gets
+    (loss, MAE) per step."""
+    R = resolution_of(params)
+    for t, nm in ((params, "params"), (m, "m"), (v, "v")):
+        _need(t, nm, params.numel())
+    if qo.dtype != torch.float32 or not qo.is_contiguous() or qo.dim() != 2 or qo.shape[1] != 4:
+        raise ValueError("qo must be a contiguous float32 (n_batches*J, 4) tensor")
+    if J is None:
+        J = qo.shape[0] // n_batches
+    if J * n_batches != qo.shape[0]:
+        raise ValueError("qo must hold n_batches * J rows")
+    if stats is not None and (stats.dtype != torch.float32 or stats.numel() < 2 * steps or not stats.is_contiguous()):
+        raise ValueError("stats must be a contiguous float32 tensor of at least 2*steps")
+    grid = make_grid(R, log_beta0)
+    ad = make_adam(**adam_kw)
+    buf, n = _workspace(params.device, ws).get(grid, J)
+    lk = {"l1": B.LOSS_L1, "mse": B.LOSS_MSE}[loss]
+    B.check("efunc_fit", B.load().efunc_fit(ctypes.byref(grid), ctypes.byref(ad), lk, _ptr(params), _ptr(m), _ptr(v),
+                                            _ptr(qo), J, n_batches, steps, step0, _ptr(stats), _ptr(buf), n,
+                                            _stream(params.device)))
+
+
+class EfuncFn(torch.autograd.Function):
+    """O = EfuncFn.apply(params, q): differentiable in params and q.
+
+    Forward: Algorithm 1.  Backward: Algorithm 2 for dL/dparams and
+    Eq. func-normal for dL/dq, both recomputed from (params, q)."""
+
+    @staticmethod
+    def forward(ctx, params, q, log_beta0=None):
+        ctx.save_for_backward(params, q)
+        ctx.log_beta0 = log_beta0
+        return efunc_forward(params.detach().contiguous(), q.detach().contiguous(), log_beta0=log_beta0)
+
+    @staticmethod
+    def backward(ctx, gO):
+        params, q = ctx.saved_tensors
+        need_q = ctx.needs_input_grad[1]
+        out = efunc_backward(params.detach().contiguous(), q.detach().contiguous(), gO.contiguous(),
+                             want_gq=need_q, log_beta0=ctx.log_beta0)
+        gp, gq = (out if need_q else (out, None))
+        if gq is not None and q.shape[1] == 4:
+            gq = torch.cat([gq, torch.zeros_like(gq[:, :1])], 1)
+        return (gp if ctx.needs_input_grad[0] else None), gq, None
+
+
+def profile(enable: bool = True):
+    B.load().efunc_profile_enable(int(enable))
+
+
+def profile_read(name: str) -> tuple[float, int]:
+    ms, cnt = ctypes.c_double(0), ctypes.c_int64(0)
+    rc = B.load().efunc_profile_read(name.encode(), ctypes.byref(ms), ctypes.byref(cnt))
+    if rc != 0:
+        raise RuntimeError(f"efunc_profile_read({name}) failed")
+    return ms.value, cnt.value
+
+
+def profile_reset():
+    B.load().efunc_profile_reset()
+
+
+def launch_count() -> int:
+    return int(B.load().efunc_launch_count())

@@ -1,0 +1,159 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "efunc.h"
+
+namespace efunc {
+
+constexpr int kSlots = 13;        // floats per centre (Eq. func-offset, f^1)
+constexpr int kW = 2;             // window half-width
+constexpr int kCentres = 64;      // (2W)^3 centres per window
+constexpr int kThreads = 128;     // threads of the fused kernel = keys per window
+constexpr int kChunk = 256;       // queries per work item at most
+constexpr int kMaxR = 256;
+constexpr int kBrick = 4;         // cells per brick edge in the sort order
+
+// Work item: one window-base cell and a contiguous slice of its sorted queries.
+//   x = first sorted row, y = number of rows (1..kChunk),
+//   z = packed cell (ux | uy << 10 | uz << 20) with u = c + 1 in [0, R].
+using Item = int4;
+
+// Per-call control block at the start of the workspace.
+struct Ctrl {
+    int n_items;        // work items produced by the sort
+    int next_item;      // dynamic work counter of the fused kernel
+    int pad[2];
+    double loss_sum;    // sum over queries of |O-o| (L1) or (O-o)^2 (MSE)
+    double abs_sum;     // sum over queries of |O-o|
+};
+
+struct Layout {
+    int P;              // bricks per axis, ceil((R+1)/4)
+    int64_t nbins;      // P^3 * 64
+    int64_t nscan_blocks;
+    int64_t max_items;
+    size_t ctrl, hist, blocksum, rank, sorted, perm, items, grad, stage, total;
+};
+
+Layout make_layout(int R, int64_t J);
+
+// Sort configuration passed to kernels.
+struct SortArgs {
+    const float *q;
+    int64_t J;
+    int q_stride;
+    int R;
+    int P;
+    int64_t nbins;
+    uint32_t *hist;      // counts, then exclusive offsets (in place)
+    unsigned long long *blocksum;
+    uint32_t *rank;
+    float4 *sorted;
+    int *perm;
+    Item *items;
+    Ctrl *ctrl;
+};
+
+// Fused-kernel arguments.
+struct FusedArgs {
+    const float *params;
+    int R;
+    float nbl0;          // -exp(log_beta0) * log2(e), folded on the host in FP64
+    const float4 *sorted;
+    const int *perm;
+    const Item *items;
+    Ctrl *ctrl;
+    // forward outputs (user order)
+    float *O;
+    float *lse;
+    float *dq;
+    // backward inputs / outputs
+    const float *gO;     // user order
+    float *grad;
+    float *gq;           // user order
+    // fit
+    int loss;
+    float inv_J;
+};
+
+struct AdamArgs {
+    float *p, *g, *m, *v;
+    int64_t n;
+    float lr, beta1, beta2, eps, wd;
+    int decoupled;
+    float step_size;        // lr / (1 - beta1^t)
+    float inv_sqrt_bc2;     // 1 / sqrt(1 - beta2^t)
+    // optional fit statistics: stats[0] = loss_sum * inv_J, stats[1] = abs_sum * inv_J
+    const Ctrl *ctrl;
+    float *stats;
+    float inv_J;
+};
+
+// Kernel identifiers for the profiler.
+enum KernelId { K_BIN = 0, K_SCAN_REDUCE, K_SCAN_TOP, K_SCAN_EMIT, K_SCATTER, K_FORWARD, K_FUSED_BWD, K_FUSED_FIT,
+                K_ADAM, K_COUNT };
+
+// Launch bookkeeping (launch counter and optional CUDA-event profiling).
+void launch_begin(int kid, cudaStream_t s);
+void launch_end(int kid, cudaStream_t s);
+
+// Launchers (defined in sort.cu, fused.cu, adam.cu).  They return the CUDA
+// error of the launch.
+cudaError_t launch_sort(const SortArgs &a, cudaStream_t s);
+cudaError_t launch_forward(const FusedArgs &a, bool with_dq, int grid, cudaStream_t s);
+cudaError_t launch_fused_backward(const FusedArgs &a, bool with_gq, int grid, cudaStream_t s);
+cudaError_t launch_fused_fit(const FusedArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_adam(const AdamArgs &a, cudaStream_t s);
+int fused_grid_size();   // persistent grid: SMs x resident blocks per SM
+
+// Window-base index along one axis: clamp(floor((q+1)*R/2 - 1/2), -1, R-1),
+// in FP32 with every operation rounded separately (no contraction into FMA).
+__device__ __forceinline__ int window_base(float q, float half_r, float rmax)
+{
+    float t = __fmul_rn(__fadd_rn(q, 1.0f), half_r);
+    float u = __fsub_rn(t, 0.5f);
+    u = (u >= -1.0f) ? u : -1.0f;   // NaN -> -1
+    u = fminf(u, rmax);
+    return (int)floorf(u);
+}
+
+// Brick-Morton bin of a cell u = (ux, uy, uz) in [0, R]^3: bricks of 4^3
+// cells in row-major order, Morton order of the 64 cells inside a brick.
+__device__ __forceinline__ uint32_t bin_of(int ux, int uy, int uz, int P)
+{
+    uint32_t brick = ((uint32_t)(ux >> 2) * P + (uint32_t)(uy >> 2)) * P + (uint32_t)(uz >> 2);
+    uint32_t lx = ux & 3, ly = uy & 3, lz = uz & 3;
+    uint32_t m = (lx & 1) << 2 | (ly & 1) << 1 | (lz & 1) | (lx & 2) << 4 | (ly & 2) << 3 | (lz & 2) << 2;
+    return brick * 64u + m;
+}
+
+__device__ __forceinline__ void cell_of_bin(uint32_t bin, int P, int &ux, int &uy, int &uz)
+{
+    uint32_t brick = bin >> 6, m = bin & 63u;
+    int bz = brick % P, by = (brick / P) % P, bx = brick / (P * P);
+    int lx = ((m >> 2) & 1) | ((m >> 4) & 2);
+    int ly = ((m >> 1) & 1) | ((m >> 3) & 2);
+    int lz = (m & 1) | ((m >> 2) & 2);
+    ux = bx * 4 + lx;
+    uy = by * 4 + ly;
+    uz = bz * 4 + lz;
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+}  // namespace efunc

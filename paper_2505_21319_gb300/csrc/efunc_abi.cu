@@ -1,0 +1,434 @@
+// The C ABI (include/efunc.h): argument validation, workspace layout, launch
+// order of the hot path, and the launch counter / event profiler.
+#include <math.h>
+#include <mutex>
+#include <string.h>
+#include <vector>
+
+#include "common.cuh"
+
+namespace efunc {
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ----------------------------------------------------------- profiling
+
+struct Pending {
+    int kid;
+    cudaEvent_t start, stop;
+};
+
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_free_events;
+double g_ms[K_COUNT];
+int64_t g_count[K_COUNT];
+int64_t g_launches = 0;
+
+const char *const kKernelNames[K_COUNT] = {"bin",     "scan_reduce",    "scan_top",  "scan_emit", "scatter",
+                                           "forward", "fused_backward", "fused_fit", "adam"};
+
+cudaEvent_t take_event()
+{
+    if (!g_free_events.empty()) {
+        cudaEvent_t e = g_free_events.back();
+        g_free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Resolves pending event pairs into totals.  Caller holds g_prof_mu.
+int drain_pending()
+{
+    int rc = 0;
+    for (Pending &p : g_pending) {
+        if (p.start && p.stop) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(p.stop) == cudaSuccess && cudaEventElapsedTime(&ms, p.start, p.stop) == cudaSuccess) {
+                g_ms[p.kid] += ms;
+                g_count[p.kid] += 1;
+            } else {
+                rc = -1;
+            }
+        }
+        if (p.start) g_free_events.push_back(p.start);
+        if (p.stop) g_free_events.push_back(p.stop);
+    }
+    g_pending.clear();
+    return rc;
+}
+
+}  // namespace
+
+void launch_begin(int kid, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ++g_launches;
+    if (!g_prof_on) return;
+    Pending p{kid, take_event(), nullptr};
+    if (p.start) cudaEventRecord(p.start, s);
+    g_pending.push_back(p);
+}
+
+void launch_end(int kid, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on || g_pending.empty() || g_pending.back().kid != kid || g_pending.back().stop) return;
+    cudaEvent_t e = take_event();
+    if (e) cudaEventRecord(e, s);
+    g_pending.back().stop = e;
+}
+
+// ------------------------------------------------------------- layout
+
+Layout make_layout(int R, int64_t J)
+{
+    Layout L{};
+    L.P = (R + 1 + kBrick - 1) / kBrick;
+    L.nbins = (int64_t)L.P * L.P * L.P * 64;
+    L.nscan_blocks = (L.nbins + 4095) / 4096;
+    L.max_items = (J + kChunk - 1) / kChunk + (J < L.nbins ? J : L.nbins);
+    const size_t A = 256;
+    size_t off = 0;
+    L.ctrl = off;      off = align_up(off + sizeof(Ctrl), A);
+    L.hist = off;      off = align_up(off + (size_t)L.nbins * 4, A);
+    L.blocksum = off;  off = align_up(off + (size_t)L.nscan_blocks * 8, A);
+    L.rank = off;      off = align_up(off + (size_t)J * 4, A);
+    L.sorted = off;    off = align_up(off + (size_t)J * 16, A);
+    L.perm = off;      off = align_up(off + (size_t)J * 4, A);
+    L.items = off;     off = align_up(off + (size_t)L.max_items * 16, A);
+    L.grad = off;      off = align_up(off + (size_t)R * R * R * kSlots * 4, A);
+    L.stage = off;     off = align_up(off + (size_t)J * 16, A);
+    L.total = off;
+    return L;
+}
+
+}  // namespace efunc
+
+using namespace efunc;
+
+namespace {
+
+constexpr int64_t kMaxJ = (int64_t)1 << 30;
+
+bool grid_ok(const efunc_grid *g) { return g && g->R >= 1 && g->R <= kMaxR; }
+
+efunc_status check_grid(const efunc_grid *g)
+{
+    if (!grid_ok(g)) return EFUNC_ERR_ARG;
+    if (g->W != kW) return EFUNC_ERR_UNSUPPORTED;
+    if (!isfinite(g->log_beta0)) return EFUNC_ERR_NONFINITE;
+    return EFUNC_OK;
+}
+
+efunc_status check_workspace(const efunc_grid *g, int64_t J, const void *ws, size_t ws_bytes)
+{
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return EFUNC_ERR_WORKSPACE;
+    if (ws_bytes < make_layout(g->R, J).total) return EFUNC_ERR_WORKSPACE;
+    return EFUNC_OK;
+}
+
+float nbl0_of(const efunc_grid *g) { return (float)(-exp((double)g->log_beta0) * 1.4426950408889634); }
+
+struct Views {
+    Layout L;
+    char *base;
+    Ctrl *ctrl() const { return reinterpret_cast<Ctrl *>(base + L.ctrl); }
+    uint32_t *hist() const { return reinterpret_cast<uint32_t *>(base + L.hist); }
+    unsigned long long *blocksum() const { return reinterpret_cast<unsigned long long *>(base + L.blocksum); }
+    uint32_t *rank() const { return reinterpret_cast<uint32_t *>(base + L.rank); }
+    float4 *sorted() const { return reinterpret_cast<float4 *>(base + L.sorted); }
+    int *perm() const { return reinterpret_cast<int *>(base + L.perm); }
+    Item *items() const { return reinterpret_cast<Item *>(base + L.items); }
+    float *grad() const { return reinterpret_cast<float *>(base + L.grad); }
+    float4 *stage() const { return reinterpret_cast<float4 *>(base + L.stage); }
+};
+
+// Clears the control block and histogram, then sorts q into the workspace
+// (or into the caller's sorted / perm buffers when given).
+cudaError_t sort_into(const Views &v, int R, const float *q, int64_t J, int q_stride, float4 *sorted, int *perm,
+                      cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(v.ctrl(), 0, sizeof(Ctrl), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(v.hist(), 0, (size_t)v.L.nbins * 4, s);
+    if (e != cudaSuccess) return e;
+    SortArgs a{};
+    a.q = q;
+    a.J = J;
+    a.q_stride = q_stride;
+    a.R = R;
+    a.P = v.L.P;
+    a.nbins = v.L.nbins;
+    a.hist = v.hist();
+    a.blocksum = v.blocksum();
+    a.rank = v.rank();
+    a.sorted = sorted;
+    a.perm = perm;
+    a.items = v.items();
+    a.ctrl = v.ctrl();
+    return launch_sort(a, s);
+}
+
+FusedArgs fused_args(const Views &v, const efunc_grid *g, const float *params)
+{
+    FusedArgs f{};
+    f.params = params;
+    f.R = g->R;
+    f.nbl0 = nbl0_of(g);
+    f.sorted = v.sorted();
+    f.perm = v.perm();
+    f.items = v.items();
+    f.ctrl = v.ctrl();
+    return f;
+}
+
+bool is_host_pointer(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the sticky-free error of an unknown pointer
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+efunc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? EFUNC_OK : EFUNC_ERR_CUDA; }
+
+efunc_status check_adam(const efunc_adam *a)
+{
+    if (!a) return EFUNC_ERR_ARG;
+    if (!isfinite(a->lr) || !isfinite(a->beta1) || !isfinite(a->beta2) || !isfinite(a->eps) ||
+        !isfinite(a->weight_decay))
+        return EFUNC_ERR_NONFINITE;
+    if (a->beta1 < 0.f || a->beta1 >= 1.f || a->beta2 < 0.f || a->beta2 >= 1.f || a->eps < 0.f ||
+        (a->decoupled != 0 && a->decoupled != 1))
+        return EFUNC_ERR_ARG;
+    return EFUNC_OK;
+}
+
+AdamArgs adam_args(const efunc_adam *ad, int64_t n, float *p, float *g, float *m, float *v, int64_t step)
+{
+    AdamArgs a{};
+    a.p = p; a.g = g; a.m = m; a.v = v;
+    a.n = n;
+    a.lr = ad->lr;
+    a.beta1 = ad->beta1;
+    a.beta2 = ad->beta2;
+    a.eps = ad->eps;
+    a.wd = ad->weight_decay;
+    a.decoupled = ad->decoupled;
+    const double bc1 = 1.0 - pow((double)ad->beta1, (double)step);
+    const double bc2 = 1.0 - pow((double)ad->beta2, (double)step);
+    a.step_size = (float)((double)ad->lr / bc1);
+    a.inv_sqrt_bc2 = (float)(1.0 / sqrt(bc2));
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t efunc_param_count(int32_t R)
+{
+    if (R < 1 || R > kMaxR) return -1;
+    return (int64_t)R * R * R * kSlots;
+}
+
+float efunc_default_log_beta0(int32_t R)
+{
+    if (R < 1) return NAN;
+    return (float)(7.0 + 2.0 * log((double)R / 32.0));
+}
+
+const char *efunc_status_str(efunc_status s)
+{
+    switch (s) {
+    case EFUNC_OK: return "ok";
+    case EFUNC_ERR_ARG: return "invalid argument";
+    case EFUNC_ERR_CUDA: return "CUDA runtime error";
+    case EFUNC_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case EFUNC_ERR_NONFINITE: return "non-finite hyper-parameter";
+    case EFUNC_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+size_t efunc_workspace_bytes(const efunc_grid *grid, int64_t J)
+{
+    if (!grid_ok(grid) || J < 0 || J > kMaxJ) return 0;
+    return make_layout(grid->R, J).total;
+}
+
+efunc_status efunc_cell_sort(const efunc_grid *grid, const float *q, int64_t J, int32_t q_stride, float *q_sorted,
+                             int32_t *perm, void *workspace, size_t workspace_bytes, efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if (J < 0 || J > kMaxJ || (q_stride != 3 && q_stride != 4)) return EFUNC_ERR_ARG;
+    if (J == 0) return EFUNC_OK;
+    if (!q || !q_sorted || !perm || (reinterpret_cast<uintptr_t>(q_sorted) & 15u)) return EFUNC_ERR_ARG;
+    if ((st = check_workspace(grid, J, workspace, workspace_bytes))) return st;
+    Views v{make_layout(grid->R, J), static_cast<char *>(workspace)};
+    return cuda_status(sort_into(v, grid->R, q, J, q_stride, reinterpret_cast<float4 *>(q_sorted), perm,
+                                 (cudaStream_t)stream));
+}
+
+efunc_status efunc_forward(const efunc_grid *grid, const float *params, const float *q, int64_t J, int32_t q_stride,
+                           float *O, float *lse, float *dOdq, void *workspace, size_t workspace_bytes,
+                           efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if (J < 0 || J > kMaxJ || (q_stride != 3 && q_stride != 4) || !params) return EFUNC_ERR_ARG;
+    if (J == 0) return EFUNC_OK;
+    if (!q || !O) return EFUNC_ERR_ARG;
+    if ((st = check_workspace(grid, J, workspace, workspace_bytes))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Views v{make_layout(grid->R, J), static_cast<char *>(workspace)};
+    cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
+    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    FusedArgs f = fused_args(v, grid, params);
+    f.O = O;
+    f.lse = lse;
+    f.dq = dOdq;
+    return cuda_status(launch_forward(f, dOdq != nullptr, fused_grid_size(), s));
+}
+
+efunc_status efunc_backward(const efunc_grid *grid, const float *params, const float *q, int64_t J,
+                            int32_t q_stride, const float *gO, float *grad, float *gq, void *workspace,
+                            size_t workspace_bytes, efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if (J < 0 || J > kMaxJ || (q_stride != 3 && q_stride != 4) || !params || !grad) return EFUNC_ERR_ARG;
+    if (J == 0) return EFUNC_OK;
+    if (!q || !gO) return EFUNC_ERR_ARG;
+    if ((st = check_workspace(grid, J, workspace, workspace_bytes))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Views v{make_layout(grid->R, J), static_cast<char *>(workspace)};
+    cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
+    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    FusedArgs f = fused_args(v, grid, params);
+    f.gO = gO;
+    f.grad = grad;
+    f.gq = gq;
+    return cuda_status(launch_fused_backward(f, gq != nullptr, fused_grid_size(), s));
+}
+
+efunc_status efunc_adam_step(const efunc_adam *adam, int64_t n, float *params, float *grad, float *m, float *v,
+                             int64_t step, efunc_stream_t stream)
+{
+    efunc_status st = check_adam(adam);
+    if (st) return st;
+    if (n < 0 || step < 1) return EFUNC_ERR_ARG;
+    if (n == 0) return EFUNC_OK;
+    if (!params || !grad || !m || !v) return EFUNC_ERR_ARG;
+    AdamArgs a = adam_args(adam, n, params, grad, m, v, step);
+    return cuda_status(launch_adam(a, (cudaStream_t)stream));
+}
+
+efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t loss, float *params, float *m,
+                       float *v, const float *qo, int64_t J, int32_t n_batches, int32_t steps, int64_t step0,
+                       float *stats, void *workspace, size_t workspace_bytes, efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if ((st = check_adam(adam))) return st;
+    if (loss != EFUNC_LOSS_L1 && loss != EFUNC_LOSS_MSE) return EFUNC_ERR_ARG;
+    if (J < 1 || J > kMaxJ || n_batches < 1 || steps < 0 || step0 < 0) return EFUNC_ERR_ARG;
+    if (!params || !m || !v || !qo) return EFUNC_ERR_ARG;
+    if ((st = check_workspace(grid, J, workspace, workspace_bytes))) return st;
+    if (steps == 0) return EFUNC_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    Views vw{make_layout(grid->R, J), static_cast<char *>(workspace)};
+    const bool q_host = is_host_pointer(qo);
+    const bool stats_host = stats && is_host_pointer(stats);
+    const int64_t n = efunc_param_count(grid->R);
+    float *grad = vw.grad();
+    // scratch for the per-step statistics when the caller's array is on the host
+    float *stats_dev = reinterpret_cast<float *>(vw.ctrl()) + 16;
+    static_assert(sizeof(Ctrl) <= 64, "control block must leave room for the statistics slot");
+
+    cudaError_t e = cudaMemsetAsync(grad, 0, (size_t)n * 4, s);
+    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    const int grid_blocks = fused_grid_size();
+    for (int32_t it = 0; it < steps; ++it) {
+        const float *src = qo + (size_t)(it % n_batches) * (size_t)J * 4;
+        const float *qdev = src;
+        if (q_host) {
+            e = cudaMemcpyAsync(vw.stage(), src, (size_t)J * 16, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+            qdev = reinterpret_cast<const float *>(vw.stage());
+        }
+        e = sort_into(vw, grid->R, qdev, J, 4, vw.sorted(), vw.perm(), s);
+        if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+        FusedArgs f = fused_args(vw, grid, params);
+        f.grad = grad;
+        f.loss = loss;
+        f.inv_J = (float)(1.0 / (double)J);
+        e = launch_fused_fit(f, grid_blocks, s);
+        if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+        AdamArgs a = adam_args(adam, n, params, grad, m, v, step0 + it + 1);
+        a.ctrl = vw.ctrl();
+        a.inv_J = f.inv_J;
+        a.stats = stats ? (stats_host ? stats_dev : stats + 2 * (size_t)it) : nullptr;
+        e = launch_adam(a, s);
+        if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (stats_host) {
+            e = cudaMemcpyAsync(stats + 2 * (size_t)it, stats_dev, 8, cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+        }
+    }
+    if (stats_host && cudaStreamSynchronize(s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    return EFUNC_OK;
+}
+
+void efunc_profile_enable(int32_t enable)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = enable != 0;
+}
+
+int32_t efunc_profile_read(const char *name, double *total_ms, int64_t *launches)
+{
+    if (!name) return -1;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int rc = drain_pending();
+    for (int k = 0; k < K_COUNT; ++k) {
+        if (strcmp(name, kKernelNames[k]) == 0) {
+            if (total_ms) *total_ms = g_ms[k];
+            if (launches) *launches = g_count[k];
+            return rc;
+        }
+    }
+    return -1;
+}
+
+void efunc_profile_reset(void)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (Pending &p : g_pending) {
+        if (p.start) g_free_events.push_back(p.start);
+        if (p.stop) g_free_events.push_back(p.stop);
+    }
+    g_pending.clear();
+    for (int k = 0; k < K_COUNT; ++k) {
+        g_ms[k] = 0.0;
+        g_count[k] = 0;
+    }
+}
+
+int64_t efunc_launch_count(void)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    return g_launches;
+}
+
+}  // extern "C"

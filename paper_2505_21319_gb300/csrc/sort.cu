@@ -1,0 +1,229 @@
+// Cell sort of the query batch (hot-path step a1).
+//
+// Every query is binned by its window-base cell u = c + 1 in [0, R]^3 (the
+// cell whose 4x4x4 centre window the query blends), so that all queries of a
+// bin share one window.  Bins are ordered in 4x4x4 bricks (row-major) with
+// Morton order inside a brick.  A counting sort:
+//   bin      histogram with warp-aggregated atomics; each query keeps its
+//            arrival rank inside its bin
+//   scan     exclusive scan of (count, work items) pairs over all bins
+//            (reduce per block / scan of block sums / scan + emit)
+//   scatter  query -> position offset[bin] + rank: float4 row + permutation
+// The scan also emits the work items of the fused kernel: every non-empty bin
+// yields ceil(count / kChunk) slices of at most kChunk sorted queries.
+#include "common.cuh"
+
+namespace efunc {
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanPerThread = 4;
+constexpr int kScanSeg = kScanThreads * kScanPerThread;   // bins per scan block
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ void load_query(const float *q, int64_t j, int stride, bool vec4, float &x, float &y,
+                                           float &z, float &w)
+{
+    if (vec4) {
+        float4 v = __ldg(reinterpret_cast<const float4 *>(q) + j);
+        x = v.x; y = v.y; z = v.z; w = v.w;
+    } else {
+        const float *r = q + j * stride;
+        x = __ldg(r); y = __ldg(r + 1); z = __ldg(r + 2);
+        w = stride == 4 ? __ldg(r + 3) : 0.0f;
+    }
+}
+
+__device__ __forceinline__ uint32_t query_bin(float x, float y, float z, float half_r, float rmax, int P)
+{
+    int ux = window_base(x, half_r, rmax) + 1;
+    int uy = window_base(y, half_r, rmax) + 1;
+    int uz = window_base(z, half_r, rmax) + 1;
+    return bin_of(ux, uy, uz, P);
+}
+
+template <bool VEC4>
+__global__ void __launch_bounds__(256) bin_kernel(SortArgs a)
+{
+    const float half_r = (float)a.R * 0.5f, rmax = (float)(a.R - 1);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j0 = warp * 32; j0 < a.J; j0 += nwarps * 32) {
+        const int64_t j = j0 + lane;
+        const bool valid = j < a.J;
+        const unsigned mask = __ballot_sync(kFull, valid);
+        if (!valid) continue;
+        float x, y, z, w;
+        load_query(a.q, j, a.q_stride, VEC4, x, y, z, w);
+        const uint32_t bin = query_bin(x, y, z, half_r, rmax, a.P);
+        // warp-aggregated increment: one atomic per distinct bin in the warp
+        const unsigned peers = __match_any_sync(mask, bin);
+        const int leader = __ffs(peers) - 1;
+        const unsigned below = peers & ((1u << lane) - 1u);
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&a.hist[bin], (uint32_t)__popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        a.rank[j] = base + (uint32_t)__popc(below);
+    }
+}
+
+// Packed scan value: low 32 bits = query count, high 32 bits = work items.
+__device__ __forceinline__ unsigned long long pack(uint32_t count)
+{
+    unsigned long long items = (count + kChunk - 1) / kChunk;
+    return (items << 32) | (unsigned long long)count;
+}
+
+// Exclusive block scan of one 64-bit value per thread; returns the block total.
+__device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long long v, unsigned long long &total)
+{
+    __shared__ unsigned long long warp_tot[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long s = lane < nw ? warp_tot[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_tot[lane] = s;
+    }
+    __syncthreads();
+    const unsigned long long prefix = wid ? warp_tot[wid - 1] : 0ull;
+    total = warp_tot[nw - 1];
+    __syncthreads();   // warp_tot is reused by the next call
+    return prefix + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(SortArgs a)
+{
+    const int64_t b0 = (int64_t)blockIdx.x * kScanSeg + (int64_t)threadIdx.x * kScanPerThread;
+    unsigned long long s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k)
+        if (b0 + k < a.nbins) s += pack(a.hist[b0 + k]);
+    unsigned long long total;
+    block_exclusive_scan(s, total);
+    if (threadIdx.x == 0) a.blocksum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_top_kernel(SortArgs a, int64_t nblocks)
+{
+    unsigned long long carry = 0;
+    for (int64_t base = 0; base < nblocks; base += kScanThreads) {
+        const int64_t i = base + threadIdx.x;
+        const unsigned long long v = i < nblocks ? a.blocksum[i] : 0ull;
+        unsigned long long total;
+        const unsigned long long ex = block_exclusive_scan(v, total);
+        if (i < nblocks) a.blocksum[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) a.ctrl->n_items = (int)(carry >> 32);
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_emit_kernel(SortArgs a)
+{
+    const int64_t b0 = (int64_t)blockIdx.x * kScanSeg + (int64_t)threadIdx.x * kScanPerThread;
+    uint32_t cnt[kScanPerThread];
+    unsigned long long s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k) {
+        cnt[k] = b0 + k < a.nbins ? a.hist[b0 + k] : 0u;
+        s += pack(cnt[k]);
+    }
+    unsigned long long total;
+    unsigned long long run = a.blocksum[blockIdx.x] + block_exclusive_scan(s, total);
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k) {
+        if (b0 + k >= a.nbins) break;
+        const uint32_t start = (uint32_t)(run & 0xffffffffull);
+        const uint32_t item0 = (uint32_t)(run >> 32);
+        a.hist[b0 + k] = start;   // counts become exclusive offsets, in place
+        if (cnt[k]) {
+            int ux, uy, uz;
+            cell_of_bin((uint32_t)(b0 + k), a.P, ux, uy, uz);
+            const int packed = ux | (uy << 10) | (uz << 20);
+            const uint32_t nit = (cnt[k] + kChunk - 1) / kChunk;
+            for (uint32_t i = 0; i < nit; ++i) {
+                const uint32_t off = i * kChunk;
+                const uint32_t len = min((uint32_t)kChunk, cnt[k] - off);
+                a.items[item0 + i] = make_int4((int)(start + off), (int)len, packed, 0);
+            }
+        }
+        run += pack(cnt[k]);
+    }
+}
+
+template <bool VEC4>
+__global__ void __launch_bounds__(256) scatter_kernel(SortArgs a)
+{
+    const float half_r = (float)a.R * 0.5f, rmax = (float)(a.R - 1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.J; j += stride) {
+        float x, y, z, w;
+        load_query(a.q, j, a.q_stride, VEC4, x, y, z, w);
+        const uint32_t bin = query_bin(x, y, z, half_r, rmax, a.P);
+        const uint32_t pos = a.hist[bin] + a.rank[j];
+        a.sorted[pos] = make_float4(x, y, z, w);
+        a.perm[pos] = (int)j;
+    }
+}
+
+int stream_grid(int64_t work, int threads)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    int64_t blocks = (work + threads - 1) / threads;
+    int64_t cap = (int64_t)sms * 8;
+    if (blocks > cap) blocks = cap;
+    return (int)(blocks < 1 ? 1 : blocks);
+}
+
+}  // namespace
+
+cudaError_t launch_sort(const SortArgs &a, cudaStream_t s)
+{
+    const bool vec4 = a.q_stride == 4 && (reinterpret_cast<uintptr_t>(a.q) & 15u) == 0;
+    const int g = stream_grid(a.J, 256);
+    const int64_t nblocks = (a.nbins + kScanSeg - 1) / kScanSeg;
+
+    launch_begin(K_BIN, s);
+    if (vec4) bin_kernel<true><<<g, 256, 0, s>>>(a);
+    else bin_kernel<false><<<g, 256, 0, s>>>(a);
+    launch_end(K_BIN, s);
+
+    launch_begin(K_SCAN_REDUCE, s);
+    scan_reduce_kernel<<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
+    launch_end(K_SCAN_REDUCE, s);
+
+    launch_begin(K_SCAN_TOP, s);
+    scan_top_kernel<<<1, kScanThreads, 0, s>>>(a, nblocks);
+    launch_end(K_SCAN_TOP, s);
+
+    launch_begin(K_SCAN_EMIT, s);
+    scan_emit_kernel<<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
+    launch_end(K_SCAN_EMIT, s);
+
+    launch_begin(K_SCATTER, s);
+    if (vec4) scatter_kernel<true><<<g, 256, 0, s>>>(a);
+    else scatter_kernel<false><<<g, 256, 0, s>>>(a);
+    launch_end(K_SCATTER, s);
+    return cudaGetLastError();
+}
+
+}  // namespace efunc

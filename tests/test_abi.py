@@ -1,0 +1,103 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads without
+a GPU, exports every symbol include/efunc.h declares, and validates arguments
+on the host (nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2505_21319_gb300 import _binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "efunc.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(efunc_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_hot_path_calls():
+    names = declared_functions()
+    for n in ("efunc_forward", "efunc_backward", "efunc_adam_step", "efunc_fit", "efunc_workspace_bytes",
+              "efunc_status_str", "efunc_cell_sort"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in B.SIGNATURES, f"binding lacks {name}"
+    assert set(B.SIGNATURES) == set(declared_functions())
+
+
+def test_host_helpers(lib):
+    assert lib.efunc_param_count(32) == 32 ** 3 * 13 == 425984
+    assert lib.efunc_param_count(0) == -1 and lib.efunc_param_count(257) == -1
+    assert abs(lib.efunc_default_log_beta0(32) - 7.0) < 1e-6
+    assert abs(lib.efunc_default_log_beta0(64) - (7.0 + 2 * 0.6931471805599453)) < 1e-6
+    for code in range(6):
+        assert lib.efunc_status_str(code)
+    assert lib.efunc_status_str(99) == b"unknown status"
+    g = B.Grid(32, 2, 7.0)
+    n1 = lib.efunc_workspace_bytes(ctypes.byref(g), 1 << 22)
+    n2 = lib.efunc_workspace_bytes(ctypes.byref(g), 1 << 10)
+    assert n1 > n2 > 0 and n1 % 256 == 0
+    assert lib.efunc_workspace_bytes(ctypes.byref(B.Grid(0, 2, 7.0)), 10) == 0
+    assert lib.efunc_workspace_bytes(ctypes.byref(g), -1) == 0
+    assert lib.efunc_launch_count() == 0
+
+
+def _fwd(lib, grid, J=16, stride=3, ws=1 << 30, ws_bytes=None, params=4096, q=8192, O=12288):
+    g = ctypes.byref(grid) if grid is not None else None
+    if ws_bytes is None:
+        ws_bytes = 1 << 40
+    return lib.efunc_forward(g, params, q, J, stride, O, None, None, ws, ws_bytes, None)
+
+
+def test_argument_validation_enqueues_nothing(lib):
+    """Invalid arguments are rejected on the host (fake, never dereferenced
+    pointers are enough to reach every check)."""
+    ok = B.Grid(8, 2, 7.0)
+    assert _fwd(lib, None) == 1
+    assert _fwd(lib, B.Grid(0, 2, 7.0)) == 1
+    assert _fwd(lib, B.Grid(300, 2, 7.0)) == 1
+    assert _fwd(lib, B.Grid(8, 3, 7.0)) == 5
+    assert _fwd(lib, B.Grid(8, 2, float("nan"))) == 4
+    assert _fwd(lib, B.Grid(8, 2, float("inf"))) == 4
+    assert _fwd(lib, ok, J=-1) == 1
+    assert _fwd(lib, ok, stride=2) == 1
+    assert _fwd(lib, ok, params=None) == 1
+    assert _fwd(lib, ok, q=None) == 1
+    assert _fwd(lib, ok, ws=None) == 3
+    assert _fwd(lib, ok, ws=(1 << 30) + 8) == 3          # misaligned
+    assert _fwd(lib, ok, ws_bytes=100) == 3              # too small
+    assert _fwd(lib, ok, J=0) == 0                       # empty batch: nothing to do
+    assert lib.efunc_launch_count() == 0
+    # backward, cell sort, Adam, fit
+    assert lib.efunc_backward(ctypes.byref(ok), 4096, 8192, 16, 3, 4096, None, None, 1 << 30, 1 << 40, None) == 1
+    assert lib.efunc_backward(ctypes.byref(ok), 4096, 8192, 0, 3, None, 4096, None, 1 << 30, 1 << 40, None) == 0
+    assert lib.efunc_cell_sort(ctypes.byref(ok), 4096, 16, 3, 8200, 4096, 1 << 30, 1 << 40, None) == 1  # misaligned out
+    ad = B.Adam(1e-3, 0.9, 0.999, 1e-8, 0.0, 0)
+    assert lib.efunc_adam_step(ctypes.byref(ad), 10, 16, 32, 48, 64, 0, None) == 1           # step 0
+    assert lib.efunc_adam_step(ctypes.byref(B.Adam(float("nan"), 0.9, 0.999, 1e-8, 0, 0)), 10, 16, 32, 48, 64, 1,
+                               None) == 4
+    assert lib.efunc_adam_step(ctypes.byref(B.Adam(1e-3, 1.0, 0.999, 1e-8, 0, 0)), 10, 16, 32, 48, 64, 1, None) == 1
+    assert lib.efunc_adam_step(ctypes.byref(ad), 0, None, None, None, None, 1, None) == 0
+    assert lib.efunc_fit(ctypes.byref(ok), ctypes.byref(ad), 2, 16, 32, 48, 64, 10, 1, 1, 0, None, 1 << 30,
+                         1 << 40, None) == 1                                                # bad loss kind
+    assert lib.efunc_fit(ctypes.byref(ok), ctypes.byref(ad), 0, 16, 32, 48, 64, 10, 0, 1, 0, None, 1 << 30,
+                         1 << 40, None) == 1                                                # no batches
+    assert lib.efunc_fit(ctypes.byref(ok), ctypes.byref(ad), 0, 16, 32, 48, 64, 10, 1, 0, 0, None, 1 << 30,
+                         1 << 40, None) == 0                                                # zero steps
+    assert lib.efunc_launch_count() == 0
+
+
+def test_profile_api_without_gpu(lib):
+    ms, cnt = ctypes.c_double(1.0), ctypes.c_int64(1)
+    lib.efunc_profile_reset()
+    assert lib.efunc_profile_read(b"fused_fit", ctypes.byref(ms), ctypes.byref(cnt)) == 0
+    assert ms.value == 0.0 and cnt.value == 0
+    assert lib.efunc_profile_read(b"nope", ctypes.byref(ms), ctypes.byref(cnt)) == -1

@@ -1,0 +1,331 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+seeded synthetic inputs.
+
+Tolerances (FP32 kernels vs FP64 oracle):
+  forward O, lse  |gpu - ref| <= 1e-6 + 1e-5 |ref|   per element
+  dO/dq, dL/dq    |gpu - ref| <= 1e-4 |ref| + 1e-5 max|ref|
+  dL/dparams      per slot type, |gpu - ref| <= 1e-4 max_slot_type |ref|
+                  (FP32 atomics: the summation order is not deterministic)
+  Adam            |gpu - ref| <= 1e-6 + 1e-5 |ref|
+The fused L1 loss takes sign(O - o); targets are placed at least 1e-3 away
+from the oracle's O so that FP32 and FP64 take the same sign decision.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2505_21319_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+SLOT_TYPES = {"Delta": [0, 1, 2], "b": [3], "b'": [4], "o": [5], "d": [6, 7, 8], "o'": [9], "d'": [10, 11, 12]}
+
+
+def lb32(R):
+    """log_beta0 as the library sees it (FP32)."""
+    return float(np.float32(oracle.default_log_beta0(R)))
+
+
+def mixed_queries(R, J, seed, shape=None):
+    """Sampled SDF points plus ties on cell faces / centres and out-of-domain points."""
+    g = synth.rng(seed)
+    shape = shape or synth.random_union(seed)
+    qo = synth.sample_batch(shape, J, seed)
+    n_tie = J // 8
+    idx = g.integers(0, R + 1, size=(n_tie, 3))
+    half = g.integers(0, 2, size=(n_tie, 3))
+    qo[:n_tie, :3] = (-1.0 + (idx + 0.5 * half) * (2.0 / R)).astype(np.float32)
+    n_out = J // 16
+    qo[n_tie:n_tie + n_out, :3] = g.uniform(-1.6, 1.6, size=(n_out, 3)).astype(np.float32)
+    return qo
+
+
+def assert_close(gpu, ref, rtol, atol, what):
+    gpu = np.asarray(gpu, dtype=np.float64)
+    err = np.abs(gpu - ref)
+    lim = atol + rtol * np.abs(ref)
+    bad = np.flatnonzero(~(err <= lim))
+    assert bad.size == 0, (f"{what}: {bad.size} of {err.size} outside tolerance; worst idx {bad[:5]} "
+                           f"gpu {gpu.ravel()[bad[:5]]} ref {ref.ravel()[bad[:5]]}")
+
+
+def assert_grad_close(gpu, ref, what, rtol=1e-4):
+    gpu = np.asarray(gpu, dtype=np.float64).reshape(-1, 13)
+    ref = ref.reshape(-1, 13)
+    for name, cols in SLOT_TYPES.items():
+        scale = np.abs(ref[:, cols]).max()
+        err = np.abs(gpu[:, cols] - ref[:, cols]).max()
+        assert err <= rtol * scale + 1e-30, f"{what} slot {name}: max err {err:.3e} vs scale {scale:.3e}"
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV)
+
+
+# ------------------------------------------------------------------ sort
+
+@pytest.mark.parametrize("R,J", [(1, 100), (4, 3001), (16, 70001), (32, 1 << 18)])
+def test_cell_sort_groups_queries_by_window(R, J):
+    qo = mixed_queries(R, J, seed=R)
+    qs, perm = api.efunc_cell_sort(to_dev(qo), R)
+    qs, perm = qs.cpu().numpy(), perm.cpu().numpy()
+    assert np.array_equal(np.sort(perm), np.arange(J))
+    np.testing.assert_array_equal(qs, qo[perm])
+    # window-base cell per sorted row, FP32 formula on the host
+    u = (qs[:, :3] + np.float32(1)) * np.float32(R * 0.5) - np.float32(0.5)
+    c = np.floor(np.clip(u, np.float32(-1), np.float32(R - 1))).astype(np.int64) + 1
+    P = (R + 1 + 3) // 4
+    brick = ((c[:, 0] >> 2) * P + (c[:, 1] >> 2)) * P + (c[:, 2] >> 2)
+    lx, ly, lz = c[:, 0] & 3, c[:, 1] & 3, c[:, 2] & 3
+    m = (lx & 1) << 2 | (ly & 1) << 1 | (lz & 1) | (lx & 2) << 4 | (ly & 2) << 3 | (lz & 2) << 2
+    key = brick * 64 + m
+    assert np.all(np.diff(key) >= 0), "rows are not grouped in brick-Morton order"
+
+
+def test_cell_sort_stride3():
+    R, J = 8, 5000
+    qo = mixed_queries(R, J, seed=3)
+    q3 = np.ascontiguousarray(qo[:, :3])
+    qs, perm = api.efunc_cell_sort(to_dev(q3), R)
+    qs, perm = qs.cpu().numpy(), perm.cpu().numpy()
+    np.testing.assert_array_equal(qs[:, :3], q3[perm])
+    assert np.all(qs[:, 3] == 0)
+
+
+# --------------------------------------------------------------- forward
+
+@pytest.mark.parametrize("R,J,pkind", [(1, 777, "random"), (2, 1000, "random"), (3, 4099, "random"),
+                                       (4, 5003, "random"), (8, 20011, "random"), (16, 65536, "init"),
+                                       (16, 40000, "random"), (32, 100003, "random")])
+def test_forward_matches_oracle(R, J, pkind):
+    qo = mixed_queries(R, J, seed=10 + R)
+    p = synth.random_params(R, seed=R) if pkind == "random" else synth.init_params(R, seed=0)
+    lb = lb32(R)
+    O, lse, dq = api.efunc_forward(to_dev(p), to_dev(qo), log_beta0=lb, want_lse=True, want_dq=True)
+    O_ref, lse_ref, dq_ref = oracle.forward(p.astype(np.float64), qo.astype(np.float64), R, 2, lb, want_dq=True)
+    assert_close(O.cpu().numpy(), O_ref, 1e-5, 1e-6, "O")
+    assert_close(lse.cpu().numpy(), lse_ref, 1e-5, 1e-6, "lse")
+    assert_close(dq.cpu().numpy(), dq_ref, 1e-4, 1e-5 * np.abs(dq_ref).max(), "dO/dq")
+
+
+def test_forward_is_deterministic_and_order_independent():
+    R, J = 16, 50000
+    qo = mixed_queries(R, J, seed=5)
+    p = to_dev(synth.random_params(R, seed=5))
+    a = api.efunc_forward(p, to_dev(qo)).cpu().numpy()
+    b = api.efunc_forward(p, to_dev(qo)).cpu().numpy()
+    perm = synth.rng(1).permutation(J)
+    c = api.efunc_forward(p, to_dev(qo[perm])).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(a[perm], c)
+
+
+def test_forward_underflow_fallback_and_far_queries():
+    """Large scales (b = +3: beta h^2 ~ 86) make every weight of many queries
+    underflow 2^-60 without the max shift, and so do queries outside the
+    domain; both take the shifted path and must still match.  Values are kept
+    small (spread 0.05): the FP32 rounding of an exponent s perturbs O by about
+    |s| 2^-23 |f - O|, and here |s| reaches ~60."""
+    R, J = 8, 4000
+    g = synth.rng(2)
+    p = synth.random_params(R, seed=2, b_scale=0.1, value_scale=0.05)
+    p[:, 3:5] += 3.0
+    q = g.uniform(-1, 1, (J, 3)).astype(np.float32)
+    far = g.uniform(-1.8, 1.8, (400, 3))
+    far[:, 0] = np.where(far[:, 0] >= 0, 1.0, -1.0) * g.uniform(1.05, 1.8, 400)
+    q[:400] = far.astype(np.float32)
+    lb = lb32(R)
+    O, lse = api.efunc_forward(to_dev(p), to_dev(q), log_beta0=lb, want_lse=True)
+    O_ref, lse_ref = oracle.forward(p.astype(np.float64), q.astype(np.float64), R, 2, lb)
+    assert (lse_ref < -60 * math.log(2)).sum() > J // 10   # the shifted path is exercised
+    assert_close(O.cpu().numpy(), O_ref, 1e-5, 1e-6, "O (underflow)")
+    assert_close(lse.cpu().numpy(), lse_ref, 1e-5, 1e-6, "lse (underflow)")
+
+
+def test_forward_edge_cases():
+    R = 4
+    p = to_dev(synth.random_params(R, seed=1))
+    # empty batch
+    O = api.efunc_forward(p, torch.empty((0, 3), device=DEV))
+    assert O.numel() == 0
+    # one query
+    q1 = np.array([[0.1, -0.2, 0.3]], np.float32)
+    O = api.efunc_forward(p, to_dev(q1)).cpu().numpy()
+    ref, _ = oracle.forward(synth.random_params(R, seed=1).astype(np.float64), q1.astype(np.float64), R, 2, lb32(R))
+    assert_close(O, ref, 1e-5, 1e-6, "single query")
+    # every query in one cell (one bin split into many work items)
+    qq = np.tile(q1, (3000, 1)) + synth.rng(0).uniform(0, 1e-3, (3000, 3)).astype(np.float32)
+    O = api.efunc_forward(p, to_dev(qq)).cpu().numpy()
+    ref, _ = oracle.forward(synth.random_params(R, seed=1).astype(np.float64), qq.astype(np.float64), R, 2, lb32(R))
+    assert_close(O, ref, 1e-5, 1e-6, "one dense cell")
+    # NaN query gives NaN, the rest is unaffected
+    qn = np.array([[np.nan, 0, 0], [0.1, 0.1, 0.1]], np.float32)
+    O = api.efunc_forward(p, to_dev(qn)).cpu().numpy()
+    assert np.isnan(O[0]) and np.isfinite(O[1])
+
+
+# -------------------------------------------------------------- backward
+
+@pytest.mark.parametrize("R,J", [(2, 1000), (3, 3001), (8, 20011), (16, 65536), (32, 60000)])
+def test_backward_matches_oracle(R, J):
+    qo = mixed_queries(R, J, seed=20 + R)
+    p = synth.random_params(R, seed=30 + R)
+    gO = synth.rng(40 + R).standard_normal(J) / J
+    lb = lb32(R)
+    grad, gq = api.efunc_backward(to_dev(p), to_dev(qo), to_dev(gO), want_gq=True, log_beta0=lb)
+    g_ref, gq_ref = oracle.backward(p.astype(np.float64), qo.astype(np.float64), gO.astype(np.float32).astype(np.float64),
+                                    R, 2, lb, want_gq=True)
+    assert_grad_close(grad.cpu().numpy(), g_ref, f"R={R}")
+    assert_close(gq.cpu().numpy(), gq_ref, 1e-4, 1e-5 * np.abs(gq_ref).max(), "dL/dq")
+
+
+def test_backward_accumulates_and_is_linear():
+    R, J = 8, 30000
+    qo = to_dev(mixed_queries(R, J, seed=3))
+    p = to_dev(synth.random_params(R, seed=3))
+    g1 = to_dev(synth.rng(1).standard_normal(J) / J)
+    g2 = to_dev(synth.rng(2).standard_normal(J) / J)
+    a = api.efunc_backward(p, qo, g1)
+    b = api.efunc_backward(p, qo, g2)
+    both = api.efunc_backward(p, qo, g1 + g2)
+    acc = api.efunc_backward(p, qo, g2, grad=a.clone())
+    scale = both.abs().max().item()
+    assert (a + b - both).abs().max().item() <= 1e-5 * scale
+    assert (acc - both).abs().max().item() <= 1e-5 * scale
+
+
+# ------------------------------------------------------------------ Adam
+
+@pytest.mark.parametrize("decoupled,wd", [(False, 0.0), (True, 0.01), (False, 0.01)])
+def test_adam_matches_oracle(decoupled, wd):
+    n = 13 * 5 ** 3 + 3   # odd length: vector body + scalar tail
+    g = synth.rng(7)
+    p0 = g.standard_normal(n).astype(np.float32)
+    p, m, v = to_dev(p0), torch.zeros(n, device=DEV), torch.zeros(n, device=DEV)
+    pr, mr, vr = p0.astype(np.float64), np.zeros(n), np.zeros(n)
+    for step in range(1, 6):
+        gr = g.standard_normal(n).astype(np.float32)
+        grad = to_dev(gr)
+        api.efunc_adam_step(p, grad, m, v, step, lr=1e-2, weight_decay=wd, decoupled=decoupled)
+        pr, mr, vr = oracle.adam(pr, gr.astype(np.float64), mr, vr, step, lr=1e-2, weight_decay=wd,
+                                 decoupled=decoupled)
+        assert grad.abs().max().item() == 0.0
+        assert_close(p.cpu().numpy(), pr, 1e-5, 1e-6, f"Adam p step {step}")
+        assert_close(m.cpu().numpy(), mr, 1e-5, 1e-7, f"Adam m step {step}")
+        assert_close(v.cpu().numpy(), vr, 1e-5, 1e-9, f"Adam v step {step}")
+
+
+# ------------------------------------------------------------- fused fit
+
+def _margin_targets(p, qo, R, seed):
+    """Targets at least 1e-3 from the oracle's O so the L1 sign is unambiguous."""
+    O_ref, _ = oracle.forward(p.astype(np.float64), qo.astype(np.float64), R, 2, lb32(R))
+    g = synth.rng(seed)
+    off = g.uniform(1e-3, 0.1, qo.shape[0]) * np.where(g.integers(0, 2, qo.shape[0]) == 0, -1.0, 1.0)
+    out = qo.copy()
+    out[:, 3] = (O_ref + off).astype(np.float32)
+    return out
+
+
+@pytest.mark.parametrize("loss", ["l1", "mse"])
+@pytest.mark.parametrize("R,J", [(4, 5000), (16, 65536)])
+def test_fused_fit_gradient_and_loss(R, J, loss):
+    """One fused step with lr = 0 exposes the gradient through Adam's first
+    moment (m = (1 - beta1) g); stats hold the loss and MAE of the step."""
+    p = synth.random_params(R, seed=R)
+    qo = _margin_targets(p, mixed_queries(R, J, seed=R), R, seed=1)
+    n = p.size
+    pd, m, v = to_dev(p), torch.zeros(n, device=DEV), torch.zeros(n, device=DEV)
+    stats = torch.zeros(2, device=DEV)
+    api.efunc_fit(pd, m, v, to_dev(qo), steps=1, loss=loss, stats=stats, lr=0.0, log_beta0=lb32(R))
+    O_ref, _ = oracle.forward(p.astype(np.float64), qo.astype(np.float64), R, 2, lb32(R))
+    gO, L, mae = oracle.loss_grad(O_ref, qo[:, 3].astype(np.float64), oracle.L1 if loss == "l1" else oracle.MSE)
+    g_ref = oracle.backward(p.astype(np.float64), qo.astype(np.float64), gO, R, 2, lb32(R))
+    assert_grad_close(m.cpu().numpy() / 0.1, g_ref, f"fused {loss}")
+    np.testing.assert_array_equal(pd.cpu().numpy(), p.reshape(-1))
+    s = stats.cpu().numpy()
+    assert abs(s[0] - L) <= 1e-5 * abs(L) + 1e-7
+    assert abs(s[1] - mae) <= 1e-5 * abs(mae) + 1e-7
+
+
+def test_fit_steps_match_oracle_trajectory():
+    """Five MSE steps with Adam against the oracle's fit loop: the parameters
+    agree wherever the gradient is far from zero (Adam's first step moves
+    every parameter by +-lr, so near-zero gradients may flip)."""
+    R, J = 4, 4000
+    shape = synth.sphere(0.5)
+    qo = synth.sample_batch(shape, J, seed=3)
+    p0 = synth.init_params(R, seed=0)
+    pd, m, v = to_dev(p0), torch.zeros(p0.size, device=DEV), torch.zeros(p0.size, device=DEV)
+    stats = torch.zeros(10, device=DEV)
+    api.efunc_fit(pd, m, v, to_dev(qo), steps=5, loss="mse", stats=stats, lr=1e-3, log_beta0=lb32(R))
+    pr, mr, vr = p0.astype(np.float64), np.zeros_like(p0, dtype=np.float64), np.zeros_like(p0, dtype=np.float64)
+    losses = []
+    for step in range(1, 6):
+        pr, mr, vr, L, mae = oracle.fit_step(pr, mr, vr, step, qo, R, loss=oracle.MSE, lr=1e-3, log_beta0=lb32(R))
+        losses.append(L)
+    s = stats.cpu().numpy().reshape(5, 2)
+    np.testing.assert_allclose(s[:, 0], losses, rtol=1e-4)
+    solid = np.abs(mr.reshape(-1)) > 1e-3 * np.abs(mr).max()
+    np.testing.assert_allclose(pd.cpu().numpy()[solid], pr.reshape(-1)[solid], rtol=1e-4, atol=1e-6)
+
+
+def test_fit_from_host_memory_matches_device():
+    R, J = 8, 20000
+    qo = synth.sample_batch(synth.random_union(1), 2 * J, seed=1)
+    p0 = synth.init_params(R, seed=1)
+    outs = []
+    for host in (False, True):
+        pd, m, v = to_dev(p0), torch.zeros(p0.size, device=DEV), torch.zeros(p0.size, device=DEV)
+        src = torch.from_numpy(qo).pin_memory() if host else to_dev(qo)
+        stats = torch.zeros(6, device="cpu" if host else DEV)
+        api.efunc_fit(pd, m, v, src, steps=3, J=J, n_batches=2, loss="l1", stats=stats, lr=1e-3)
+        torch.cuda.synchronize()
+        outs.append((pd.cpu().numpy(), stats.cpu().numpy()))
+    np.testing.assert_allclose(outs[0][1], outs[1][1], rtol=1e-5)
+    np.testing.assert_allclose(outs[0][0], outs[1][0], rtol=1e-4, atol=2e-6)
+
+
+# ------------------------------------------------ full-size configuration
+
+def test_full_size_32cubed_sampled_against_oracle():
+    """R = 32, J = 2^22 (the benchmark workload, same launch configuration):
+    every output is produced by one launch over all queries; a seeded sample
+    is compared with the oracle one by one.  For the backward, dL/dO is
+    non-zero only on a sample, so the full launch's gradient must equal the
+    oracle's gradient over that sample."""
+    R, J = 32, 1 << 22
+    shape = synth.random_union(0)
+    qo = synth.sample_batch(shape, J, seed=0)
+    p = synth.random_params(R, seed=0, delta_scale=0.3, b_scale=0.2, value_scale=0.3)
+    lb = lb32(R)
+    qd, pd = to_dev(qo), to_dev(p)
+    O = api.efunc_forward(pd, qd, log_beta0=lb).cpu().numpy()
+    sample = synth.rng(9).choice(J, 4096, replace=False)
+    O_ref, _ = oracle.forward(p.astype(np.float64), qo[sample].astype(np.float64), R, 2, lb)
+    assert_close(O[sample], O_ref, 1e-5, 1e-6, "O at 2^22")
+    gO = np.zeros(J, np.float32)
+    bs = synth.rng(10).choice(J, 2048, replace=False)
+    gO[bs] = synth.rng(11).standard_normal(2048).astype(np.float32) * 1e-3
+    grad = api.efunc_backward(pd, qd, to_dev(gO), log_beta0=lb).cpu().numpy()
+    g_ref = oracle.backward(p.astype(np.float64), qo[bs].astype(np.float64), gO[bs].astype(np.float64), R, 2, lb)
+    assert_grad_close(grad, g_ref, "grad at 2^22")
+
+
+def test_autograd_function_matches_oracle():
+    R, J = 8, 3000
+    p = synth.random_params(R, seed=12)
+    q = mixed_queries(R, J, seed=12)[:, :3].copy()
+    pd = to_dev(p).requires_grad_(True)
+    qd = to_dev(q).requires_grad_(True)
+    O = api.EfuncFn.apply(pd, qd, lb32(R))
+    w = synth.rng(0).standard_normal(J)
+    (O * to_dev(w)).sum().backward()
+    g_ref, gq_ref = oracle.backward(p.astype(np.float64), q.astype(np.float64), w.astype(np.float32).astype(np.float64),
+                                    R, 2, lb32(R), want_gq=True)
+    assert_grad_close(pd.grad.cpu().numpy(), g_ref, "autograd params")
+    assert_close(qd.grad.cpu().numpy(), gq_ref, 1e-4, 1e-5 * np.abs(gq_ref).max(), "autograd q")
