@@ -1,0 +1,389 @@
+"""Benchmark of the efunc hot path on GB300.
+
+One step = one fitting iteration on a fresh batch of J = 2^22 (x, y, z, SDF)
+rows at R = 32 (32^3 x 13 parameters): cell sort, fused forward + L1 loss
+gradient + backward (gradient scatter), Adam.  The batch pool (3 batches of
+64 MiB, 192 MiB > the 129 MB L2) is resident in HBM before the timed region;
+consecutive steps use different batches.
+
+Printed JSON line (rank 0):
+  value           query-points/s over all ranks (J * steps * ranks / time)
+  roofline        the fused forward/backward kernel against the FP32 pipe
+                  (ALU bound): algorithmic FP32 operations per launch /
+                  average launch time from CUDA events on its stream
+  e2e             the same metric through efunc_fit with the batches in
+                  pinned host memory: every step copies its batch to the
+                  device and reads the (loss, MAE) pair back
+  cpu_baseline    the FP64 oracle on the host cores, on a sample
+  clocks          nvidia-smi samples taken during the timed region
+
+``--impl reference`` times the FP64 oracle (the only reference available) on
+the same workload, a bounded sample per step.
+
+Multi-GPU: replicas only.  Under torchrun every rank fits its own batch pool
+on its own GPU; no collective touches the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+R_DEFAULT = 32
+J_DEFAULT = 1 << 22
+N_BATCHES = 3
+LR = 1e-3
+# Algorithmic FP32 operations per (query, centre) of the fused fit step:
+# forward 12 per key (difference 3, squared distance 3, scale 1, value 3,
+# two accumulations 2) for both keys of the centre, backward 18 for the grid
+# key and 21 for the offset key (recomputed difference, distance, exponent,
+# weight times dL/dO, value, residual, and the 5 / 8 gradient sums).
+OPS_PER_CENTRE = 2 * 12 + 18 + 21
+EX2_PER_CENTRE = 4
+FP32_LANES_PER_SM = 128
+WORKLOAD = "C2 plain fit: 32^3x13 FP32 grid, 2^22 queries/step (50% uniform, 50% surface+N(0,0.01^2)), " \
+           "union of 8 random primitives, L1 loss, Adam lr 1e-3"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def centres_per_query(q: np.ndarray, R: int) -> np.ndarray:
+    """Window size (number of centres) of every query, from the FP32 window rule."""
+    u = (q[:, :3] + np.float32(1)) * np.float32(R * 0.5) - np.float32(0.5)
+    c = np.floor(np.clip(u, np.float32(-1), np.float32(R - 1))).astype(np.int64)
+    n = np.minimum(c + 2, R - 1) - np.maximum(c - 1, 0) + 1
+    return n.prod(axis=1)
+
+
+class ClockSampler:
+    """nvidia-smi samples of one GPU while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = np.array([r[0] for r in rows])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower().startswith("active")})
+        load = sm[sm >= 0.5 * sm.max()] if sm.max() > 0 else sm
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": float(rows[0][1]), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------ CPU baseline
+
+def _oracle_chunk(args):
+    params, qo, R, lb = args
+    import oracle
+    O, _ = oracle.forward(params, qo, R, 2, lb)
+    gO, L, mae = oracle.loss_grad(O, qo[:, 3], oracle.L1)
+    gO *= len(O)   # the chunk's share of dL/dO; rescaled by the caller
+    grad = oracle.backward(params, qo, gO, R, 2, lb)
+    return grad, float(np.abs(O - qo[:, 3]).sum())
+
+
+def oracle_step(pool, params, qo, R, lb, cores):
+    """Oracle fit step on qo: forward, L1 gradient, backward (split over the
+    pool's processes), Adam on the full grid."""
+    import oracle
+    chunks = np.array_split(qo.astype(np.float64), cores)
+    res = pool.map(_oracle_chunk, [(params, c, R, lb) for c in chunks if len(c)])
+    grad = sum(r[0] for r in res) / len(qo)
+    return grad
+
+
+def cpu_baseline(qo: np.ndarray, R: int, lb: float, seconds: float = 12.0):
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    params = __import__("paper_2505_21319_gb300.synth", fromlist=["synth"]).init_params(R, 0).astype(np.float64)
+    m = np.zeros_like(params)
+    v = np.zeros_like(params)
+    with ctx.Pool(cores) as pool:
+        n = 512 * cores
+        t0 = time.perf_counter()
+        oracle_step(pool, params, qo[:n], R, lb, cores)
+        dt = time.perf_counter() - t0
+        n = int(min(len(qo), max(n, n * seconds / max(dt, 1e-3))))
+        t0 = time.perf_counter()
+        grad = oracle_step(pool, params, qo[:n], R, lb, cores)
+        oracle.adam(params, grad, m, v, 1, lr=LR)
+        dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "query-pts/s", "cores": cores, "kind": "oracle",
+            "sample": f"one fit step (forward, L1 gradient, backward, Adam) on the first {n} queries of the "
+                      f"2^22 batch at 32^3, FP64, {cores} spawn processes"}
+
+
+# ------------------------------------------------------------------ main
+
+def make_pool(R, J, n_batches, rank):
+    from paper_2505_21319_gb300 import synth
+    shape = synth.random_union(0)
+    return np.concatenate([synth.sample_batch(shape, J, seed=1000 * rank + b) for b in range(n_batches)])
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2505_21319_gb300 import synth
+    oracle.build()
+    R = R_DEFAULT
+    lb = float(np.float32(oracle.default_log_beta0(R)))
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    params = synth.init_params(R, 0).astype(np.float64)
+    m = np.zeros_like(params)
+    v = np.zeros_like(params)
+    qo = synth.sample_batch(synth.random_union(0), 1 << 18, seed=0)
+    budget = 150.0   # seconds for warm-up + timed steps
+    with ctx.Pool(cores) as pool:
+        n = 256 * cores
+        t0 = time.perf_counter()
+        oracle_step(pool, params, qo[:n], R, lb, cores)
+        per_q = (time.perf_counter() - t0) / n
+        S = int(max(64, min(len(qo), budget / max(1, args.steps + args.warmup) / per_q)))
+        step = 0
+        for _ in range(args.warmup):
+            step += 1
+            g = oracle_step(pool, params, qo[(step * S) % (len(qo) - S):][:S], R, lb, cores)
+            params, m, v = oracle.adam(params, g, m, v, step, lr=LR)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step += 1
+            g = oracle_step(pool, params, qo[(step * S) % (len(qo) - S):][:S], R, lb, cores)
+            params, m, v = oracle.adam(params, g, m, v, step, lr=LR)
+        dt = time.perf_counter() - t0
+    value = S * args.steps / dt
+    sample = f"{S} queries of the 32^3 workload per step (bounded sample), FP64 oracle over {cores} processes"
+    print(json.dumps({
+        "impl": "reference", "metric": "fwd+bwd query-pts/s @32^3x13", "value": value, "unit": "query-pts/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (oracle on a bounded sample per step)", "R": R, "J_per_step": S},
+        "cpu_baseline": {"value": value, "unit": "query-pts/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "query-pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2505_21319_gb300 import api
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    R, J = R_DEFAULT, J_DEFAULT
+    lb = api.default_log_beta0(R)
+    t0 = time.perf_counter()
+    pool_np = make_pool(R, J, N_BATCHES, rank)
+    log(f"[bench] rank {rank}: batch pool {pool_np.shape} generated in {time.perf_counter() - t0:.1f}s")
+    cpu_line = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu_line = cpu_baseline(pool_np[:J], R, float(np.float32(lb)))
+        log(f"[bench] cpu baseline {cpu_line['value']:.3e} q/s")
+
+    from paper_2505_21319_gb300 import synth
+    n = R ** 3 * 13
+    pool = torch.from_numpy(pool_np).to(dev)
+    params = torch.from_numpy(synth.init_params(R, seed=rank)).to(dev)
+    m = torch.zeros(n, device=dev)
+    v = torch.zeros(n, device=dev)
+    ws_buf = api.Workspace(dev)
+    stats_w = torch.zeros(2 * args.warmup, device=dev)
+    stats = torch.zeros(2 * args.steps, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    api.efunc_fit(params, m, v, pool, steps=args.warmup, J=J, n_batches=N_BATCHES, stats=stats_w, lr=LR,
+                  ws=ws_buf)
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: K fit steps, device-resident inputs
+    api.profile_reset()
+    api.profile(True)
+    launches0 = api.launch_count()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        api.efunc_fit(params, m, v, pool, steps=args.steps, J=J, n_batches=N_BATCHES, step0=args.warmup,
+                      stats=stats, lr=LR, ws=ws_buf)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            dist.barrier()
+    launches = api.launch_count() - launches0
+    api.profile(False)
+    ms = start.elapsed_time(end) / args.steps
+    fused_ms, fused_n = api.profile_read("fused_fit")
+    kernel_ms = {k: api.profile_read(k)[0] / max(1, api.profile_read(k)[1])
+                 for k in ("bin", "scan_reduce", "scan_top", "scan_emit", "scatter", "fused_fit", "adam")}
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = J * ws / (ms * 1e-3)
+    st = stats.view(-1, 2).cpu().numpy()
+
+    # ---- roofline of the fused kernel (ALU bound)
+    ops_per_launch = 0.0
+    for b in range(N_BATCHES):
+        nc = centres_per_query(pool_np[b * J:(b + 1) * J], R).astype(np.float64)
+        ops_per_launch += nc.sum() * OPS_PER_CENTRE / N_BATCHES
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = 2070.0
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        sm_max = float(peaks.get("sm_max_mhz", sm_max))
+    except (OSError, ValueError):
+        pass
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12   # T FP32 ops/s
+    avg_fused = fused_ms / max(1, fused_n)
+    achieved = ops_per_launch / (avg_fused * 1e-3) / 1e12
+    clocks = clk.summary()
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        host_pool = torch.from_numpy(pool_np).pin_memory()
+        host_stats = torch.zeros(2, dtype=torch.float32).pin_memory()
+        for s in range(3):
+            api.efunc_fit(params, m, v, host_pool, steps=1, J=J, n_batches=N_BATCHES, step0=10 ** 6 + s,
+                          stats=host_stats, lr=LR, ws=ws_buf)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for s in range(args.e2e_steps):
+            # one step per call: batch s mod 3 copied from pinned memory, (loss, MAE) read back
+            off = (s % N_BATCHES) * J
+            api.efunc_fit(params, m, v, host_pool[off:off + J], steps=1, J=J, n_batches=1,
+                          step0=2 * 10 ** 6 + s, stats=host_stats, lr=LR, ws=ws_buf)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": J * ws * args.e2e_steps / dt, "unit": "query-pts/s", "h2d_bytes_per_step": J * 16,
+               "d2h_bytes_per_step": 8, "steps": args.e2e_steps}
+
+    if rank == 0:
+        line = {
+            "metric": "fwd+bwd query-pts/s @32^3x13",
+            "value": value,
+            "unit": "query-pts/s",
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "R": R, "J_per_step": J, "batches": N_BATCHES,
+                       "l2": "inputs larger than L2: 3 batches x 64 MiB cycle, 192 MiB > 129 MB",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": {"bound": "alu", "kernel": "fused_fit", "achieved": achieved, "peak": peak,
+                         "unit": "T FP32 op/s", "frac": achieved / peak, "traffic": None,
+                         "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_fused,
+                         "peak_from": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz"},
+            "kernel_ms": kernel_ms,
+            "e2e": e2e,
+            "cpu_baseline": cpu_line,
+            "clocks": clocks,
+            "gpu_launches": launches,
+            "fit": {"steps_total": args.warmup + args.steps, "loss_first_timed": float(st[0, 0]),
+                    "mae_first_timed": float(st[0, 1]), "mae_last": float(st[-1, 1])},
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

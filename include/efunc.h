@@ -75,9 +75,11 @@ typedef enum { EFUNC_LOSS_L1 = 0, EFUNC_LOSS_MSE = 1 } efunc_loss;
 
 /* Adam (decoupled = 0: weight_decay added to the gradient) or AdamW
  * (decoupled = 1: p *= 1 - lr*weight_decay), torch.optim semantics.
- * Sec. 3.4 fits with Adam; Sec. 4.2 uses AdamW with lr 6e-4. */
+ * Sec. 3.4 fits with Adam; Sec. 4.2 uses AdamW with lr 6e-4.  The
+ * hyper-parameters are double so that 1 - beta2 and the bias corrections are
+ * formed before rounding to the FP32 arithmetic of the kernel. */
 typedef struct {
-    float lr, beta1, beta2, eps, weight_decay;
+    double lr, beta1, beta2, eps, weight_decay;
     int32_t decoupled;
 } efunc_adam;
 
@@ -170,8 +172,8 @@ void efunc_profile_enable(int32_t enable);
 
 /* Waits for the recorded events and folds them into per-kernel totals.
  * Writes the total milliseconds and launch count of kernel `name` (one of
- * "bin", "scan_reduce", "scan_top", "scan_emit", "scatter", "forward",
- * "fused_backward", "fused_fit", "adam").  Returns 0 on success, -1 for an
+ * "bin", "scan_reduce", "scan_top", "scan_emit", "scatter", "pack_keys",
+ * "forward", "fused_backward", "fused_fit", "adam").  Returns 0 on success, -1 for an
  * unknown name or a CUDA error. */
 int32_t efunc_profile_read(const char *name, double *total_ms, int64_t *launches);
 

@@ -54,7 +54,7 @@ def _load():
             i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
             lib.ora_window_base.argtypes = [ctypes.c_float, i32]
             lib.ora_window_base.restype = i32
-            lib.ora_forward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
+            lib.ora_forward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp, dp, dp]
             lib.ora_backward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
             lib.ora_forward_global.argtypes = [i32, f64, dp, dp, i64, i32, dp, dp]
             lib.ora_loss_grad.argtypes = [i32, dp, dp, i64, dp, dp, dp]
@@ -97,20 +97,36 @@ def _check(params, q, R):
     return params, q
 
 
-def forward(params, q, R: int, W: int = 2, log_beta0: float | None = None, want_dq: bool = False):
-    """O(q_j), lse_j (and dO/dq_j) for the windowed O^{+Delta} model.
+def forward(params, q, R: int, W: int = 2, log_beta0: float | None = None, want_dq: bool = False,
+            want_kappa: bool = False, want_dq_sens: bool = False):
+    """O(q_j), lse_j (and dO/dq_j, and kappa_j) for the windowed O^{+Delta} model.
 
     Sec. 3.3 Eq. func-offset evaluated by Algorithm 1 (Sec. 3.5) with the
     log-sum-exp shift; dO/dq from Eq. func-normal.  ``q`` is (J, >=3); only the
-    first three columns are read.  W >= R is the paper's global support."""
+    first three columns are read.  W >= R is the paper's global support.
+    kappa_j = sum softmax (|exponent| + 1) |f - O| is the condition number of
+    O_j with respect to relative rounding of the exponents and the weights (a
+    diagnostic used to derive floating-point tolerances).  dq_sens_j =
+    2 ||sum softmax beta (q - key)|| is the factor by which an error in O_j
+    enters dO/dq_j."""
     lb = default_log_beta0(R) if log_beta0 is None else float(log_beta0)
     params, q = _check(params, q, R)
     J = q.shape[0]
     O = np.zeros(J)
     lse = np.zeros(J)
     dq = np.zeros((J, 3)) if want_dq else None
-    _load().ora_forward(R, W, lb, _ptr(params), _ptr(q), J, q.shape[1], _ptr(O), _ptr(lse), _ptr(dq))
-    return (O, lse, dq) if want_dq else (O, lse)
+    kappa = np.zeros(J) if want_kappa else None
+    sens = np.zeros(J) if want_dq_sens else None
+    _load().ora_forward(R, W, lb, _ptr(params), _ptr(q), J, q.shape[1], _ptr(O), _ptr(lse), _ptr(dq), _ptr(kappa),
+                        _ptr(sens))
+    out = [O, lse]
+    if want_dq:
+        out.append(dq)
+    if want_kappa:
+        out.append(kappa)
+    if want_dq_sens:
+        out.append(sens)
+    return tuple(out)
 
 
 def backward(params, q, gO, R: int, W: int = 2, log_beta0: float | None = None, want_gq: bool = False):

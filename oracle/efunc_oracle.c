@@ -126,10 +126,14 @@ static void eval_key(const key_t_ *k, const double *q, double r[3], double *d2, 
 /* --------------------------------------------------------------- forward */
 
 /* Algorithm 1 for one query over the windowed key set.  Returns O, the
- * log-normaliser lse = log(sum exp(expo)) and, if dq != NULL, dO/dq from
- * Eq. func-normal. */
+ * log-normaliser lse = log(sum exp(expo)), if dq != NULL dO/dq from
+ * Eq. func-normal, and if kappa != NULL the condition number of O with respect
+ * to relative perturbations of the exponents and of the individual weights,
+ *     kappa = sum_keys softmax * (|expo| + 1) * |f - O|
+ * (dO/dexpo_i = softmax_i (f_i - O)): an evaluation that perturbs every
+ * exponent and every weight by a relative error u is off by about u * kappa. */
 static void forward_one(const double *params, int R, int W, double log_beta0, const double *q,
-                        double *O_out, double *lse_out, double *dq)
+                        double *O_out, double *lse_out, double *dq, double *kappa, double *dq_sens)
 {
     int lo[3], hi[3];
     window_range(q, R, W, lo, hi);
@@ -162,6 +166,35 @@ static void forward_one(const double *params, int R, int W, double log_beta0, co
     *O_out = O;
     if (lse_out) *lse_out = M + log(e);
 
+    if (kappa) {
+        double k_sum = 0.0;
+        for (int a = lo[0]; a <= hi[0]; ++a)
+            for (int b = lo[1]; b <= hi[1]; ++b)
+                for (int c = lo[2]; c <= hi[2]; ++c)
+                    for (int s = 0; s < 2; ++s) {
+                        key_t_ k = make_key(params, R, log_beta0, a, b, c, s);
+                        eval_key(&k, q, r, &d2, &expo, &f);
+                        k_sum += exp(expo - M) / e * (fabs(expo) + 1.0) * fabs(f - O);
+                    }
+        *kappa = k_sum;
+    }
+
+    if (dq_sens) {
+        /* dO/dq contains 2 O sum softmax beta (q - p): an error in O moves it by
+         * that error times 2 ||sum softmax beta (q - p)||. */
+        double v[3] = {0.0, 0.0, 0.0};
+        for (int a = lo[0]; a <= hi[0]; ++a)
+            for (int b = lo[1]; b <= hi[1]; ++b)
+                for (int c = lo[2]; c <= hi[2]; ++c)
+                    for (int s = 0; s < 2; ++s) {
+                        key_t_ k = make_key(params, R, log_beta0, a, b, c, s);
+                        eval_key(&k, q, r, &d2, &expo, &f);
+                        double w = exp(expo - M) / e;
+                        for (int x = 0; x < 3; ++x) v[x] += w * k.beta * r[x];
+                    }
+        *dq_sens = 2.0 * sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    }
+
     if (dq) {
         /* Eq. func-normal: dO/dq = sum softmax * (df/dq + 2 beta (q - p)(O - f)),
          * df/dq = d for the first-order value. */
@@ -181,13 +214,14 @@ static void forward_one(const double *params, int R, int W, double log_beta0, co
 }
 
 /* Forward over J queries.  q: J rows of q_stride doubles (x, y, z first).
- * O, lse: J doubles each (lse may be NULL).  dq: J*3 doubles or NULL. */
+ * O, lse: J doubles each (lse may be NULL).  dq: J*3 doubles or NULL.
+ * kappa, dq_sens: J doubles or NULL (diagnostics, see forward_one). */
 void ora_forward(int R, int W, double log_beta0, const double *params, const double *q, int64_t J,
-                 int q_stride, double *O, double *lse, double *dq)
+                 int q_stride, double *O, double *lse, double *dq, double *kappa, double *dq_sens)
 {
     for (int64_t j = 0; j < J; ++j)
         forward_one(params, R, W, log_beta0, q + j * q_stride, &O[j], lse ? &lse[j] : NULL,
-                    dq ? dq + 3 * j : NULL);
+                    dq ? dq + 3 * j : NULL, kappa ? &kappa[j] : NULL, dq_sens ? &dq_sens[j] : NULL);
 }
 
 /* -------------------------------------------------------------- backward */
@@ -211,7 +245,7 @@ void ora_backward(int R, int W, double log_beta0, const double *params, const do
     for (int64_t j = 0; j < J; ++j) {
         const double *qj = q + j * q_stride;
         double O, lse, dq[3];
-        forward_one(params, R, W, log_beta0, qj, &O, &lse, gq ? dq : NULL);
+        forward_one(params, R, W, log_beta0, qj, &O, &lse, gq ? dq : NULL, NULL, NULL);
         if (gq) {
             gq[3 * j + 0] = gO[j] * dq[0];
             gq[3 * j + 1] = gO[j] * dq[1];

@@ -26,8 +26,8 @@ class Grid(ctypes.Structure):
 
 
 class Adam(ctypes.Structure):
-    _fields_ = [("lr", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float),
-                ("weight_decay", c_float), ("decoupled", c_int32)]
+    _fields_ = [("lr", c_double), ("beta1", c_double), ("beta2", c_double), ("eps", c_double),
+                ("weight_decay", c_double), ("decoupled", c_int32)]
 
 
 # name -> (restype, argtypes); the order follows include/efunc.h

@@ -14,10 +14,10 @@ namespace {
 __device__ __forceinline__ void adam_one(const AdamArgs &a, float &p, float &g, float &m, float &v)
 {
     float gi = g;
-    if (a.decoupled) p *= 1.0f - a.lr * a.wd;
+    if (a.decoupled) p *= a.decay;
     else gi = fmaf(a.wd, p, gi);
-    m = fmaf(a.beta1, m, (1.0f - a.beta1) * gi);
-    v = fmaf(a.beta2, v, (1.0f - a.beta2) * gi * gi);
+    m = fmaf(a.beta1, m, a.one_minus_beta1 * gi);
+    v = fmaf(a.beta2, v, a.one_minus_beta2 * gi * gi);
     const float denom = sqrtf(v) * a.inv_sqrt_bc2 + a.eps;
     p -= a.step_size * m / denom;
     g = 0.0f;

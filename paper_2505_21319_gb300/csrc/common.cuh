@@ -35,7 +35,7 @@ struct Layout {
     int64_t nbins;      // P^3 * 64
     int64_t nscan_blocks;
     int64_t max_items;
-    size_t ctrl, hist, blocksum, rank, sorted, perm, items, grad, stage, total;
+    size_t ctrl, hist, blocksum, rank, sorted, perm, items, keys, grad, stage, total;
 };
 
 Layout make_layout(int R, int64_t J);
@@ -57,11 +57,27 @@ struct SortArgs {
     Ctrl *ctrl;
 };
 
+// Key records of one centre, 4 float4 (64 bytes), built once per call by the
+// pack kernel from the 13 parameters:
+//   [0] (0, 0, 0, -beta log2(e))        [1] (o, d)
+//   [2] (Delta, -beta' log2(e))         [3] (o', d')
+// The scales are formed in FP64 and rounded once.  Key positions are not
+// stored: the fused kernel forms them in window-local coordinates,
+// (i - c) h for the grid key and (i - c) h + Delta for the offset key, so that
+// no absolute position near +-1 is ever rounded.
+constexpr int kKeyRecords = 4;
+
+struct PackArgs {
+    const float *params;
+    float4 *keys;
+    int R;
+    double log_beta0;
+};
+
 // Fused-kernel arguments.
 struct FusedArgs {
-    const float *params;
+    const float4 *keys;  // packed key records, R^3 * 4
     int R;
-    float nbl0;          // -exp(log_beta0) * log2(e), folded on the host in FP64
     const float4 *sorted;
     const int *perm;
     const Item *items;
@@ -82,7 +98,9 @@ struct FusedArgs {
 struct AdamArgs {
     float *p, *g, *m, *v;
     int64_t n;
-    float lr, beta1, beta2, eps, wd;
+    // FP32 constants formed in FP64 on the host
+    float beta1, one_minus_beta1, beta2, one_minus_beta2, eps, wd;
+    float decay;            // 1 - lr*wd (AdamW)
     int decoupled;
     float step_size;        // lr / (1 - beta1^t)
     float inv_sqrt_bc2;     // 1 / sqrt(1 - beta2^t)
@@ -93,8 +111,8 @@ struct AdamArgs {
 };
 
 // Kernel identifiers for the profiler.
-enum KernelId { K_BIN = 0, K_SCAN_REDUCE, K_SCAN_TOP, K_SCAN_EMIT, K_SCATTER, K_FORWARD, K_FUSED_BWD, K_FUSED_FIT,
-                K_ADAM, K_COUNT };
+enum KernelId { K_BIN = 0, K_SCAN_REDUCE, K_SCAN_TOP, K_SCAN_EMIT, K_SCATTER, K_PACK_KEYS, K_FORWARD, K_FUSED_BWD,
+                K_FUSED_FIT, K_ADAM, K_COUNT };
 
 // Launch bookkeeping (launch counter and optional CUDA-event profiling).
 void launch_begin(int kid, cudaStream_t s);
@@ -103,6 +121,7 @@ void launch_end(int kid, cudaStream_t s);
 // Launchers (defined in sort.cu, fused.cu, adam.cu).  They return the CUDA
 // error of the launch.
 cudaError_t launch_sort(const SortArgs &a, cudaStream_t s);
+cudaError_t launch_pack_keys(const PackArgs &a, cudaStream_t s);
 cudaError_t launch_forward(const FusedArgs &a, bool with_dq, int grid, cudaStream_t s);
 cudaError_t launch_fused_backward(const FusedArgs &a, bool with_gq, int grid, cudaStream_t s);
 cudaError_t launch_fused_fit(const FusedArgs &a, int grid, cudaStream_t s);

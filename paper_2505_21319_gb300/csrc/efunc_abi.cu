@@ -28,8 +28,8 @@ double g_ms[K_COUNT];
 int64_t g_count[K_COUNT];
 int64_t g_launches = 0;
 
-const char *const kKernelNames[K_COUNT] = {"bin",     "scan_reduce",    "scan_top",  "scan_emit", "scatter",
-                                           "forward", "fused_backward", "fused_fit", "adam"};
+const char *const kKernelNames[K_COUNT] = {"bin",       "scan_reduce", "scan_top",       "scan_emit", "scatter",
+                                           "pack_keys", "forward",     "fused_backward", "fused_fit", "adam"};
 
 cudaEvent_t take_event()
 {
@@ -103,6 +103,7 @@ Layout make_layout(int R, int64_t J)
     L.sorted = off;    off = align_up(off + (size_t)J * 16, A);
     L.perm = off;      off = align_up(off + (size_t)J * 4, A);
     L.items = off;     off = align_up(off + (size_t)L.max_items * 16, A);
+    L.keys = off;      off = align_up(off + (size_t)R * R * R * kKeyRecords * 16, A);
     L.grad = off;      off = align_up(off + (size_t)R * R * R * kSlots * 4, A);
     L.stage = off;     off = align_up(off + (size_t)J * 16, A);
     L.total = off;
@@ -134,8 +135,6 @@ efunc_status check_workspace(const efunc_grid *g, int64_t J, const void *ws, siz
     return EFUNC_OK;
 }
 
-float nbl0_of(const efunc_grid *g) { return (float)(-exp((double)g->log_beta0) * 1.4426950408889634); }
-
 struct Views {
     Layout L;
     char *base;
@@ -146,6 +145,7 @@ struct Views {
     float4 *sorted() const { return reinterpret_cast<float4 *>(base + L.sorted); }
     int *perm() const { return reinterpret_cast<int *>(base + L.perm); }
     Item *items() const { return reinterpret_cast<Item *>(base + L.items); }
+    float4 *keys() const { return reinterpret_cast<float4 *>(base + L.keys); }
     float *grad() const { return reinterpret_cast<float *>(base + L.grad); }
     float4 *stage() const { return reinterpret_cast<float4 *>(base + L.stage); }
 };
@@ -176,12 +176,22 @@ cudaError_t sort_into(const Views &v, int R, const float *q, int64_t J, int q_st
     return launch_sort(a, s);
 }
 
-FusedArgs fused_args(const Views &v, const efunc_grid *g, const float *params)
+// Packs the parameters into key records, then fills the fused-kernel arguments.
+cudaError_t pack_keys(const Views &v, const efunc_grid *g, const float *params, cudaStream_t s)
+{
+    PackArgs p{};
+    p.params = params;
+    p.keys = v.keys();
+    p.R = g->R;
+    p.log_beta0 = (double)g->log_beta0;
+    return launch_pack_keys(p, s);
+}
+
+FusedArgs fused_args(const Views &v, const efunc_grid *g)
 {
     FusedArgs f{};
-    f.params = params;
+    f.keys = v.keys();
     f.R = g->R;
-    f.nbl0 = nbl0_of(g);
     f.sorted = v.sorted();
     f.perm = v.perm();
     f.items = v.items();
@@ -207,7 +217,7 @@ efunc_status check_adam(const efunc_adam *a)
     if (!isfinite(a->lr) || !isfinite(a->beta1) || !isfinite(a->beta2) || !isfinite(a->eps) ||
         !isfinite(a->weight_decay))
         return EFUNC_ERR_NONFINITE;
-    if (a->beta1 < 0.f || a->beta1 >= 1.f || a->beta2 < 0.f || a->beta2 >= 1.f || a->eps < 0.f ||
+    if (a->beta1 < 0.0 || a->beta1 >= 1.0 || a->beta2 < 0.0 || a->beta2 >= 1.0 || a->eps < 0.0 ||
         (a->decoupled != 0 && a->decoupled != 1))
         return EFUNC_ERR_ARG;
     return EFUNC_OK;
@@ -218,15 +228,17 @@ AdamArgs adam_args(const efunc_adam *ad, int64_t n, float *p, float *g, float *m
     AdamArgs a{};
     a.p = p; a.g = g; a.m = m; a.v = v;
     a.n = n;
-    a.lr = ad->lr;
-    a.beta1 = ad->beta1;
-    a.beta2 = ad->beta2;
-    a.eps = ad->eps;
-    a.wd = ad->weight_decay;
+    a.beta1 = (float)ad->beta1;
+    a.one_minus_beta1 = (float)(1.0 - ad->beta1);
+    a.beta2 = (float)ad->beta2;
+    a.one_minus_beta2 = (float)(1.0 - ad->beta2);
+    a.eps = (float)ad->eps;
+    a.wd = (float)ad->weight_decay;
+    a.decay = (float)(1.0 - ad->lr * ad->weight_decay);
     a.decoupled = ad->decoupled;
-    const double bc1 = 1.0 - pow((double)ad->beta1, (double)step);
-    const double bc2 = 1.0 - pow((double)ad->beta2, (double)step);
-    a.step_size = (float)((double)ad->lr / bc1);
+    const double bc1 = 1.0 - pow(ad->beta1, (double)step);
+    const double bc2 = 1.0 - pow(ad->beta2, (double)step);
+    a.step_size = (float)(ad->lr / bc1);
     a.inv_sqrt_bc2 = (float)(1.0 / sqrt(bc2));
     return a;
 }
@@ -293,8 +305,9 @@ efunc_status efunc_forward(const efunc_grid *grid, const float *params, const fl
     cudaStream_t s = (cudaStream_t)stream;
     Views v{make_layout(grid->R, J), static_cast<char *>(workspace)};
     cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
+    if (e == cudaSuccess) e = pack_keys(v, grid, params, s);
     if (e != cudaSuccess) return EFUNC_ERR_CUDA;
-    FusedArgs f = fused_args(v, grid, params);
+    FusedArgs f = fused_args(v, grid);
     f.O = O;
     f.lse = lse;
     f.dq = dOdq;
@@ -314,8 +327,9 @@ efunc_status efunc_backward(const efunc_grid *grid, const float *params, const f
     cudaStream_t s = (cudaStream_t)stream;
     Views v{make_layout(grid->R, J), static_cast<char *>(workspace)};
     cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
+    if (e == cudaSuccess) e = pack_keys(v, grid, params, s);
     if (e != cudaSuccess) return EFUNC_ERR_CUDA;
-    FusedArgs f = fused_args(v, grid, params);
+    FusedArgs f = fused_args(v, grid);
     f.gO = gO;
     f.grad = grad;
     f.gq = gq;
@@ -368,8 +382,9 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
             qdev = reinterpret_cast<const float *>(vw.stage());
         }
         e = sort_into(vw, grid->R, qdev, J, 4, vw.sorted(), vw.perm(), s);
+        if (e == cudaSuccess) e = pack_keys(vw, grid, params, s);
         if (e != cudaSuccess) return EFUNC_ERR_CUDA;
-        FusedArgs f = fused_args(vw, grid, params);
+        FusedArgs f = fused_args(vw, grid);
         f.grad = grad;
         f.loss = loss;
         f.inv_J = (float)(1.0 / (double)J);

@@ -6,11 +6,15 @@
 // i.e. the same 128 keys (64 grid keys k_i and 64 offset keys k_i + Delta_i,
 // one softmax over their union, Eq. func-offset).  A persistent CTA of 128
 // threads takes items from a device counter and, per item:
-//   1. stages the window's keys in shared memory (params are L2-resident):
-//      key position, -beta*log2(e), value constant and linear term;
+//   1. stages the window's packed key records in shared memory (the records
+//      are L2-resident: 64 bytes per centre), with key positions in
+//      window-local coordinates (origin at the centre of index c, the window
+//      base); queries are shifted into the same frame when loaded;
 //   2. forward, thread per query (2 or 4 threads per query for sparse cells):
 //      e = sum 2^{s}, m = sum 2^{s} f with s = -beta log2(e) ||q - key||^2,
-//      O = m / e, lse2 = log2 e (Algorithm 1 in base 2).  If e underflows
+//      O = m / e, lse2 = log2 e (Algorithm 1 in base 2).  The keys are summed
+//      in four interleaved classes combined in a fixed tree, so a query's
+//      result does not depend on how many threads share it.  If e underflows
 //      (every key far away in units of its scale) the query is recomputed
 //      with the maximum exponent subtracted;
 //   3. backward, thread per key (Algorithm 2 turned around: each key loops
@@ -29,8 +33,32 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kLn2 = 0.69314718055994531f;
+constexpr int kClasses = 4;   // interleaved summation classes of the forward
 
 enum Mode { FORWARD = 0, BACKWARD = 1, FIT = 2 };
+
+// --------------------------------------------------------------- pack
+
+__global__ void __launch_bounds__(256) pack_keys_kernel(PackArgs a)
+{
+    const int I = a.R * a.R * a.R;
+    const double log2e = 1.4426950408889634;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I; i += gridDim.x * blockDim.x) {
+        const float *th = a.params + (size_t)i * kSlots;
+        float v[kSlots];
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) v[s] = __ldg(th + s);
+        const float nbl_g = (float)(-exp(a.log_beta0 + (double)v[3]) * log2e);
+        const float nbl_o = (float)(-exp(a.log_beta0 + (double)v[4]) * log2e);
+        float4 *k = a.keys + (size_t)i * kKeyRecords;
+        k[0] = make_float4(0.f, 0.f, 0.f, nbl_g);
+        k[1] = make_float4(v[5], v[6], v[7], v[8]);
+        k[2] = make_float4(v[0], v[1], v[2], nbl_o);
+        k[3] = make_float4(v[9], v[10], v[11], v[12]);
+    }
+}
+
+// ------------------------------------------------------------ forward
 
 // One key's contribution to (e, m) for a query at (x, y, z), shifted by M2.
 __device__ __forceinline__ void fwd_key(const float4 A, const float4 B, float x, float y, float z, float M2,
@@ -50,7 +78,116 @@ __device__ __forceinline__ float key_exponent(const float4 A, float x, float y, 
     return A.w * fmaf(rx, rx, fmaf(ry, ry, rz * rz));
 }
 
-// Thread-per-key backward loop over the item's queries.
+// Combines the per-class partial sums of a query held by KQ lanes in the
+// fixed order ((c0 + c1) + (c2 + c3)).  Lane `part` holds classes
+// part + KQ*i, i < 4/KQ.
+template <int KQ>
+__device__ __forceinline__ float combine_classes(const float *v)
+{
+    if (KQ == 1) return (v[0] + v[1]) + (v[2] + v[3]);
+    if (KQ == 2) {
+        const float lo = v[0] + __shfl_xor_sync(kFull, v[0], 1);
+        const float hi = v[1] + __shfl_xor_sync(kFull, v[1], 1);
+        return lo + hi;
+    }
+    const float s1 = v[0] + __shfl_xor_sync(kFull, v[0], 1);
+    return s1 + __shfl_xor_sync(kFull, s1, 2);
+}
+
+// (e, m) of one query over the window's keys, classes as above.
+template <int KQ>
+__device__ __forceinline__ void fwd_sums(const float4 *skA, const float4 *skB, int nc, int part, float x, float y,
+                                         float z, float M2, float &e, float &m)
+{
+    constexpr int CPL = kClasses / KQ;
+    float ev[CPL], mv[CPL];
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) ev[i] = mv[i] = 0.f;
+#pragma unroll
+    for (int set = 0; set < 2; ++set) {
+        const float4 *A = skA + set * kCentres, *B = skB + set * kCentres;
+        for (int base = 0; base < nc; base += kClasses) {
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                const int k = base + part + KQ * i;
+                if (k < nc) fwd_key(A[k], B[k], x, y, z, M2, ev[i], mv[i]);
+            }
+        }
+    }
+    e = combine_classes<KQ>(ev);
+    m = combine_classes<KQ>(mv);
+}
+
+// Eq. func-normal: dO/dq = sum w (d + 2 beta (q - key)(O - f)), same classes.
+template <int KQ>
+__device__ __forceinline__ void dq_sums(const float4 *skA, const float4 *skB, int nc, int part, float x, float y,
+                                        float z, float lse2, float O, float &gx, float &gy, float &gz)
+{
+    constexpr int CPL = kClasses / KQ;
+    float ax[CPL], ay[CPL], az[CPL];
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) ax[i] = ay[i] = az[i] = 0.f;
+#pragma unroll
+    for (int set = 0; set < 2; ++set) {
+        const float4 *A = skA + set * kCentres, *B = skB + set * kCentres;
+        for (int base = 0; base < nc; base += kClasses) {
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                const int k = base + part + KQ * i;
+                if (k < nc) {
+                    const float4 a = A[k], b = B[k];
+                    const float rx = x - a.x, ry = y - a.y, rz = z - a.z;
+                    const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                    const float w = ex2_approx(fmaf(a.w, d2, -lse2));
+                    const float f = fmaf(b.y, rx, fmaf(b.z, ry, fmaf(b.w, rz, b.x)));
+                    const float c = w * (-2.f * kLn2) * a.w * (O - f);   // 2 beta w (O - f)
+                    ax[i] = fmaf(w, b.y, fmaf(c, rx, ax[i]));
+                    ay[i] = fmaf(w, b.z, fmaf(c, ry, ay[i]));
+                    az[i] = fmaf(w, b.w, fmaf(c, rz, az[i]));
+                }
+            }
+        }
+    }
+    gx = combine_classes<KQ>(ax);
+    gy = combine_classes<KQ>(ay);
+    gz = combine_classes<KQ>(az);
+}
+
+struct FwdOut {
+    float O, lse2;
+};
+
+// Forward of the query held by this lane group: fast path without shift,
+// shifted recomputation for groups whose sum underflowed.
+template <int KQ>
+__device__ __forceinline__ FwdOut forward_query(const float4 *skA, const float4 *skB, int nc, int part, float4 q)
+{
+    float e, m;
+    fwd_sums<KQ>(skA, skB, nc, part, q.x, q.y, q.z, 0.f, e, m);
+    float M2 = 0.f;
+    const bool tiny = !(e >= 0x1p-60f);   // identical in every lane of the group
+    if (__any_sync(kFull, tiny)) {
+        float mx = -INFINITY;
+        for (int k = part; k < nc; k += KQ) {
+            mx = fmaxf(mx, key_exponent(skA[k], q.x, q.y, q.z));
+            mx = fmaxf(mx, key_exponent(skA[kCentres + k], q.x, q.y, q.z));
+        }
+#pragma unroll
+        for (int o = 1; o < KQ; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+        float e2, m2;
+        fwd_sums<KQ>(skA, skB, nc, part, q.x, q.y, q.z, mx, e2, m2);
+        if (tiny) {
+            e = e2;
+            m = m2;
+            M2 = mx;
+        }
+    }
+    return {m / e, M2 + lg2_approx(e)};
+}
+
+// ----------------------------------------------------------- backward
+
+// Thread-per-key loop over the item's queries.
 template <bool OFFSET>
 __device__ __forceinline__ void bwd_key_loop(const float4 A, const float4 B, const float4 *__restrict__ sq0,
                                              const float2 *__restrict__ sq1, int n, float acc[8])
@@ -81,6 +218,62 @@ __device__ __forceinline__ void bwd_key_loop(const float4 A, const float4 B, con
     acc[5] = adx; acc[6] = ady; acc[7] = adz;
 }
 
+// ------------------------------------------------------------- kernel
+
+template <int MODE, bool DQ, int KQ>
+__device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *skA, const float4 *skB, float4 *sq0,
+                                              float2 *sq1, int start, int n, int nc, float3 orig, float &loss_acc,
+                                              float &abs_acc)
+{
+    constexpr int LG = KQ == 1 ? 0 : (KQ == 2 ? 1 : 2);
+    const int t = threadIdx.x;
+    const int part = t & (KQ - 1);
+    constexpr int per_round = kThreads / KQ;
+    for (int base = 0; base < n; base += per_round) {
+        const int qi = base + (t >> LG);
+        const bool valid = qi < n;
+        float4 q = a.sorted[start + (valid ? qi : 0)];
+        q.x -= orig.x;   // window-local coordinates
+        q.y -= orig.y;
+        q.z -= orig.z;
+        const FwdOut r = forward_query<KQ>(skA, skB, nc, part, q);
+        const float O = r.O, lse2 = r.lse2;
+
+        float gO = 0.f;
+        int j_user = 0;
+        if (MODE != FIT) j_user = valid ? a.perm[start + qi] : 0;
+        if (MODE == FIT) {
+            const float diff = O - q.w;
+            if (a.loss == EFUNC_LOSS_L1) gO = diff > 0.f ? a.inv_J : (diff < 0.f ? -a.inv_J : 0.f);
+            else gO = 2.f * diff * a.inv_J;
+            if (valid && part == 0) {
+                loss_acc += a.loss == EFUNC_LOSS_L1 ? fabsf(diff) : diff * diff;
+                abs_acc += fabsf(diff);
+            }
+        } else if (MODE == BACKWARD) {
+            gO = valid ? __ldg(a.gO + j_user) : 0.f;
+        } else if (valid && part == 0) {
+            a.O[j_user] = O;
+            if (a.lse) a.lse[j_user] = lse2 * kLn2;
+        }
+        if (DQ) {
+            float gx, gy, gz;
+            dq_sums<KQ>(skA, skB, nc, part, q.x, q.y, q.z, lse2, O, gx, gy, gz);
+            if (valid && part == 0) {
+                float *dst = MODE == FORWARD ? a.dq : a.gq;
+                const float s = MODE == FORWARD ? 1.f : gO;
+                dst[3 * (size_t)j_user + 0] = s * gx;
+                dst[3 * (size_t)j_user + 1] = s * gy;
+                dst[3 * (size_t)j_user + 2] = s * gz;
+            }
+        }
+        if (MODE != FORWARD && valid && part == 0) {
+            sq0[qi] = make_float4(q.x, q.y, q.z, lse2);
+            sq1[qi] = make_float2(O, gO);
+        }
+    }
+}
+
 template <int MODE, bool DQ>
 __global__ void __launch_bounds__(kThreads) fused_kernel(FusedArgs a)
 {
@@ -93,7 +286,6 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(FusedArgs a)
 
     const int t = threadIdx.x;
     const int R = a.R;
-    const float fR = (float)R;
     float loss_acc = 0.f, abs_acc = 0.f;
 
     for (;;) {
@@ -111,122 +303,30 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(FusedArgs a)
         const int nz = min(cz + kW, R - 1) - loz + 1;
         const int nc = nx * ny * nz;
 
-        // ---- 1. stage the window's keys
+        // window origin: centre of index (cx, cy, cz), exact for power-of-two R
+        const float fR = (float)R;
+        const float3 orig = make_float3((float)(2 * cx + 1 - R) / fR, (float)(2 * cy + 1 - R) / fR,
+                                        (float)(2 * cz + 1 - R) / fR);
+
+        // ---- 1. stage the window's key records, positions relative to orig
         if (t < nc) {
             const int oz = t % nz, oy = (t / nz) % ny, ox = t / (ny * nz);
             const int ia = lox + ox, ib = loy + oy, ic = loz + oz;
-            const float *th = a.params + ((size_t)((size_t)ia * R + ib) * R + ic) * kSlots;
-            float v[kSlots];
-#pragma unroll
-            for (int s = 0; s < kSlots; ++s) v[s] = __ldg(th + s);
-            const float kx = (float)(2 * ia + 1 - R) / fR;
-            const float ky = (float)(2 * ib + 1 - R) / fR;
-            const float kz = (float)(2 * ic + 1 - R) / fR;
-            // -beta*log2(e) = (-exp(log_beta0)*log2(e)) * exp(b); the first
-            // factor is folded on the host in double precision.
-            skA[t] = make_float4(kx, ky, kz, a.nbl0 * expf(v[3]));
-            skB[t] = make_float4(v[5], v[6], v[7], v[8]);
-            skA[kCentres + t] = make_float4(kx + v[0], ky + v[1], kz + v[2], a.nbl0 * expf(v[4]));
-            skB[kCentres + t] = make_float4(v[9], v[10], v[11], v[12]);
+            const float4 *k = a.keys + (((size_t)ia * R + ib) * R + ic) * kKeyRecords;
+            const float gx = (float)(2 * (ia - cx)) / fR, gy = (float)(2 * (ib - cy)) / fR,
+                        gz = (float)(2 * (ic - cz)) / fR;
+            const float4 k0 = k[0], k2 = k[2];
+            skA[t] = make_float4(gx, gy, gz, k0.w);
+            skB[t] = k[1];
+            skA[kCentres + t] = make_float4(gx + k2.x, gy + k2.y, gz + k2.z, k2.w);
+            skB[kCentres + t] = k[3];
         }
         __syncthreads();
 
         // ---- 2. forward, one (or 2 / 4) threads per query
-        const int lg = n > 64 ? 0 : (n > 32 ? 1 : 2);
-        const int kq = 1 << lg;
-        const int part = t & (kq - 1);
-        const int per_round = kThreads >> lg;
-        for (int base = 0; base < n; base += per_round) {
-            const int qi = base + (t >> lg);
-            const bool valid = qi < n;
-            const float4 q = a.sorted[start + (valid ? qi : 0)];
-            float e = 0.f, m = 0.f, M2 = 0.f;
-            for (int k = part; k < nc; k += kq) fwd_key(skA[k], skB[k], q.x, q.y, q.z, 0.f, e, m);
-            for (int k = part; k < nc; k += kq) fwd_key(skA[kCentres + k], skB[kCentres + k], q.x, q.y, q.z, 0.f, e, m);
-            for (int o = 1; o < kq; o <<= 1) {
-                e += __shfl_xor_sync(kFull, e, o);
-                m += __shfl_xor_sync(kFull, m, o);
-            }
-            const bool tiny = !(e >= 0x1p-60f);
-            if (__any_sync(kFull, tiny)) {
-                // every key far away in units of its scale: subtract the max exponent
-                float mx = -INFINITY;
-                for (int k = part; k < nc; k += kq) {
-                    mx = fmaxf(mx, key_exponent(skA[k], q.x, q.y, q.z));
-                    mx = fmaxf(mx, key_exponent(skA[kCentres + k], q.x, q.y, q.z));
-                }
-                for (int o = 1; o < kq; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
-                M2 = mx;
-                e = 0.f;
-                m = 0.f;
-                for (int k = part; k < nc; k += kq) fwd_key(skA[k], skB[k], q.x, q.y, q.z, M2, e, m);
-                for (int k = part; k < nc; k += kq)
-                    fwd_key(skA[kCentres + k], skB[kCentres + k], q.x, q.y, q.z, M2, e, m);
-                for (int o = 1; o < kq; o <<= 1) {
-                    e += __shfl_xor_sync(kFull, e, o);
-                    m += __shfl_xor_sync(kFull, m, o);
-                }
-            }
-            const float O = m / e;
-            const float lse2 = M2 + lg2_approx(e);
-
-            float gO = 0.f;
-            int j_user = 0;
-            if (MODE != FIT) j_user = valid ? a.perm[start + qi] : 0;
-            if (MODE == FIT) {
-                const float diff = O - q.w;
-                if (a.loss == EFUNC_LOSS_L1)
-                    gO = diff > 0.f ? a.inv_J : (diff < 0.f ? -a.inv_J : 0.f);
-                else
-                    gO = 2.f * diff * a.inv_J;
-                if (valid && part == 0) {
-                    loss_acc += a.loss == EFUNC_LOSS_L1 ? fabsf(diff) : diff * diff;
-                    abs_acc += fabsf(diff);
-                }
-            } else if (MODE == BACKWARD) {
-                gO = valid ? __ldg(a.gO + j_user) : 0.f;
-            } else {
-                if (valid && part == 0) {
-                    a.O[j_user] = O;
-                    if (a.lse) a.lse[j_user] = lse2 * kLn2;
-                }
-            }
-
-            if (DQ) {
-                // Eq. func-normal: dO/dq = sum w (d + 2 beta (q - key)(O - f))
-                float gx = 0.f, gy = 0.f, gz = 0.f;
-                for (int s = 0; s < 2; ++s) {
-                    for (int k = part; k < nc; k += kq) {
-                        const float4 A = skA[s * kCentres + k], B = skB[s * kCentres + k];
-                        const float rx = q.x - A.x, ry = q.y - A.y, rz = q.z - A.z;
-                        const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                        const float w = ex2_approx(fmaf(A.w, d2, -lse2));
-                        const float f = fmaf(B.y, rx, fmaf(B.z, ry, fmaf(B.w, rz, B.x)));
-                        // 2 beta = -2 ln2 * A.w
-                        const float c = w * (-2.f * kLn2) * A.w * (O - f);
-                        gx = fmaf(w, B.y, fmaf(c, rx, gx));
-                        gy = fmaf(w, B.z, fmaf(c, ry, gy));
-                        gz = fmaf(w, B.w, fmaf(c, rz, gz));
-                    }
-                }
-                for (int o = 1; o < kq; o <<= 1) {
-                    gx += __shfl_xor_sync(kFull, gx, o);
-                    gy += __shfl_xor_sync(kFull, gy, o);
-                    gz += __shfl_xor_sync(kFull, gz, o);
-                }
-                if (valid && part == 0) {
-                    float *dst = MODE == FORWARD ? a.dq : a.gq;
-                    const float s = MODE == FORWARD ? 1.f : gO;
-                    dst[3 * (size_t)j_user + 0] = s * gx;
-                    dst[3 * (size_t)j_user + 1] = s * gy;
-                    dst[3 * (size_t)j_user + 2] = s * gz;
-                }
-            }
-            if (MODE != FORWARD && valid && part == 0) {
-                sq0[qi] = make_float4(q.x, q.y, q.z, lse2);
-                sq1[qi] = make_float2(O, gO);
-            }
-        }
+        if (n > 64) forward_phase<MODE, DQ, 1>(a, skA, skB, sq0, sq1, start, n, nc, orig, loss_acc, abs_acc);
+        else if (n > 32) forward_phase<MODE, DQ, 2>(a, skA, skB, sq0, sq1, start, n, nc, orig, loss_acc, abs_acc);
+        else forward_phase<MODE, DQ, 4>(a, skA, skB, sq0, sq1, start, n, nc, orig, loss_acc, abs_acc);
 
         if (MODE == FORWARD) continue;
 
@@ -240,7 +340,7 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(FusedArgs a)
             if (offset) bwd_key_loop<true>(A, B, sq0, sq1, n, acc);
             else bwd_key_loop<false>(A, B, sq0, sq1, n, acc);
             const int oz = c % nz, oy = (c / nz) % ny, ox = c / (ny * nz);
-            float *gr = a.grad + ((size_t)((size_t)(lox + ox) * R + (loy + oy)) * R + (loz + oz)) * kSlots;
+            float *gr = a.grad + (((size_t)(lox + ox) * R + (loy + oy)) * R + (loz + oz)) * kSlots;
             const float beta = -A.w * kLn2;
             if (!offset) {
                 atomicAdd(gr + 5, acc[0]);
@@ -285,21 +385,41 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(FusedArgs a)
     }
 }
 
+int sm_count()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
 }  // namespace
 
 int fused_grid_size()
 {
     static int g = 0;
     if (!g) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel<FIT, false>, kThreads, 0);
-        if (sms <= 0) sms = 1;
         if (per_sm <= 0) per_sm = 1;
-        g = sms * per_sm;
+        g = sm_count() * per_sm;
     }
     return g;
+}
+
+cudaError_t launch_pack_keys(const PackArgs &a, cudaStream_t s)
+{
+    const int I = a.R * a.R * a.R;
+    int blocks = (I + 255) / 256;
+    if (blocks > sm_count() * 8) blocks = sm_count() * 8;
+    launch_begin(K_PACK_KEYS, s);
+    pack_keys_kernel<<<blocks, 256, 0, s>>>(a);
+    launch_end(K_PACK_KEYS, s);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_forward(const FusedArgs &a, bool with_dq, int grid, cudaStream_t s)

@@ -175,3 +175,40 @@ def random_params(R: int, seed: int, delta_scale: float = 0.3, b_scale: float = 
     p[:, 5:13] = g.standard_normal((R ** 3, 8)) * value_scale
     return p.astype(np.float32)
 
+
+
+def _grid_positions(R: int) -> np.ndarray:
+    c = -1.0 + (np.arange(R) + 0.5) * (2.0 / R)
+    a, b, d = np.meshgrid(c, c, c, indexing="ij")
+    return np.stack([a.ravel(), b.ravel(), d.ravel()], 1)
+
+
+def _sdf_grad(shape: Shape, x: np.ndarray, eps: float = 1e-5) -> np.ndarray:
+    g = np.empty_like(x)
+    for a in range(3):
+        dx = np.zeros(3)
+        dx[a] = eps
+        g[:, a] = (shape.sdf(x + dx) - shape.sdf(x - dx)) / (2 * eps)
+    return g
+
+
+def sdf_params(shape: Shape, R: int, seed: int, noise: float = 0.02, delta_scale: float = 0.3,
+               b_scale: float = 0.3) -> np.ndarray:
+    """(R^3, 13) float32 parameters shaped like a fitted grid: every key's
+    value is the first-order Taylor expansion of the shape's SDF about the
+    key (constant = SDF there, linear term = its gradient) plus N(0, noise^2)
+    perturbations; offsets U(-delta_scale, delta_scale) grid spacings;
+    log-scales N(0, b_scale^2)."""
+    g = rng(seed)
+    h = 2.0 / R
+    k = _grid_positions(R)
+    delta = g.uniform(-delta_scale, delta_scale, size=(R ** 3, 3)) * h
+    p = np.empty((R ** 3, 13))
+    p[:, 0:3] = delta
+    p[:, 3:5] = g.standard_normal((R ** 3, 2)) * b_scale
+    p[:, 5] = shape.sdf(k) + noise * g.standard_normal(R ** 3)
+    p[:, 6:9] = _sdf_grad(shape, k) + noise * g.standard_normal((R ** 3, 3))
+    ko = k + delta
+    p[:, 9] = shape.sdf(ko) + noise * g.standard_normal(R ** 3)
+    p[:, 10:13] = _sdf_grad(shape, ko) + noise * g.standard_normal((R ** 3, 3))
+    return p.astype(np.float32)
