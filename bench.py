@@ -56,6 +56,36 @@ WORKLOAD = "C2 plain fit: 32^3x13 FP32 grid, 2^22 queries/step (50% uniform, 50%
            "union of 8 random primitives, L1 loss, Adam lr 1e-3"
 
 
+def fused_traffic():
+    """DRAM bytes per fused launch from the committed ncu summary, or None when
+    the kernel's sources changed since that capture."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in ("paper_2505_21319_gb300/csrc/fused.cu", "paper_2505_21319_gb300/csrc/common.cuh"):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "fused_fit_32cubed_2p22.md")).read()
+    except OSError:
+        return None
+    sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    tb = re.search(r"traffic_bytes_per_launch:\s*(\d+)", txt)
+    if not sha or not tb or sha.group(1) != h.hexdigest():
+        return None
+    return int(tb.group(1))
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Max of a per-rank scalar over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -299,11 +329,8 @@ def main():
     ms = start.elapsed_time(end) / args.steps
     fused_ms, fused_n = api.profile_read("fused_fit")
     kernel_ms = {k: api.profile_read(k)[0] / max(1, api.profile_read(k)[1])
-                 for k in ("bin", "scan_reduce", "scan_top", "scan_emit", "scatter", "fused_fit", "adam")}
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+                 for k in ("bin", "scan_reduce", "scan_top", "scan_emit", "scatter", "pack_keys", "fused_fit", "adam")}
+    ms = max_over_ranks(ms, dev)
     value = J * ws / (ms * 1e-3)
     st = stats.view(-1, 2).cpu().numpy()
 
@@ -343,10 +370,7 @@ def main():
                           step0=2 * 10 ** 6 + s, stats=host_stats, lr=LR, ws=ws_buf)
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, dev)
         e2e = {"value": J * ws * args.e2e_steps / dt, "unit": "query-pts/s", "h2d_bytes_per_step": J * 16,
                "d2h_bytes_per_step": 8, "steps": args.e2e_steps}
 
@@ -368,7 +392,7 @@ def main():
                        "l2": "inputs larger than L2: 3 batches x 64 MiB cycle, 192 MiB > 129 MB",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "alu", "kernel": "fused_fit", "achieved": achieved, "peak": peak,
-                         "unit": "T FP32 op/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "T FP32 op/s", "frac": achieved / peak, "traffic": fused_traffic(),
                          "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_fused,
                          "peak_from": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz"},
             "kernel_ms": kernel_ms,
