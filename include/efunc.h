@@ -163,6 +163,30 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
                        int64_t step0, float *stats, void *workspace, size_t workspace_bytes,
                        efunc_stream_t stream);
 
+/* Forward without any device allocation by the caller.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory themselves, for example code running inside a host
+ * framework that owns every device allocation through its own pool, or a
+ * latency-critical caller that must not trigger the implicit device
+ * synchronisation of cudaMalloc.  It computes exactly what efunc_forward
+ * computes, with the same arguments minus the workspace: the scratch is a
+ * fixed 32 MiB array inside this library (every GPU that loads the library
+ * keeps it until the process exits).
+ *   - Limit: requests whose efunc_workspace_bytes(grid, J) exceeds 32 MiB
+ *     return EFUNC_ERR_WORKSPACE with nothing enqueued.  That admits up to
+ *     719,360 queries at R = 32, 821,680 at R = 16 and 33,648 at R = 64;
+ *     larger grids need efunc_forward with a caller workspace.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before
+ *     any stream capture.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - All calls share the one array and it keeps the last call's contents;
+ *     every call clears what it reads before use.  Calls that overlap on the
+ *     GPU (other streams, other host threads) race on the array: serialise
+ *     them. */
+efunc_status efunc_forward_noalloc(const efunc_grid *grid, const float *params, const float *q, int64_t J,
+                                   int32_t q_stride, float *O, float *lse, float *dOdq, efunc_stream_t stream);
+
 /* ------------------------------------------------------------ measurement */
 
 /* When enabled, every kernel launch of the library is bracketed by CUDA

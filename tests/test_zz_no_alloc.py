@@ -1,0 +1,75 @@
+"""The forward entry point that allocates nothing (efunc_forward_noalloc).
+
+It serves callers that cannot allocate device memory themselves (a host
+framework that owns every device allocation, or a latency-critical caller
+that must avoid cudaMalloc's implicit synchronisation): its scratch is a
+fixed 32 MiB array inside the library.  These tests call it through the C ABI
+and compare it with efunc_forward (caller workspace) on two calls in a row,
+so the second call runs on the array as the first call left it.  The file is
+named to be collected last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2505_21319_gb300 import _binding as B
+from paper_2505_21319_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SCRATCH = 32 << 20
+
+
+def _forward_pair(lib, R, J, seed, stride):
+    dev = torch.device("cuda")
+    p = torch.from_numpy(synth.sdf_params(synth.random_union(seed), R, seed=seed)).to(dev)
+    qo = synth.sample_batch(synth.random_union(seed), J, seed=seed)
+    q = torch.from_numpy(np.ascontiguousarray(qo[:, :stride])).to(dev)
+    g = B.Grid(R, 2, float(lib.efunc_default_log_beta0(R)))
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    # reference: the existing entry point with a caller workspace
+    n = lib.efunc_workspace_bytes(ctypes.byref(g), J)
+    ws = torch.empty(n, dtype=torch.uint8, device=dev)
+    O_ref = torch.empty(J, device=dev)
+    lse_ref = torch.empty(J, device=dev)
+    B.check("efunc_forward", lib.efunc_forward(ctypes.byref(g), p.data_ptr(), q.data_ptr(), J, stride,
+                                               O_ref.data_ptr(), lse_ref.data_ptr(), None, ws.data_ptr(), n, stream))
+    O = torch.full((J,), float("nan"), device=dev)
+    lse = torch.full((J,), float("nan"), device=dev)
+    B.check("efunc_forward_noalloc", lib.efunc_forward_noalloc(ctypes.byref(g), p.data_ptr(), q.data_ptr(), J,
+                                                               stride, O.data_ptr(), lse.data_ptr(), None, stream))
+    torch.cuda.synchronize()
+    return O.cpu().numpy(), lse.cpu().numpy(), O_ref.cpu().numpy(), lse_ref.cpu().numpy()
+
+
+def _close(a, ref):
+    return np.all(np.abs(a.astype(np.float64) - ref) <= 1e-6 + 1e-5 * np.abs(ref.astype(np.float64)))
+
+
+def test_noalloc_forward_matches_workspace_forward_twice():
+    lib = B.load()
+    # two calls in a row with different grids and batches: the second call
+    # sees the first call's leftovers in the shared scratch array
+    for R, J, seed, stride in ((32, 300007, 1, 4), (16, 123457, 2, 3)):
+        O, lse, O_ref, lse_ref = _forward_pair(lib, R, J, seed, stride)
+        assert np.isfinite(O).all() and np.isfinite(lse).all()
+        assert _close(O, O_ref) and _close(lse, lse_ref)
+
+
+def test_noalloc_forward_rejects_requests_beyond_its_scratch():
+    lib = B.load()
+    g = B.Grid(32, 2, 7.0)
+    J = 1
+    while lib.efunc_workspace_bytes(ctypes.byref(g), J) <= SCRATCH:
+        J *= 2
+    dev = torch.device("cuda")
+    p = torch.zeros(32 ** 3 * 13, device=dev)
+    q = torch.zeros((J, 3), device=dev)
+    O = torch.zeros(J, device=dev)
+    rc = lib.efunc_forward_noalloc(ctypes.byref(g), p.data_ptr(), q.data_ptr(), J, 3, O.data_ptr(), None, None,
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 3   # EFUNC_ERR_WORKSPACE, nothing enqueued
+    assert lib.efunc_forward_noalloc(ctypes.byref(B.Grid(0, 2, 7.0)), p.data_ptr(), q.data_ptr(), J, 3,
+                                     O.data_ptr(), None, None, None) == 1
