@@ -6,10 +6,11 @@
 // i.e. the same 128 keys (64 grid keys k_i and 64 offset keys k_i + Delta_i,
 // one softmax over their union, Eq. func-offset).  A persistent CTA of 128
 // threads takes items from a device counter and, per item:
-//   1. stages the window's packed key records in shared memory (the records
-//      are L2-resident: 64 bytes per centre), with key positions in
-//      window-local coordinates (origin at the centre of index c, the window
-//      base); queries are shifted into the same frame when loaded;
+//   1. receives the item's query tile and the window's key records in shared
+//      memory through TMA bulk copies (cp.async.bulk + mbarrier) issued while
+//      the previous item was being computed (two buffers), then rewrites the
+//      key positions into window-local coordinates (origin at the centre of
+//      index c, the window base; queries are shifted into the same frame);
 //   2. forward, thread per query (2 or 4 threads per query for sparse cells):
 //      e = sum 2^{s}, m = sum 2^{s} f with s = -beta log2(e) ||q - key||^2,
 //      O = m / e, lse2 = log2 e (Algorithm 1 in base 2).  The keys are summed
@@ -24,7 +25,8 @@
 //      issues one FP32 atomic per slot per item.
 // No per-query intermediate leaves the CTA: the only outputs are O / lse /
 // dO/dq (forward), the gradient grid and dL/dq (backward), and the loss sums
-// (fit).
+// (fit).  Every wait on a copy is bounded (about a second of clock cycles);
+// on expiry the CTA records an error in the control block and returns.
 #include "common.cuh"
 
 namespace efunc {
@@ -33,9 +35,104 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kLn2 = 0.69314718055994531f;
-constexpr int kClasses = 4;   // interleaved summation classes of the forward
+constexpr int kClasses = 4;                       // interleaved summation classes of the forward
+constexpr long long kWaitCycles = 2000000000ll;   // bound of every copy wait (~1 s)
 
 enum Mode { FORWARD = 0, BACKWARD = 1, FIT = 2 };
+
+// Shared key tile of one window: centre c holds 4 float4 records,
+//   rec[4c + 0] = (grid key position, -beta log2 e)    rec[4c + 1] = (o, d)
+//   rec[4c + 2] = (offset key position, -beta' log2 e) rec[4c + 3] = (o', d')
+// with positions in window-local coordinates; set 0 = grid keys, 1 = offset keys.
+__device__ __forceinline__ float4 keyA(const float4 *rec, int set, int k) { return rec[4 * k + 2 * set]; }
+__device__ __forceinline__ float4 keyB(const float4 *rec, int set, int k) { return rec[4 * k + 2 * set + 1]; }
+
+// ------------------------------------------------------- TMA / mbarrier
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `parity` of the barrier; false after kWaitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+// Bulk copy global -> shared, completion counted in bytes on the barrier.
+// Addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+struct Window {
+    int cx, cy, cz, lox, loy, loz, nx, ny, nz, nc;
+};
+
+__device__ __forceinline__ Window window_of(const Item item, int R)
+{
+    Window w;
+    w.cx = (item.z & 1023) - 1;
+    w.cy = ((item.z >> 10) & 1023) - 1;
+    w.cz = ((item.z >> 20) & 1023) - 1;
+    w.lox = max(w.cx - kW + 1, 0);
+    w.loy = max(w.cy - kW + 1, 0);
+    w.loz = max(w.cz - kW + 1, 0);
+    w.nx = min(w.cx + kW, R - 1) - w.lox + 1;
+    w.ny = min(w.cy + kW, R - 1) - w.loy + 1;
+    w.nz = min(w.cz + kW, R - 1) - w.loz + 1;
+    w.nc = w.nx * w.ny * w.nz;
+    return w;
+}
+
+// One thread: arm the buffer's barrier and copy the item's queries (n x 16 B)
+// and its window's key records (rows of nz centres x 64 B) into shared memory.
+__device__ __forceinline__ void issue_item(const FusedArgs &a, const Item item, float4 *rec, float4 *qt,
+                                           uint64_t *bar)
+{
+    const Window w = window_of(item, a.R);
+    mbar_arrive_expect_tx(bar, (uint32_t)item.y * 16u + (uint32_t)w.nc * 64u);
+    bulk_g2s(qt, a.sorted + item.x, (uint32_t)item.y * 16u, bar);
+    const uint32_t row = (uint32_t)w.nz * 64u;
+    for (int ox = 0; ox < w.nx; ++ox)
+        for (int oy = 0; oy < w.ny; ++oy) {
+            const size_t ci = ((size_t)(w.lox + ox) * a.R + (w.loy + oy)) * a.R + w.loz;
+            bulk_g2s(rec + (size_t)(ox * w.ny + oy) * w.nz * kKeyRecords, a.keys + ci * kKeyRecords, row, bar);
+        }
+}
 
 // --------------------------------------------------------------- pack
 
@@ -96,8 +193,8 @@ __device__ __forceinline__ float combine_classes(const float *v)
 
 // (e, m) of one query over the window's keys, classes as above.
 template <int KQ>
-__device__ __forceinline__ void fwd_sums(const float4 *skA, const float4 *skB, int nc, int part, float x, float y,
-                                         float z, float M2, float &e, float &m)
+__device__ __forceinline__ void fwd_sums(const float4 *rec, int nc, int part, float x, float y, float z, float M2,
+                                         float &e, float &m)
 {
     constexpr int CPL = kClasses / KQ;
     float ev[CPL], mv[CPL];
@@ -105,12 +202,70 @@ __device__ __forceinline__ void fwd_sums(const float4 *skA, const float4 *skB, i
     for (int i = 0; i < CPL; ++i) ev[i] = mv[i] = 0.f;
 #pragma unroll
     for (int set = 0; set < 2; ++set) {
-        const float4 *A = skA + set * kCentres, *B = skB + set * kCentres;
         for (int base = 0; base < nc; base += kClasses) {
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
                 const int k = base + part + KQ * i;
-                if (k < nc) fwd_key(A[k], B[k], x, y, z, M2, ev[i], mv[i]);
+                if (k < nc) fwd_key(keyA(rec, set, k), keyB(rec, set, k), x, y, z, M2, ev[i], mv[i]);
+            }
+        }
+    }
+    e = combine_classes<KQ>(ev);
+    m = combine_classes<KQ>(mv);
+}
+
+// Full window (nc = 64, the interior case).  Grid keys sit on the lattice
+// (i - c) h, i - c in {-1, 0, 1, 2} per axis, so their distance terms are
+// formed once per query and axis: d2 = (X2[ox] + Y2[oy]) + Z2[oz].  Offset
+// keys take the generic path.  Classes as in fwd_sums: class i of lane `part`
+// is the z offset oz = part + KQ i.
+template <int KQ>
+__device__ __forceinline__ void fwd_sums_full(const float4 *rec, int part, float h, float x, float y, float z,
+                                              float &e, float &m)
+{
+    constexpr int CPL = kClasses / KQ;
+    float ev[CPL], mv[CPL];
+    float ry[4], y2[4], rz[CPL], z2[CPL];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        ry[a] = y - (float)(a - 1) * h;
+        y2[a] = ry[a] * ry[a];
+    }
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) {
+        rz[i] = z - (float)(part + KQ * i - 1) * h;
+        z2[i] = rz[i] * rz[i];
+        ev[i] = mv[i] = 0.f;
+    }
+    const float4 *P = rec + 4 * part;
+#pragma unroll 1
+    for (int ox = 0; ox < 4; ++ox) {
+        const float rx = x - (float)(ox - 1) * h;
+        const float x2 = rx * rx;
+        const float4 *Po = P + 4 * 16 * ox;
+#pragma unroll
+        for (int oy = 0; oy < 4; ++oy) {
+            const float xy = x2 + y2[oy];
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                const int k = oy * 4 + KQ * i;
+                const float nbl = Po[4 * k].w;
+                const float4 b = Po[4 * k + 1];
+                const float l = ex2_approx(nbl * (xy + z2[i]));
+                const float f = fmaf(b.y, rx, fmaf(b.z, ry[oy], fmaf(b.w, rz[i], b.x)));
+                ev[i] += l;
+                mv[i] = fmaf(l, f, mv[i]);
+            }
+        }
+    }
+#pragma unroll 1
+    for (int k0 = 0; k0 < kCentres; k0 += 16) {
+#pragma unroll
+        for (int kk = 0; kk < 16; kk += kClasses) {
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                const int k = k0 + kk + KQ * i;
+                fwd_key(P[4 * k + 2], P[4 * k + 3], x, y, z, 0.f, ev[i], mv[i]);
             }
         }
     }
@@ -120,8 +275,8 @@ __device__ __forceinline__ void fwd_sums(const float4 *skA, const float4 *skB, i
 
 // Eq. func-normal: dO/dq = sum w (d + 2 beta (q - key)(O - f)), same classes.
 template <int KQ>
-__device__ __forceinline__ void dq_sums(const float4 *skA, const float4 *skB, int nc, int part, float x, float y,
-                                        float z, float lse2, float O, float &gx, float &gy, float &gz)
+__device__ __forceinline__ void dq_sums(const float4 *rec, int nc, int part, float x, float y, float z, float lse2,
+                                        float O, float &gx, float &gy, float &gz)
 {
     constexpr int CPL = kClasses / KQ;
     float ax[CPL], ay[CPL], az[CPL];
@@ -129,13 +284,12 @@ __device__ __forceinline__ void dq_sums(const float4 *skA, const float4 *skB, in
     for (int i = 0; i < CPL; ++i) ax[i] = ay[i] = az[i] = 0.f;
 #pragma unroll
     for (int set = 0; set < 2; ++set) {
-        const float4 *A = skA + set * kCentres, *B = skB + set * kCentres;
         for (int base = 0; base < nc; base += kClasses) {
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
                 const int k = base + part + KQ * i;
                 if (k < nc) {
-                    const float4 a = A[k], b = B[k];
+                    const float4 a = keyA(rec, set, k), b = keyB(rec, set, k);
                     const float rx = x - a.x, ry = y - a.y, rz = z - a.z;
                     const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
                     const float w = ex2_approx(fmaf(a.w, d2, -lse2));
@@ -159,23 +313,25 @@ struct FwdOut {
 
 // Forward of the query held by this lane group: fast path without shift,
 // shifted recomputation for groups whose sum underflowed.
-template <int KQ>
-__device__ __forceinline__ FwdOut forward_query(const float4 *skA, const float4 *skB, int nc, int part, float4 q)
+template <int KQ, bool FULL>
+__device__ __forceinline__ FwdOut forward_query(const float4 *rec, int nc, int part, float h, float4 q)
 {
     float e, m;
-    fwd_sums<KQ>(skA, skB, nc, part, q.x, q.y, q.z, 0.f, e, m);
+    if (FULL) fwd_sums_full<KQ>(rec, part, h, q.x, q.y, q.z, e, m);
+    else fwd_sums<KQ>(rec, nc, part, q.x, q.y, q.z, 0.f, e, m);
     float M2 = 0.f;
     const bool tiny = !(e >= 0x1p-60f);   // identical in every lane of the group
     if (__any_sync(kFull, tiny)) {
         float mx = -INFINITY;
         for (int k = part; k < nc; k += KQ) {
-            mx = fmaxf(mx, key_exponent(skA[k], q.x, q.y, q.z));
-            mx = fmaxf(mx, key_exponent(skA[kCentres + k], q.x, q.y, q.z));
+            mx = fmaxf(mx, key_exponent(keyA(rec, 0, k), q.x, q.y, q.z));
+            mx = fmaxf(mx, key_exponent(keyA(rec, 1, k), q.x, q.y, q.z));
         }
 #pragma unroll
         for (int o = 1; o < KQ; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+        // the shifted sums take the generic path in every window shape
         float e2, m2;
-        fwd_sums<KQ>(skA, skB, nc, part, q.x, q.y, q.z, mx, e2, m2);
+        fwd_sums<KQ>(rec, nc, part, q.x, q.y, q.z, mx, e2, m2);
         if (tiny) {
             e = e2;
             m = m2;
@@ -187,22 +343,21 @@ __device__ __forceinline__ FwdOut forward_query(const float4 *skA, const float4 
 
 // ----------------------------------------------------------- backward
 
-// Thread-per-key loop over the item's queries.
+// Thread-per-key loop over the item's queries, two queries per iteration:
+// sqA[j] = (q_j local, lse2_j), sqB[j/2] = (O_j, gO_j, O_j+1, gO_j+1); an odd
+// count is padded with a copy of the last query carrying dL/dO = 0.
 template <bool OFFSET>
-__device__ __forceinline__ void bwd_key_loop(const float4 A, const float4 B, const float4 *__restrict__ sq0,
-                                             const float2 *__restrict__ sq1, int n, float acc[8])
+__device__ __forceinline__ void bwd_key_loop(const float4 A, const float4 B, const float4 *__restrict__ sqA,
+                                             const float4 *__restrict__ sqB, int n, float acc[8])
 {
     float ag = 0.f, arx = 0.f, ary = 0.f, arz = 0.f, ab = 0.f, adx = 0.f, ady = 0.f, adz = 0.f;
-#pragma unroll 4
-    for (int j = 0; j < n; ++j) {
-        const float4 Q = sq0[j];
-        const float2 S = sq1[j];
+    auto one = [&](const float4 Q, float O, float gO) {
         const float rx = Q.x - A.x, ry = Q.y - A.y, rz = Q.z - A.z;
         const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
         const float w = ex2_approx(fmaf(A.w, d2, -Q.w));
-        const float g = w * S.y;
+        const float g = w * gO;
         const float f = fmaf(B.y, rx, fmaf(B.z, ry, fmaf(B.w, rz, B.x)));
-        const float gd = g * (f - S.x);
+        const float gd = g * (f - O);
         ag += g;
         arx = fmaf(g, rx, arx);
         ary = fmaf(g, ry, ary);
@@ -213,6 +368,13 @@ __device__ __forceinline__ void bwd_key_loop(const float4 A, const float4 B, con
             ady = fmaf(gd, ry, ady);
             adz = fmaf(gd, rz, adz);
         }
+    };
+    const int pairs = (n + 1) >> 1;
+#pragma unroll 2
+    for (int jp = 0; jp < pairs; ++jp) {
+        const float4 Q0 = sqA[2 * jp], Q1 = sqA[2 * jp + 1], S = sqB[jp];
+        one(Q0, S.x, S.y);
+        one(Q1, S.z, S.w);
     }
     acc[0] = ag; acc[1] = arx; acc[2] = ary; acc[3] = arz; acc[4] = ab;
     acc[5] = adx; acc[6] = ady; acc[7] = adz;
@@ -220,9 +382,12 @@ __device__ __forceinline__ void bwd_key_loop(const float4 A, const float4 B, con
 
 // ------------------------------------------------------------- kernel
 
-template <int MODE, bool DQ, int KQ>
-__device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *skA, const float4 *skB, float4 *sq0,
-                                              float2 *sq1, int start, int n, int nc, float3 orig, float &loss_acc,
+// Forward over the item's queries.  qt holds the raw query tile (x, y, z,
+// target); a query's row is rewritten in place with (local position, lse2)
+// by the lane that owns it, after every lane of its group has read it.
+template <int MODE, bool DQ, int KQ, bool FULL>
+__device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *rec, float4 *qt, float4 *sqB,
+                                              int start, int n, int nc, float3 orig, float h, float &loss_acc,
                                               float &abs_acc)
 {
     constexpr int LG = KQ == 1 ? 0 : (KQ == 2 ? 1 : 2);
@@ -232,16 +397,22 @@ __device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *
     for (int base = 0; base < n; base += per_round) {
         const int qi = base + (t >> LG);
         const bool valid = qi < n;
-        float4 q = a.sorted[start + (valid ? qi : 0)];
-        q.x -= orig.x;   // window-local coordinates
-        q.y -= orig.y;
-        q.z -= orig.z;
-        const FwdOut r = forward_query<KQ>(skA, skB, nc, part, q);
+        int j_user = 0;
+        if (MODE != FIT) j_user = valid ? __ldg(a.perm + start + qi) : 0;   // issued before the long compute
+        float4 q;
+        if (valid) {
+            q = qt[qi];
+            q.x -= orig.x;   // window-local coordinates
+            q.y -= orig.y;
+            q.z -= orig.z;
+        } else {
+            // lanes without a query evaluate the window centre (never stored)
+            q = make_float4(0.5f * h, 0.5f * h, 0.5f * h, 0.f);
+        }
+        const FwdOut r = forward_query<KQ, FULL>(rec, nc, part, h, q);
         const float O = r.O, lse2 = r.lse2;
 
         float gO = 0.f;
-        int j_user = 0;
-        if (MODE != FIT) j_user = valid ? a.perm[start + qi] : 0;
         if (MODE == FIT) {
             const float diff = O - q.w;
             if (a.loss == EFUNC_LOSS_L1) gO = diff > 0.f ? a.inv_J : (diff < 0.f ? -a.inv_J : 0.f);
@@ -258,7 +429,7 @@ __device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *
         }
         if (DQ) {
             float gx, gy, gz;
-            dq_sums<KQ>(skA, skB, nc, part, q.x, q.y, q.z, lse2, O, gx, gy, gz);
+            dq_sums<KQ>(rec, nc, part, q.x, q.y, q.z, lse2, O, gx, gy, gz);
             if (valid && part == 0) {
                 float *dst = MODE == FORWARD ? a.dq : a.gq;
                 const float s = MODE == FORWARD ? 1.f : gO;
@@ -267,99 +438,174 @@ __device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *
                 dst[3 * (size_t)j_user + 2] = s * gz;
             }
         }
-        if (MODE != FORWARD && valid && part == 0) {
-            sq0[qi] = make_float4(q.x, q.y, q.z, lse2);
-            sq1[qi] = make_float2(O, gO);
+        if (MODE != FORWARD) {
+            __syncwarp();   // every lane of the group has read its row of qt
+            if (valid && part == 0) {
+                const float4 qa = make_float4(q.x, q.y, q.z, lse2);
+                float2 *sqB2 = reinterpret_cast<float2 *>(sqB);
+                qt[qi] = qa;
+                sqB2[qi] = make_float2(O, gO);
+                if (qi == n - 1 && (n & 1)) {   // pad the last pair: same query, no gradient
+                    qt[n] = qa;
+                    sqB2[n] = make_float2(O, 0.f);
+                }
+            }
         }
     }
 }
 
 template <int MODE, bool DQ>
-__global__ void __launch_bounds__(kThreads) fused_kernel(FusedArgs a)
+__global__ void __launch_bounds__(kThreads, 8) fused_kernel(FusedArgs a)
 {
-    __shared__ float4 skA[2 * kCentres];   // key position, -beta*log2(e)
-    __shared__ float4 skB[2 * kCentres];   // value constant, value linear term
-    __shared__ float4 sq0[MODE == FORWARD ? 1 : kChunk];   // query, lse2
-    __shared__ float2 sq1[MODE == FORWARD ? 1 : kChunk];   // O, dL/dO
-    __shared__ int s_item;
+    // Two buffers: item i lands in buffer i & 1 (TMA bulk copies issued during
+    // item i - 1) while item i - 1 is computed from the other buffer.
+    __shared__ __align__(128) float4 s_rec[2][kCentres * kKeyRecords];   // key records
+    __shared__ __align__(128) float4 s_qt[2][kChunk];                      // query tile
+    __shared__ __align__(16) float4 s_sqB[2][MODE == FORWARD ? 1 : kChunk / 2];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ Item s_meta[2];
+    __shared__ int s_item[2];
     __shared__ float s_red[2][kThreads / 32];
 
     const int t = threadIdx.x;
     const int R = a.R;
+    const float invR = 1.f / (float)R;    // exact for power-of-two R
+    const float h = 2.f * invR;
+    const int n_items = a.ctrl->n_items;
     float loss_acc = 0.f, abs_acc = 0.f;
 
+    // Thread 0 runs the item pipeline one item ahead, keeping every latency
+    // behind compute: the next index is fetched during the previous item,
+    // its descriptor is loaded before the forward, the bulk copies into the
+    // free buffer are issued after it (s_item >= n_items with a bare arrive
+    // means "no more items").
+    int next_idx = 0;
+    Item next_item = make_int4(0, 0, 0, 0);
+    if (t == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const int first = atomicAdd(&a.ctrl->next_item, 1);
+        s_item[0] = first;
+        if (first < n_items) {
+            const Item it0 = a.items[first];
+            s_meta[0] = it0;
+            issue_item(a, it0, s_rec[0], s_qt[0], &s_bar[0]);
+        } else {
+            mbar_arrive(&s_bar[0]);
+        }
+        next_idx = atomicAdd(&a.ctrl->next_item, 1);
+    }
+    __syncthreads();   // barriers initialised
+    int buf = 0;
+    uint32_t uses = 0;   // items started; parity of buffer b's next phase = (uses >> 1) & 1
     for (;;) {
-        __syncthreads();   // the previous item is fully consumed
-        if (t == 0) s_item = atomicAdd(&a.ctrl->next_item, 1);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= a.ctrl->n_items) break;
-        const Item item = a.items[it];
-        const int start = item.x, n = item.y;
-        const int cx = (item.z & 1023) - 1, cy = ((item.z >> 10) & 1023) - 1, cz = ((item.z >> 20) & 1023) - 1;
-        const int lox = max(cx - kW + 1, 0), loy = max(cy - kW + 1, 0), loz = max(cz - kW + 1, 0);
-        const int nx = min(cx + kW, R - 1) - lox + 1;
-        const int ny = min(cy + kW, R - 1) - loy + 1;
-        const int nz = min(cz + kW, R - 1) - loz + 1;
-        const int nc = nx * ny * nz;
-
-        // window origin: centre of index (cx, cy, cz), exact for power-of-two R
-        const float fR = (float)R;
-        const float3 orig = make_float3((float)(2 * cx + 1 - R) / fR, (float)(2 * cy + 1 - R) / fR,
-                                        (float)(2 * cz + 1 - R) / fR);
-
-        // ---- 1. stage the window's key records, positions relative to orig
+        // ---- 1. wait for the item's tiles, then localise the key positions
+        const bool ok = mbar_wait_bounded(&s_bar[buf], (uses >> 1) & 1);
+        const int it = s_item[buf];
+        if (__syncthreads_or(!ok)) {
+            // a copy did not land in time: record it, let in-flight copies
+            // drain (bounded), leave
+            if (t == 0) {
+                atomicOr(&a.ctrl->error, 1);
+                mbar_wait_bounded(&s_bar[buf], (uses >> 1) & 1);
+            }
+            break;
+        }
+        if (it >= n_items) break;
+        const Item item = s_meta[buf];
+        const Window w = window_of(item, R);
+        const int start = item.x, n = item.y, nc = w.nc;
+        const bool full = nc == kCentres;
+        float4 *rec = s_rec[buf], *qt = s_qt[buf], *qB = s_sqB[buf];
+        const float3 orig = make_float3((float)(2 * w.cx + 1 - R) * invR, (float)(2 * w.cy + 1 - R) * invR,
+                                        (float)(2 * w.cz + 1 - R) * invR);
         if (t < nc) {
-            const int oz = t % nz, oy = (t / nz) % ny, ox = t / (ny * nz);
-            const int ia = lox + ox, ib = loy + oy, ic = loz + oz;
-            const float4 *k = a.keys + (((size_t)ia * R + ib) * R + ic) * kKeyRecords;
-            const float gx = (float)(2 * (ia - cx)) / fR, gy = (float)(2 * (ib - cy)) / fR,
-                        gz = (float)(2 * (ic - cz)) / fR;
-            const float4 k0 = k[0], k2 = k[2];
-            skA[t] = make_float4(gx, gy, gz, k0.w);
-            skB[t] = k[1];
-            skA[kCentres + t] = make_float4(gx + k2.x, gy + k2.y, gz + k2.z, k2.w);
-            skB[kCentres + t] = k[3];
+            int ox, oy, oz;
+            if (full) {
+                ox = t >> 4; oy = (t >> 2) & 3; oz = t & 3;
+            } else {
+                oz = t % w.nz; oy = (t / w.nz) % w.ny; ox = t / (w.ny * w.nz);
+            }
+            const float gx = (float)(2 * (w.lox + ox - w.cx)) * invR, gy = (float)(2 * (w.loy + oy - w.cy)) * invR,
+                        gz = (float)(2 * (w.loz + oz - w.cz)) * invR;
+            float4 *r = rec + 4 * t;
+            const float4 g = r[0], o = r[2];
+            r[0] = make_float4(gx, gy, gz, g.w);
+            r[2] = make_float4(gx + o.x, gy + o.y, gz + o.z, o.w);
         }
         __syncthreads();
+
+        // the next item's descriptor (its index arrived during the last item)
+        if (t == 0 && next_idx < n_items) next_item = a.items[next_idx];
 
         // ---- 2. forward, one (or 2 / 4) threads per query
-        if (n > 64) forward_phase<MODE, DQ, 1>(a, skA, skB, sq0, sq1, start, n, nc, orig, loss_acc, abs_acc);
-        else if (n > 32) forward_phase<MODE, DQ, 2>(a, skA, skB, sq0, sq1, start, n, nc, orig, loss_acc, abs_acc);
-        else forward_phase<MODE, DQ, 4>(a, skA, skB, sq0, sq1, start, n, nc, orig, loss_acc, abs_acc);
+        if (full) {
+            if (n > 64) forward_phase<MODE, DQ, 1, true>(a, rec, qt, qB, start, n, nc, orig, h, loss_acc, abs_acc);
+            else if (n > 32) forward_phase<MODE, DQ, 2, true>(a, rec, qt, qB, start, n, nc, orig, h, loss_acc, abs_acc);
+            else forward_phase<MODE, DQ, 4, true>(a, rec, qt, qB, start, n, nc, orig, h, loss_acc, abs_acc);
+        } else {
+            if (n > 64) forward_phase<MODE, DQ, 1, false>(a, rec, qt, qB, start, n, nc, orig, h, loss_acc, abs_acc);
+            else if (n > 32) forward_phase<MODE, DQ, 2, false>(a, rec, qt, qB, start, n, nc, orig, h, loss_acc, abs_acc);
+            else forward_phase<MODE, DQ, 4, false>(a, rec, qt, qB, start, n, nc, orig, h, loss_acc, abs_acc);
+        }
 
-        if (MODE == FORWARD) continue;
-
-        // ---- 3. backward, one thread per key
-        __syncthreads();
-        const int c = t & (kCentres - 1);
-        if (c < nc) {
-            const bool offset = t >= kCentres;
-            const float4 A = skA[t], B = skB[t];
-            float acc[8];
-            if (offset) bwd_key_loop<true>(A, B, sq0, sq1, n, acc);
-            else bwd_key_loop<false>(A, B, sq0, sq1, n, acc);
-            const int oz = c % nz, oy = (c / nz) % ny, ox = c / (ny * nz);
-            float *gr = a.grad + (((size_t)(lox + ox) * R + (loy + oy)) * R + (loz + oz)) * kSlots;
-            const float beta = -A.w * kLn2;
-            if (!offset) {
-                atomicAdd(gr + 5, acc[0]);
-                atomicAdd(gr + 6, acc[1]);
-                atomicAdd(gr + 7, acc[2]);
-                atomicAdd(gr + 8, acc[3]);
-                atomicAdd(gr + 3, -beta * acc[4]);
+        // ---- prefetch the next item into the other buffer (free: every
+        // thread has finished the item before), and fetch the index after it
+        if (t == 0) {
+            s_item[buf ^ 1] = next_idx;
+            if (next_idx < n_items) {
+                s_meta[buf ^ 1] = next_item;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_item(a, next_item, s_rec[buf ^ 1], s_qt[buf ^ 1], &s_bar[buf ^ 1]);
+                next_idx = atomicAdd(&a.ctrl->next_item, 1);   // consumed one item later
             } else {
-                atomicAdd(gr + 9, acc[0]);
-                atomicAdd(gr + 10, acc[1]);
-                atomicAdd(gr + 11, acc[2]);
-                atomicAdd(gr + 12, acc[3]);
-                atomicAdd(gr + 4, -beta * acc[4]);
-                // dO/dDelta = w (-d' + 2 beta' (q - key)(f' - O))
-                atomicAdd(gr + 0, fmaf(-B.y, acc[0], 2.f * beta * acc[5]));
-                atomicAdd(gr + 1, fmaf(-B.z, acc[0], 2.f * beta * acc[6]));
-                atomicAdd(gr + 2, fmaf(-B.w, acc[0], 2.f * beta * acc[7]));
+                mbar_arrive(&s_bar[buf ^ 1]);
             }
         }
+
+        if (MODE != FORWARD) {
+            // ---- 3. backward, one thread per key
+            __syncthreads();
+            const int c = t & (kCentres - 1);
+            if (c < nc) {
+                const bool offset = t >= kCentres;
+                const float4 A = keyA(rec, offset, c), B = keyB(rec, offset, c);
+                float acc[8];
+                if (offset) bwd_key_loop<true>(A, B, qt, qB, n, acc);
+                else bwd_key_loop<false>(A, B, qt, qB, n, acc);
+                int ox, oy, oz;
+                if (full) {
+                    ox = c >> 4; oy = (c >> 2) & 3; oz = c & 3;
+                } else {
+                    oz = c % w.nz; oy = (c / w.nz) % w.ny; ox = c / (w.ny * w.nz);
+                }
+                float *gr = a.grad + (((size_t)(w.lox + ox) * R + (w.loy + oy)) * R + (w.loz + oz)) * kSlots;
+                const float beta = -A.w * kLn2;
+                if (!offset) {
+                    atomicAdd(gr + 5, acc[0]);
+                    atomicAdd(gr + 6, acc[1]);
+                    atomicAdd(gr + 7, acc[2]);
+                    atomicAdd(gr + 8, acc[3]);
+                    atomicAdd(gr + 3, -beta * acc[4]);
+                } else {
+                    atomicAdd(gr + 9, acc[0]);
+                    atomicAdd(gr + 10, acc[1]);
+                    atomicAdd(gr + 11, acc[2]);
+                    atomicAdd(gr + 12, acc[3]);
+                    atomicAdd(gr + 4, -beta * acc[4]);
+                    // dO/dDelta = w (-d' + 2 beta' (q - key)(f' - O))
+                    atomicAdd(gr + 0, fmaf(-B.y, acc[0], 2.f * beta * acc[5]));
+                    atomicAdd(gr + 1, fmaf(-B.z, acc[0], 2.f * beta * acc[6]));
+                    atomicAdd(gr + 2, fmaf(-B.w, acc[0], 2.f * beta * acc[7]));
+                }
+            }
+        }
+        // order this thread's shared-memory accesses of the buffer before the
+        // bulk copy that will refill it two items later
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        ++uses;
+        buf ^= 1;
     }
 
     if (MODE == FIT) {
@@ -375,9 +621,9 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(FusedArgs a)
         __syncthreads();
         if (t == 0) {
             double l = 0.0, ab = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) {
-                l += s_red[0][w];
-                ab += s_red[1][w];
+            for (int wi = 0; wi < kThreads / 32; ++wi) {
+                l += s_red[0][wi];
+                ab += s_red[1][wi];
             }
             atomicAdd(&a.ctrl->loss_sum, l);
             atomicAdd(&a.ctrl->abs_sum, ab);
