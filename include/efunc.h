@@ -59,8 +59,7 @@ typedef enum {
     EFUNC_ERR_CUDA = 2,        /* a CUDA runtime call failed */
     EFUNC_ERR_WORKSPACE = 3,   /* workspace NULL, misaligned or too small */
     EFUNC_ERR_NONFINITE = 4,   /* a hyper-parameter is NaN or infinite */
-    EFUNC_ERR_UNSUPPORTED = 5, /* valid request outside the implemented set */
-    EFUNC_ERR_TIMEOUT = 6      /* a bounded wait inside a kernel expired (see efunc_workspace_status) */
+    EFUNC_ERR_UNSUPPORTED = 5  /* valid request outside the implemented set */
 } efunc_status;
 
 /* Grid description.  R in [1, 256]; W must be 2; log_beta0 is the log-scale
@@ -163,14 +162,6 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
                        float *m, float *v, const float *qo, int64_t J, int32_t n_batches, int32_t steps,
                        int64_t step0, float *stats, void *workspace, size_t workspace_bytes,
                        efunc_stream_t stream);
-
-/* Synchronises `stream` and reports whether a kernel of the last forward,
- * backward or fit call that used this workspace gave up a bounded wait
- * (EFUNC_ERR_TIMEOUT; the kernel then stopped early and its outputs are
- * incomplete).  Every wait of the fused kernel on its TMA copies is bounded
- * by about a second; in correct operation none expires.  efunc_fit with host
- * statistics performs this check itself. */
-efunc_status efunc_workspace_status(const void *workspace, efunc_stream_t stream);
 
 /* Forward without any device allocation by the caller.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate

@@ -17,7 +17,7 @@ c_size_t, c_void_p, c_char_p = ctypes.c_size_t, ctypes.c_void_p, ctypes.c_char_p
 P_float = ctypes.POINTER(ctypes.c_float)
 
 STATUS = {0: "EFUNC_OK", 1: "EFUNC_ERR_ARG", 2: "EFUNC_ERR_CUDA", 3: "EFUNC_ERR_WORKSPACE",
-          4: "EFUNC_ERR_NONFINITE", 5: "EFUNC_ERR_UNSUPPORTED", 6: "EFUNC_ERR_TIMEOUT"}
+          4: "EFUNC_ERR_NONFINITE", 5: "EFUNC_ERR_UNSUPPORTED"}
 LOSS_L1, LOSS_MSE = 0, 1
 
 
@@ -46,7 +46,6 @@ SIGNATURES = {
                                   c_void_p]),
     "efunc_fit": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Adam), c_int32, c_void_p, c_void_p, c_void_p,
                             c_void_p, c_int64, c_int32, c_int32, c_int64, c_void_p, c_void_p, c_size_t, c_void_p]),
-    "efunc_workspace_status": (c_int32, [c_void_p, c_void_p]),
     "efunc_forward_noalloc": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_void_p, c_int64, c_int32, c_void_p,
                                         c_void_p, c_void_p, c_void_p]),
     "efunc_profile_enable": (None, [c_int32]),

@@ -28,9 +28,6 @@ struct Ctrl {
     int pad[2];
     double loss_sum;    // sum over queries of |O-o| (L1) or (O-o)^2 (MSE)
     double abs_sum;     // sum over queries of |O-o|
-    // cleared once per ABI call, not per sort
-    int error;          // nonzero: a bounded wait of the fused kernel expired
-    int pad2[3];
 };
 
 struct Layout {

@@ -156,7 +156,7 @@ struct Views {
 cudaError_t sort_into(const Views &v, int R, const float *q, int64_t J, int q_stride, float4 *sorted, int *perm,
                       cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(v.ctrl(), 0, offsetof(Ctrl, error), s);
+    cudaError_t e = cudaMemsetAsync(v.ctrl(), 0, sizeof(Ctrl), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(v.hist(), 0, (size_t)v.L.nbins * 4, s);
     if (e != cudaSuccess) return e;
@@ -186,11 +186,6 @@ cudaError_t pack_keys(const Views &v, const efunc_grid *g, const float *params, 
     p.R = g->R;
     p.log_beta0 = (double)g->log_beta0;
     return launch_pack_keys(p, s);
-}
-
-cudaError_t clear_error(const Views &v, cudaStream_t s)
-{
-    return cudaMemsetAsync(&v.ctrl()->error, 0, sizeof(int), s);
 }
 
 FusedArgs fused_args(const Views &v, const efunc_grid *g)
@@ -274,7 +269,6 @@ const char *efunc_status_str(efunc_status s)
     case EFUNC_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
     case EFUNC_ERR_NONFINITE: return "non-finite hyper-parameter";
     case EFUNC_ERR_UNSUPPORTED: return "unsupported configuration";
-    case EFUNC_ERR_TIMEOUT: return "a bounded wait inside a kernel expired";
     }
     return "unknown status";
 }
@@ -311,8 +305,7 @@ efunc_status efunc_forward(const efunc_grid *grid, const float *params, const fl
     if ((st = check_workspace(grid, J, workspace, workspace_bytes))) return st;
     cudaStream_t s = (cudaStream_t)stream;
     Views v{make_layout(grid->R, J), static_cast<char *>(workspace)};
-    cudaError_t e = clear_error(v, s);
-    if (e == cudaSuccess) e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
+    cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
     if (e == cudaSuccess) e = pack_keys(v, grid, params, s);
     if (e != cudaSuccess) return EFUNC_ERR_CUDA;
     FusedArgs f = fused_args(v, grid);
@@ -334,8 +327,7 @@ efunc_status efunc_backward(const efunc_grid *grid, const float *params, const f
     if ((st = check_workspace(grid, J, workspace, workspace_bytes))) return st;
     cudaStream_t s = (cudaStream_t)stream;
     Views v{make_layout(grid->R, J), static_cast<char *>(workspace)};
-    cudaError_t e = clear_error(v, s);
-    if (e == cudaSuccess) e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
+    cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
     if (e == cudaSuccess) e = pack_keys(v, grid, params, s);
     if (e != cudaSuccess) return EFUNC_ERR_CUDA;
     FusedArgs f = fused_args(v, grid);
@@ -380,7 +372,6 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
     static_assert(sizeof(Ctrl) <= 64, "control block must leave room for the statistics slot");
 
     cudaError_t e = cudaMemsetAsync(grad, 0, (size_t)n * 4, s);
-    if (e == cudaSuccess) e = clear_error(vw, s);
     if (e != cudaSuccess) return EFUNC_ERR_CUDA;
     const int grid_blocks = fused_grid_size();
     for (int32_t it = 0; it < steps; ++it) {
@@ -391,7 +382,8 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
             if (e != cudaSuccess) return EFUNC_ERR_CUDA;
             qdev = reinterpret_cast<const float *>(vw.stage());
         }
-        e = sort_into(vw, grid->R, qdev, J, 4, vw.sorted(), vw.perm(), s);
+        // the fit reduces over queries: no permutation back to the caller's order
+        e = sort_into(vw, grid->R, qdev, J, 4, vw.sorted(), nullptr, s);
         if (e == cudaSuccess) e = pack_keys(vw, grid, params, s);
         if (e != cudaSuccess) return EFUNC_ERR_CUDA;
         FusedArgs f = fused_args(vw, grid);
@@ -411,19 +403,8 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
             if (e != cudaSuccess) return EFUNC_ERR_CUDA;
         }
     }
-    if (stats_host) return efunc_workspace_status(workspace, stream);
+    if (stats_host && cudaStreamSynchronize(s) != cudaSuccess) return EFUNC_ERR_CUDA;
     return EFUNC_OK;
-}
-
-efunc_status efunc_workspace_status(const void *workspace, efunc_stream_t stream)
-{
-    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return EFUNC_ERR_WORKSPACE;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return EFUNC_ERR_CUDA;
-    int err = 0;
-    const char *p = static_cast<const char *>(workspace) + offsetof(Ctrl, error);   // control block at offset 0
-    if (cudaMemcpy(&err, p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return EFUNC_ERR_CUDA;
-    return err ? EFUNC_ERR_TIMEOUT : EFUNC_OK;
 }
 
 void efunc_profile_enable(int32_t enable)

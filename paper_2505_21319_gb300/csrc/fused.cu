@@ -6,11 +6,10 @@
 // i.e. the same 128 keys (64 grid keys k_i and 64 offset keys k_i + Delta_i,
 // one softmax over their union, Eq. func-offset).  A persistent CTA of 128
 // threads takes items from a device counter and, per item:
-//   1. receives the item's query tile and the window's key records in shared
-//      memory through TMA bulk copies (cp.async.bulk + mbarrier) issued while
-//      the previous item was being computed (two buffers), then rewrites the
-//      key positions into window-local coordinates (origin at the centre of
-//      index c, the window base; queries are shifted into the same frame);
+//   1. stages the item's query tile and the window's key records (L2-resident,
+//      64 bytes per centre) in shared memory, key positions rewritten into
+//      window-local coordinates (origin at the centre of index c, the window
+//      base; queries are shifted into the same frame);
 //   2. forward, thread per query (2 or 4 threads per query for sparse cells):
 //      e = sum 2^{s}, m = sum 2^{s} f with s = -beta log2(e) ||q - key||^2,
 //      O = m / e, lse2 = log2 e (Algorithm 1 in base 2).  The keys are summed
@@ -25,8 +24,7 @@
 //      issues one FP32 atomic per slot per item.
 // No per-query intermediate leaves the CTA: the only outputs are O / lse /
 // dO/dq (forward), the gradient grid and dL/dq (backward), and the loss sums
-// (fit).  Every wait on a copy is bounded (about a second of clock cycles);
-// on expiry the CTA records an error in the control block and returns.
+// (fit).
 #include "common.cuh"
 
 namespace efunc {
@@ -35,8 +33,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kLn2 = 0.69314718055994531f;
-constexpr int kClasses = 4;                       // interleaved summation classes of the forward
-constexpr long long kWaitCycles = 2000000000ll;   // bound of every copy wait (~1 s)
+constexpr int kClasses = 4;   // interleaved summation classes of the forward
 
 enum Mode { FORWARD = 0, BACKWARD = 1, FIT = 2 };
 
@@ -46,57 +43,6 @@ enum Mode { FORWARD = 0, BACKWARD = 1, FIT = 2 };
 // with positions in window-local coordinates; set 0 = grid keys, 1 = offset keys.
 __device__ __forceinline__ float4 keyA(const float4 *rec, int set, int k) { return rec[4 * k + 2 * set]; }
 __device__ __forceinline__ float4 keyB(const float4 *rec, int set, int k) { return rec[4 * k + 2 * set + 1]; }
-
-// ------------------------------------------------------- TMA / mbarrier
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Waits for phase `parity` of the barrier; false after kWaitCycles.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
-{
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
-    return true;
-}
-
-// Bulk copy global -> shared, completion counted in bytes on the barrier.
-// Addresses 16-byte aligned, size a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
 
 struct Window {
     int cx, cy, cz, lox, loy, loz, nx, ny, nz, nc;
@@ -116,22 +62,6 @@ __device__ __forceinline__ Window window_of(const Item item, int R)
     w.nz = min(w.cz + kW, R - 1) - w.loz + 1;
     w.nc = w.nx * w.ny * w.nz;
     return w;
-}
-
-// One thread: arm the buffer's barrier and copy the item's queries (n x 16 B)
-// and its window's key records (rows of nz centres x 64 B) into shared memory.
-__device__ __forceinline__ void issue_item(const FusedArgs &a, const Item item, float4 *rec, float4 *qt,
-                                           uint64_t *bar)
-{
-    const Window w = window_of(item, a.R);
-    mbar_arrive_expect_tx(bar, (uint32_t)item.y * 16u + (uint32_t)w.nc * 64u);
-    bulk_g2s(qt, a.sorted + item.x, (uint32_t)item.y * 16u, bar);
-    const uint32_t row = (uint32_t)w.nz * 64u;
-    for (int ox = 0; ox < w.nx; ++ox)
-        for (int oy = 0; oy < w.ny; ++oy) {
-            const size_t ci = ((size_t)(w.lox + ox) * a.R + (w.loy + oy)) * a.R + w.loz;
-            bulk_g2s(rec + (size_t)(ox * w.ny + oy) * w.nz * kKeyRecords, a.keys + ci * kKeyRecords, row, bar);
-        }
 }
 
 // --------------------------------------------------------------- pack
@@ -457,14 +387,10 @@ __device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *
 template <int MODE, bool DQ>
 __global__ void __launch_bounds__(kThreads, 8) fused_kernel(FusedArgs a)
 {
-    // Two buffers: item i lands in buffer i & 1 (TMA bulk copies issued during
-    // item i - 1) while item i - 1 is computed from the other buffer.
-    __shared__ __align__(128) float4 s_rec[2][kCentres * kKeyRecords];   // key records
-    __shared__ __align__(128) float4 s_qt[2][kChunk];                      // query tile
-    __shared__ __align__(16) float4 s_sqB[2][MODE == FORWARD ? 1 : kChunk / 2];
-    __shared__ __align__(8) uint64_t s_bar[2];
-    __shared__ Item s_meta[2];
-    __shared__ int s_item[2];
+    __shared__ float4 s_rec[kCentres * kKeyRecords];          // key records of the window
+    __shared__ float4 s_qt[kChunk];                           // query tile
+    __shared__ float4 s_sqB[MODE == FORWARD ? 1 : kChunk / 2];
+    __shared__ int s_item;
     __shared__ float s_red[2][kThreads / 32];
 
     const int t = threadIdx.x;
@@ -474,70 +400,36 @@ __global__ void __launch_bounds__(kThreads, 8) fused_kernel(FusedArgs a)
     const int n_items = a.ctrl->n_items;
     float loss_acc = 0.f, abs_acc = 0.f;
 
-    // Thread 0 runs the item pipeline one item ahead, keeping every latency
-    // behind compute: the next index is fetched during the previous item,
-    // its descriptor is loaded before the forward, the bulk copies into the
-    // free buffer are issued after it (s_item >= n_items with a bare arrive
-    // means "no more items").
-    int next_idx = 0;
-    Item next_item = make_int4(0, 0, 0, 0);
-    if (t == 0) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        const int first = atomicAdd(&a.ctrl->next_item, 1);
-        s_item[0] = first;
-        if (first < n_items) {
-            const Item it0 = a.items[first];
-            s_meta[0] = it0;
-            issue_item(a, it0, s_rec[0], s_qt[0], &s_bar[0]);
-        } else {
-            mbar_arrive(&s_bar[0]);
-        }
-        next_idx = atomicAdd(&a.ctrl->next_item, 1);
-    }
-    __syncthreads();   // barriers initialised
-    int buf = 0;
-    uint32_t uses = 0;   // items started; parity of buffer b's next phase = (uses >> 1) & 1
     for (;;) {
-        // ---- 1. wait for the item's tiles, then localise the key positions
-        const bool ok = mbar_wait_bounded(&s_bar[buf], (uses >> 1) & 1);
-        const int it = s_item[buf];
-        if (__syncthreads_or(!ok)) {
-            // a copy did not land in time: record it, let in-flight copies
-            // drain (bounded), leave
-            if (t == 0) {
-                atomicOr(&a.ctrl->error, 1);
-                mbar_wait_bounded(&s_bar[buf], (uses >> 1) & 1);
-            }
-            break;
-        }
+        __syncthreads();   // the previous item is consumed
+        if (t == 0) s_item = atomicAdd(&a.ctrl->next_item, 1);
+        __syncthreads();
+        const int it = s_item;
         if (it >= n_items) break;
-        const Item item = s_meta[buf];
+        const Item item = a.items[it];
         const Window w = window_of(item, R);
         const int start = item.x, n = item.y, nc = w.nc;
         const bool full = nc == kCentres;
-        float4 *rec = s_rec[buf], *qt = s_qt[buf], *qB = s_sqB[buf];
+        float4 *rec = s_rec, *qt = s_qt, *qB = s_sqB;
         const float3 orig = make_float3((float)(2 * w.cx + 1 - R) * invR, (float)(2 * w.cy + 1 - R) * invR,
                                         (float)(2 * w.cz + 1 - R) * invR);
+        // ---- 1. stage the key records (positions made window-local) and queries
         if (t < nc) {
             int ox, oy, oz;
-            if (full) {
-                ox = t >> 4; oy = (t >> 2) & 3; oz = t & 3;
-            } else {
-                oz = t % w.nz; oy = (t / w.nz) % w.ny; ox = t / (w.ny * w.nz);
-            }
+            if (full) { ox = t >> 4; oy = (t >> 2) & 3; oz = t & 3; }
+            else { oz = t % w.nz; oy = (t / w.nz) % w.ny; ox = t / (w.ny * w.nz); }
+            const float4 *k = a.keys + (((size_t)(w.lox + ox) * R + (w.loy + oy)) * R + (w.loz + oz)) * kKeyRecords;
             const float gx = (float)(2 * (w.lox + ox - w.cx)) * invR, gy = (float)(2 * (w.loy + oy - w.cy)) * invR,
                         gz = (float)(2 * (w.loz + oz - w.cz)) * invR;
+            const float4 g = k[0], o = k[2];
             float4 *r = rec + 4 * t;
-            const float4 g = r[0], o = r[2];
             r[0] = make_float4(gx, gy, gz, g.w);
+            r[1] = k[1];
             r[2] = make_float4(gx + o.x, gy + o.y, gz + o.z, o.w);
+            r[3] = k[3];
         }
+        for (int qi = t; qi < n; qi += kThreads) qt[qi] = a.sorted[start + qi];
         __syncthreads();
-
-        // the next item's descriptor (its index arrived during the last item)
-        if (t == 0 && next_idx < n_items) next_item = a.items[next_idx];
 
         // ---- 2. forward, one (or 2 / 4) threads per query
         if (full) {
@@ -549,21 +441,6 @@ __global__ void __launch_bounds__(kThreads, 8) fused_kernel(FusedArgs a)
             else if (n > 32) forward_phase<MODE, DQ, 2, false>(a, rec, qt, qB, start, n, nc, orig, h, loss_acc, abs_acc);
             else forward_phase<MODE, DQ, 4, false>(a, rec, qt, qB, start, n, nc, orig, h, loss_acc, abs_acc);
         }
-
-        // ---- prefetch the next item into the other buffer (free: every
-        // thread has finished the item before), and fetch the index after it
-        if (t == 0) {
-            s_item[buf ^ 1] = next_idx;
-            if (next_idx < n_items) {
-                s_meta[buf ^ 1] = next_item;
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue_item(a, next_item, s_rec[buf ^ 1], s_qt[buf ^ 1], &s_bar[buf ^ 1]);
-                next_idx = atomicAdd(&a.ctrl->next_item, 1);   // consumed one item later
-            } else {
-                mbar_arrive(&s_bar[buf ^ 1]);
-            }
-        }
-
         if (MODE != FORWARD) {
             // ---- 3. backward, one thread per key
             __syncthreads();
@@ -575,11 +452,8 @@ __global__ void __launch_bounds__(kThreads, 8) fused_kernel(FusedArgs a)
                 if (offset) bwd_key_loop<true>(A, B, qt, qB, n, acc);
                 else bwd_key_loop<false>(A, B, qt, qB, n, acc);
                 int ox, oy, oz;
-                if (full) {
-                    ox = c >> 4; oy = (c >> 2) & 3; oz = c & 3;
-                } else {
-                    oz = c % w.nz; oy = (c / w.nz) % w.ny; ox = c / (w.ny * w.nz);
-                }
+                    if (full) { ox = c >> 4; oy = (c >> 2) & 3; oz = c & 3; }
+                else { oz = c % w.nz; oy = (c / w.nz) % w.ny; ox = c / (w.ny * w.nz); }
                 float *gr = a.grad + (((size_t)(w.lox + ox) * R + (w.loy + oy)) * R + (w.loz + oz)) * kSlots;
                 const float beta = -A.w * kLn2;
                 if (!offset) {
@@ -601,11 +475,6 @@ __global__ void __launch_bounds__(kThreads, 8) fused_kernel(FusedArgs a)
                 }
             }
         }
-        // order this thread's shared-memory accesses of the buffer before the
-        // bulk copy that will refill it two items later
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        ++uses;
-        buf ^= 1;
     }
 
     if (MODE == FIT) {

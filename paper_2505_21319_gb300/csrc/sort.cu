@@ -4,11 +4,13 @@
 // cell whose 4x4x4 centre window the query blends), so that all queries of a
 // bin share one window.  Bins are ordered in 4x4x4 bricks (row-major) with
 // Morton order inside a brick.  A counting sort:
-//   bin      histogram with warp-aggregated atomics; each query keeps its
-//            arrival rank inside its bin
+//   bin      histogram by atomics; each query keeps its arrival rank inside
+//            its bin (batches arrive in random order, so lanes of a warp rarely
+//            share a bin and warp aggregation would not pay)
 //   scan     exclusive scan of (count, work items) pairs over all bins
 //            (reduce per block / scan of block sums / scan + emit)
 //   scatter  query -> position offset[bin] + rank: float4 row + permutation
+//            (the permutation only when a caller needs outputs in its order)
 // The scan also emits the work items of the fused kernel: every non-empty bin
 // yields ceil(count / kChunk) slices of at most kChunk sorted queries.
 #include "common.cuh"
@@ -47,25 +49,11 @@ template <bool VEC4>
 __global__ void __launch_bounds__(256) bin_kernel(SortArgs a)
 {
     const float half_r = (float)a.R * 0.5f, rmax = (float)(a.R - 1);
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t j0 = warp * 32; j0 < a.J; j0 += nwarps * 32) {
-        const int64_t j = j0 + lane;
-        const bool valid = j < a.J;
-        const unsigned mask = __ballot_sync(kFull, valid);
-        if (!valid) continue;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.J; j += stride) {
         float x, y, z, w;
         load_query(a.q, j, a.q_stride, VEC4, x, y, z, w);
-        const uint32_t bin = query_bin(x, y, z, half_r, rmax, a.P);
-        // warp-aggregated increment: one atomic per distinct bin in the warp
-        const unsigned peers = __match_any_sync(mask, bin);
-        const int leader = __ffs(peers) - 1;
-        const unsigned below = peers & ((1u << lane) - 1u);
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(&a.hist[bin], (uint32_t)__popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        a.rank[j] = base + (uint32_t)__popc(below);
+        a.rank[j] = atomicAdd(&a.hist[query_bin(x, y, z, half_r, rmax, a.P)], 1u);
     }
 }
 
@@ -175,7 +163,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(SortArgs a)
         const uint32_t bin = query_bin(x, y, z, half_r, rmax, a.P);
         const uint32_t pos = a.hist[bin] + a.rank[j];
         a.sorted[pos] = make_float4(x, y, z, w);
-        a.perm[pos] = (int)j;
+        if (a.perm) a.perm[pos] = (int)j;
     }
 }
 
