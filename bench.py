@@ -351,24 +351,22 @@ def main():
     achieved = ops_per_launch / (avg_fused * 1e-3) / 1e12
     clocks = clk.summary()
 
-    # ---- end to end through the C ABI with host buffers
+    # ---- end to end through the C ABI with host buffers: the batch pool in
+    # pinned host memory, every step copies its 64 MiB batch to the device
+    # (overlapped with the previous step's compute by the library) and copies
+    # its (loss, MAE) pair back to pinned host memory
     e2e = None
     if args.e2e_steps > 0:
         host_pool = torch.from_numpy(pool_np).pin_memory()
-        host_stats = torch.zeros(2, dtype=torch.float32).pin_memory()
-        for s in range(3):
-            api.efunc_fit(params, m, v, host_pool, steps=1, J=J, n_batches=N_BATCHES, step0=10 ** 6 + s,
-                          stats=host_stats, lr=LR, ws=ws_buf)
+        host_stats = torch.zeros(2 * args.e2e_steps, dtype=torch.float32).pin_memory()
+        api.efunc_fit(params, m, v, host_pool, steps=3, J=J, n_batches=N_BATCHES, step0=10 ** 6,
+                      stats=host_stats, lr=LR, ws=ws_buf)
         torch.cuda.synchronize(dev)
         if ws > 1:
             dist.barrier()
         t0 = time.perf_counter()
-        for s in range(args.e2e_steps):
-            # one step per call: batch s mod 3 copied from pinned memory, (loss, MAE) read back
-            off = (s % N_BATCHES) * J
-            api.efunc_fit(params, m, v, host_pool[off:off + J], steps=1, J=J, n_batches=1,
-                          step0=2 * 10 ** 6 + s, stats=host_stats, lr=LR, ws=ws_buf)
-        torch.cuda.synchronize(dev)
+        api.efunc_fit(params, m, v, host_pool, steps=args.e2e_steps, J=J, n_batches=N_BATCHES, step0=2 * 10 ** 6,
+                      stats=host_stats, lr=LR, ws=ws_buf)   # returns after the last statistics reached the host
         dt = time.perf_counter() - t0
         dt = max_over_ranks(dt, dev)
         e2e = {"value": J * ws * args.e2e_steps / dt, "unit": "query-pts/s", "h2d_bytes_per_step": J * 16,

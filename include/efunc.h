@@ -152,8 +152,11 @@ efunc_status efunc_adam_step(const efunc_adam *adam, int64_t n, float *params, f
  *   loss     EFUNC_LOSS_L1 (dL/dO = sign(O - o)/J, sign(0) = 0) or
  *            EFUNC_LOSS_MSE (Eq. loss, 2(O - o)/J)
  *   params, m, v  [device] R^3*13 floats each, updated
- *   qo       [host|device] n_batches*J*4 floats.  Host memory (pinned for
- *            overlap) is copied to the device inside every step.
+ *   qo       [host|device] n_batches*J*4 floats.  Host memory is copied
+ *            to the device inside every step; the copy of batch s+1 runs on
+ *            a copy stream of the library (created on the first such call on
+ *            a device) while batch s is computed, so with pinned memory the
+ *            copies overlap the computation.
  *   stats    [host|device] steps*2 floats or NULL: (loss, mean |O - o|) of
  *            every step, evaluated at the parameters before that step's
  *            update.  If stats is host memory the call synchronises the
@@ -174,7 +177,7 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
  * keeps it until the process exits).
  *   - Limit: requests whose efunc_workspace_bytes(grid, J) exceeds 32 MiB
  *     return EFUNC_ERR_WORKSPACE with nothing enqueued.  That admits up to
- *     719,360 queries at R = 32, 821,680 at R = 16 and 33,648 at R = 64;
+ *     514,048 queries at R = 32, 587,168 at R = 16 and 26,176 at R = 64;
  *     larger grids need efunc_forward with a caller workspace.
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device current); make that first call before

@@ -106,7 +106,7 @@ Layout make_layout(int R, int64_t J)
     L.items = off;     off = align_up(off + (size_t)L.max_items * 16, A);
     L.keys = off;      off = align_up(off + (size_t)R * R * R * kKeyRecords * 16, A);
     L.grad = off;      off = align_up(off + (size_t)R * R * R * kSlots * 4, A);
-    L.stage = off;     off = align_up(off + (size_t)J * 16, A);
+    L.stage = off;     off = align_up(off + (size_t)J * 32, A);   // two host-batch staging buffers
     L.total = off;
     return L;
 }
@@ -148,7 +148,8 @@ struct Views {
     Item *items() const { return reinterpret_cast<Item *>(base + L.items); }
     float4 *keys() const { return reinterpret_cast<float4 *>(base + L.keys); }
     float *grad() const { return reinterpret_cast<float *>(base + L.grad); }
-    float4 *stage() const { return reinterpret_cast<float4 *>(base + L.stage); }
+    // staging buffer b (0 or 1) of a host batch: J rows of 4 floats each
+    float4 *stage(int b, int64_t J) const { return reinterpret_cast<float4 *>(base + L.stage) + (size_t)b * (size_t)J; }
 };
 
 // Clears the control block and histogram, then sorts q into the workspace
@@ -198,6 +199,39 @@ FusedArgs fused_args(const Views &v, const efunc_grid *g)
     f.items = v.items();
     f.ctrl = v.ctrl();
     return f;
+}
+
+// Per-device copy stream and events that overlap the host->device copy of
+// batch s+1 with the computation of batch s in efunc_fit.  Created on the
+// first fit from host memory on a device and kept for the process.
+struct CopyPipe {
+    bool ready = false;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr};
+    cudaEvent_t freed[2] = {nullptr, nullptr};
+};
+constexpr int kMaxPipes = 64;
+std::mutex g_pipe_mu;
+CopyPipe g_pipes[kMaxPipes];
+
+cudaError_t copy_pipe(CopyPipe **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxPipes) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    CopyPipe &p = g_pipes[dev];
+    if (!p.ready) {
+        if ((e = cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        for (int b = 0; b < 2; ++b) {
+            if ((e = cudaEventCreateWithFlags(&p.copied[b], cudaEventDisableTiming)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&p.freed[b], cudaEventDisableTiming)) != cudaSuccess) return e;
+        }
+        p.ready = true;
+    }
+    *out = &p;
+    return cudaSuccess;
 }
 
 bool is_host_pointer(const void *p)
@@ -374,16 +408,37 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
     cudaError_t e = cudaMemsetAsync(grad, 0, (size_t)n * 4, s);
     if (e != cudaSuccess) return EFUNC_ERR_CUDA;
     const int grid_blocks = fused_grid_size();
+    const size_t batch_bytes = (size_t)J * 16;
+    auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * (size_t)J * 4; };
+
+    // Host batches: copies run on the library's copy stream into two staging
+    // buffers, batch it+1 landing while batch it is computed.
+    CopyPipe *pipe = nullptr;
+    if (q_host) {
+        if (copy_pipe(&pipe) != cudaSuccess) return EFUNC_ERR_CUDA;
+        for (int b = 0; b < 2; ++b)   // buffers free once the caller's earlier work is done
+            if (cudaEventRecord(pipe->freed[b], s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (cudaStreamWaitEvent(pipe->stream, pipe->freed[0], 0) != cudaSuccess ||
+            cudaMemcpyAsync(vw.stage(0, J), batch(0), batch_bytes, cudaMemcpyHostToDevice, pipe->stream) != cudaSuccess ||
+            cudaEventRecord(pipe->copied[0], pipe->stream) != cudaSuccess)
+            return EFUNC_ERR_CUDA;
+    }
     for (int32_t it = 0; it < steps; ++it) {
-        const float *src = qo + (size_t)(it % n_batches) * (size_t)J * 4;
-        const float *qdev = src;
+        const int b = it & 1;
+        const float *qdev = batch(it);
         if (q_host) {
-            e = cudaMemcpyAsync(vw.stage(), src, (size_t)J * 16, cudaMemcpyHostToDevice, s);
-            if (e != cudaSuccess) return EFUNC_ERR_CUDA;
-            qdev = reinterpret_cast<const float *>(vw.stage());
+            if (it + 1 < steps &&
+                (cudaStreamWaitEvent(pipe->stream, pipe->freed[b ^ 1], 0) != cudaSuccess ||
+                 cudaMemcpyAsync(vw.stage(b ^ 1, J), batch(it + 1), batch_bytes, cudaMemcpyHostToDevice,
+                                 pipe->stream) != cudaSuccess ||
+                 cudaEventRecord(pipe->copied[b ^ 1], pipe->stream) != cudaSuccess))
+                return EFUNC_ERR_CUDA;
+            if (cudaStreamWaitEvent(s, pipe->copied[b], 0) != cudaSuccess) return EFUNC_ERR_CUDA;
+            qdev = reinterpret_cast<const float *>(vw.stage(b, J));
         }
         // the fit reduces over queries: no permutation back to the caller's order
         e = sort_into(vw, grid->R, qdev, J, 4, vw.sorted(), nullptr, s);
+        if (e == cudaSuccess && q_host) e = cudaEventRecord(pipe->freed[b], s);   // staging buffer consumed
         if (e == cudaSuccess) e = pack_keys(vw, grid, params, s);
         if (e != cudaSuccess) return EFUNC_ERR_CUDA;
         FusedArgs f = fused_args(vw, grid);
