@@ -46,10 +46,14 @@ N_BATCHES = 3
 LR = 1e-3
 # Algorithmic FP32 operations per (query, centre) of the fused fit step:
 # forward 12 per key (difference 3, squared distance 3, scale 1, value 3,
-# two accumulations 2) for both keys of the centre, backward 18 for the grid
-# key and 21 for the offset key (recomputed difference, distance, exponent,
-# weight times dL/dO, value, residual, and the 5 / 8 gradient sums).
-OPS_PER_CENTRE = 2 * 12 + 18 + 21
+# two accumulations 2), backward 18 for the grid key and 21 for the offset
+# key (recomputed difference, distance, exponent, weight times dL/dO, value,
+# residual, and the 5 / 8 gradient sums).  In an interior (full 4x4x4)
+# window the grid keys sit on the lattice, so their forward needs 7 (the
+# squared distance from per-axis terms formed once per query: 24 operations).
+OPS_PER_CENTRE = 12 + 12 + 18 + 21
+OPS_PER_CENTRE_FULL = 7 + 12 + 18 + 21
+OPS_PER_QUERY_FULL_SETUP = 24
 EX2_PER_CENTRE = 4
 FP32_LANES_PER_SM = 128
 WORKLOAD = "C2 plain fit: 32^3x13 FP32 grid, 2^22 queries/step (50% uniform, 50% surface+N(0,0.01^2)), " \
@@ -95,6 +99,14 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def algorithmic_ops(q: np.ndarray, R: int) -> float:
+    """Exact algorithmic FP32 operations of one fused fit launch over the batch q."""
+    nc = centres_per_query(q, R)
+    full = nc == 64
+    return float(full.sum()) * (64 * OPS_PER_CENTRE_FULL + OPS_PER_QUERY_FULL_SETUP) + \
+        float(nc[~full].sum()) * OPS_PER_CENTRE
 
 
 def centres_per_query(q: np.ndarray, R: int) -> np.ndarray:
@@ -335,10 +347,7 @@ def main():
     st = stats.view(-1, 2).cpu().numpy()
 
     # ---- roofline of the fused kernel (ALU bound)
-    ops_per_launch = 0.0
-    for b in range(N_BATCHES):
-        nc = centres_per_query(pool_np[b * J:(b + 1) * J], R).astype(np.float64)
-        ops_per_launch += nc.sum() * OPS_PER_CENTRE / N_BATCHES
+    ops_per_launch = sum(algorithmic_ops(pool_np[b * J:(b + 1) * J], R) for b in range(N_BATCHES)) / N_BATCHES
     props = torch.cuda.get_device_properties(dev)
     sm_max = 2070.0
     try:
