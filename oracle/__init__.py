@@ -57,9 +57,11 @@ def _load():
             lib.ora_forward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp, dp, dp]
             lib.ora_backward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
             lib.ora_forward_global.argtypes = [i32, f64, dp, dp, i64, i32, dp, dp]
+            lib.ora_backward_grad.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
             lib.ora_loss_grad.argtypes = [i32, dp, dp, i64, dp, dp, dp]
             lib.ora_adam.argtypes = [i64, dp, dp, dp, dp, i64, f64, f64, f64, f64, f64, i32]
-            for fn in ("ora_forward", "ora_backward", "ora_forward_global", "ora_loss_grad", "ora_adam"):
+            for fn in ("ora_forward", "ora_backward", "ora_forward_global", "ora_loss_grad", "ora_adam",
+                       "ora_backward_grad"):
                 getattr(lib, fn).restype = None
             _lib = lib
     return _lib
@@ -145,6 +147,32 @@ def backward(params, q, gO, R: int, W: int = 2, log_beta0: float | None = None, 
     _load().ora_backward(R, W, lb, _ptr(params), _ptr(q), J, q.shape[1], _ptr(gO), _ptr(grad), _ptr(gq))
     grad = grad.reshape(R ** 3, NSLOT)
     return (grad, gq) if want_gq else grad
+
+
+def backward_grad(params, q, gO, gG, R: int, W: int = 2, log_beta0: float | None = None):
+    """dL/dtheta (R^3, 13) for L = sum_j gO_j O(q_j) + gG_j . dO/dq(q_j).
+
+    The backward through Eq. func-normal (Sec. 3.2) that a loss on the query
+    gradient needs (the Eikonal condition |dO/dq|^2 = 1); gO or gG may be None."""
+    lb = default_log_beta0(R) if log_beta0 is None else float(log_beta0)
+    params, q = _check(params, q, R)
+    J = q.shape[0]
+    go = None if gO is None else _f64(gO).reshape(-1)
+    gg = None if gG is None else _f64(gG).reshape(J, 3)
+    grad = np.zeros(R ** 3 * NSLOT)
+    _load().ora_backward_grad(R, W, lb, _ptr(params), _ptr(q), J, q.shape[1], _ptr(go), _ptr(gg), _ptr(grad))
+    return grad.reshape(R ** 3, NSLOT)
+
+
+def eikonal_loss_grad(G, weight: float = 1.0):
+    """Eikonal term of Sec. 3.2 in the paper's squared form: weight * mean_j
+    (|G_j|^2 - 1)^2 and its gradient with respect to G (J, 3)."""
+    G = _f64(G).reshape(-1, 3)
+    J = G.shape[0]
+    res = (G ** 2).sum(1) - 1.0
+    loss = weight * float((res ** 2).mean()) if J else 0.0
+    gG = weight * 4.0 * res[:, None] * G / J
+    return loss, gG
 
 
 def forward_global(params, q, R: int, log_beta0: float | None = None):

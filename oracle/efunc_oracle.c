@@ -18,7 +18,8 @@
  *   Forward   (Sec. 3.5, Algorithm 1): e_j = sum_i l, m_j = sum_i l f, O = m/e.
  *   Backward  (Sec. 3.6, Algorithm 2 and the closed-form dO/dk, dO/dbeta,
  *             dO/dphi that follow it).
- *   dO/dq     (Sec. 3.2, Eq. func-normal).
+ *   dO/dq     (Sec. 3.2, Eq. func-normal), and the backward through it (the
+ *             parameter gradient of a loss on dO/dq, e.g. the Eikonal term).
  *   Loss      (Sec. 3.4, Eq. loss: MSE) and the L1 variant.
  *   Adam      (Sec. 3.4 / Sec. 4.2 name Adam / AdamW; torch.optim semantics).
  *
@@ -278,6 +279,91 @@ void ora_backward(int R, int W, double log_beta0, const double *params, const do
                             gr[4] += k.beta * dbeta;
                             for (int x = 0; x < 3; ++x)
                                 gr[x] += gl * (-k.d[x] + 2.0 * k.beta * r[x] * (f - O));
+                        }
+                    }
+    }
+}
+
+/* ------------------------------------------- backward through dO/dq */
+
+/* Gradient of L = sum_j [ gO_j O(q_j) + gG_j . G(q_j) ] with respect to the
+ * parameters, G = dO/dq of Eq. func-normal.  The second term is what a loss
+ * on the query gradient (the Eikonal condition |dO/dq|^2 = 1 of Sec. 3.2, or
+ * a normal-alignment loss) needs.  Derivation (per query, u = gG_j): write
+ * every key's contribution to G as w (a + (f - O) t) with a = d (the value's
+ * linear term), t = ds/dq = -2 beta (q - p), w the softmax weight.  With
+ * h = u.a + (f - O)(u.t), H = u.G = sum w h and T = sum w (u.t), a change of
+ * one key's exponent s, value f, slope a and gradient t gives
+ *   d(u.G) = w { ds [(h - H) - (f - O) T] + df [(u.t) - T] + u.da + (f - O) u.dt }
+ * (the normaliser and O are differentiated through; O changes by
+ * w [ds (f - O) + df]).  Per parameter of a key:
+ *   o:      df = 1
+ *   d:      df = q - p,  da = unit vector
+ *   beta:   ds = -|q - p|^2,  dt = -2 (q - p)        (chain rule to b: * beta)
+ *   key p:  ds = 2 beta (q - p),  df = -d,  dt = 2 beta I   (Delta of offset keys)
+ * gO may be NULL (no value term); gG may be NULL (plain backward).
+ * grad: R^3*13 doubles, ACCUMULATED into. */
+void ora_backward_grad(int R, int W, double log_beta0, const double *params, const double *q, int64_t J,
+                       int q_stride, const double *gO, const double *gG, double *grad)
+{
+    for (int64_t j = 0; j < J; ++j) {
+        const double *qj = q + j * q_stride;
+        double O, lse, G[3];
+        forward_one(params, R, W, log_beta0, qj, &O, &lse, G, NULL, NULL);
+        const double go = gO ? gO[j] : 0.0;
+        const double u[3] = {gG ? gG[3 * j] : 0.0, gG ? gG[3 * j + 1] : 0.0, gG ? gG[3 * j + 2] : 0.0};
+        int lo[3], hi[3];
+        window_range(qj, R, W, lo, hi);
+        double r[3], d2, expo, f;
+        /* V = sum w beta (q - p), T = -2 u.V, H = u.G */
+        double V[3] = {0.0, 0.0, 0.0};
+        for (int a = lo[0]; a <= hi[0]; ++a)
+            for (int b = lo[1]; b <= hi[1]; ++b)
+                for (int c = lo[2]; c <= hi[2]; ++c)
+                    for (int s = 0; s < 2; ++s) {
+                        key_t_ k = make_key(params, R, log_beta0, a, b, c, s);
+                        eval_key(&k, qj, r, &d2, &expo, &f);
+                        double w = exp(expo - lse);
+                        for (int x = 0; x < 3; ++x) V[x] += w * k.beta * r[x];
+                    }
+        const double T = -2.0 * (u[0] * V[0] + u[1] * V[1] + u[2] * V[2]);
+        const double H = u[0] * G[0] + u[1] * G[1] + u[2] * G[2];
+        for (int a = lo[0]; a <= hi[0]; ++a)
+            for (int b = lo[1]; b <= hi[1]; ++b)
+                for (int c = lo[2]; c <= hi[2]; ++c)
+                    for (int s = 0; s < 2; ++s) {
+                        key_t_ k = make_key(params, R, log_beta0, a, b, c, s);
+                        eval_key(&k, qj, r, &d2, &expo, &f);
+                        const double w = exp(expo - lse);
+                        const double dlt = f - O;
+                        double ut = 0.0, ua = 0.0, ur = 0.0;
+                        for (int x = 0; x < 3; ++x) {
+                            ut += u[x] * (-2.0 * k.beta * r[x]);
+                            ua += u[x] * k.d[x];
+                            ur += u[x] * r[x];
+                        }
+                        const double h = ua + dlt * ut;
+                        const double e1 = ut - T;
+                        const double hH = (h - H) - dlt * T;
+                        /* d(u.G) and d O per parameter, then weighted by u / gO */
+                        const double g_o = w * e1 + go * w;
+                        double g_d[3], g_p[3];
+                        for (int x = 0; x < 3; ++x) {
+                            g_d[x] = w * (r[x] * e1 + u[x]) + go * w * r[x];
+                            g_p[x] = w * (2.0 * k.beta * r[x] * hH - k.d[x] * e1 + 2.0 * k.beta * dlt * u[x]) +
+                                     go * w * (-k.d[x] + 2.0 * k.beta * r[x] * dlt);
+                        }
+                        const double g_beta = w * (-d2 * hH - 2.0 * dlt * ur) + go * w * (-d2 * dlt);
+                        double *gr = grad + ((size_t)((size_t)a * R + b) * R + c) * NSLOT;
+                        if (s == 0) {
+                            gr[5] += g_o;
+                            gr[6] += g_d[0]; gr[7] += g_d[1]; gr[8] += g_d[2];
+                            gr[3] += k.beta * g_beta;
+                        } else {
+                            gr[9] += g_o;
+                            gr[10] += g_d[0]; gr[11] += g_d[1]; gr[12] += g_d[2];
+                            gr[4] += k.beta * g_beta;
+                            gr[0] += g_p[0]; gr[1] += g_p[1]; gr[2] += g_p[2];
                         }
                     }
     }

@@ -374,3 +374,64 @@ def test_fit_decreases_mae_on_sphere():
         maes.append(mae)
     assert all(b < a for a, b in zip(maes, maes[1:]))
     assert maes[-1] < 0.75 * maes[0]
+
+
+# ------------------------------------------- backward through dO/dq pins
+
+@pytest.mark.parametrize("R,W", [(3, 3), (6, 2)])
+def test_backward_through_query_gradient_matches_central_differences(R, W):
+    """The parameter gradient of L = sum gO.O + gG.dO/dq (Eq. func-normal
+    differentiated once more) against FP64 central differences of the
+    oracle's dO/dq, itself pinned by finite differences of O, for all 13 slots."""
+    lb = oracle.default_log_beta0(R) - 1.0
+    p = synth.random_params(R, seed=90 + R, delta_scale=0.6, b_scale=0.5).astype(np.float64)
+    rng = synth.rng(91 + R)
+    q = rng.uniform(-0.95, 0.95, (5, 3))
+    if W < R:
+        t = (q + 1) * R / 2 - 0.5
+        frac = t - np.floor(t)
+        q = np.where(np.minimum(frac, 1 - frac) < 1e-3, q + 0.01, q)
+    q = q.astype(np.float32).astype(np.float64)
+    gO = rng.standard_normal(q.shape[0])
+    gG = rng.standard_normal((q.shape[0], 3))
+    grad = oracle.backward_grad(p, q, gO, gG, R, W, lb)
+
+    def L(pp):
+        O, _, G = oracle.forward(pp, q, R, W, lb, want_dq=True)
+        return float(gO @ O + (gG * G).sum())
+
+    touched = np.flatnonzero(np.abs(grad).sum(1) > 0)
+    sel = rng.choice(touched, size=min(8, touched.size), replace=False)
+    an, fd = [], []
+    for i in sel:
+        for s in range(13):
+            hstep = 1e-6 * max(1.0, abs(p[i, s]))
+            pp, pm = p.copy(), p.copy()
+            pp[i, s] += hstep
+            pm[i, s] -= hstep
+            fd.append((L(pp) - L(pm)) / (2 * hstep))
+            an.append(grad[i, s])
+    an, fd = np.array(an), np.array(fd)
+    np.testing.assert_allclose(an, fd, rtol=2e-6, atol=2e-7 * np.abs(an).max())
+
+
+def test_backward_through_query_gradient_reduces_to_plain_backward():
+    """gG = 0 leaves the value term only: Algorithm 2's gradient."""
+    R = 5
+    p = synth.random_params(R, seed=3).astype(np.float64)
+    q = queries(8, 40, spread=1.0)
+    gO = synth.rng(1).standard_normal(40)
+    np.testing.assert_allclose(oracle.backward_grad(p, q, gO, None, R), oracle.backward(p, q, gO, R),
+                               rtol=1e-12, atol=1e-14)
+    np.testing.assert_array_equal(oracle.backward_grad(p, q, None, None, R), 0.0)
+
+
+def test_eikonal_loss_gradient_matches_torch():
+    """Eikonal term in the squared form of Sec. 3.2, mean over queries."""
+    G = synth.rng(4).standard_normal((33, 3))
+    Gt = torch.tensor(G, requires_grad=True)
+    Lt = 0.3 * (((Gt ** 2).sum(1) - 1.0) ** 2).mean()
+    Lt.backward()
+    L, gG = oracle.eikonal_loss_grad(G, weight=0.3)
+    assert abs(L - Lt.item()) < 1e-14
+    np.testing.assert_allclose(gG, Gt.grad.numpy(), rtol=1e-13, atol=1e-15)
