@@ -139,6 +139,23 @@ efunc_status efunc_backward(const efunc_grid *grid, const float *params, const f
                             int32_t q_stride, const float *gO, float *grad, float *gq, void *workspace,
                             size_t workspace_bytes, efunc_stream_t stream);
 
+/* Backward through the value and its query gradient: ACCUMULATES
+ *   grad[i*13 + s] += sum_j [ gO_j dO(q_j)/dtheta + gG_j . d(dO/dq)(q_j)/dtheta ]
+ * where dO/dq is Eq. func-normal (Sec. 3.2).  The second term is what a loss
+ * on the query gradient needs: the Eikonal condition |dO/dq|^2 = 1 that
+ * Sec. 3.2 states for signed distance functions, or a normal-alignment loss
+ * (Sec. 4.6 uses dO/dq as the surface normal).  Per query it needs, besides
+ * the forward, H = gG . dO/dq and T = -2 gG . sum softmax beta (q - key); the
+ * per-key gradient then follows from differentiating every key's
+ * contribution w (d + (f - O) ds/dq) to dO/dq once more.
+ *   gO       [device] J floats or NULL (no value term)
+ *   gG       [device] J x 3 floats or NULL (then this is efunc_backward)
+ *   grad     [device] R^3*13 floats, accumulated into
+ * At least one of gO, gG must be given. */
+efunc_status efunc_backward_grad(const efunc_grid *grid, const float *params, const float *q, int64_t J,
+                                 int32_t q_stride, const float *gO, const float *gG, float *grad, void *workspace,
+                                 size_t workspace_bytes, efunc_stream_t stream);
+
 /* One Adam/AdamW step over n floats (Sec. 3.4), step is 1-based (bias
  * correction).  params, m, v are updated in place; grad is read and then
  * zeroed.  All four [device], n >= 0. */
@@ -151,19 +168,24 @@ efunc_status efunc_adam_step(const efunc_adam *adam, int64_t n, float *params, f
  * step0 + s + 1.
  *   loss     EFUNC_LOSS_L1 (dL/dO = sign(O - o)/J, sign(0) = 0) or
  *            EFUNC_LOSS_MSE (Eq. loss, 2(O - o)/J)
+ *   eikonal_weight  >= 0: adds weight * mean_j (|dO/dq(q_j)|^2 - 1)^2, the
+ *            Eikonal condition of Sec. 3.2 in its squared form, whose
+ *            gradient goes through efunc_backward_grad's second-order term
+ *            inside the fused kernel; 0 disables it
  *   params, m, v  [device] R^3*13 floats each, updated
  *   qo       [host|device] n_batches*J*4 floats.  Host memory is copied
  *            to the device inside every step; the copy of batch s+1 runs on
  *            a copy stream of the library (created on the first such call on
  *            a device) while batch s is computed, so with pinned memory the
  *            copies overlap the computation.
- *   stats    [host|device] steps*2 floats or NULL: (loss, mean |O - o|) of
- *            every step, evaluated at the parameters before that step's
+ *   stats    [host|device] steps*2 floats or NULL: (loss including the
+ *            Eikonal term, mean |O - o|) of every step, evaluated at the
+ *            parameters before that step's
  *            update.  If stats is host memory the call synchronises the
  *            stream before returning. */
-efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t loss, float *params,
-                       float *m, float *v, const float *qo, int64_t J, int32_t n_batches, int32_t steps,
-                       int64_t step0, float *stats, void *workspace, size_t workspace_bytes,
+efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t loss, float eikonal_weight,
+                       float *params, float *m, float *v, const float *qo, int64_t J, int32_t n_batches,
+                       int32_t steps, int64_t step0, float *stats, void *workspace, size_t workspace_bytes,
                        efunc_stream_t stream);
 
 /* Forward without any device allocation by the caller.  The paper has no

@@ -42,10 +42,13 @@ SIGNATURES = {
                                 c_void_p, c_void_p, c_size_t, c_void_p]),
     "efunc_backward": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p,
                                  c_void_p, c_void_p, c_size_t, c_void_p]),
+    "efunc_backward_grad": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p,
+                                      c_void_p, c_void_p, c_size_t, c_void_p]),
     "efunc_adam_step": (c_int32, [ctypes.POINTER(Adam), c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,
                                   c_void_p]),
-    "efunc_fit": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Adam), c_int32, c_void_p, c_void_p, c_void_p,
-                            c_void_p, c_int64, c_int32, c_int32, c_int64, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "efunc_fit": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Adam), c_int32, c_float, c_void_p, c_void_p,
+                            c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int64, c_void_p, c_void_p, c_size_t,
+                            c_void_p]),
     "efunc_forward_noalloc": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_void_p, c_int64, c_int32, c_void_p,
                                         c_void_p, c_void_p, c_void_p]),
     "efunc_profile_enable": (None, [c_int32]),

@@ -138,6 +138,29 @@ def efunc_backward(params: torch.Tensor, q: torch.Tensor, gO: torch.Tensor, grad
     return (grad, gq) if want_gq else grad
 
 
+def efunc_backward_grad(params: torch.Tensor, q: torch.Tensor, gO: torch.Tensor | None, gG: torch.Tensor | None,
+                        grad: torch.Tensor | None = None, log_beta0: float | None = None,
+                        ws: Workspace | None = None):
+    """Accumulate dL/dparams for L = sum gO.O + gG . dO/dq (backward through
+    Eq. func-normal, e.g. for an Eikonal loss)."""
+    R = resolution_of(params)
+    _need(params, "params")
+    J, stride = _queries(q)
+    if gO is not None:
+        _need(gO, "gO", J)
+    if gG is not None:
+        _need(gG, "gG", 3 * J)
+    if grad is None:
+        grad = torch.zeros_like(params)
+    _need(grad, "grad", params.numel())
+    grid = make_grid(R, log_beta0)
+    buf, n = _workspace(q.device, ws).get(grid, J)
+    B.check("efunc_backward_grad", B.load().efunc_backward_grad(ctypes.byref(grid), _ptr(params), _ptr(q), J, stride,
+                                                                _ptr(gO), _ptr(gG), _ptr(grad), _ptr(buf), n,
+                                                                _stream(q.device)))
+    return grad
+
+
 def make_adam(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, decoupled=False) -> B.Adam:
     return B.Adam(lr, beta1, beta2, eps, weight_decay, int(bool(decoupled)))
 
@@ -153,7 +176,7 @@ def efunc_adam_step(params, grad, m, v, step: int, **adam_kw):
 
 def efunc_fit(params, m, v, qo, steps: int, J: int | None = None, n_batches: int = 1, step0: int = 0,
               loss: str = "l1", stats=None, log_beta0: float | None = None, ws: Workspace | None = None,
-              **adam_kw):
+              eikonal_weight: float = 0.0, **adam_kw):
     """Fitting loop (Sec. 3.4) on batches of (x, y, z, target) rows.
 
     ``qo`` is a CUDA tensor or a (pinned) CPU tensor of n_batches*J rows of 4
@@ -174,7 +197,8 @@ def efunc_fit(params, m, v, qo, steps: int, J: int | None = None, n_batches: int
     ad = make_adam(**adam_kw)
     buf, n = _workspace(params.device, ws).get(grid, J)
     lk = {"l1": B.LOSS_L1, "mse": B.LOSS_MSE}[loss]
-    B.check("efunc_fit", B.load().efunc_fit(ctypes.byref(grid), ctypes.byref(ad), lk, _ptr(params), _ptr(m), _ptr(v),
+    B.check("efunc_fit", B.load().efunc_fit(ctypes.byref(grid), ctypes.byref(ad), lk, float(eikonal_weight),
+                                            _ptr(params), _ptr(m), _ptr(v),
                                             _ptr(qo), J, n_batches, steps, step0, _ptr(stats), _ptr(buf), n,
                                             _stream(params.device)))
 

@@ -26,7 +26,7 @@ struct Ctrl {
     int n_items;        // work items produced by the sort
     int next_item;      // dynamic work counter of the fused kernel
     int pad[2];
-    double loss_sum;    // sum over queries of |O-o| (L1) or (O-o)^2 (MSE)
+    double loss_sum;    // sum over queries of |O-o| (L1) or (O-o)^2 (MSE), plus the Eikonal term
     double abs_sum;     // sum over queries of |O-o|
 };
 
@@ -87,12 +87,14 @@ struct FusedArgs {
     float *lse;
     float *dq;
     // backward inputs / outputs
-    const float *gO;     // user order
+    const float *gO;     // user order, or NULL (no value term) in second-order mode
+    const float *gG;     // user order J x 3: dL/d(dO/dq) (second-order backward)
     float *grad;
     float *gq;           // user order
     // fit
     int loss;
     float inv_J;
+    float eik_weight;    // weight of the Eikonal term (|dO/dq|^2 - 1)^2 in the fit
 };
 
 struct AdamArgs {
@@ -123,8 +125,8 @@ void launch_end(int kid, cudaStream_t s);
 cudaError_t launch_sort(const SortArgs &a, cudaStream_t s);
 cudaError_t launch_pack_keys(const PackArgs &a, cudaStream_t s);
 cudaError_t launch_forward(const FusedArgs &a, bool with_dq, int grid, cudaStream_t s);
-cudaError_t launch_fused_backward(const FusedArgs &a, bool with_gq, int grid, cudaStream_t s);
-cudaError_t launch_fused_fit(const FusedArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_fused_backward(const FusedArgs &a, bool with_gq, bool second_order, int grid, cudaStream_t s);
+cudaError_t launch_fused_fit(const FusedArgs &a, bool eikonal, int grid, cudaStream_t s);
 cudaError_t launch_adam(const AdamArgs &a, cudaStream_t s);
 int fused_grid_size();   // persistent grid: SMs x resident blocks per SM
 

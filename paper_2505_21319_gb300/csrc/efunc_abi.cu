@@ -368,7 +368,30 @@ efunc_status efunc_backward(const efunc_grid *grid, const float *params, const f
     f.gO = gO;
     f.grad = grad;
     f.gq = gq;
-    return cuda_status(launch_fused_backward(f, gq != nullptr, fused_grid_size(), s));
+    return cuda_status(launch_fused_backward(f, gq != nullptr, false, fused_grid_size(), s));
+}
+
+efunc_status efunc_backward_grad(const efunc_grid *grid, const float *params, const float *q, int64_t J,
+                                 int32_t q_stride, const float *gO, const float *gG, float *grad, void *workspace,
+                                 size_t workspace_bytes, efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if (J < 0 || J > kMaxJ || (q_stride != 3 && q_stride != 4) || !params || !grad) return EFUNC_ERR_ARG;
+    if (J == 0) return EFUNC_OK;
+    if (!q || (!gO && !gG)) return EFUNC_ERR_ARG;
+    if ((st = check_workspace(grid, J, workspace, workspace_bytes))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Views v{make_layout(grid->R, J), static_cast<char *>(workspace)};
+    cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
+    if (e == cudaSuccess) e = pack_keys(v, grid, params, s);
+    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    FusedArgs f = fused_args(v, grid);
+    f.gO = gO;
+    f.gG = gG;
+    f.grad = grad;
+    if (!gG) return cuda_status(launch_fused_backward(f, false, false, fused_grid_size(), s));
+    return cuda_status(launch_fused_backward(f, false, true, fused_grid_size(), s));
 }
 
 efunc_status efunc_adam_step(const efunc_adam *adam, int64_t n, float *params, float *grad, float *m, float *v,
@@ -383,14 +406,16 @@ efunc_status efunc_adam_step(const efunc_adam *adam, int64_t n, float *params, f
     return cuda_status(launch_adam(a, (cudaStream_t)stream));
 }
 
-efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t loss, float *params, float *m,
-                       float *v, const float *qo, int64_t J, int32_t n_batches, int32_t steps, int64_t step0,
-                       float *stats, void *workspace, size_t workspace_bytes, efunc_stream_t stream)
+efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t loss, float eikonal_weight,
+                       float *params, float *m, float *v, const float *qo, int64_t J, int32_t n_batches, int32_t steps,
+                       int64_t step0, float *stats, void *workspace, size_t workspace_bytes, efunc_stream_t stream)
 {
     efunc_status st = check_grid(grid);
     if (st) return st;
     if ((st = check_adam(adam))) return st;
     if (loss != EFUNC_LOSS_L1 && loss != EFUNC_LOSS_MSE) return EFUNC_ERR_ARG;
+    if (!isfinite(eikonal_weight)) return EFUNC_ERR_NONFINITE;
+    if (eikonal_weight < 0.f) return EFUNC_ERR_ARG;
     if (J < 1 || J > kMaxJ || n_batches < 1 || steps < 0 || step0 < 0) return EFUNC_ERR_ARG;
     if (!params || !m || !v || !qo) return EFUNC_ERR_ARG;
     if ((st = check_workspace(grid, J, workspace, workspace_bytes))) return st;
@@ -445,7 +470,8 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
         f.grad = grad;
         f.loss = loss;
         f.inv_J = (float)(1.0 / (double)J);
-        e = launch_fused_fit(f, grid_blocks, s);
+        f.eik_weight = eikonal_weight;
+        e = launch_fused_fit(f, eikonal_weight > 0.f, grid_blocks, s);
         if (e != cudaSuccess) return EFUNC_ERR_CUDA;
         AdamArgs a = adam_args(adam, n, params, grad, m, v, step0 + it + 1);
         a.ctrl = vw.ctrl();

@@ -237,6 +237,48 @@ __device__ __forceinline__ void dq_sums(const float4 *rec, int nc, int part, flo
     gz = combine_classes<KQ>(az);
 }
 
+// dO/dq (as dq_sums) together with V = sum w beta (q - key), the two
+// per-query sums the backward through dO/dq needs; same classes.
+template <int KQ>
+__device__ __forceinline__ void gv_sums(const float4 *rec, int nc, int part, float x, float y, float z, float lse2,
+                                        float O, float G[3], float V[3])
+{
+    constexpr int CPL = kClasses / KQ;
+    float ax[CPL], ay[CPL], az[CPL], vx[CPL], vy[CPL], vz[CPL];
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) ax[i] = ay[i] = az[i] = vx[i] = vy[i] = vz[i] = 0.f;
+#pragma unroll
+    for (int set = 0; set < 2; ++set) {
+        for (int base = 0; base < nc; base += kClasses) {
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                const int k = base + part + KQ * i;
+                if (k < nc) {
+                    const float4 a = keyA(rec, set, k), b = keyB(rec, set, k);
+                    const float rx = x - a.x, ry = y - a.y, rz = z - a.z;
+                    const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                    const float w = ex2_approx(fmaf(a.w, d2, -lse2));
+                    const float f = fmaf(b.y, rx, fmaf(b.z, ry, fmaf(b.w, rz, b.x)));
+                    const float wb = w * (-kLn2) * a.w;               // w beta
+                    const float c = 2.f * wb * (O - f);                // 2 beta w (O - f)
+                    ax[i] = fmaf(w, b.y, fmaf(c, rx, ax[i]));
+                    ay[i] = fmaf(w, b.z, fmaf(c, ry, ay[i]));
+                    az[i] = fmaf(w, b.w, fmaf(c, rz, az[i]));
+                    vx[i] = fmaf(wb, rx, vx[i]);
+                    vy[i] = fmaf(wb, ry, vy[i]);
+                    vz[i] = fmaf(wb, rz, vz[i]);
+                }
+            }
+        }
+    }
+    G[0] = combine_classes<KQ>(ax);
+    G[1] = combine_classes<KQ>(ay);
+    G[2] = combine_classes<KQ>(az);
+    V[0] = combine_classes<KQ>(vx);
+    V[1] = combine_classes<KQ>(vy);
+    V[2] = combine_classes<KQ>(vz);
+}
+
 struct FwdOut {
     float O, lse2;
 };
@@ -310,15 +352,84 @@ __device__ __forceinline__ void bwd_key_loop(const float4 A, const float4 B, con
     acc[5] = adx; acc[6] = ady; acc[7] = adz;
 }
 
+// Thread-per-key loop of the second-order backward: the value term (as
+// bwd_key_loop, dL/dO = gO) plus the gradient of u . dO/dq per query, with
+// per-query rows sqA[j] = (q local, lse2), sqE[j] = (O, gO, H, T),
+// sqU[j] = (u, 0), H = u . dO/dq, T = -2 u . sum w beta (q - key).  For one
+// key (w its weight, r = q - key, dlt = f - O, t = -2 beta r):
+//   d(u.G)/do    = w (u.t - T)
+//   d(u.G)/dd    = w (r (u.t - T) + u)
+//   d(u.G)/dbeta = w (-|r|^2 [(h - H) - dlt T] - 2 dlt u.r),  h = u.d + dlt u.t
+//   d(u.G)/dkey  = w (2 beta r [(h - H) - dlt T] - d (u.t - T) + 2 beta dlt u)
+// Accumulators: acc[0..7] value term as bwd_key_loop; acc[8] sum w (u.t - T),
+// acc[9..11] sum w (u.t - T) r + w u, acc[12] sum w (...) of dbeta,
+// acc[13..15] sum w [(h - H) - dlt T] r, acc[16..18] sum w dlt u.
+template <bool OFFSET>
+__device__ __forceinline__ void bwd2_key_loop(const float4 A, const float4 B, const float4 *__restrict__ sqA,
+                                              const float4 *__restrict__ sqE, const float4 *__restrict__ sqU, int n,
+                                              float acc[19])
+{
+    const float beta = -A.w * kLn2;
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f, v6 = 0.f, v7 = 0.f;
+    float e0 = 0.f, ex = 0.f, ey = 0.f, ez = 0.f, eb = 0.f, px = 0.f, py = 0.f, pz = 0.f, qx = 0.f, qy = 0.f,
+          qz = 0.f;
+#pragma unroll 2
+    for (int j = 0; j < n; ++j) {
+        const float4 Q = sqA[j], E = sqE[j], U = sqU[j];
+        const float rx = Q.x - A.x, ry = Q.y - A.y, rz = Q.z - A.z;
+        const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        const float w = ex2_approx(fmaf(A.w, d2, -Q.w));
+        const float f = fmaf(B.y, rx, fmaf(B.z, ry, fmaf(B.w, rz, B.x)));
+        const float dlt = f - E.x;
+        // value term
+        const float g = w * E.y;
+        const float gd = g * dlt;
+        v0 += g;
+        v1 = fmaf(g, rx, v1);
+        v2 = fmaf(g, ry, v2);
+        v3 = fmaf(g, rz, v3);
+        v4 = fmaf(gd, d2, v4);
+        if (OFFSET) {
+            v5 = fmaf(gd, rx, v5);
+            v6 = fmaf(gd, ry, v6);
+            v7 = fmaf(gd, rz, v7);
+        }
+        // gradient term
+        const float ur = fmaf(U.x, rx, fmaf(U.y, ry, U.z * rz));
+        const float ut = -2.f * beta * ur;
+        const float ua = fmaf(U.x, B.y, fmaf(U.y, B.z, U.z * B.w));
+        const float h = fmaf(dlt, ut, ua);
+        const float we1 = w * (ut - E.w);
+        const float hH = fmaf(-dlt, E.w, h - E.z);
+        e0 += we1;
+        ex = fmaf(we1, rx, fmaf(w, U.x, ex));
+        ey = fmaf(we1, ry, fmaf(w, U.y, ey));
+        ez = fmaf(we1, rz, fmaf(w, U.z, ez));
+        eb = fmaf(w, fmaf(-d2, hH, -2.f * dlt * ur), eb);
+        if (OFFSET) {
+            const float whH = w * hH, wd = w * dlt;
+            px = fmaf(whH, rx, px);
+            py = fmaf(whH, ry, py);
+            pz = fmaf(whH, rz, pz);
+            qx = fmaf(wd, U.x, qx);
+            qy = fmaf(wd, U.y, qy);
+            qz = fmaf(wd, U.z, qz);
+        }
+    }
+    acc[0] = v0; acc[1] = v1; acc[2] = v2; acc[3] = v3; acc[4] = v4; acc[5] = v5; acc[6] = v6; acc[7] = v7;
+    acc[8] = e0; acc[9] = ex; acc[10] = ey; acc[11] = ez; acc[12] = eb;
+    acc[13] = px; acc[14] = py; acc[15] = pz; acc[16] = qx; acc[17] = qy; acc[18] = qz;
+}
+
 // ------------------------------------------------------------- kernel
 
 // Forward over the item's queries.  qt holds the raw query tile (x, y, z,
 // target); a query's row is rewritten in place with (local position, lse2)
 // by the lane that owns it, after every lane of its group has read it.
-template <int MODE, bool DQ, int KQ, bool FULL>
+template <int MODE, bool DQ, bool GEIK, int KQ, bool FULL>
 __device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *rec, float4 *qt, float4 *sqB,
-                                              int start, int n, int nc, float3 orig, float h, float &loss_acc,
-                                              float &abs_acc)
+                                              float4 *sqE, float4 *sqU, int start, int n, int nc, float3 orig,
+                                              float h, float &loss_acc, float &abs_acc)
 {
     constexpr int LG = KQ == 1 ? 0 : (KQ == 2 ? 1 : 2);
     const int t = threadIdx.x;
@@ -352,7 +463,7 @@ __device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *
                 abs_acc += fabsf(diff);
             }
         } else if (MODE == BACKWARD) {
-            gO = valid ? __ldg(a.gO + j_user) : 0.f;
+            gO = (valid && a.gO) ? __ldg(a.gO + j_user) : 0.f;
         } else if (valid && part == 0) {
             a.O[j_user] = O;
             if (a.lse) a.lse[j_user] = lse2 * kLn2;
@@ -367,6 +478,32 @@ __device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *
                 dst[3 * (size_t)j_user + 1] = s * gy;
                 dst[3 * (size_t)j_user + 2] = s * gz;
             }
+        }
+        float4 rowE = make_float4(O, gO, 0.f, 0.f), rowU = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (GEIK) {
+            // second order: u = dL/d(dO/dq), H = u . dO/dq, T = -2 u . sum w beta (q - key)
+            float G[3], V[3];
+            gv_sums<KQ>(rec, nc, part, q.x, q.y, q.z, lse2, O, G, V);
+            float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+            if (MODE == FIT) {
+                // Eikonal term of Sec. 3.2 in the squared form: weight (|G|^2 - 1)^2 / J
+                const float res = fmaf(G[0], G[0], fmaf(G[1], G[1], fmaf(G[2], G[2], -1.f)));
+                const float c = 4.f * a.eik_weight * res * a.inv_J;
+                u0 = c * G[0]; u1 = c * G[1]; u2 = c * G[2];
+                if (valid && part == 0) loss_acc += a.eik_weight * res * res;
+            } else if (valid) {
+                u0 = __ldg(a.gG + 3 * (size_t)j_user);
+                u1 = __ldg(a.gG + 3 * (size_t)j_user + 1);
+                u2 = __ldg(a.gG + 3 * (size_t)j_user + 2);
+            }
+            const float H = fmaf(u0, G[0], fmaf(u1, G[1], u2 * G[2]));
+            const float T = -2.f * fmaf(u0, V[0], fmaf(u1, V[1], u2 * V[2]));
+            rowE = make_float4(O, gO, H, T);
+            rowU = make_float4(u0, u1, u2, 0.f);
+        }
+        if (GEIK && valid && part == 0) {
+            sqE[qi] = rowE;
+            sqU[qi] = rowU;
         }
         if (MODE != FORWARD) {
             __syncwarp();   // every lane of the group has read its row of qt
@@ -384,12 +521,14 @@ __device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *
     }
 }
 
-template <int MODE, bool DQ>
-__global__ void __launch_bounds__(kThreads, 8) fused_kernel(FusedArgs a)
+template <int MODE, bool DQ, bool GEIK>
+__global__ void __launch_bounds__(kThreads, GEIK ? 5 : 8) fused_kernel(FusedArgs a)
 {
     __shared__ float4 s_rec[kCentres * kKeyRecords];          // key records of the window
     __shared__ float4 s_qt[kChunk];                           // query tile
     __shared__ float4 s_sqB[MODE == FORWARD ? 1 : kChunk / 2];
+    __shared__ float4 s_sqE[GEIK ? kChunk : 1];               // (O, gO, H, T) per query
+    __shared__ float4 s_sqU[GEIK ? kChunk : 1];               // (u, 0) per query
     __shared__ int s_item;
     __shared__ float s_red[2][kThreads / 32];
 
@@ -433,13 +572,13 @@ __global__ void __launch_bounds__(kThreads, 8) fused_kernel(FusedArgs a)
 
         // ---- 2. forward, one (or 2 / 4) threads per query
         if (full) {
-            if (n > 64) forward_phase<MODE, DQ, 1, true>(a, rec, qt, qB, start, n, nc, orig, h, loss_acc, abs_acc);
-            else if (n > 32) forward_phase<MODE, DQ, 2, true>(a, rec, qt, qB, start, n, nc, orig, h, loss_acc, abs_acc);
-            else forward_phase<MODE, DQ, 4, true>(a, rec, qt, qB, start, n, nc, orig, h, loss_acc, abs_acc);
+            if (n > 64) forward_phase<MODE, DQ, GEIK, 1, true>(a, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+            else if (n > 32) forward_phase<MODE, DQ, GEIK, 2, true>(a, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+            else forward_phase<MODE, DQ, GEIK, 4, true>(a, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
         } else {
-            if (n > 64) forward_phase<MODE, DQ, 1, false>(a, rec, qt, qB, start, n, nc, orig, h, loss_acc, abs_acc);
-            else if (n > 32) forward_phase<MODE, DQ, 2, false>(a, rec, qt, qB, start, n, nc, orig, h, loss_acc, abs_acc);
-            else forward_phase<MODE, DQ, 4, false>(a, rec, qt, qB, start, n, nc, orig, h, loss_acc, abs_acc);
+            if (n > 64) forward_phase<MODE, DQ, GEIK, 1, false>(a, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+            else if (n > 32) forward_phase<MODE, DQ, GEIK, 2, false>(a, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+            else forward_phase<MODE, DQ, GEIK, 4, false>(a, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
         }
         if (MODE != FORWARD) {
             // ---- 3. backward, one thread per key
@@ -448,30 +587,42 @@ __global__ void __launch_bounds__(kThreads, 8) fused_kernel(FusedArgs a)
             if (c < nc) {
                 const bool offset = t >= kCentres;
                 const float4 A = keyA(rec, offset, c), B = keyB(rec, offset, c);
-                float acc[8];
-                if (offset) bwd_key_loop<true>(A, B, qt, qB, n, acc);
-                else bwd_key_loop<false>(A, B, qt, qB, n, acc);
+                float acc[19];
+                if (GEIK) {
+                    if (offset) bwd2_key_loop<true>(A, B, qt, s_sqE, s_sqU, n, acc);
+                    else bwd2_key_loop<false>(A, B, qt, s_sqE, s_sqU, n, acc);
+                } else {
+                    if (offset) bwd_key_loop<true>(A, B, qt, qB, n, acc);
+                    else bwd_key_loop<false>(A, B, qt, qB, n, acc);
+                    for (int i = 8; i < 19; ++i) acc[i] = 0.f;
+                }
                 int ox, oy, oz;
                     if (full) { ox = c >> 4; oy = (c >> 2) & 3; oz = c & 3; }
                 else { oz = c % w.nz; oy = (c / w.nz) % w.ny; ox = c / (w.ny * w.nz); }
                 float *gr = a.grad + (((size_t)(w.lox + ox) * R + (w.loy + oy)) * R + (w.loz + oz)) * kSlots;
                 const float beta = -A.w * kLn2;
+                // value term (dO/dtheta) plus, in second-order mode, the
+                // gradient term d(u . dO/dq)/dtheta
+                const float go = acc[0] + acc[8];
+                const float gdx = acc[1] + acc[9], gdy = acc[2] + acc[10], gdz = acc[3] + acc[11];
+                const float gb = beta * (-acc[4] + acc[12]);
                 if (!offset) {
-                    atomicAdd(gr + 5, acc[0]);
-                    atomicAdd(gr + 6, acc[1]);
-                    atomicAdd(gr + 7, acc[2]);
-                    atomicAdd(gr + 8, acc[3]);
-                    atomicAdd(gr + 3, -beta * acc[4]);
+                    atomicAdd(gr + 5, go);
+                    atomicAdd(gr + 6, gdx);
+                    atomicAdd(gr + 7, gdy);
+                    atomicAdd(gr + 8, gdz);
+                    atomicAdd(gr + 3, gb);
                 } else {
-                    atomicAdd(gr + 9, acc[0]);
-                    atomicAdd(gr + 10, acc[1]);
-                    atomicAdd(gr + 11, acc[2]);
-                    atomicAdd(gr + 12, acc[3]);
-                    atomicAdd(gr + 4, -beta * acc[4]);
-                    // dO/dDelta = w (-d' + 2 beta' (q - key)(f' - O))
-                    atomicAdd(gr + 0, fmaf(-B.y, acc[0], 2.f * beta * acc[5]));
-                    atomicAdd(gr + 1, fmaf(-B.z, acc[0], 2.f * beta * acc[6]));
-                    atomicAdd(gr + 2, fmaf(-B.w, acc[0], 2.f * beta * acc[7]));
+                    atomicAdd(gr + 9, go);
+                    atomicAdd(gr + 10, gdx);
+                    atomicAdd(gr + 11, gdy);
+                    atomicAdd(gr + 12, gdz);
+                    atomicAdd(gr + 4, gb);
+                    // dO/dDelta = w (-d' + 2 beta' (q - key)(f' - O)); d(u.G)/dDelta as above
+                    const float tb = 2.f * beta;
+                    atomicAdd(gr + 0, fmaf(-B.y, go, tb * (acc[5] + acc[13] + acc[16])));
+                    atomicAdd(gr + 1, fmaf(-B.z, go, tb * (acc[6] + acc[14] + acc[17])));
+                    atomicAdd(gr + 2, fmaf(-B.w, go, tb * (acc[7] + acc[15] + acc[18])));
                 }
             }
         }
@@ -519,7 +670,7 @@ int fused_grid_size()
     static int g = 0;
     if (!g) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel<FIT, false>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel<FIT, false, false>, kThreads, 0);
         if (per_sm <= 0) per_sm = 1;
         g = sm_count() * per_sm;
     }
@@ -540,25 +691,27 @@ cudaError_t launch_pack_keys(const PackArgs &a, cudaStream_t s)
 cudaError_t launch_forward(const FusedArgs &a, bool with_dq, int grid, cudaStream_t s)
 {
     launch_begin(K_FORWARD, s);
-    if (with_dq) fused_kernel<FORWARD, true><<<grid, kThreads, 0, s>>>(a);
-    else fused_kernel<FORWARD, false><<<grid, kThreads, 0, s>>>(a);
+    if (with_dq) fused_kernel<FORWARD, true, false><<<grid, kThreads, 0, s>>>(a);
+    else fused_kernel<FORWARD, false, false><<<grid, kThreads, 0, s>>>(a);
     launch_end(K_FORWARD, s);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fused_backward(const FusedArgs &a, bool with_gq, int grid, cudaStream_t s)
+cudaError_t launch_fused_backward(const FusedArgs &a, bool with_gq, bool second_order, int grid, cudaStream_t s)
 {
     launch_begin(K_FUSED_BWD, s);
-    if (with_gq) fused_kernel<BACKWARD, true><<<grid, kThreads, 0, s>>>(a);
-    else fused_kernel<BACKWARD, false><<<grid, kThreads, 0, s>>>(a);
+    if (second_order) fused_kernel<BACKWARD, false, true><<<grid, kThreads, 0, s>>>(a);
+    else if (with_gq) fused_kernel<BACKWARD, true, false><<<grid, kThreads, 0, s>>>(a);
+    else fused_kernel<BACKWARD, false, false><<<grid, kThreads, 0, s>>>(a);
     launch_end(K_FUSED_BWD, s);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fused_fit(const FusedArgs &a, int grid, cudaStream_t s)
+cudaError_t launch_fused_fit(const FusedArgs &a, bool eikonal, int grid, cudaStream_t s)
 {
     launch_begin(K_FUSED_FIT, s);
-    fused_kernel<FIT, false><<<grid, kThreads, 0, s>>>(a);
+    if (eikonal) fused_kernel<FIT, false, true><<<grid, kThreads, 0, s>>>(a);
+    else fused_kernel<FIT, false, false><<<grid, kThreads, 0, s>>>(a);
     launch_end(K_FUSED_FIT, s);
     return cudaGetLastError();
 }

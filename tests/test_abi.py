@@ -86,12 +86,18 @@ def test_argument_validation_enqueues_nothing(lib):
                                None) == 4
     assert lib.efunc_adam_step(ctypes.byref(B.Adam(1e-3, 1.0, 0.999, 1e-8, 0, 0)), 10, 16, 32, 48, 64, 1, None) == 1
     assert lib.efunc_adam_step(ctypes.byref(ad), 0, None, None, None, None, 1, None) == 0
-    assert lib.efunc_fit(ctypes.byref(ok), ctypes.byref(ad), 2, 16, 32, 48, 64, 10, 1, 1, 0, None, 1 << 30,
+    assert lib.efunc_fit(ctypes.byref(ok), ctypes.byref(ad), 2, 0.0, 16, 32, 48, 64, 10, 1, 1, 0, None, 1 << 30,
                          1 << 40, None) == 1                                                # bad loss kind
-    assert lib.efunc_fit(ctypes.byref(ok), ctypes.byref(ad), 0, 16, 32, 48, 64, 10, 0, 1, 0, None, 1 << 30,
+    assert lib.efunc_fit(ctypes.byref(ok), ctypes.byref(ad), 0, 0.0, 16, 32, 48, 64, 10, 0, 1, 0, None, 1 << 30,
                          1 << 40, None) == 1                                                # no batches
-    assert lib.efunc_fit(ctypes.byref(ok), ctypes.byref(ad), 0, 16, 32, 48, 64, 10, 1, 0, 0, None, 1 << 30,
+    assert lib.efunc_fit(ctypes.byref(ok), ctypes.byref(ad), 0, -1.0, 16, 32, 48, 64, 10, 1, 1, 0, None, 1 << 30,
+                         1 << 40, None) == 1                                                # negative weight
+    assert lib.efunc_fit(ctypes.byref(ok), ctypes.byref(ad), 0, float("nan"), 16, 32, 48, 64, 10, 1, 1, 0, None,
+                         1 << 30, 1 << 40, None) == 4                                       # non-finite weight
+    assert lib.efunc_fit(ctypes.byref(ok), ctypes.byref(ad), 0, 0.0, 16, 32, 48, 64, 10, 1, 0, 0, None, 1 << 30,
                          1 << 40, None) == 0                                                # zero steps
+    assert lib.efunc_backward_grad(ctypes.byref(ok), 4096, 8192, 16, 3, None, None, 4096, 1 << 30, 1 << 40,
+                                   None) == 1                                               # neither gO nor gG
     assert lib.efunc_launch_count() == 0
 
 

@@ -385,3 +385,86 @@ def test_autograd_function_matches_oracle():
                                            want_dq_sens=True)
     assert_grad_close(pd.grad.cpu().numpy(), g_ref, "autograd params")
     assert_dq_close(qd.grad.cpu().numpy(), gq_ref, sens, O_tol(O_ref, kappa), "autograd q", scale=w32)
+
+
+# ------------------------------------------- backward through dO/dq (NEXT-1)
+
+@pytest.mark.parametrize("R,J,pkind,with_gO", [(2, 1000, "random", True), (3, 3001, "random", False),
+                                               (8, 20011, "random", True), (16, 65536, "sdf", True),
+                                               (32, 60000, "sdf", True), (32, 60000, "sdf", False)])
+def test_backward_through_query_gradient_matches_oracle(R, J, pkind, with_gO):
+    """dL/dparams for L = sum gO O + gG . dO/dq (a loss on Eq. func-normal),
+    on the bounding volume (with cell-face ties).  Queries outside it are
+    covered below: their dO/dq inherits O's rounding amplified by
+    sens = 2 ||sum w beta (q - key)|| (~10^3 at 0.5 outside)."""
+    qo = mixed_queries(R, J, seed=50 + R)
+    qo = qo[np.all(np.abs(qo[:, :3]) <= 1, axis=1)]
+    J = qo.shape[0]
+    p = params_of(pkind, R, 60 + R)
+    g = synth.rng(70 + R)
+    gO = (g.standard_normal(J) / J).astype(np.float32) if with_gO else None
+    gG = (g.standard_normal((J, 3)) / J).astype(np.float32)
+    lb = lb32(R)
+    grad = api.efunc_backward_grad(to_dev(p), to_dev(qo), None if gO is None else to_dev(gO), to_dev(gG),
+                                   log_beta0=lb)
+    g_ref = oracle.backward_grad(p.astype(np.float64), qo.astype(np.float64),
+                                 None if gO is None else gO.astype(np.float64), gG.astype(np.float64), R, 2, lb)
+    assert_grad_close(grad.cpu().numpy(), g_ref, f"second order R={R}")
+
+
+def test_backward_through_query_gradient_outside_the_domain():
+    """Batches with 1/16 of the queries up to 0.6 outside the domain: those
+    queries' dO/dq carries a relative error up to sens * tol_O ~ 1300 * 1e-6,
+    so the per-slot bound is 2e-3 of the slot's largest gradient."""
+    R, J = 32, 60000
+    qo = mixed_queries(R, J, seed=82)
+    p = params_of("sdf", R, 92)
+    g = synth.rng(7)
+    gO = (g.standard_normal(J) / J).astype(np.float32)
+    gG = (g.standard_normal((J, 3)) / J).astype(np.float32)
+    grad = api.efunc_backward_grad(to_dev(p), to_dev(qo), to_dev(gO), to_dev(gG), log_beta0=lb32(R))
+    g_ref = oracle.backward_grad(p.astype(np.float64), qo.astype(np.float64), gO.astype(np.float64),
+                                 gG.astype(np.float64), R, 2, lb32(R))
+    assert_grad_close(grad.cpu().numpy(), g_ref, "second order, queries outside", rtol=2e-3)
+
+
+@pytest.mark.parametrize("loss", ["mse", "l1"])
+def test_fused_fit_with_eikonal_term(loss):
+    """One fused step with an Eikonal weight and lr = 0: Adam's first moment
+    exposes the gradient of value loss + weight * mean (|dO/dq|^2 - 1)^2."""
+    R, J, lam = 16, 50000, 0.05
+    p = params_of("sdf", R, 3)
+    qo = _margin_targets(p, mixed_queries(R, J, seed=4), R, seed=5)
+    pd, m, v = to_dev(p), torch.zeros(p.size, device=DEV), torch.zeros(p.size, device=DEV)
+    stats = torch.zeros(2, device=DEV)
+    api.efunc_fit(pd, m, v, to_dev(qo), steps=1, loss=loss, stats=stats, lr=0.0, log_beta0=lb32(R),
+                  eikonal_weight=lam)
+    p64, q64 = p.astype(np.float64), qo.astype(np.float64)
+    O_ref, _, G_ref = oracle.forward(p64, q64, R, 2, lb32(R), want_dq=True)
+    gO, L, mae = oracle.loss_grad(O_ref, q64[:, 3], oracle.L1 if loss == "l1" else oracle.MSE)
+    Le, gG = oracle.eikonal_loss_grad(G_ref, weight=lam)
+    g_ref = oracle.backward_grad(p64, q64, gO, gG, R, 2, lb32(R))
+    assert_grad_close(m.cpu().numpy() / 0.1, g_ref, f"fit + Eikonal ({loss})")
+    s = stats.cpu().numpy()
+    assert abs(s[0] - (L + Le)) <= 1e-4 * abs(L + Le)
+    assert abs(s[1] - mae) <= 1e-5 * abs(mae) + 1e-7
+
+
+def test_eikonal_fit_keeps_the_gradient_norm_near_one():
+    """600 Adam steps (lr 1e-3, L1) on the sphere: without the Eikonal term the
+    held-out residual mean (|dO/dq|^2 - 1)^2 grows as the fit sharpens (to
+    ~24 in this configuration); with weight 1 it stays near 0.3."""
+    R, J = 16, 1 << 16
+    shape = synth.sphere(0.5)
+    qo = to_dev(synth.sample_batch(shape, J, seed=0))
+    held = synth.sample_batch(shape, 8192, seed=1)
+    res = {}
+    for lam in (0.0, 1.0):
+        p = to_dev(synth.init_params(R, seed=0))
+        m = torch.zeros(p.numel(), device=DEV)
+        v = torch.zeros(p.numel(), device=DEV)
+        api.efunc_fit(p, m, v, qo, steps=600, loss="l1", lr=1e-3, eikonal_weight=lam)
+        _, G = api.efunc_forward(p, to_dev(held[:, :3].copy()), want_dq=True)
+        G = G.cpu().numpy().astype(np.float64)
+        res[lam] = float((((G ** 2).sum(1) - 1.0) ** 2).mean())
+    assert res[1.0] < 0.2 * res[0.0] and res[1.0] < 1.0
