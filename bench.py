@@ -278,6 +278,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--eikonal-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -360,6 +361,27 @@ def main():
     achieved = ops_per_launch / (avg_fused * 1e-3) / 1e12
     clocks = clk.summary()
 
+    # ---- the same fit with the Eikonal term (NEXT-1: second-order fused
+    # backward through dO/dq), timed the same way on a shorter run
+    eik = None
+    if args.eikonal_steps > 0:
+        api.efunc_fit(params, m, v, pool, steps=3, J=J, n_batches=N_BATCHES, step0=5 * 10 ** 6, lr=LR, ws=ws_buf,
+                      eikonal_weight=0.1)
+        torch.cuda.synchronize(dev)
+        api.profile_reset()
+        api.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        api.efunc_fit(params, m, v, pool, steps=args.eikonal_steps, J=J, n_batches=N_BATCHES, step0=6 * 10 ** 6,
+                      lr=LR, ws=ws_buf, eikonal_weight=0.1)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        api.profile(False)
+        ems = max_over_ranks(e0.elapsed_time(e1) / args.eikonal_steps, dev)
+        fm, fn = api.profile_read("fused_fit")
+        eik = {"value": J * ws / (ems * 1e-3), "unit": "query-pts/s", "ms_per_step": ems,
+               "fused_ms": fm / max(1, fn), "steps": args.eikonal_steps, "eikonal_weight": 0.1}
+
     # ---- end to end through the C ABI with host buffers: the batch pool in
     # pinned host memory, every step copies its 64 MiB batch to the device
     # (overlapped with the previous step's compute by the library) and copies
@@ -404,6 +426,7 @@ def main():
                          "peak_from": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz"},
             "kernel_ms": kernel_ms,
             "e2e": e2e,
+            "eikonal_fit": eik,
             "cpu_baseline": cpu_line,
             "clocks": clocks,
             "gpu_launches": launches,

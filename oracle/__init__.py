@@ -58,10 +58,11 @@ def _load():
             lib.ora_backward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
             lib.ora_forward_global.argtypes = [i32, f64, dp, dp, i64, i32, dp, dp]
             lib.ora_backward_grad.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
+            lib.ora_mean_shift.argtypes = [i32, f64, dp, i64, dp]
             lib.ora_loss_grad.argtypes = [i32, dp, dp, i64, dp, dp, dp]
             lib.ora_adam.argtypes = [i64, dp, dp, dp, dp, i64, f64, f64, f64, f64, f64, i32]
             for fn in ("ora_forward", "ora_backward", "ora_forward_global", "ora_loss_grad", "ora_adam",
-                       "ora_backward_grad"):
+                       "ora_backward_grad", "ora_mean_shift"):
                 getattr(lib, fn).restype = None
             _lib = lib
     return _lib
@@ -173,6 +174,16 @@ def eikonal_loss_grad(G, weight: float = 1.0):
     loss = weight * float((res ** 2).mean()) if J else 0.0
     gG = weight * 4.0 * res[:, None] * G / J
     return loss, gG
+
+
+def mean_shift(pts, R: int, bandwidth: float = 100.0):
+    """Mean-shift offset initialisation of Sec. 3.3: (R^3, 3) offsets Delta_i =
+    softmax-weighted mean of the surface points (weights exp(-bw |k_i - s|^2))
+    minus the centre k_i."""
+    pts = _f64(pts).reshape(-1, 3)
+    delta = np.zeros((R ** 3, 3))
+    _load().ora_mean_shift(R, float(bandwidth), _ptr(pts), pts.shape[0], _ptr(delta))
+    return delta
 
 
 def forward_global(params, q, R: int, log_beta0: float | None = None):

@@ -21,6 +21,7 @@
  *   dO/dq     (Sec. 3.2, Eq. func-normal), and the backward through it (the
  *             parameter gradient of a loss on dO/dq, e.g. the Eikonal term).
  *   Loss      (Sec. 3.4, Eq. loss: MSE) and the L1 variant.
+ *   Offsets   (Sec. 3.3, mean-shift initialisation from surface points).
  *   Adam      (Sec. 3.4 / Sec. 4.2 name Adam / AdamW; torch.optim semantics).
  *
  * Readings of the paper that this file fixes (the paper is silent on them):
@@ -400,6 +401,38 @@ void ora_forward_global(int R, double log_beta0, const double *params, const dou
         }
         O[j] = m / e;
     }
+}
+
+/* ---------------------------------------------------- mean-shift init */
+
+/* Offset initialisation of Sec. 3.3: for every grid centre k_i
+ *   Delta_i = sum_n exp(-bw ||k_i - s_n||^2) s_n / sum_n exp(-bw ||k_i - s_n||^2) - k_i
+ * over N surface points s_n (bw = 100 in the paper), evaluated with the
+ * largest exponent subtracted (the ratio is unchanged and stays defined for
+ * centres far from every point).  pts: N x 3 doubles; delta: R^3 x 3 doubles. */
+void ora_mean_shift(int R, double bw, const double *pts, int64_t N, double *delta)
+{
+    for (int a = 0; a < R; ++a)
+        for (int b = 0; b < R; ++b)
+            for (int c = 0; c < R; ++c) {
+                const double k[3] = {centre_coord(a, R), centre_coord(b, R), centre_coord(c, R)};
+                double M = -INFINITY;
+                for (int64_t n = 0; n < N; ++n) {
+                    double d2 = 0.0;
+                    for (int x = 0; x < 3; ++x) d2 += (k[x] - pts[3 * n + x]) * (k[x] - pts[3 * n + x]);
+                    if (-bw * d2 > M) M = -bw * d2;
+                }
+                double Z = 0.0, S[3] = {0.0, 0.0, 0.0};
+                for (int64_t n = 0; n < N; ++n) {
+                    double d2 = 0.0;
+                    for (int x = 0; x < 3; ++x) d2 += (k[x] - pts[3 * n + x]) * (k[x] - pts[3 * n + x]);
+                    const double w = exp(-bw * d2 - M);
+                    Z += w;
+                    for (int x = 0; x < 3; ++x) S[x] += w * pts[3 * n + x];
+                }
+                double *dl = delta + 3 * ((size_t)((size_t)a * R + b) * R + c);
+                for (int x = 0; x < 3; ++x) dl[x] = S[x] / Z - k[x];
+            }
 }
 
 /* ------------------------------------------------------------------ loss */

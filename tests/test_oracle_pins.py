@@ -435,3 +435,41 @@ def test_eikonal_loss_gradient_matches_torch():
     L, gG = oracle.eikonal_loss_grad(G, weight=0.3)
     assert abs(L - Lt.item()) < 1e-14
     np.testing.assert_allclose(gG, Gt.grad.numpy(), rtol=1e-13, atol=1e-15)
+
+
+# -------------------------------------------------- mean-shift init pins
+
+def test_mean_shift_single_point_and_symmetric_pair():
+    """Sec. 3.3: with one surface point every centre's offset points at it;
+    with two points equidistant from a centre the offset points at their
+    midpoint."""
+    R = 4
+    k = centres(R)
+    s = np.array([[0.3, -0.2, 0.1]])
+    np.testing.assert_allclose(oracle.mean_shift(s, R), s - k, rtol=0, atol=1e-15)
+    # two points mirrored through centre 0
+    d = np.array([0.1, 0.05, -0.2])
+    pts = np.stack([k[0] + d, k[0] - d])
+    np.testing.assert_allclose(oracle.mean_shift(pts, R)[0], 0.0, atol=1e-15)
+
+
+def test_mean_shift_bandwidth_limits():
+    """Large bandwidth: the weight concentrates on the nearest point (argmin
+    of the distance); small bandwidth: all points weigh the same (the mean)."""
+    R = 3
+    pts = synth.rng(5).uniform(-1, 1, (50, 3))
+    k = centres(R)
+    near = pts[np.argmin(scipy.spatial.distance.cdist(k, pts, "sqeuclidean"), axis=1)]
+    np.testing.assert_allclose(oracle.mean_shift(pts, R, bandwidth=1e6), near - k, atol=1e-9)
+    np.testing.assert_allclose(oracle.mean_shift(pts, R, bandwidth=1e-9), pts.mean(0) - k, atol=1e-8)
+
+
+def test_mean_shift_far_centres_stay_defined():
+    """Points far from a centre (every exp(-100 d^2) underflows in FP64) still
+    give a finite offset, equal to the large-bandwidth (nearest point) limit
+    when one point dominates."""
+    pts = np.array([[0.9, 0.9, 0.9], [0.95, 0.9, 0.9]])
+    d = oracle.mean_shift(pts, 2, bandwidth=1000.0)
+    assert np.all(np.isfinite(d))
+    k = centres(2)
+    np.testing.assert_allclose(d[0], pts[0] - k[0], atol=1e-12)
