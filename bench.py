@@ -56,6 +56,10 @@ OPS_PER_CENTRE_FULL = 7 + 12 + 18 + 21
 OPS_PER_QUERY_FULL_SETUP = 24
 EX2_PER_CENTRE = 4
 FP32_LANES_PER_SM = 128
+# FP32-pipe operations of one (centre, point) pair of the mean-shift
+# initialisation: 3 differences, 3 for the squared norm, 1 scale, 1 compare,
+# 1 exponent difference, 1 add to Z, 3 FMAs into S (the ex2 runs on the MUFU)
+MEAN_SHIFT_OPS_PER_PAIR = 13
 WORKLOAD = "C2 plain fit: 32^3x13 FP32 grid, 2^22 queries/step (50% uniform, 50% surface+N(0,0.01^2)), " \
            "union of 8 random primitives, L1 loss, Adam lr 1e-3"
 
@@ -279,6 +283,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--eikonal-steps", type=int, default=100)
+    ap.add_argument("--mean-shift-reps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -382,6 +387,32 @@ def main():
         eik = {"value": J * ws / (ems * 1e-3), "unit": "query-pts/s", "ms_per_step": ems,
                "fused_ms": fm / max(1, fn), "steps": args.eikonal_steps, "eikonal_weight": 0.1}
 
+    # ---- mean-shift offset initialisation (Sec. 3.3): R^3 centres x 16384
+    # surface points, 13 FP32-pipe operations and one ex2 per pair
+    ms_init = None
+    if args.mean_shift_reps > 0:
+        n_pts = 16384
+        pts = torch.from_numpy(synth.surface_points(synth.random_union(0), n_pts, synth.rng(77))
+                               .astype(np.float32)).to(dev)
+        scratch = params.clone()
+        for _ in range(3):
+            api.efunc_mean_shift_init(scratch, pts)
+        torch.cuda.synchronize(dev)
+        api.profile_reset()
+        api.profile(True)
+        for _ in range(args.mean_shift_reps):
+            api.efunc_mean_shift_init(scratch, pts)
+        torch.cuda.synchronize(dev)
+        api.profile(False)
+        mt, mn = api.profile_read("mean_shift")
+        mms = mt / max(1, mn)
+        pairs = R ** 3 * n_pts
+        ms_ach = pairs * MEAN_SHIFT_OPS_PER_PAIR / (mms * 1e-3) / 1e12
+        ms_init = {"ms": mms, "pairs_per_s": pairs / (mms * 1e-3), "R": R, "points": n_pts, "bandwidth": 100.0,
+                   "achieved": ms_ach, "peak": peak, "unit": "T FP32 op/s", "frac": ms_ach / peak,
+                   "ops_per_pair": MEAN_SHIFT_OPS_PER_PAIR}
+        del scratch, pts
+
     # ---- end to end through the C ABI with host buffers: the batch pool in
     # pinned host memory, every step copies its 64 MiB batch to the device
     # (overlapped with the previous step's compute by the library) and copies
@@ -427,6 +458,7 @@ def main():
             "kernel_ms": kernel_ms,
             "e2e": e2e,
             "eikonal_fit": eik,
+            "mean_shift_init": ms_init,
             "cpu_baseline": cpu_line,
             "clocks": clocks,
             "gpu_launches": launches,

@@ -212,6 +212,16 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
 efunc_status efunc_forward_noalloc(const efunc_grid *grid, const float *params, const float *q, int64_t J,
                                    int32_t q_stride, float *O, float *lse, float *dOdq, efunc_stream_t stream);
 
+/* Mean-shift offset initialisation (Sec. 3.3): writes, for every centre,
+ *   Delta_i = sum_n exp(-bw |k_i - s_n|^2) s_n / sum_n exp(-bw |k_i - s_n|^2) - k_i
+ * into params slots 0..2 (the other slots are left as they are), with the
+ * largest exponent subtracted so that centres far from every point still get
+ * a defined offset.  The paper uses bw = 100 and N = 16384 surface points.
+ *   pts      [device] N x 3 floats
+ *   params   [device] R^3*13 floats, slots 0..2 written */
+efunc_status efunc_mean_shift_init(const efunc_grid *grid, const float *pts, int64_t N, float bandwidth,
+                                   float *params, efunc_stream_t stream);
+
 /* ------------------------------------------------------------ measurement */
 
 /* When enabled, every kernel launch of the library is bracketed by CUDA
@@ -222,7 +232,7 @@ void efunc_profile_enable(int32_t enable);
 /* Waits for the recorded events and folds them into per-kernel totals.
  * Writes the total milliseconds and launch count of kernel `name` (one of
  * "bin", "scan_reduce", "scan_top", "scan_emit", "scatter", "pack_keys",
- * "forward", "fused_backward", "fused_fit", "adam").  Returns 0 on success, -1 for an
+ * "forward", "fused_backward", "fused_fit", "adam", "mean_shift").  Returns 0 on success, -1 for an
  * unknown name or a CUDA error. */
 int32_t efunc_profile_read(const char *name, double *total_ms, int64_t *launches);
 

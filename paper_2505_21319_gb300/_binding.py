@@ -51,6 +51,7 @@ SIGNATURES = {
                             c_void_p]),
     "efunc_forward_noalloc": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_void_p, c_int64, c_int32, c_void_p,
                                         c_void_p, c_void_p, c_void_p]),
+    "efunc_mean_shift_init": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_int64, c_float, c_void_p, c_void_p]),
     "efunc_profile_enable": (None, [c_int32]),
     "efunc_profile_read": (c_int32, [c_char_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     "efunc_profile_reset": (None, []),

@@ -161,6 +161,20 @@ def efunc_backward_grad(params: torch.Tensor, q: torch.Tensor, gO: torch.Tensor 
     return grad
 
 
+def efunc_mean_shift_init(params: torch.Tensor, pts: torch.Tensor, bandwidth: float = 100.0):
+    """Write the mean-shift offsets of Sec. 3.3 into params slots 0..2 (in place)."""
+    R = resolution_of(params)
+    _need(params, "params")
+    _need(pts, "pts")
+    if pts.dim() != 2 or pts.shape[1] != 3:
+        raise ValueError("pts must be (N, 3)")
+    grid = make_grid(R)
+    B.check("efunc_mean_shift_init", B.load().efunc_mean_shift_init(ctypes.byref(grid), _ptr(pts), pts.shape[0],
+                                                                    float(bandwidth), _ptr(params),
+                                                                    _stream(params.device)))
+    return params
+
+
 def make_adam(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, decoupled=False) -> B.Adam:
     return B.Adam(lr, beta1, beta2, eps, weight_decay, int(bool(decoupled)))
 

@@ -112,9 +112,17 @@ struct AdamArgs {
     float inv_J;
 };
 
+struct MeanShiftArgs {
+    const float *pts;    // N x 3 surface points
+    int64_t N;
+    int R;
+    float sigma;         // sqrt(bandwidth * log2(e)): coordinate scale of the base-2 exponent
+    float *params;       // R^3 x 13, slots 0..2 written
+};
+
 // Kernel identifiers for the profiler.
 enum KernelId { K_BIN = 0, K_SCAN_REDUCE, K_SCAN_TOP, K_SCAN_EMIT, K_SCATTER, K_PACK_KEYS, K_FORWARD, K_FUSED_BWD,
-                K_FUSED_FIT, K_ADAM, K_COUNT };
+                K_FUSED_FIT, K_ADAM, K_MEAN_SHIFT, K_COUNT };
 
 // Launch bookkeeping (launch counter and optional CUDA-event profiling).
 void launch_begin(int kid, cudaStream_t s);
@@ -128,6 +136,7 @@ cudaError_t launch_forward(const FusedArgs &a, bool with_dq, int grid, cudaStrea
 cudaError_t launch_fused_backward(const FusedArgs &a, bool with_gq, bool second_order, int grid, cudaStream_t s);
 cudaError_t launch_fused_fit(const FusedArgs &a, bool eikonal, int grid, cudaStream_t s);
 cudaError_t launch_adam(const AdamArgs &a, cudaStream_t s);
+cudaError_t launch_mean_shift(const MeanShiftArgs &a, cudaStream_t s);
 int fused_grid_size();   // persistent grid: SMs x resident blocks per SM
 
 // Window-base index along one axis: clamp(floor((q+1)*R/2 - 1/2), -1, R-1),

@@ -30,7 +30,8 @@ int64_t g_count[K_COUNT];
 int64_t g_launches = 0;
 
 const char *const kKernelNames[K_COUNT] = {"bin",       "scan_reduce", "scan_top",       "scan_emit", "scatter",
-                                           "pack_keys", "forward",     "fused_backward", "fused_fit", "adam"};
+                                           "pack_keys", "forward",     "fused_backward", "fused_fit", "adam",
+                                           "mean_shift"};
 
 cudaEvent_t take_event()
 {
@@ -486,6 +487,22 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
     }
     if (stats_host && cudaStreamSynchronize(s) != cudaSuccess) return EFUNC_ERR_CUDA;
     return EFUNC_OK;
+}
+
+efunc_status efunc_mean_shift_init(const efunc_grid *grid, const float *pts, int64_t N, float bandwidth,
+                                   float *params, efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if (!isfinite(bandwidth)) return EFUNC_ERR_NONFINITE;
+    if (N < 1 || N > kMaxJ || !(bandwidth > 0.f) || !pts || !params) return EFUNC_ERR_ARG;
+    MeanShiftArgs a{};
+    a.pts = pts;
+    a.N = N;
+    a.R = grid->R;
+    a.sigma = (float)sqrt((double)bandwidth * 1.4426950408889634);
+    a.params = params;
+    return cuda_status(launch_mean_shift(a, (cudaStream_t)stream));
 }
 
 void efunc_profile_enable(int32_t enable)

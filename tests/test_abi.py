@@ -98,6 +98,12 @@ def test_argument_validation_enqueues_nothing(lib):
                          1 << 40, None) == 0                                                # zero steps
     assert lib.efunc_backward_grad(ctypes.byref(ok), 4096, 8192, 16, 3, None, None, 4096, 1 << 30, 1 << 40,
                                    None) == 1                                               # neither gO nor gG
+    assert lib.efunc_mean_shift_init(ctypes.byref(ok), 4096, 0, 100.0, 8192, None) == 1       # no points
+    assert lib.efunc_mean_shift_init(ctypes.byref(ok), 4096, 10, 0.0, 8192, None) == 1        # bandwidth 0
+    assert lib.efunc_mean_shift_init(ctypes.byref(ok), 4096, 10, -1.0, 8192, None) == 1
+    assert lib.efunc_mean_shift_init(ctypes.byref(ok), 4096, 10, float("inf"), 8192, None) == 4
+    assert lib.efunc_mean_shift_init(ctypes.byref(ok), None, 10, 100.0, 8192, None) == 1
+    assert lib.efunc_mean_shift_init(ctypes.byref(B.Grid(0, 2, 7.0)), 4096, 10, 100.0, 8192, None) == 1
     assert lib.efunc_launch_count() == 0
 
 
