@@ -59,6 +59,10 @@ def _load():
             lib.ora_forward_global.argtypes = [i32, f64, dp, dp, i64, i32, dp, dp]
             lib.ora_backward_grad.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
             lib.ora_mean_shift.argtypes = [i32, f64, dp, i64, dp]
+            lib.ora_variant_channels.argtypes = [i32, i32, i32]
+            lib.ora_variant_channels.restype = i32
+            lib.ora_variant_forward.argtypes = [i32, i32, f64, i32, i32, i32, dp, dp, i64, i32, dp, dp]
+            lib.ora_variant_backward.argtypes = [i32, i32, f64, i32, i32, i32, dp, dp, i64, i32, dp, dp]
             lib.ora_loss_grad.argtypes = [i32, dp, dp, i64, dp, dp, dp]
             lib.ora_adam.argtypes = [i64, dp, dp, dp, dp, i64, f64, f64, f64, f64, f64, i32]
             for fn in ("ora_forward", "ora_backward", "ora_forward_global", "ora_loss_grad", "ora_adam",
@@ -184,6 +188,50 @@ def mean_shift(pts, R: int, bandwidth: float = 100.0):
     delta = np.zeros((R ** 3, 3))
     _load().ora_mean_shift(R, float(bandwidth), _ptr(pts), pts.shape[0], _ptr(delta))
     return delta
+
+
+def variant_channels(sets: int, deg: int, learn: int) -> int:
+    """Floats per centre of an ablation variant (Table tab:ablation "Ch");
+    -1 for an invalid description.  sets: 1 grid keys, 2 offset keys, 3 both;
+    deg: value polynomial degree 0..3; learn: 1 learnable scales."""
+    return int(_load().ora_variant_channels(int(sets), int(deg), int(learn)))
+
+
+def _variant_check(params, q, R, sets, deg, learn):
+    ch = variant_channels(sets, deg, learn)
+    if ch < 0:
+        raise ValueError("invalid variant")
+    params = _f64(params).reshape(R ** 3, ch)
+    q = _f64(q)
+    if q.ndim != 2 or q.shape[1] not in (3, 4):
+        raise ValueError("q must be (J, 3) or (J, 4)")
+    return params, q, ch
+
+
+def variant_forward(params, q, R: int, sets: int, deg: int, learn: int, W: int = 2,
+                    log_beta0: float | None = None):
+    """(O, lse) of an ablation variant (Table tab:ablation) at the queries."""
+    lb = default_log_beta0(R) if log_beta0 is None else float(log_beta0)
+    params, q, _ = _variant_check(params, q, R, sets, deg, learn)
+    J = q.shape[0]
+    O, lse = np.zeros(J), np.zeros(J)
+    _load().ora_variant_forward(R, W, lb, sets, deg, learn, _ptr(params), _ptr(q), J, q.shape[1], _ptr(O),
+                                _ptr(lse))
+    return O, lse
+
+
+def variant_backward(params, q, gO, R: int, sets: int, deg: int, learn: int, W: int = 2,
+                     log_beta0: float | None = None):
+    """sum_j gO_j dO_j/dparams of an ablation variant, (R^3, channels)."""
+    lb = default_log_beta0(R) if log_beta0 is None else float(log_beta0)
+    params, q, ch = _variant_check(params, q, R, sets, deg, learn)
+    gO = _f64(gO).reshape(-1)
+    if gO.shape[0] != q.shape[0]:
+        raise ValueError("gO must have one entry per query")
+    grad = np.zeros((R ** 3, ch))
+    _load().ora_variant_backward(R, W, lb, sets, deg, learn, _ptr(params), _ptr(q), q.shape[0], q.shape[1],
+                                 _ptr(gO), _ptr(grad))
+    return grad
 
 
 def forward_global(params, q, R: int, log_beta0: float | None = None):

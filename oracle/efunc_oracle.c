@@ -435,6 +435,204 @@ void ora_mean_shift(int R, double bw, const double *pts, int64_t N, double *delt
             }
 }
 
+/* ------------------------------------------------- ablation variants */
+
+/* The configurations of Table tab:ablation as one family (Sec. 3.2
+ * Eq. func-interp and Eq. poly-func, Sec. 3.3 Eq. func-offset):
+ *   sets   1 = grid keys k_i only (Config-G-*), 2 = offset keys k_i + Delta_i
+ *          only (Config-Full-1/2), 3 = both under one softmax (Full-3/4)
+ *   deg    degree of the value polynomial, 0..3, in Taylor form
+ *            f(x) = o + sum_a d_a x_a + 1/2 sum_ab S_ab x_a x_b
+ *                   + 1/6 sum_abc T_abc x_a x_b x_c
+ *          with S and T symmetric (the "..." of Eq. poly-func read as the
+ *          next Taylor term)
+ *   learn  1: a log-scale b per key, beta = exp(log_beta0 + b);
+ *          0: beta = exp(log_beta0) fixed (Config-G-1..4)
+ * Channels per centre, in the tuple order of Eq. func-offset:
+ *   [Delta (3) if offset keys] [b of each key set if learn] [phi of each key set]
+ * phi = (o, d_x, d_y, d_z, S_xx, S_yy, S_zz, S_xy, S_xz, S_yz, T_xxx, T_yyy,
+ * T_zzz, T_xxy, T_xxz, T_xyy, T_yyz, T_xzz, T_yzz, T_xyz) truncated to 1, 4,
+ * 10 or 20 entries; grid set first.  sets = 3, deg = 1, learn = 1 is the
+ * 13-float layout above.  Only the offset keys move (grid keys are fixed in
+ * every configuration of the table). */
+
+static const int VAR_NV[4] = {1, 4, 10, 20};
+
+static int var_nsets(int sets) { return (sets & 1) + ((sets >> 1) & 1); }
+
+int ora_variant_channels(int sets, int deg, int learn)
+{
+    if (sets < 1 || sets > 3 || deg < 0 || deg > 3 || (learn != 0 && learn != 1)) return -1;
+    return ((sets & 2) ? 3 : 0) + learn * var_nsets(sets) + VAR_NV[deg] * var_nsets(sets);
+}
+
+/* channel of key set s's log-scale (-1 if fixed) and of its first phi entry */
+static void var_channels_of(int sets, int deg, int learn, int s, int *i_b, int *i_phi)
+{
+    int base = (sets & 2) ? 3 : 0;
+    int rank = (s == 1 && (sets & 1)) ? 1 : 0;   /* position among the present sets */
+    *i_b = learn ? base + rank : -1;
+    *i_phi = base + learn * var_nsets(sets) + VAR_NV[deg] * rank;
+}
+
+/* index into phi of the symmetric cubic coefficient T_abc */
+static int var_cubic_index(int a, int b, int c)
+{
+    int t;
+    if (a > b) { t = a; a = b; b = t; }
+    if (b > c) { t = b; b = c; c = t; }
+    if (a > b) { t = a; a = b; b = t; }
+    if (a == b && b == c) return 10 + a;                       /* xxx yyy zzz */
+    if (a == 0 && b == 0) return c == 1 ? 13 : 14;             /* xxy xxz */
+    if (a == 0 && b == 1 && c == 1) return 15;                 /* xyy */
+    if (a == 1 && b == 1) return 16;                           /* yyz */
+    if (a == 0 && b == 2) return 17;                           /* xzz */
+    if (a == 1 && b == 2) return 18;                           /* yzz */
+    return 19;                                                 /* xyz */
+}
+
+/* f(x) and grad f(x) of the Taylor-form polynomial of degree deg */
+static void var_poly(int deg, const double *phi, const double x[3], double *f, double g[3])
+{
+    double S[3][3] = {{0}}, T[3][3][3] = {{{0}}};
+    if (deg >= 2) {
+        S[0][0] = phi[4]; S[1][1] = phi[5]; S[2][2] = phi[6];
+        S[0][1] = S[1][0] = phi[7];
+        S[0][2] = S[2][0] = phi[8];
+        S[1][2] = S[2][1] = phi[9];
+    }
+    if (deg >= 3)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                for (int c = 0; c < 3; ++c) T[a][b][c] = phi[var_cubic_index(a, b, c)];
+    double v = phi[0];
+    for (int a = 0; a < 3; ++a) g[a] = 0.0;
+    if (deg >= 1)
+        for (int a = 0; a < 3; ++a) {
+            v += phi[1 + a] * x[a];
+            g[a] += phi[1 + a];
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            v += 0.5 * S[a][b] * x[a] * x[b];
+            g[a] += S[a][b] * x[b];
+            for (int c = 0; c < 3; ++c) {
+                v += T[a][b][c] * x[a] * x[b] * x[c] / 6.0;
+                g[a] += 0.5 * T[a][b][c] * x[b] * x[c];
+            }
+        }
+    *f = v;
+}
+
+typedef struct {
+    double p[3];
+    double beta;
+    const double *phi;
+    double *grad_phi;   /* NULL in the forward */
+    double *grad_b;     /* NULL if the scale is fixed */
+    double *grad_delta; /* NULL for grid keys */
+} var_key_t;
+
+static var_key_t var_make_key(const double *params, double *grad, int R, double log_beta0, int sets, int deg,
+                              int learn, int a, int b, int c, int s)
+{
+    int ch = ora_variant_channels(sets, deg, learn), i_b, i_phi;
+    var_channels_of(sets, deg, learn, s, &i_b, &i_phi);
+    size_t row = ((size_t)((size_t)a * R + b) * R + c) * (size_t)ch;
+    const double *th = params + row;
+    var_key_t k;
+    k.p[0] = centre_coord(a, R);
+    k.p[1] = centre_coord(b, R);
+    k.p[2] = centre_coord(c, R);
+    if (s == 1) {
+        k.p[0] += th[0]; k.p[1] += th[1]; k.p[2] += th[2];
+    }
+    k.beta = exp(log_beta0 + (learn ? th[i_b] : 0.0));
+    k.phi = th + i_phi;
+    k.grad_phi = grad ? grad + row + i_phi : NULL;
+    k.grad_b = (grad && learn) ? grad + row + i_b : NULL;
+    k.grad_delta = (grad && s == 1) ? grad + row : NULL;
+    return k;
+}
+
+/* O and lse of one query (Algorithm 1 with the maximum exponent subtracted);
+ * with grad != NULL also accumulates gO * dO/dtheta into grad (Algorithm 2):
+ *   dO/dphi_m   = softmax * df/dphi_m (f is linear in phi: f evaluated at the
+ *                 unit vector e_m)
+ *   dO/db       = softmax * beta * (-||x||^2 (f - O))
+ *   dO/dDelta   = softmax * (-grad f(x) + 2 beta x (f - O)),  x = q - key */
+static void variant_one(const double *params, double *grad, double gO, int R, int W, double log_beta0, int sets,
+                        int deg, int learn, const double *q, double *O_out, double *lse_out)
+{
+    int lo[3], hi[3];
+    window_range(q, R, W, lo, hi);
+    double M = -INFINITY, O = 0.0, lse = 0.0;
+    /* pass 0: maximum exponent; pass 1: e_j, m_j; pass 2: gradients */
+    for (int pass = 0; pass < 3; ++pass) {
+        double e = 0.0, m = 0.0;
+        for (int a = lo[0]; a <= hi[0]; ++a)
+            for (int b = lo[1]; b <= hi[1]; ++b)
+                for (int c = lo[2]; c <= hi[2]; ++c)
+                    for (int s = 0; s < 2; ++s) {
+                        if (!(sets & (1 << s))) continue;
+                        var_key_t k = var_make_key(params, pass == 2 ? grad : NULL, R, log_beta0, sets, deg, learn,
+                                                   a, b, c, s);
+                        double x[3] = {q[0] - k.p[0], q[1] - k.p[1], q[2] - k.p[2]};
+                        double d2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+                        double expo = -k.beta * d2;
+                        double f, g[3];
+                        var_poly(deg, k.phi, x, &f, g);
+                        if (pass == 0) {
+                            if (expo > M) M = expo;
+                        } else if (pass == 1) {
+                            double l = exp(expo - M);
+                            e += l;
+                            m += l * f;
+                        } else {
+                            double gl = gO * exp(expo - lse);
+                            for (int i = 0; i < VAR_NV[deg]; ++i) {
+                                double unit[20] = {0}, fu, gu[3];
+                                unit[i] = 1.0;
+                                var_poly(deg, unit, x, &fu, gu);
+                                k.grad_phi[i] += gl * fu;
+                            }
+                            if (k.grad_b) *k.grad_b += gl * k.beta * (-d2 * (f - O));
+                            if (k.grad_delta)
+                                for (int i = 0; i < 3; ++i)
+                                    k.grad_delta[i] += gl * (-g[i] + 2.0 * k.beta * x[i] * (f - O));
+                        }
+                    }
+        if (pass == 1) {
+            O = m / e;
+            lse = M + log(e);
+            *O_out = O;
+            if (lse_out) *lse_out = lse;
+            if (!grad) return;
+        }
+    }
+}
+
+/* Forward of a variant over J queries (rows of q_stride doubles).
+ * O, lse: J doubles (lse may be NULL). */
+void ora_variant_forward(int R, int W, double log_beta0, int sets, int deg, int learn, const double *params,
+                         const double *q, int64_t J, int q_stride, double *O, double *lse)
+{
+    for (int64_t j = 0; j < J; ++j)
+        variant_one(params, NULL, 0.0, R, W, log_beta0, sets, deg, learn, q + j * q_stride, &O[j],
+                    lse ? &lse[j] : NULL);
+}
+
+/* Backward of a variant: grad (R^3 * channels doubles) ACCUMULATES
+ * sum_j gO_j dO_j/dtheta. */
+void ora_variant_backward(int R, int W, double log_beta0, int sets, int deg, int learn, const double *params,
+                          const double *q, int64_t J, int q_stride, const double *gO, double *grad)
+{
+    for (int64_t j = 0; j < J; ++j) {
+        double O;
+        variant_one(params, grad, gO[j], R, W, log_beta0, sets, deg, learn, q + j * q_stride, &O, NULL);
+    }
+}
+
 /* ------------------------------------------------------------------ loss */
 
 /* Eq. loss (MSE) and the L1 variant: the upstream gradient dL/dO_j and the

@@ -473,3 +473,162 @@ def test_mean_shift_far_centres_stay_defined():
     assert np.all(np.isfinite(d))
     k = centres(2)
     np.testing.assert_allclose(d[0], pts[0] - k[0], atol=1e-12)
+
+
+# ------------------------------------------------ ablation variant pins
+
+def taylor_params(R, sets, deg, learn, seed, global_poly):
+    """Parameters of a variant whose every key holds the Taylor coefficients,
+    about its own position, of one global polynomial P of degree <= deg
+    (P(x) = c + g.x + 1/2 x^T H x + 1/6 T[x,x,x], H and T symmetric)."""
+    c, gv, H, T = global_poly
+    ch = oracle.variant_channels(sets, deg, learn)
+    rng = synth.rng(seed)
+    p = np.zeros((R ** 3, ch))
+    k = centres(R)
+    base = 0
+    if sets & 2:
+        p[:, 0:3] = rng.uniform(-0.4, 0.4, (R ** 3, 3)) * (2.0 / R)
+        base = 3
+    nsets = (sets & 1) + ((sets >> 1) & 1)
+    if learn:
+        p[:, base:base + nsets] = rng.normal(0.0, 0.5, (R ** 3, nsets))
+    nv = [1, 4, 10, 20][deg]
+    off = base + learn * nsets
+    tri = [(0, 0, 0), (1, 1, 1), (2, 2, 2), (0, 0, 1), (0, 0, 2), (0, 1, 1), (1, 1, 2), (0, 2, 2), (1, 2, 2), (0, 1, 2)]
+    for s_i, s in enumerate([s for s in (0, 1) if sets & (1 << s)]):
+        pos = k + (p[:, 0:3] if s == 1 else 0.0)
+        val = c + pos @ gv + 0.5 * np.einsum("na,ab,nb->n", pos, H, pos) + np.einsum("abc,na,nb,nc->n", T, pos, pos, pos) / 6
+        grad = gv + pos @ H + 0.5 * np.einsum("abc,nb,nc->na", T, pos, pos)
+        hess = H + np.einsum("abc,nc->nab", T, pos)
+        phi = np.zeros((R ** 3, 20))
+        phi[:, 0] = val
+        phi[:, 1:4] = grad
+        phi[:, 4:7] = hess[:, [0, 1, 2], [0, 1, 2]]
+        phi[:, 7] = hess[:, 0, 1]
+        phi[:, 8] = hess[:, 0, 2]
+        phi[:, 9] = hess[:, 1, 2]
+        for i, (a, b, cc) in enumerate(tri):
+            phi[:, 10 + i] = T[a, b, cc]
+        p[:, off + s_i * nv: off + (s_i + 1) * nv] = phi[:, :nv]
+    return p
+
+
+def random_global_poly(deg, seed):
+    rng = synth.rng(seed)
+    c = rng.normal()
+    g = rng.normal(size=3) if deg >= 1 else np.zeros(3)
+    H = rng.normal(size=(3, 3)) if deg >= 2 else np.zeros((3, 3))
+    H = H + H.T
+    T = np.zeros((3, 3, 3))
+    if deg >= 3:
+        A = rng.normal(size=(3, 3, 3))
+        import itertools
+        for perm in itertools.permutations(range(3)):
+            T += np.transpose(A, perm)
+        T /= 6
+    return c, g, H, T
+
+
+def test_variant_channels_match_table_ablation():
+    """Column 'Ch' and '# Params' of Table tab:ablation for every grid and
+    full configuration: the oracle's channel count for (sets, deg, learn)."""
+    g = json.load(open(os.path.join(GOLDEN, "param_counts.json")))
+    for r in g["table_ablation"]:
+        ch = oracle.variant_channels(*r["variant"])
+        assert ch == r["floats_per_centre"], r["config"]
+        assert r["R"] ** 3 * ch == r["value"], r["config"]
+    assert oracle.variant_channels(0, 1, 1) == -1 and oracle.variant_channels(1, 4, 1) == -1
+
+
+@pytest.mark.parametrize("R,W", [(3, 3), (6, 2)])
+def test_variant_default_layout_reduces_to_the_pinned_model(R, W):
+    """sets = 3, deg = 1, learn = 1 is the 13-float model of Eq. func-offset:
+    forward and backward equal the oracle's (pinned) main functions."""
+    p = synth.random_params(R, seed=31 + R, delta_scale=0.6, b_scale=0.5).astype(np.float64)
+    q = queries(32 + R, 60)
+    O, lse = oracle.variant_forward(p, q, R, 3, 1, 1, W)
+    O0, lse0 = oracle.forward(p, q, R, W)[:2]
+    np.testing.assert_allclose(O, O0, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(lse, lse0, rtol=0, atol=1e-12)
+    gO = synth.rng(33).standard_normal(q.shape[0])
+    np.testing.assert_allclose(oracle.variant_backward(p, q, gO, R, 3, 1, 1, W), oracle.backward(p, q, gO, R, W),
+                               rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("sets", [1, 2, 3])
+@pytest.mark.parametrize("deg", [0, 1, 2, 3])
+def test_variant_polynomial_reproduction(sets, deg):
+    """Eq. poly-func in Taylor form is exact for polynomials of its degree:
+    when every key holds the Taylor coefficients of one global polynomial P
+    (deg <= the value degree) about its own position, the softmax blend is
+    P(q) for any scales and offsets (partition of unity + shift invariance).
+    A wrong 1/2 or 1/6 factor, a wrong symmetric multiplicity or a swapped
+    coefficient breaks it."""
+    R = 4
+    for learn in (0, 1):
+        P = random_global_poly(deg, 40 + 4 * deg + sets)
+        p = taylor_params(R, sets, deg, learn, 50 + sets, P)
+        q = queries(60 + deg, 80, spread=1.05)
+        O, _ = oracle.variant_forward(p, q, R, sets, deg, learn)
+        c, g, H, T = P
+        exact = c + q @ g + 0.5 * np.einsum("na,ab,nb->n", q, H, q) + np.einsum("abc,na,nb,nc->n", T, q, q, q) / 6
+        np.testing.assert_allclose(O, exact, rtol=0, atol=1e-11 * max(1.0, np.abs(exact).max()))
+        # every key agrees with the blend, so the log-scale gradients vanish
+        if learn:
+            gO = synth.rng(7).standard_normal(q.shape[0])
+            grad = oracle.variant_backward(p, q, gO, R, sets, deg, learn)
+            b0 = 3 if sets & 2 else 0
+            nsets = (sets & 1) + ((sets >> 1) & 1)
+            np.testing.assert_allclose(grad[:, b0:b0 + nsets], 0.0, atol=1e-10)
+
+
+def test_variant_degree0_fixed_scale_is_the_normalised_rbf():
+    """Config-G-1 (grid keys, degree 0, fixed scale) is Eq. nrbf: the blend
+    of the values with scipy's softmax of -beta |q - k|^2 over the window."""
+    R, W = 3, 3
+    lb = 2.0
+    v = synth.rng(5).standard_normal(R ** 3)
+    q = queries(6, 50)
+    O, _ = oracle.variant_forward(v[:, None], q, R, 1, 0, 0, W, lb)
+    d2 = scipy.spatial.distance.cdist(q, centres(R), "sqeuclidean")
+    ref = (scipy.special.softmax(-math.exp(lb) * d2, axis=1) * v[None, :]).sum(1)
+    np.testing.assert_allclose(O, ref, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("sets,deg,learn", [(1, 0, 0), (1, 1, 1), (1, 2, 1), (1, 3, 0), (2, 1, 1), (2, 3, 1),
+                                            (3, 2, 1)])
+def test_variant_gradients_match_central_differences(sets, deg, learn):
+    """The variant backward (Algorithm 2 closed forms with the polynomial's
+    own gradient for the key offset) against FP64 central differences of the
+    variant forward, every channel of a sample of touched centres."""
+    R = 4
+    ch = oracle.variant_channels(sets, deg, learn)
+    rng = synth.rng(70 + deg + 4 * sets)
+    p = rng.normal(0.0, 0.3, (R ** 3, ch))
+    if sets & 2:
+        p[:, 0:3] = rng.uniform(-0.3, 0.3, (R ** 3, 3)) * (2.0 / R)
+    lb = oracle.default_log_beta0(R) - 1.0
+    q = rng.uniform(-0.9, 0.9, (6, 3))
+    t = (q + 1) * R / 2 - 0.5
+    frac = t - np.floor(t)
+    q = np.where(np.minimum(frac, 1 - frac) < 1e-3, q + 0.01, q).astype(np.float32).astype(np.float64)
+    gO = rng.standard_normal(q.shape[0])
+    grad = oracle.variant_backward(p, q, gO, R, sets, deg, learn, 2, lb)
+
+    def L(pp):
+        return float(gO @ oracle.variant_forward(pp, q, R, sets, deg, learn, 2, lb)[0])
+
+    touched = np.flatnonzero(np.abs(grad).sum(1) > 0)
+    sel = rng.choice(touched, size=min(6, touched.size), replace=False)
+    an, fd = [], []
+    for i in sel:
+        for s in range(ch):
+            hstep = 1e-6 * max(1.0, abs(p[i, s]))
+            pp, pm = p.copy(), p.copy()
+            pp[i, s] += hstep
+            pm[i, s] -= hstep
+            fd.append((L(pp) - L(pm)) / (2 * hstep))
+            an.append(grad[i, s])
+    an, fd = np.array(an), np.array(fd)
+    np.testing.assert_allclose(an, fd, rtol=2e-6, atol=2e-8 * max(1.0, np.abs(an).max()))
