@@ -113,6 +113,30 @@ def algorithmic_ops(q: np.ndarray, R: int) -> float:
         float(nc[~full].sum()) * OPS_PER_CENTRE
 
 
+def variant_ops_per_key(deg: int, learn: int, offset: bool) -> int:
+    """Algorithmic FP32 operations of one (query, key) pair of a variant's
+    fused fit: forward (squared distance 6, exponent 1, monomials, polynomial
+    nv - 1, sums 2) plus backward (distance 6, exponent 1, upstream 1,
+    monomials, nv accumulations; the value f, f - O and the log-scale term
+    when the scale is learnt or the key moves; 3 offset terms and, for degree
+    >= 2, the polynomial's gradient and its 3 accumulations for offset keys).
+    Degree 1 with both key sets reproduces the default model's 12 + 18 / 21."""
+    nv = [1, 4, 10, 20][deg]
+    mono = [0, 0, 6, 16][deg]
+    fwd = 6 + 1 + mono + (nv - 1) + 2
+    bwd = 6 + 1 + 1 + mono + nv
+    if learn or offset:
+        bwd += (nv - 1) + 3
+    if offset:
+        bwd += 3 + ([0, 0, 9, 30][deg] + 3 if deg >= 2 else 0)
+    return fwd + bwd
+
+
+def variant_algorithmic_ops(q: np.ndarray, R: int, sets: int, deg: int, learn: int) -> float:
+    per_centre = sum(variant_ops_per_key(deg, learn, s == 2) for s in (1, 2) if sets & s)
+    return float(centres_per_query(q, R).sum()) * per_centre
+
+
 def centres_per_query(q: np.ndarray, R: int) -> np.ndarray:
     """Window size (number of centres) of every query, from the FP32 window rule."""
     u = (q[:, :3] + np.float32(1)) * np.float32(R * 0.5) - np.float32(0.5)
@@ -284,6 +308,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--eikonal-steps", type=int, default=100)
     ap.add_argument("--mean-shift-reps", type=int, default=20)
+    ap.add_argument("--variant-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -413,6 +438,39 @@ def main():
                    "ops_per_pair": MEAN_SHIFT_OPS_PER_PAIR}
         del scratch, pts
 
+    # ---- ablation variants of Table tab:ablation: the same fit (sort, pack,
+    # fused forward + L1 + backward, Adam) with each configuration's layout
+    variants = None
+    if args.variant_steps > 0:
+        variants = {}
+        for name in ("G-6", "G-7", "G-8", "Full-1"):
+            var = api.VARIANTS[name]
+            ch = api.variant_channels(name)
+            vp = torch.from_numpy((synth.rng(rank).standard_normal(R ** 3 * ch) * 1e-3).astype(np.float32)).to(dev)
+            vm, vv = torch.zeros_like(vp), torch.zeros_like(vp)
+            vws = api.VariantWorkspace(dev)
+            api.efunc_variant_fit(name, vp, vm, vv, pool, steps=3, J=J, n_batches=N_BATCHES, lr=LR, ws=vws)
+            torch.cuda.synchronize(dev)
+            api.profile_reset()
+            api.profile(True)
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            api.efunc_variant_fit(name, vp, vm, vv, pool, steps=args.variant_steps, J=J, n_batches=N_BATCHES,
+                                  step0=3, lr=LR, ws=vws)
+            v1.record(stream)
+            torch.cuda.synchronize(dev)
+            api.profile(False)
+            vms = max_over_ranks(v0.elapsed_time(v1) / args.variant_steps, dev)
+            fm, fn = api.profile_read("variant_fit")
+            kms = fm / max(1, fn)
+            vops = sum(variant_algorithmic_ops(pool_np[b * J:(b + 1) * J], R, *var) for b in range(N_BATCHES)) / N_BATCHES
+            vach = vops / (kms * 1e-3) / 1e12
+            variants[name] = {"variant": list(var), "channels": ch, "value": J * ws / (vms * 1e-3),
+                              "unit": "query-pts/s", "ms_per_step": vms, "fit_kernel_ms": kms,
+                              "achieved": vach, "peak": peak, "unit_roofline": "T FP32 op/s", "frac": vach / peak,
+                              "ops_per_launch": vops, "steps": args.variant_steps}
+            del vp, vm, vv, vws
+
     # ---- end to end through the C ABI with host buffers: the batch pool in
     # pinned host memory, every step copies its 64 MiB batch to the device
     # (overlapped with the previous step's compute by the library) and copies
@@ -459,6 +517,7 @@ def main():
             "e2e": e2e,
             "eikonal_fit": eik,
             "mean_shift_init": ms_init,
+            "variants": variants,
             "cpu_baseline": cpu_line,
             "clocks": clocks,
             "gpu_launches": launches,

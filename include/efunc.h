@@ -83,6 +83,33 @@ typedef struct {
     int32_t decoupled;
 } efunc_adam;
 
+/* Ablation variant of the representation (Table tab:ablation, Sec. 4.3).
+ *   sets         EFUNC_KEYS_GRID: fixed grid keys only (Config-G-*);
+ *                EFUNC_KEYS_OFFSET: offset keys k_i + Delta_i only
+ *                (Config-Full-1/2, learnable key positions);
+ *                EFUNC_KEYS_BOTH: both under one softmax (Full-3/4,
+ *                Eq. func-offset)
+ *   degree       0..3, degree of the value polynomial of Sec. 3.2
+ *                Eq. poly-func in Taylor form
+ *                  f(x) = o + d.x + 1/2 x^T S x + 1/6 T[x, x, x]
+ *                with S, T symmetric
+ *   learn_scale  1: a log-scale b per key, beta = exp(log_beta0 + b);
+ *                0: beta = exp(log_beta0) (Config-G-1..4)
+ * Parameter layout per centre (row of efunc_variant_channels floats), in the
+ * tuple order of Eq. func-offset: [Delta (3), if offset keys] [b of each key
+ * set, if learn_scale] [phi of each key set], grid set first, with
+ *   phi = (o, d_x, d_y, d_z, S_xx, S_yy, S_zz, S_xy, S_xz, S_yz, T_xxx,
+ *          T_yyy, T_zzz, T_xxy, T_xxz, T_xyy, T_yyz, T_xzz, T_yzz, T_xyz)
+ * truncated to 1, 4, 10 or 20 entries.  {EFUNC_KEYS_BOTH, 1, 1} is the
+ * 13-float layout of the default model. */
+typedef enum { EFUNC_KEYS_GRID = 1, EFUNC_KEYS_OFFSET = 2, EFUNC_KEYS_BOTH = 3 } efunc_key_sets;
+
+typedef struct {
+    int32_t sets;
+    int32_t degree;
+    int32_t learn_scale;
+} efunc_variant;
+
 /* ---------------------------------------------------------------- helpers */
 
 /* Number of floats in the parameter grid, R^3 * 13 (Sec. 3.3: theta in
@@ -222,6 +249,42 @@ efunc_status efunc_forward_noalloc(const efunc_grid *grid, const float *params, 
 efunc_status efunc_mean_shift_init(const efunc_grid *grid, const float *pts, int64_t N, float bandwidth,
                                    float *params, efunc_stream_t stream);
 
+/* ------------------------------------------------------- ablation variants */
+
+/* Floats per centre of a variant (the "Ch" column of Table tab:ablation:
+ * G-1..G-4 1/4/10/20, G-5..G-8 2/5/11/21, Full-1/2 8, Full-3/4 13); -1 for
+ * an invalid description. */
+int32_t efunc_variant_channels(const efunc_variant *variant);
+
+/* Workspace bytes of every variant call below for J queries; 0 if the grid
+ * or the variant is invalid. */
+size_t efunc_variant_workspace_bytes(const efunc_grid *grid, const efunc_variant *variant, int64_t J);
+
+/* Forward of a variant (Algorithm 1 over the windowed keys of its key sets,
+ * values of its degree): O and optionally lse per query, in the caller's
+ * order.  Arguments as efunc_forward; params [device] R^3 x channels. */
+efunc_status efunc_variant_forward(const efunc_grid *grid, const efunc_variant *variant, const float *params,
+                                   const float *q, int64_t J, int32_t q_stride, float *O, float *lse,
+                                   void *workspace, size_t workspace_bytes, efunc_stream_t stream);
+
+/* Backward of a variant (Algorithm 2): ACCUMULATES sum_j gO_j dO_j/dparams
+ * into grad [device, R^3 x channels].  dO/dphi = softmax * (Taylor factor) *
+ * monomial; dO/db = softmax * beta * (-|q - key|^2 (f - O)) for learnable
+ * scales; dO/dDelta = softmax * (2 beta (q - key)(f - O) - grad f) for
+ * offset keys.  Grid keys are fixed. */
+efunc_status efunc_variant_backward(const efunc_grid *grid, const efunc_variant *variant, const float *params,
+                                    const float *q, int64_t J, int32_t q_stride, const float *gO, float *grad,
+                                    void *workspace, size_t workspace_bytes, efunc_stream_t stream);
+
+/* Fitting loop of a variant (Sec. 3.4), as efunc_fit without the Eikonal
+ * term: per step sort, pack, fused forward + loss + backward, Adam on
+ * R^3 x channels floats.  qo and stats must be device memory (a host pointer
+ * returns EFUNC_ERR_ARG). */
+efunc_status efunc_variant_fit(const efunc_grid *grid, const efunc_variant *variant, const efunc_adam *adam,
+                               int32_t loss, float *params, float *m, float *v, const float *qo, int64_t J,
+                               int32_t n_batches, int32_t steps, int64_t step0, float *stats, void *workspace,
+                               size_t workspace_bytes, efunc_stream_t stream);
+
 /* ------------------------------------------------------------ measurement */
 
 /* When enabled, every kernel launch of the library is bracketed by CUDA
@@ -232,7 +295,8 @@ void efunc_profile_enable(int32_t enable);
 /* Waits for the recorded events and folds them into per-kernel totals.
  * Writes the total milliseconds and launch count of kernel `name` (one of
  * "bin", "scan_reduce", "scan_top", "scan_emit", "scatter", "pack_keys",
- * "forward", "fused_backward", "fused_fit", "adam", "mean_shift").  Returns 0 on success, -1 for an
+ * "forward", "fused_backward", "fused_fit", "adam", "mean_shift", "variant_pack",
+ * "variant_forward", "variant_backward", "variant_fit").  Returns 0 on success, -1 for an
  * unknown name or a CUDA error. */
 int32_t efunc_profile_read(const char *name, double *total_ms, int64_t *launches);
 

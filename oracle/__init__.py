@@ -61,7 +61,7 @@ def _load():
             lib.ora_mean_shift.argtypes = [i32, f64, dp, i64, dp]
             lib.ora_variant_channels.argtypes = [i32, i32, i32]
             lib.ora_variant_channels.restype = i32
-            lib.ora_variant_forward.argtypes = [i32, i32, f64, i32, i32, i32, dp, dp, i64, i32, dp, dp]
+            lib.ora_variant_forward.argtypes = [i32, i32, f64, i32, i32, i32, dp, dp, i64, i32, dp, dp, dp, dp]
             lib.ora_variant_backward.argtypes = [i32, i32, f64, i32, i32, i32, dp, dp, i64, i32, dp, dp]
             lib.ora_loss_grad.argtypes = [i32, dp, dp, i64, dp, dp, dp]
             lib.ora_adam.argtypes = [i64, dp, dp, dp, dp, i64, f64, f64, f64, f64, f64, i32]
@@ -209,15 +209,19 @@ def _variant_check(params, q, R, sets, deg, learn):
 
 
 def variant_forward(params, q, R: int, sets: int, deg: int, learn: int, W: int = 2,
-                    log_beta0: float | None = None):
-    """(O, lse) of an ablation variant (Table tab:ablation) at the queries."""
+                    log_beta0: float | None = None, want_diag: bool = False):
+    """(O, lse) of an ablation variant (Table tab:ablation) at the queries;
+    with want_diag also (kappa, fabs): the condition number of O under
+    relative rounding of exponents and weights, and sum softmax * sum |terms
+    of f| (the scale of f's own rounding)."""
     lb = default_log_beta0(R) if log_beta0 is None else float(log_beta0)
     params, q, _ = _variant_check(params, q, R, sets, deg, learn)
     J = q.shape[0]
     O, lse = np.zeros(J), np.zeros(J)
+    kap, fab = (np.zeros(J), np.zeros(J)) if want_diag else (None, None)
     _load().ora_variant_forward(R, W, lb, sets, deg, learn, _ptr(params), _ptr(q), J, q.shape[1], _ptr(O),
-                                _ptr(lse))
-    return O, lse
+                                _ptr(lse), _ptr(kap), _ptr(fab))
+    return (O, lse, kap, fab) if want_diag else (O, lse)
 
 
 def variant_backward(params, q, gO, R: int, sets: int, deg: int, learn: int, W: int = 2,

@@ -562,7 +562,8 @@ static var_key_t var_make_key(const double *params, double *grad, int R, double 
  *   dO/db       = softmax * beta * (-||x||^2 (f - O))
  *   dO/dDelta   = softmax * (-grad f(x) + 2 beta x (f - O)),  x = q - key */
 static void variant_one(const double *params, double *grad, double gO, int R, int W, double log_beta0, int sets,
-                        int deg, int learn, const double *q, double *O_out, double *lse_out)
+                        int deg, int learn, const double *q, double *O_out, double *lse_out, double *kappa,
+                        double *fabs_out)
 {
     int lo[3], hi[3];
     window_range(q, R, W, lo, hi);
@@ -588,6 +589,18 @@ static void variant_one(const double *params, double *grad, double gO, int R, in
                             double l = exp(expo - M);
                             e += l;
                             m += l * f;
+                        } else if (!grad) {
+                            /* diagnostics: kappa as in forward_one; fabs = sum softmax *
+                             * sum_m |phi_m df/dphi_m|, the scale of the rounding of f */
+                            double w = exp(expo - lse), fa = 0.0;
+                            for (int i = 0; i < VAR_NV[deg]; ++i) {
+                                double unit[20] = {0}, fu, gu[3];
+                                unit[i] = 1.0;
+                                var_poly(deg, unit, x, &fu, gu);
+                                fa += fabs(k.phi[i] * fu);
+                            }
+                            *kappa += w * (fabs(expo) + 1.0) * fabs(f - O);
+                            *fabs_out += w * fa;
                         } else {
                             double gl = gO * exp(expo - lse);
                             for (int i = 0; i < VAR_NV[deg]; ++i) {
@@ -607,19 +620,23 @@ static void variant_one(const double *params, double *grad, double gO, int R, in
             lse = M + log(e);
             *O_out = O;
             if (lse_out) *lse_out = lse;
-            if (!grad) return;
+            if (!grad && !kappa) return;
+            if (kappa) *kappa = *fabs_out = 0.0;
         }
     }
 }
 
 /* Forward of a variant over J queries (rows of q_stride doubles).
- * O, lse: J doubles (lse may be NULL). */
+ * O, lse: J doubles (lse may be NULL).  kappa, fabs: J doubles or both NULL
+ * (diagnostics for FP32 tolerances: kappa as in ora_forward, fabs = sum of
+ * softmax times the sum of the absolute terms of f). */
 void ora_variant_forward(int R, int W, double log_beta0, int sets, int deg, int learn, const double *params,
-                         const double *q, int64_t J, int q_stride, double *O, double *lse)
+                         const double *q, int64_t J, int q_stride, double *O, double *lse, double *kappa,
+                         double *fabs_out)
 {
     for (int64_t j = 0; j < J; ++j)
         variant_one(params, NULL, 0.0, R, W, log_beta0, sets, deg, learn, q + j * q_stride, &O[j],
-                    lse ? &lse[j] : NULL);
+                    lse ? &lse[j] : NULL, kappa ? &kappa[j] : NULL, kappa ? &fabs_out[j] : NULL);
 }
 
 /* Backward of a variant: grad (R^3 * channels doubles) ACCUMULATES
@@ -629,7 +646,7 @@ void ora_variant_backward(int R, int W, double log_beta0, int sets, int deg, int
 {
     for (int64_t j = 0; j < J; ++j) {
         double O;
-        variant_one(params, grad, gO[j], R, W, log_beta0, sets, deg, learn, q + j * q_stride, &O, NULL);
+        variant_one(params, grad, gO[j], R, W, log_beta0, sets, deg, learn, q + j * q_stride, &O, NULL, NULL, NULL);
     }
 }
 

@@ -30,6 +30,12 @@ class Adam(ctypes.Structure):
                 ("weight_decay", c_double), ("decoupled", c_int32)]
 
 
+class Variant(ctypes.Structure):
+    _fields_ = [("sets", c_int32), ("degree", c_int32), ("learn_scale", c_int32)]
+
+
+KEYS_GRID, KEYS_OFFSET, KEYS_BOTH = 1, 2, 3
+
 # name -> (restype, argtypes); the order follows include/efunc.h
 SIGNATURES = {
     "efunc_param_count": (c_int64, [c_int32]),
@@ -52,6 +58,15 @@ SIGNATURES = {
     "efunc_forward_noalloc": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_void_p, c_int64, c_int32, c_void_p,
                                         c_void_p, c_void_p, c_void_p]),
     "efunc_mean_shift_init": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_int64, c_float, c_void_p, c_void_p]),
+    "efunc_variant_channels": (c_int32, [ctypes.POINTER(Variant)]),
+    "efunc_variant_workspace_bytes": (c_size_t, [ctypes.POINTER(Grid), ctypes.POINTER(Variant), c_int64]),
+    "efunc_variant_forward": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Variant), c_void_p, c_void_p, c_int64,
+                                        c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "efunc_variant_backward": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Variant), c_void_p, c_void_p, c_int64,
+                                         c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "efunc_variant_fit": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Variant), ctypes.POINTER(Adam), c_int32,
+                                    c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int64,
+                                    c_void_p, c_void_p, c_size_t, c_void_p]),
     "efunc_profile_enable": (None, [c_int32]),
     "efunc_profile_read": (c_int32, [c_char_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     "efunc_profile_reset": (None, []),

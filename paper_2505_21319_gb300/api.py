@@ -175,6 +175,125 @@ def efunc_mean_shift_init(params: torch.Tensor, pts: torch.Tensor, bandwidth: fl
     return params
 
 
+# Configurations of Table tab:ablation: (key sets, value degree, learnable scale)
+VARIANTS = {
+    "G-1": (B.KEYS_GRID, 0, 0), "G-2": (B.KEYS_GRID, 1, 0), "G-3": (B.KEYS_GRID, 2, 0), "G-4": (B.KEYS_GRID, 3, 0),
+    "G-5": (B.KEYS_GRID, 0, 1), "G-6": (B.KEYS_GRID, 1, 1), "G-7": (B.KEYS_GRID, 2, 1), "G-8": (B.KEYS_GRID, 3, 1),
+    "Full-1": (B.KEYS_OFFSET, 1, 1), "Full-3": (B.KEYS_BOTH, 1, 1),
+}
+
+
+def make_variant(variant) -> B.Variant:
+    """A Variant from a Table tab:ablation name or a (sets, degree, learn_scale) tuple."""
+    if isinstance(variant, B.Variant):
+        return variant
+    sets, deg, learn = VARIANTS[variant] if isinstance(variant, str) else variant
+    return B.Variant(int(sets), int(deg), int(learn))
+
+
+def variant_channels(variant) -> int:
+    ch = int(B.load().efunc_variant_channels(ctypes.byref(make_variant(variant))))
+    if ch < 0:
+        raise ValueError(f"invalid variant {variant}")
+    return ch
+
+
+class VariantWorkspace(Workspace):
+    """Grow-only device scratch for the variant calls."""
+
+    def get_variant(self, grid: B.Grid, var: B.Variant, J: int) -> tuple[torch.Tensor, int]:
+        n = int(B.load().efunc_variant_workspace_bytes(ctypes.byref(grid), ctypes.byref(var), int(J)))
+        if n == 0:
+            raise ValueError("invalid grid, variant or query count")
+        if self.buf is None or self.buf.numel() < n:
+            self.buf = torch.empty(n, dtype=torch.uint8, device=self.device)
+        return self.buf, n
+
+
+_variant_ws: dict = {}
+
+
+def _vworkspace(device, ws):
+    if ws is not None:
+        return ws
+    key = torch.device(device).index if torch.device(device).index is not None else torch.cuda.current_device()
+    if key not in _variant_ws:
+        _variant_ws[key] = VariantWorkspace(torch.device("cuda", key))
+    return _variant_ws[key]
+
+
+def _variant_resolution(params, ch):
+    n = params.numel() // ch
+    R = int(round(n ** (1.0 / 3.0)))
+    if R ** 3 * ch != params.numel():
+        raise ValueError(f"params must hold R^3 * {ch} floats")
+    return R
+
+
+def efunc_variant_forward(variant, params: torch.Tensor, q: torch.Tensor, log_beta0: float | None = None,
+                          want_lse: bool = False, ws=None):
+    """O(q) of a Table tab:ablation variant; optionally lse."""
+    var = make_variant(variant)
+    R = _variant_resolution(params, variant_channels(var))
+    _need(params, "params")
+    J, stride = _queries(q)
+    grid = make_grid(R, log_beta0)
+    O = torch.empty(J, dtype=torch.float32, device=q.device)
+    lse = torch.empty(J, dtype=torch.float32, device=q.device) if want_lse else None
+    buf, n = _vworkspace(q.device, ws).get_variant(grid, var, J)
+    B.check("efunc_variant_forward", B.load().efunc_variant_forward(
+        ctypes.byref(grid), ctypes.byref(var), _ptr(params), _ptr(q), J, stride, _ptr(O), _ptr(lse), _ptr(buf), n,
+        _stream(q.device)))
+    return (O, lse) if want_lse else O
+
+
+def efunc_variant_backward(variant, params: torch.Tensor, q: torch.Tensor, gO: torch.Tensor,
+                           grad: torch.Tensor | None = None, log_beta0: float | None = None, ws=None):
+    """Accumulate sum_j gO_j dO_j/dparams of a variant into ``grad``."""
+    var = make_variant(variant)
+    R = _variant_resolution(params, variant_channels(var))
+    _need(params, "params")
+    J, stride = _queries(q)
+    _need(gO, "gO", J)
+    if grad is None:
+        grad = torch.zeros_like(params)
+    _need(grad, "grad", params.numel())
+    grid = make_grid(R, log_beta0)
+    buf, n = _vworkspace(q.device, ws).get_variant(grid, var, J)
+    B.check("efunc_variant_backward", B.load().efunc_variant_backward(
+        ctypes.byref(grid), ctypes.byref(var), _ptr(params), _ptr(q), J, stride, _ptr(gO), _ptr(grad), _ptr(buf), n,
+        _stream(q.device)))
+    return grad
+
+
+def efunc_variant_fit(variant, params, m, v, qo, steps: int, J: int | None = None, n_batches: int = 1,
+                      step0: int = 0, loss: str = "l1", stats=None, log_beta0: float | None = None, ws=None,
+                      **adam_kw):
+    """Fitting loop (Sec. 3.4) of a variant on device batches of (x, y, z, target) rows."""
+    var = make_variant(variant)
+    R = _variant_resolution(params, variant_channels(var))
+    for t, nm in ((params, "params"), (m, "m"), (v, "v")):
+        _need(t, nm, params.numel())
+    _need(qo, "qo")
+    if qo.dim() != 2 or qo.shape[1] != 4:
+        raise ValueError("qo must be (n_batches*J, 4)")
+    if J is None:
+        J = qo.shape[0] // n_batches
+    if J * n_batches != qo.shape[0]:
+        raise ValueError("qo must hold n_batches * J rows")
+    if stats is not None:
+        _need(stats, "stats")
+        if stats.numel() < 2 * steps:
+            raise ValueError("stats must hold at least 2*steps floats")
+    grid = make_grid(R, log_beta0)
+    ad = make_adam(**adam_kw)
+    buf, n = _vworkspace(params.device, ws).get_variant(grid, var, J)
+    lk = {"l1": B.LOSS_L1, "mse": B.LOSS_MSE}[loss]
+    B.check("efunc_variant_fit", B.load().efunc_variant_fit(
+        ctypes.byref(grid), ctypes.byref(var), ctypes.byref(ad), lk, _ptr(params), _ptr(m), _ptr(v), _ptr(qo), J,
+        n_batches, steps, step0, _ptr(stats), _ptr(buf), n, _stream(params.device)))
+
+
 def make_adam(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, decoupled=False) -> B.Adam:
     return B.Adam(lr, beta1, beta2, eps, weight_decay, int(bool(decoupled)))
 

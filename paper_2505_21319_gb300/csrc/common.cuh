@@ -38,7 +38,10 @@ struct Layout {
     size_t ctrl, hist, blocksum, rank, sorted, perm, items, keys, grad, stage, total;
 };
 
-Layout make_layout(int R, int64_t J);
+// Workspace layout for R^3 centres and J queries; key_records (float4) and
+// channels (floats) per centre size the key-record and gradient regions
+// (the default model: 4 and 13; the ablation variants need other sizes).
+Layout make_layout(int R, int64_t J, int key_records = 4, int channels = 13);
 
 // Sort configuration passed to kernels.
 struct SortArgs {
@@ -120,9 +123,35 @@ struct MeanShiftArgs {
     float *params;       // R^3 x 13, slots 0..2 written
 };
 
+// Ablation variants (Table tab:ablation): key sets, value degree, learnable
+// scales.  One persistent kernel per (mode, sets, degree) over the same
+// cell-sorted work items as the default model.
+struct VariantArgs {
+    int sets;            // 1 grid keys, 2 offset keys, 3 both
+    int deg;             // value polynomial degree 0..3
+    int learn;           // learnable log-scales
+    int channels;        // floats per centre
+    const float *params; // R^3 x channels
+    double log_beta0;
+    float4 *keys;        // packed records: R^3 x nsets x (1 + ceil(nv / 4)) float4
+    int R;
+    const float4 *sorted;
+    const int *perm;
+    const Item *items;
+    Ctrl *ctrl;
+    float *O;            // forward outputs (user order)
+    float *lse;
+    const float *gO;     // backward input (user order)
+    float *grad;         // R^3 x channels, accumulated
+    int loss;            // fit
+    float inv_J;
+};
+
+enum VariantMode { VAR_FORWARD = 0, VAR_BACKWARD = 1, VAR_FIT = 2 };
+
 // Kernel identifiers for the profiler.
 enum KernelId { K_BIN = 0, K_SCAN_REDUCE, K_SCAN_TOP, K_SCAN_EMIT, K_SCATTER, K_PACK_KEYS, K_FORWARD, K_FUSED_BWD,
-                K_FUSED_FIT, K_ADAM, K_MEAN_SHIFT, K_COUNT };
+                K_FUSED_FIT, K_ADAM, K_MEAN_SHIFT, K_VAR_PACK, K_VAR_FORWARD, K_VAR_BACKWARD, K_VAR_FIT, K_COUNT };
 
 // Launch bookkeeping (launch counter and optional CUDA-event profiling).
 void launch_begin(int kid, cudaStream_t s);
@@ -137,6 +166,9 @@ cudaError_t launch_fused_backward(const FusedArgs &a, bool with_gq, bool second_
 cudaError_t launch_fused_fit(const FusedArgs &a, bool eikonal, int grid, cudaStream_t s);
 cudaError_t launch_adam(const AdamArgs &a, cudaStream_t s);
 cudaError_t launch_mean_shift(const MeanShiftArgs &a, cudaStream_t s);
+cudaError_t launch_variant_pack(const VariantArgs &a, cudaStream_t s);
+cudaError_t launch_variant(const VariantArgs &a, int mode, cudaStream_t s);
+int variant_key_records(int sets, int deg);   // float4 records per centre
 int fused_grid_size();   // persistent grid: SMs x resident blocks per SM
 
 // Window-base index along one axis: clamp(floor((q+1)*R/2 - 1/2), -1, R-1),

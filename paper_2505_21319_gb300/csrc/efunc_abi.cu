@@ -31,7 +31,8 @@ int64_t g_launches = 0;
 
 const char *const kKernelNames[K_COUNT] = {"bin",       "scan_reduce", "scan_top",       "scan_emit", "scatter",
                                            "pack_keys", "forward",     "fused_backward", "fused_fit", "adam",
-                                           "mean_shift"};
+                                           "mean_shift", "variant_pack", "variant_forward", "variant_backward",
+                                           "variant_fit"};
 
 cudaEvent_t take_event()
 {
@@ -89,7 +90,7 @@ void launch_end(int kid, cudaStream_t s)
 
 // ------------------------------------------------------------- layout
 
-Layout make_layout(int R, int64_t J)
+Layout make_layout(int R, int64_t J, int key_records, int channels)
 {
     Layout L{};
     L.P = (R + 1 + kBrick - 1) / kBrick;
@@ -105,8 +106,8 @@ Layout make_layout(int R, int64_t J)
     L.sorted = off;    off = align_up(off + (size_t)J * 16, A);
     L.perm = off;      off = align_up(off + (size_t)J * 4, A);
     L.items = off;     off = align_up(off + (size_t)L.max_items * 16, A);
-    L.keys = off;      off = align_up(off + (size_t)R * R * R * kKeyRecords * 16, A);
-    L.grad = off;      off = align_up(off + (size_t)R * R * R * kSlots * 4, A);
+    L.keys = off;      off = align_up(off + (size_t)R * R * R * key_records * 16, A);
+    L.grad = off;      off = align_up(off + (size_t)R * R * R * channels * 4, A);
     L.stage = off;     off = align_up(off + (size_t)J * 32, A);   // two host-batch staging buffers
     L.total = off;
     return L;
@@ -257,6 +258,53 @@ efunc_status check_adam(const efunc_adam *a)
         (a->decoupled != 0 && a->decoupled != 1))
         return EFUNC_ERR_ARG;
     return EFUNC_OK;
+}
+
+// ------------------------------------------------------- ablation variants
+
+constexpr int kVariantNV[4] = {1, 4, 10, 20};
+
+bool variant_ok(const efunc_variant *v)
+{
+    return v && v->sets >= 1 && v->sets <= 3 && v->degree >= 0 && v->degree <= 3 &&
+           (v->learn_scale == 0 || v->learn_scale == 1);
+}
+
+int variant_channels_of(const efunc_variant *v)
+{
+    const int ns = (v->sets & 1) + ((v->sets >> 1) & 1);
+    return ((v->sets & 2) ? 3 : 0) + v->learn_scale * ns + kVariantNV[v->degree] * ns;
+}
+
+Layout variant_layout(const efunc_grid *g, const efunc_variant *v, int64_t J)
+{
+    return make_layout(g->R, J, variant_key_records(v->sets, v->degree), variant_channels_of(v));
+}
+
+efunc_status check_variant_workspace(const efunc_grid *g, const efunc_variant *v, int64_t J, const void *ws,
+                                     size_t ws_bytes)
+{
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return EFUNC_ERR_WORKSPACE;
+    if (ws_bytes < variant_layout(g, v, J).total) return EFUNC_ERR_WORKSPACE;
+    return EFUNC_OK;
+}
+
+VariantArgs variant_args(const Views &vw, const efunc_grid *g, const efunc_variant *v, const float *params)
+{
+    VariantArgs a{};
+    a.sets = v->sets;
+    a.deg = v->degree;
+    a.learn = v->learn_scale;
+    a.channels = variant_channels_of(v);
+    a.params = params;
+    a.log_beta0 = (double)g->log_beta0;
+    a.keys = vw.keys();
+    a.R = g->R;
+    a.sorted = vw.sorted();
+    a.perm = vw.perm();
+    a.items = vw.items();
+    a.ctrl = vw.ctrl();
+    return a;
 }
 
 AdamArgs adam_args(const efunc_adam *ad, int64_t n, float *p, float *g, float *m, float *v, int64_t step)
@@ -503,6 +551,102 @@ efunc_status efunc_mean_shift_init(const efunc_grid *grid, const float *pts, int
     a.sigma = (float)sqrt((double)bandwidth * 1.4426950408889634);
     a.params = params;
     return cuda_status(launch_mean_shift(a, (cudaStream_t)stream));
+}
+
+int32_t efunc_variant_channels(const efunc_variant *variant)
+{
+    if (!variant_ok(variant)) return -1;
+    const int ns = (variant->sets & 1) + ((variant->sets >> 1) & 1);
+    return ((variant->sets & 2) ? 3 : 0) + variant->learn_scale * ns + kVariantNV[variant->degree] * ns;
+}
+
+size_t efunc_variant_workspace_bytes(const efunc_grid *grid, const efunc_variant *variant, int64_t J)
+{
+    if (!grid_ok(grid) || !variant_ok(variant) || J < 0 || J > kMaxJ) return 0;
+    return variant_layout(grid, variant, J).total;
+}
+
+efunc_status efunc_variant_forward(const efunc_grid *grid, const efunc_variant *variant, const float *params,
+                                   const float *q, int64_t J, int32_t q_stride, float *O, float *lse,
+                                   void *workspace, size_t workspace_bytes, efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if (!variant_ok(variant)) return EFUNC_ERR_ARG;
+    if (J < 0 || J > kMaxJ || (q_stride != 3 && q_stride != 4) || !params) return EFUNC_ERR_ARG;
+    if (J == 0) return EFUNC_OK;
+    if (!q || !O) return EFUNC_ERR_ARG;
+    if ((st = check_variant_workspace(grid, variant, J, workspace, workspace_bytes))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Views v{variant_layout(grid, variant, J), static_cast<char *>(workspace)};
+    cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
+    VariantArgs a = variant_args(v, grid, variant, params);
+    if (e == cudaSuccess) e = launch_variant_pack(a, s);
+    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    a.O = O;
+    a.lse = lse;
+    return cuda_status(launch_variant(a, VAR_FORWARD, s));
+}
+
+efunc_status efunc_variant_backward(const efunc_grid *grid, const efunc_variant *variant, const float *params,
+                                    const float *q, int64_t J, int32_t q_stride, const float *gO, float *grad,
+                                    void *workspace, size_t workspace_bytes, efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if (!variant_ok(variant)) return EFUNC_ERR_ARG;
+    if (J < 0 || J > kMaxJ || (q_stride != 3 && q_stride != 4) || !params || !grad) return EFUNC_ERR_ARG;
+    if (J == 0) return EFUNC_OK;
+    if (!q || !gO) return EFUNC_ERR_ARG;
+    if ((st = check_variant_workspace(grid, variant, J, workspace, workspace_bytes))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Views v{variant_layout(grid, variant, J), static_cast<char *>(workspace)};
+    cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
+    VariantArgs a = variant_args(v, grid, variant, params);
+    if (e == cudaSuccess) e = launch_variant_pack(a, s);
+    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    a.gO = gO;
+    a.grad = grad;
+    return cuda_status(launch_variant(a, VAR_BACKWARD, s));
+}
+
+efunc_status efunc_variant_fit(const efunc_grid *grid, const efunc_variant *variant, const efunc_adam *adam,
+                               int32_t loss, float *params, float *m, float *v, const float *qo, int64_t J,
+                               int32_t n_batches, int32_t steps, int64_t step0, float *stats, void *workspace,
+                               size_t workspace_bytes, efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if (!variant_ok(variant)) return EFUNC_ERR_ARG;
+    if ((st = check_adam(adam))) return st;
+    if (loss != EFUNC_LOSS_L1 && loss != EFUNC_LOSS_MSE) return EFUNC_ERR_ARG;
+    if (J < 1 || J > kMaxJ || n_batches < 1 || steps < 0 || step0 < 0) return EFUNC_ERR_ARG;
+    if (!params || !m || !v || !qo) return EFUNC_ERR_ARG;
+    if ((st = check_variant_workspace(grid, variant, J, workspace, workspace_bytes))) return st;
+    if (steps == 0) return EFUNC_OK;
+    if (is_host_pointer(qo) || (stats && is_host_pointer(stats))) return EFUNC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Views vw{variant_layout(grid, variant, J), static_cast<char *>(workspace)};
+    const int64_t n = (int64_t)grid->R * grid->R * grid->R * efunc_variant_channels(variant);
+    float *grad = vw.grad();
+    if (cudaMemsetAsync(grad, 0, (size_t)n * 4, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    for (int32_t it = 0; it < steps; ++it) {
+        const float *qdev = qo + (size_t)(it % n_batches) * (size_t)J * 4;
+        cudaError_t e = sort_into(vw, grid->R, qdev, J, 4, vw.sorted(), nullptr, s);
+        VariantArgs a = variant_args(vw, grid, variant, params);
+        if (e == cudaSuccess) e = launch_variant_pack(a, s);
+        if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+        a.grad = grad;
+        a.loss = loss;
+        a.inv_J = (float)(1.0 / (double)J);
+        if (launch_variant(a, VAR_FIT, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        AdamArgs ad = adam_args(adam, n, params, grad, m, v, step0 + it + 1);
+        ad.ctrl = vw.ctrl();
+        ad.inv_J = a.inv_J;
+        ad.stats = stats ? stats + 2 * (size_t)it : nullptr;
+        if (launch_adam(ad, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    }
+    return EFUNC_OK;
 }
 
 void efunc_profile_enable(int32_t enable)

@@ -212,3 +212,38 @@ def sdf_params(shape: Shape, R: int, seed: int, noise: float = 0.02, delta_scale
     p[:, 9] = shape.sdf(ko) + noise * g.standard_normal(R ** 3)
     p[:, 10:13] = _sdf_grad(shape, ko) + noise * g.standard_normal((R ** 3, 3))
     return p.astype(np.float32)
+
+
+def variant_params(shape: Shape | None, R: int, sets: int, deg: int, learn: int, seed: int, noise: float = 0.02,
+                   delta_scale: float = 0.3, b_scale: float = 0.3, high_scale: float = 1.0) -> np.ndarray:
+    """(R^3, channels) float32 parameters of an ablation variant in the layout
+    [Delta (3) if offset keys] [b per key set if learnable] [phi per key set]
+    (grid set first), phi = (o, d, S (6), T (10)) truncated to the degree.
+    With a shape: o and d are the SDF and its gradient at the key plus
+    N(0, noise^2), second and third order entries N(0, high_scale^2); without
+    one every value entry is N(0, 0.5^2).  Offsets U(+-delta_scale) grid
+    spacings, log-scales N(0, b_scale^2)."""
+    g = rng(seed)
+    nv = [1, 4, 10, 20][deg]
+    nsets = (sets & 1) + ((sets >> 1) & 1)
+    base = 3 if sets & 2 else 0
+    ch = base + learn * nsets + nv * nsets
+    p = np.zeros((R ** 3, ch))
+    k = _grid_positions(R)
+    delta = g.uniform(-delta_scale, delta_scale, size=(R ** 3, 3)) * (2.0 / R)
+    if sets & 2:
+        p[:, 0:3] = delta
+    if learn:
+        p[:, base:base + nsets] = g.standard_normal((R ** 3, nsets)) * b_scale
+    off = base + learn * nsets
+    for si, s in enumerate([s for s in (0, 1) if sets & (1 << s)]):
+        pos = k + (delta if s == 1 else 0.0)
+        phi = np.zeros((R ** 3, 20))
+        if shape is None:
+            phi[:] = g.standard_normal((R ** 3, 20)) * 0.5
+        else:
+            phi[:, 0] = shape.sdf(pos) + noise * g.standard_normal(R ** 3)
+            phi[:, 1:4] = _sdf_grad(shape, pos) + noise * g.standard_normal((R ** 3, 3))
+            phi[:, 4:20] = g.standard_normal((R ** 3, 16)) * high_scale
+        p[:, off + si * nv: off + (si + 1) * nv] = phi[:, :nv]
+    return p.astype(np.float32)

@@ -107,6 +107,36 @@ def test_argument_validation_enqueues_nothing(lib):
     assert lib.efunc_launch_count() == 0
 
 
+def test_variant_helpers_and_validation(lib):
+    """Channel counts of the ablation variants and host-side rejection of
+    invalid variant requests (nothing launches)."""
+    from paper_2505_21319_gb300 import api
+    for name, (sets, deg, learn) in api.VARIANTS.items():
+        ch = lib.efunc_variant_channels(ctypes.byref(B.Variant(sets, deg, learn)))
+        assert ch == {"G-1": 1, "G-2": 4, "G-3": 10, "G-4": 20, "G-5": 2, "G-6": 5, "G-7": 11, "G-8": 21,
+                      "Full-1": 8, "Full-3": 13}[name]
+    for bad in ((0, 1, 1), (4, 1, 1), (1, 4, 1), (1, -1, 0), (3, 1, 2)):
+        assert lib.efunc_variant_channels(ctypes.byref(B.Variant(*bad))) == -1
+    assert lib.efunc_variant_channels(None) == -1
+    g = B.Grid(8, 2, 7.0)
+    v = B.Variant(3, 3, 1)
+    big = lib.efunc_variant_workspace_bytes(ctypes.byref(g), ctypes.byref(v), 1 << 16)
+    small = lib.efunc_variant_workspace_bytes(ctypes.byref(g), ctypes.byref(B.Variant(1, 0, 0)), 1 << 16)
+    assert big > small > 0 and big % 256 == 0
+    assert lib.efunc_variant_workspace_bytes(ctypes.byref(g), ctypes.byref(B.Variant(0, 1, 1)), 10) == 0
+    fwd = lib.efunc_variant_forward
+    assert fwd(ctypes.byref(g), ctypes.byref(B.Variant(5, 1, 1)), 4096, 8192, 16, 3, 12288, None, 1 << 30, 1 << 40,
+               None) == 1                                                                   # bad variant
+    assert fwd(ctypes.byref(g), ctypes.byref(v), 4096, 8192, 16, 3, 12288, None, 1 << 30, 100, None) == 3
+    assert fwd(ctypes.byref(g), ctypes.byref(v), 4096, 8192, 0, 3, None, None, 1 << 30, 1 << 40, None) == 0
+    assert lib.efunc_variant_backward(ctypes.byref(g), ctypes.byref(v), 4096, 8192, 16, 3, None, 4096, 1 << 30,
+                                      1 << 40, None) == 1                                    # no gO
+    ad = B.Adam(1e-3, 0.9, 0.999, 1e-8, 0.0, 0)
+    assert lib.efunc_variant_fit(ctypes.byref(g), ctypes.byref(v), ctypes.byref(ad), 0, 16, 32, 48, 64, 10, 0, 1, 0,
+                                 None, 1 << 30, 1 << 40, None) == 1                          # no batches
+    assert lib.efunc_launch_count() == 0
+
+
 def test_profile_api_without_gpu(lib):
     ms, cnt = ctypes.c_double(1.0), ctypes.c_int64(1)
     lib.efunc_profile_reset()
