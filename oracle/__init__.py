@@ -63,6 +63,8 @@ def _load():
             lib.ora_variant_channels.restype = i32
             lib.ora_variant_forward.argtypes = [i32, i32, f64, i32, i32, i32, dp, dp, i64, i32, dp, dp, dp, dp]
             lib.ora_variant_backward.argtypes = [i32, i32, f64, i32, i32, i32, dp, dp, i64, i32, dp, dp]
+            lib.ora_cosine_forward.argtypes = [i32, i32, f64, i32, dp, dp, i64, i32, dp]
+            lib.ora_cosine_backward.argtypes = [i32, i32, f64, i32, dp, dp, i64, i32, dp, dp]
             lib.ora_loss_grad.argtypes = [i32, dp, dp, i64, dp, dp, dp]
             lib.ora_adam.argtypes = [i64, dp, dp, dp, dp, i64, f64, f64, f64, f64, f64, i32]
             for fn in ("ora_forward", "ora_backward", "ora_forward_global", "ora_loss_grad", "ora_adam",
@@ -235,6 +237,34 @@ def variant_backward(params, q, gO, R: int, sets: int, deg: int, learn: int, W: 
     grad = np.zeros((R ** 3, ch))
     _load().ora_variant_backward(R, W, lb, sets, deg, learn, _ptr(params), _ptr(q), q.shape[0], q.shape[1],
                                  _ptr(gO), _ptr(grad))
+    return grad
+
+
+def _cosine_check(params, q, R, B):
+    params = _f64(params).reshape(B, R ** 3, 5)
+    q = _f64(q)
+    if q.ndim != 2 or q.shape[1] not in (3, 4):
+        raise ValueError("q must be (J, 3) or (J, 4)")
+    return params, q
+
+
+def cosine_forward(params, q, R: int, B: int, W: int = 2, log_beta0: float | None = None):
+    """S(q) of the cosine-series decomposition (Sec. 4.4): B bands of
+    Config-G-6 grids (B x R^3 x 5), weights cos(b pi q_x) cos(b pi q_y) cos(b pi q_z)."""
+    lb = default_log_beta0(R) if log_beta0 is None else float(log_beta0)
+    params, q = _cosine_check(params, q, R, B)
+    S = np.zeros(q.shape[0])
+    _load().ora_cosine_forward(R, W, lb, B, _ptr(params), _ptr(q), q.shape[0], q.shape[1], _ptr(S))
+    return S
+
+
+def cosine_backward(params, q, gS, R: int, B: int, W: int = 2, log_beta0: float | None = None):
+    """sum_j gS_j dS_j/dparams, (B, R^3, 5)."""
+    lb = default_log_beta0(R) if log_beta0 is None else float(log_beta0)
+    params, q = _cosine_check(params, q, R, B)
+    gS = _f64(gS).reshape(-1)
+    grad = np.zeros((B, R ** 3, 5))
+    _load().ora_cosine_backward(R, W, lb, B, _ptr(params), _ptr(q), q.shape[0], q.shape[1], _ptr(gS), _ptr(grad))
     return grad
 
 

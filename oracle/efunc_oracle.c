@@ -650,6 +650,53 @@ void ora_variant_backward(int R, int W, double log_beta0, int sets, int deg, int
     }
 }
 
+/* ---------------------------------------------- cosine-series decomposition */
+
+/* Sec. 4.4 Eq. o-as-value / Eq. cosine-series: S(q) = sum_b w_b(q) O_b(q)
+ * with cosine weights and one Config-G-6 representation per band (grid keys,
+ * first-order values, learnable scales: 5 floats per centre).  Readings: the
+ * weight of band b at a 3-D query is the separable cosine
+ *   w_b(q) = cos(b pi q_x) cos(b pi q_y) cos(b pi q_z),
+ * and there are B bands b = 0 .. B-1 (20480 B parameters at 16^3, and B = 1
+ * is Config-G-6).  params: B blocks of R^3 x 5 floats, band-major. */
+static double cosine_weight(int b, const double *q)
+{
+    const double pi = 3.14159265358979323846;
+    return cos(b * pi * q[0]) * cos(b * pi * q[1]) * cos(b * pi * q[2]);
+}
+
+void ora_cosine_forward(int R, int W, double log_beta0, int B, const double *params, const double *q, int64_t J,
+                        int q_stride, double *S)
+{
+    const size_t band = (size_t)R * R * R * 5;
+    for (int64_t j = 0; j < J; ++j) {
+        const double *qj = q + j * q_stride;
+        double s = 0.0;
+        for (int b = 0; b < B; ++b) {
+            double O;
+            variant_one(params + b * band, NULL, 0.0, R, W, log_beta0, 1, 1, 1, qj, &O, NULL, NULL, NULL);
+            s += cosine_weight(b, qj) * O;
+        }
+        S[j] = s;
+    }
+}
+
+/* dS/dtheta_b = w_b(q) dO_b/dtheta_b: each band's backward with upstream
+ * gS_j w_b(q_j).  grad (B x R^3 x 5) is ACCUMULATED into. */
+void ora_cosine_backward(int R, int W, double log_beta0, int B, const double *params, const double *q, int64_t J,
+                         int q_stride, const double *gS, double *grad)
+{
+    const size_t band = (size_t)R * R * R * 5;
+    for (int64_t j = 0; j < J; ++j) {
+        const double *qj = q + j * q_stride;
+        for (int b = 0; b < B; ++b) {
+            double O;
+            variant_one(params + b * band, grad + b * band, gS[j] * cosine_weight(b, qj), R, W, log_beta0, 1, 1, 1,
+                        qj, &O, NULL, NULL, NULL);
+        }
+    }
+}
+
 /* ------------------------------------------------------------------ loss */
 
 /* Eq. loss (MSE) and the L1 variant: the upstream gradient dL/dO_j and the

@@ -632,3 +632,64 @@ def test_variant_gradients_match_central_differences(sets, deg, learn):
             an.append(grad[i, s])
     an, fd = np.array(an), np.array(fd)
     np.testing.assert_allclose(an, fd, rtol=2e-6, atol=2e-8 * max(1.0, np.abs(an).max()))
+
+
+# ------------------------------------------- cosine-series decomposition pins
+
+def test_cosine_series_one_band_is_config_g6():
+    """Sec. 4.4: with one band (b = 0, weight cos 0 = 1) the decomposition is
+    Config-G-6 at the same resolution."""
+    R = 5
+    p = synth.variant_params(synth.random_union(3), R, 1, 1, 1, seed=3).astype(np.float64)
+    q = queries(4, 70)
+    S = oracle.cosine_forward(p[None], q, R, 1)
+    O, _ = oracle.variant_forward(p, q, R, 1, 1, 1)
+    np.testing.assert_allclose(S, O, rtol=0, atol=1e-15)
+    gS = synth.rng(5).standard_normal(q.shape[0])
+    np.testing.assert_allclose(oracle.cosine_backward(p[None], q, gS, R, 1)[0],
+                               oracle.variant_backward(p, q, gS, R, 1, 1, 1), rtol=0, atol=1e-14)
+
+
+def test_cosine_series_of_constant_bands_is_the_cosine_sum():
+    """Bands holding constant values c_b (partition of unity: O_b = c_b for
+    any scales) give S(q) = sum_b c_b cos(b pi x) cos(b pi y) cos(b pi z),
+    the truncated Fourier cosine series of Eq. cosine-series."""
+    R, B = 4, 5
+    rng = synth.rng(8)
+    c = rng.standard_normal(B)
+    p = np.zeros((B, R ** 3, 5))
+    p[:, :, 0] = rng.normal(0.0, 0.5, (B, R ** 3))
+    p[:, :, 1] = c[:, None]
+    q = queries(9, 100, spread=1.0)
+    S = oracle.cosine_forward(p, q, R, B)
+    b = np.arange(B)[None, :]
+    ref = (c[None, :] * np.cos(b * np.pi * q[:, 0:1]) * np.cos(b * np.pi * q[:, 1:2]) *
+           np.cos(b * np.pi * q[:, 2:3])).sum(1)
+    np.testing.assert_allclose(S, ref, rtol=0, atol=1e-13)
+
+
+def test_cosine_series_gradients_match_central_differences():
+    R, B = 4, 3
+    rng = synth.rng(12)
+    p = rng.normal(0.0, 0.3, (B, R ** 3, 5))
+    lb = oracle.default_log_beta0(R) - 1.0
+    q = rng.uniform(-0.9, 0.9, (5, 3))
+    t = (q + 1) * R / 2 - 0.5
+    frac = t - np.floor(t)
+    q = np.where(np.minimum(frac, 1 - frac) < 1e-3, q + 0.01, q).astype(np.float32).astype(np.float64)
+    gS = rng.standard_normal(q.shape[0])
+    grad = oracle.cosine_backward(p, q, gS, R, B, 2, lb)
+    flat = grad.reshape(-1, 5)
+    touched = np.flatnonzero(np.abs(flat).sum(1) > 0)
+    sel = rng.choice(touched, size=min(8, touched.size), replace=False)
+    an, fd = [], []
+    for i in sel:
+        for s in range(5):
+            hstep = 1e-6 * max(1.0, abs(p.reshape(-1, 5)[i, s]))
+            pp, pm = p.copy().reshape(-1, 5), p.copy().reshape(-1, 5)
+            pp[i, s] += hstep
+            pm[i, s] -= hstep
+            fd.append((gS @ oracle.cosine_forward(pp, q, R, B, 2, lb) - gS @ oracle.cosine_forward(pm, q, R, B, 2, lb))
+                      / (2 * hstep))
+            an.append(flat[i, s])
+    np.testing.assert_allclose(np.array(an), np.array(fd), rtol=2e-6, atol=2e-8 * max(1.0, np.abs(an).max()))
