@@ -309,6 +309,7 @@ def main():
     ap.add_argument("--eikonal-steps", type=int, default=100)
     ap.add_argument("--mean-shift-reps", type=int, default=20)
     ap.add_argument("--variant-steps", type=int, default=50)
+    ap.add_argument("--cosine-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -471,6 +472,39 @@ def main():
                               "ops_per_launch": vops, "steps": args.variant_steps}
             del vp, vm, vv, vws
 
+    # ---- cosine-series decomposition (Sec. 4.4): B bands of 16^3 Config-G-6
+    # grids, the paper's resolution, fitted on the same batches
+    cosine = None
+    if args.cosine_steps > 0:
+        cosine = {}
+        Rc = 16
+        for Bc in (1, 4, 8):
+            cp = torch.from_numpy((synth.rng(rank).standard_normal(Bc * Rc ** 3 * 5) * 1e-3).astype(np.float32)).to(dev)
+            cm, cv = torch.zeros_like(cp), torch.zeros_like(cp)
+            cws = api.CosineWorkspace(dev)
+            api.efunc_cosine_fit(Bc, cp, cm, cv, pool, steps=3, J=J, n_batches=N_BATCHES, lr=LR, ws=cws)
+            torch.cuda.synchronize(dev)
+            api.profile_reset()
+            api.profile(True)
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            api.efunc_cosine_fit(Bc, cp, cm, cv, pool, steps=args.cosine_steps, J=J, n_batches=N_BATCHES, step0=3,
+                                 lr=LR, ws=cws)
+            c1.record(stream)
+            torch.cuda.synchronize(dev)
+            api.profile(False)
+            cms = max_over_ranks(c0.elapsed_time(c1) / args.cosine_steps, dev)
+            fm, fn = api.profile_read("cosine_fit")
+            kms = fm / max(1, fn)
+            cops = Bc * sum(variant_algorithmic_ops(pool_np[b * J:(b + 1) * J], Rc, 1, 1, 1)
+                            for b in range(N_BATCHES)) / N_BATCHES
+            cach = cops / (kms * 1e-3) / 1e12
+            cosine[f"B={Bc}"] = {"bands": Bc, "R": Rc, "value": J * ws / (cms * 1e-3), "unit": "query-pts/s",
+                                 "ms_per_step": cms, "fit_kernel_ms": kms, "achieved": cach, "peak": peak,
+                                 "unit_roofline": "T FP32 op/s", "frac": cach / peak, "ops_per_launch": cops,
+                                 "steps": args.cosine_steps}
+            del cp, cm, cv, cws
+
     # ---- end to end through the C ABI with host buffers: the batch pool in
     # pinned host memory, every step copies its 64 MiB batch to the device
     # (overlapped with the previous step's compute by the library) and copies
@@ -518,6 +552,7 @@ def main():
             "eikonal_fit": eik,
             "mean_shift_init": ms_init,
             "variants": variants,
+            "cosine_series": cosine,
             "cpu_baseline": cpu_line,
             "clocks": clocks,
             "gpu_launches": launches,

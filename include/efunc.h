@@ -285,6 +285,39 @@ efunc_status efunc_variant_fit(const efunc_grid *grid, const efunc_variant *vari
                                int32_t n_batches, int32_t steps, int64_t step0, float *stats, void *workspace,
                                size_t workspace_bytes, efunc_stream_t stream);
 
+/* ------------------------------------------- cosine-series decomposition */
+
+/* Function decomposition of Sec. 4.4 (Eq. o-as-value, Eq. cosine-series):
+ *   S(q) = sum_{b=0}^{B-1} w_b(q) O_b(q),
+ *   w_b(q) = cos(b pi q_x) cos(b pi q_y) cos(b pi q_z),
+ * with every band O_b a Config-G-6 representation (fixed grid keys, first
+ * order values, learnable log-scale: 5 floats per centre, (b, o, d_x, d_y,
+ * d_z)).  The paper's 3-D weight "cos(b pi q)" is read as the separable
+ * product, and its B bands as b = 0 .. B-1 (20480 B floats at 16^3; B = 1
+ * is Config-G-6).  bands in [1, 16].
+ *   params  [device] B x R^3 x 5 floats, band-major
+ * Workspace: efunc_cosine_workspace_bytes (0 for an invalid grid, band count
+ * or J). */
+size_t efunc_cosine_workspace_bytes(const efunc_grid *grid, int32_t bands, int64_t J);
+
+/* S at J queries (caller's order), arguments as efunc_forward. */
+efunc_status efunc_cosine_forward(const efunc_grid *grid, int32_t bands, const float *params, const float *q,
+                                  int64_t J, int32_t q_stride, float *S, void *workspace, size_t workspace_bytes,
+                                  efunc_stream_t stream);
+
+/* ACCUMULATES sum_j gS_j dS_j/dparams into grad [device, B x R^3 x 5]:
+ * band b's backward (Algorithm 2) with upstream gS_j w_b(q_j). */
+efunc_status efunc_cosine_backward(const efunc_grid *grid, int32_t bands, const float *params, const float *q,
+                                   int64_t J, int32_t q_stride, const float *gS, float *grad, void *workspace,
+                                   size_t workspace_bytes, efunc_stream_t stream);
+
+/* Fitting loop of S (Sec. 4.4 optimises S as in Eq. loss), as
+ * efunc_variant_fit: device batches and statistics only. */
+efunc_status efunc_cosine_fit(const efunc_grid *grid, int32_t bands, const efunc_adam *adam, int32_t loss,
+                              float *params, float *m, float *v, const float *qo, int64_t J, int32_t n_batches,
+                              int32_t steps, int64_t step0, float *stats, void *workspace, size_t workspace_bytes,
+                              efunc_stream_t stream);
+
 /* ------------------------------------------------------------ measurement */
 
 /* When enabled, every kernel launch of the library is bracketed by CUDA
@@ -296,7 +329,8 @@ void efunc_profile_enable(int32_t enable);
  * Writes the total milliseconds and launch count of kernel `name` (one of
  * "bin", "scan_reduce", "scan_top", "scan_emit", "scatter", "pack_keys",
  * "forward", "fused_backward", "fused_fit", "adam", "mean_shift", "variant_pack",
- * "variant_forward", "variant_backward", "variant_fit").  Returns 0 on success, -1 for an
+ * "variant_forward", "variant_backward", "variant_fit", "cosine_pack",
+ * "cosine_forward", "cosine_backward", "cosine_fit").  Returns 0 on success, -1 for an
  * unknown name or a CUDA error. */
 int32_t efunc_profile_read(const char *name, double *total_ms, int64_t *launches);
 

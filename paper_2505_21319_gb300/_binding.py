@@ -67,6 +67,14 @@ SIGNATURES = {
     "efunc_variant_fit": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Variant), ctypes.POINTER(Adam), c_int32,
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int64,
                                     c_void_p, c_void_p, c_size_t, c_void_p]),
+    "efunc_cosine_workspace_bytes": (c_size_t, [ctypes.POINTER(Grid), c_int32, c_int64]),
+    "efunc_cosine_forward": (c_int32, [ctypes.POINTER(Grid), c_int32, c_void_p, c_void_p, c_int64, c_int32, c_void_p,
+                                       c_void_p, c_size_t, c_void_p]),
+    "efunc_cosine_backward": (c_int32, [ctypes.POINTER(Grid), c_int32, c_void_p, c_void_p, c_int64, c_int32,
+                                        c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "efunc_cosine_fit": (c_int32, [ctypes.POINTER(Grid), c_int32, ctypes.POINTER(Adam), c_int32, c_void_p, c_void_p,
+                                   c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int64, c_void_p, c_void_p,
+                                   c_size_t, c_void_p]),
     "efunc_profile_enable": (None, [c_int32]),
     "efunc_profile_read": (c_int32, [c_char_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     "efunc_profile_reset": (None, []),

@@ -294,6 +294,91 @@ def efunc_variant_fit(variant, params, m, v, qo, steps: int, J: int | None = Non
         n_batches, steps, step0, _ptr(stats), _ptr(buf), n, _stream(params.device)))
 
 
+class CosineWorkspace(Workspace):
+    """Grow-only device scratch for the cosine-series calls."""
+
+    def get_cosine(self, grid: B.Grid, bands: int, J: int) -> tuple[torch.Tensor, int]:
+        n = int(B.load().efunc_cosine_workspace_bytes(ctypes.byref(grid), int(bands), int(J)))
+        if n == 0:
+            raise ValueError("invalid grid, band count or query count")
+        if self.buf is None or self.buf.numel() < n:
+            self.buf = torch.empty(n, dtype=torch.uint8, device=self.device)
+        return self.buf, n
+
+
+_cosine_ws: dict = {}
+
+
+def _cworkspace(device, ws):
+    if ws is not None:
+        return ws
+    key = torch.device(device).index if torch.device(device).index is not None else torch.cuda.current_device()
+    if key not in _cosine_ws:
+        _cosine_ws[key] = CosineWorkspace(torch.device("cuda", key))
+    return _cosine_ws[key]
+
+
+def _cosine_resolution(params, bands):
+    return _variant_resolution(params, 5 * bands)
+
+
+def efunc_cosine_forward(bands: int, params: torch.Tensor, q: torch.Tensor, log_beta0: float | None = None,
+                         ws=None):
+    """S(q) of the cosine-series decomposition (Sec. 4.4); params (B, R^3, 5)."""
+    R = _cosine_resolution(params, bands)
+    _need(params, "params")
+    J, stride = _queries(q)
+    grid = make_grid(R, log_beta0)
+    S = torch.empty(J, dtype=torch.float32, device=q.device)
+    buf, n = _cworkspace(q.device, ws).get_cosine(grid, bands, J)
+    B.check("efunc_cosine_forward", B.load().efunc_cosine_forward(
+        ctypes.byref(grid), int(bands), _ptr(params), _ptr(q), J, stride, _ptr(S), _ptr(buf), n, _stream(q.device)))
+    return S
+
+
+def efunc_cosine_backward(bands: int, params: torch.Tensor, q: torch.Tensor, gS: torch.Tensor,
+                          grad: torch.Tensor | None = None, log_beta0: float | None = None, ws=None):
+    """Accumulate sum_j gS_j dS_j/dparams into ``grad``."""
+    R = _cosine_resolution(params, bands)
+    _need(params, "params")
+    J, stride = _queries(q)
+    _need(gS, "gS", J)
+    if grad is None:
+        grad = torch.zeros_like(params)
+    _need(grad, "grad", params.numel())
+    grid = make_grid(R, log_beta0)
+    buf, n = _cworkspace(q.device, ws).get_cosine(grid, bands, J)
+    B.check("efunc_cosine_backward", B.load().efunc_cosine_backward(
+        ctypes.byref(grid), int(bands), _ptr(params), _ptr(q), J, stride, _ptr(gS), _ptr(grad), _ptr(buf), n,
+        _stream(q.device)))
+    return grad
+
+
+def efunc_cosine_fit(bands: int, params, m, v, qo, steps: int, J: int | None = None, n_batches: int = 1,
+                     step0: int = 0, loss: str = "l1", stats=None, log_beta0: float | None = None, ws=None,
+                     **adam_kw):
+    """Fitting loop of S (Sec. 4.4) on device batches of (x, y, z, target) rows."""
+    R = _cosine_resolution(params, bands)
+    for t, nm in ((params, "params"), (m, "m"), (v, "v")):
+        _need(t, nm, params.numel())
+    _need(qo, "qo")
+    if qo.dim() != 2 or qo.shape[1] != 4:
+        raise ValueError("qo must be (n_batches*J, 4)")
+    if J is None:
+        J = qo.shape[0] // n_batches
+    if J * n_batches != qo.shape[0]:
+        raise ValueError("qo must hold n_batches * J rows")
+    if stats is not None:
+        _need(stats, "stats")
+    grid = make_grid(R, log_beta0)
+    ad = make_adam(**adam_kw)
+    buf, n = _cworkspace(params.device, ws).get_cosine(grid, bands, J)
+    lk = {"l1": B.LOSS_L1, "mse": B.LOSS_MSE}[loss]
+    B.check("efunc_cosine_fit", B.load().efunc_cosine_fit(
+        ctypes.byref(grid), int(bands), ctypes.byref(ad), lk, _ptr(params), _ptr(m), _ptr(v), _ptr(qo), J,
+        n_batches, steps, step0, _ptr(stats), _ptr(buf), n, _stream(params.device)))
+
+
 def make_adam(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, decoupled=False) -> B.Adam:
     return B.Adam(lr, beta1, beta2, eps, weight_decay, int(bool(decoupled)))
 

@@ -149,9 +149,31 @@ struct VariantArgs {
 
 enum VariantMode { VAR_FORWARD = 0, VAR_BACKWARD = 1, VAR_FIT = 2 };
 
+// Cosine-series decomposition (Sec. 4.4): B bands of Config-G-6 grids
+// (5 floats per centre: b, o, d), S(q) = sum_b w_b(q) O_b(q).
+constexpr int kMaxBands = 16;
+
+struct CosineArgs {
+    int B;               // bands, 1..kMaxBands
+    const float *params; // B x R^3 x 5, band-major
+    double log_beta0;
+    float4 *keys;        // packed records: B x R^3 x 2 float4
+    int R;
+    const float4 *sorted;
+    const int *perm;
+    const Item *items;
+    Ctrl *ctrl;
+    float *S;            // forward output (user order)
+    const float *gS;     // backward input (user order)
+    float *grad;         // B x R^3 x 5, accumulated
+    int loss;
+    float inv_J;
+};
+
 // Kernel identifiers for the profiler.
 enum KernelId { K_BIN = 0, K_SCAN_REDUCE, K_SCAN_TOP, K_SCAN_EMIT, K_SCATTER, K_PACK_KEYS, K_FORWARD, K_FUSED_BWD,
-                K_FUSED_FIT, K_ADAM, K_MEAN_SHIFT, K_VAR_PACK, K_VAR_FORWARD, K_VAR_BACKWARD, K_VAR_FIT, K_COUNT };
+                K_FUSED_FIT, K_ADAM, K_MEAN_SHIFT, K_VAR_PACK, K_VAR_FORWARD, K_VAR_BACKWARD, K_VAR_FIT, K_COS_PACK, K_COS_FORWARD, K_COS_BACKWARD,
+                K_COS_FIT, K_COUNT };
 
 // Launch bookkeeping (launch counter and optional CUDA-event profiling).
 void launch_begin(int kid, cudaStream_t s);
@@ -169,6 +191,8 @@ cudaError_t launch_mean_shift(const MeanShiftArgs &a, cudaStream_t s);
 cudaError_t launch_variant_pack(const VariantArgs &a, cudaStream_t s);
 cudaError_t launch_variant(const VariantArgs &a, int mode, cudaStream_t s);
 int variant_key_records(int sets, int deg);   // float4 records per centre
+cudaError_t launch_cosine_pack(const CosineArgs &a, cudaStream_t s);
+cudaError_t launch_cosine(const CosineArgs &a, int mode, cudaStream_t s);   // mode: VariantMode
 int fused_grid_size();   // persistent grid: SMs x resident blocks per SM
 
 // Window-base index along one axis: clamp(floor((q+1)*R/2 - 1/2), -1, R-1),

@@ -32,7 +32,8 @@ int64_t g_launches = 0;
 const char *const kKernelNames[K_COUNT] = {"bin",       "scan_reduce", "scan_top",       "scan_emit", "scatter",
                                            "pack_keys", "forward",     "fused_backward", "fused_fit", "adam",
                                            "mean_shift", "variant_pack", "variant_forward", "variant_backward",
-                                           "variant_fit"};
+                                           "variant_fit", "cosine_pack", "cosine_forward", "cosine_backward",
+                                           "cosine_fit"};
 
 cudaEvent_t take_event()
 {
@@ -296,6 +297,34 @@ VariantArgs variant_args(const Views &vw, const efunc_grid *g, const efunc_varia
     a.deg = v->degree;
     a.learn = v->learn_scale;
     a.channels = variant_channels_of(v);
+    a.params = params;
+    a.log_beta0 = (double)g->log_beta0;
+    a.keys = vw.keys();
+    a.R = g->R;
+    a.sorted = vw.sorted();
+    a.perm = vw.perm();
+    a.items = vw.items();
+    a.ctrl = vw.ctrl();
+    return a;
+}
+
+// ---------------------------------------------- cosine-series decomposition
+
+bool bands_ok(int32_t B) { return B >= 1 && B <= kMaxBands; }
+
+Layout cosine_layout(const efunc_grid *g, int32_t B, int64_t J) { return make_layout(g->R, J, 2 * B, 5 * B); }
+
+efunc_status check_cosine_workspace(const efunc_grid *g, int32_t B, int64_t J, const void *ws, size_t ws_bytes)
+{
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return EFUNC_ERR_WORKSPACE;
+    if (ws_bytes < cosine_layout(g, B, J).total) return EFUNC_ERR_WORKSPACE;
+    return EFUNC_OK;
+}
+
+CosineArgs cosine_args(const Views &vw, const efunc_grid *g, int32_t B, const float *params)
+{
+    CosineArgs a{};
+    a.B = B;
     a.params = params;
     a.log_beta0 = (double)g->log_beta0;
     a.keys = vw.keys();
@@ -640,6 +669,94 @@ efunc_status efunc_variant_fit(const efunc_grid *grid, const efunc_variant *vari
         a.loss = loss;
         a.inv_J = (float)(1.0 / (double)J);
         if (launch_variant(a, VAR_FIT, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        AdamArgs ad = adam_args(adam, n, params, grad, m, v, step0 + it + 1);
+        ad.ctrl = vw.ctrl();
+        ad.inv_J = a.inv_J;
+        ad.stats = stats ? stats + 2 * (size_t)it : nullptr;
+        if (launch_adam(ad, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    }
+    return EFUNC_OK;
+}
+
+size_t efunc_cosine_workspace_bytes(const efunc_grid *grid, int32_t bands, int64_t J)
+{
+    if (!grid_ok(grid) || !bands_ok(bands) || J < 0 || J > kMaxJ) return 0;
+    return cosine_layout(grid, bands, J).total;
+}
+
+efunc_status efunc_cosine_forward(const efunc_grid *grid, int32_t bands, const float *params, const float *q,
+                                  int64_t J, int32_t q_stride, float *S, void *workspace, size_t workspace_bytes,
+                                  efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if (!bands_ok(bands)) return EFUNC_ERR_ARG;
+    if (J < 0 || J > kMaxJ || (q_stride != 3 && q_stride != 4) || !params) return EFUNC_ERR_ARG;
+    if (J == 0) return EFUNC_OK;
+    if (!q || !S) return EFUNC_ERR_ARG;
+    if ((st = check_cosine_workspace(grid, bands, J, workspace, workspace_bytes))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Views v{cosine_layout(grid, bands, J), static_cast<char *>(workspace)};
+    cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
+    CosineArgs a = cosine_args(v, grid, bands, params);
+    if (e == cudaSuccess) e = launch_cosine_pack(a, s);
+    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    a.S = S;
+    return cuda_status(launch_cosine(a, VAR_FORWARD, s));
+}
+
+efunc_status efunc_cosine_backward(const efunc_grid *grid, int32_t bands, const float *params, const float *q,
+                                   int64_t J, int32_t q_stride, const float *gS, float *grad, void *workspace,
+                                   size_t workspace_bytes, efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if (!bands_ok(bands)) return EFUNC_ERR_ARG;
+    if (J < 0 || J > kMaxJ || (q_stride != 3 && q_stride != 4) || !params || !grad) return EFUNC_ERR_ARG;
+    if (J == 0) return EFUNC_OK;
+    if (!q || !gS) return EFUNC_ERR_ARG;
+    if ((st = check_cosine_workspace(grid, bands, J, workspace, workspace_bytes))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Views v{cosine_layout(grid, bands, J), static_cast<char *>(workspace)};
+    cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
+    CosineArgs a = cosine_args(v, grid, bands, params);
+    if (e == cudaSuccess) e = launch_cosine_pack(a, s);
+    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    a.gS = gS;
+    a.grad = grad;
+    return cuda_status(launch_cosine(a, VAR_BACKWARD, s));
+}
+
+efunc_status efunc_cosine_fit(const efunc_grid *grid, int32_t bands, const efunc_adam *adam, int32_t loss,
+                              float *params, float *m, float *v, const float *qo, int64_t J, int32_t n_batches,
+                              int32_t steps, int64_t step0, float *stats, void *workspace, size_t workspace_bytes,
+                              efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if (!bands_ok(bands)) return EFUNC_ERR_ARG;
+    if ((st = check_adam(adam))) return st;
+    if (loss != EFUNC_LOSS_L1 && loss != EFUNC_LOSS_MSE) return EFUNC_ERR_ARG;
+    if (J < 1 || J > kMaxJ || n_batches < 1 || steps < 0 || step0 < 0) return EFUNC_ERR_ARG;
+    if (!params || !m || !v || !qo) return EFUNC_ERR_ARG;
+    if ((st = check_cosine_workspace(grid, bands, J, workspace, workspace_bytes))) return st;
+    if (steps == 0) return EFUNC_OK;
+    if (is_host_pointer(qo) || (stats && is_host_pointer(stats))) return EFUNC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Views vw{cosine_layout(grid, bands, J), static_cast<char *>(workspace)};
+    const int64_t n = (int64_t)grid->R * grid->R * grid->R * 5 * bands;
+    float *grad = vw.grad();
+    if (cudaMemsetAsync(grad, 0, (size_t)n * 4, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    for (int32_t it = 0; it < steps; ++it) {
+        const float *qdev = qo + (size_t)(it % n_batches) * (size_t)J * 4;
+        cudaError_t e = sort_into(vw, grid->R, qdev, J, 4, vw.sorted(), nullptr, s);
+        CosineArgs a = cosine_args(vw, grid, bands, params);
+        if (e == cudaSuccess) e = launch_cosine_pack(a, s);
+        if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+        a.grad = grad;
+        a.loss = loss;
+        a.inv_J = (float)(1.0 / (double)J);
+        if (launch_cosine(a, VAR_FIT, s) != cudaSuccess) return EFUNC_ERR_CUDA;
         AdamArgs ad = adam_args(adam, n, params, grad, m, v, step0 + it + 1);
         ad.ctrl = vw.ctrl();
         ad.inv_J = a.inv_J;

@@ -137,6 +137,24 @@ def test_variant_helpers_and_validation(lib):
     assert lib.efunc_launch_count() == 0
 
 
+def test_cosine_helpers_and_validation(lib):
+    g = B.Grid(16, 2, 7.0)
+    n1 = lib.efunc_cosine_workspace_bytes(ctypes.byref(g), 1, 1 << 16)
+    n8 = lib.efunc_cosine_workspace_bytes(ctypes.byref(g), 8, 1 << 16)
+    assert n8 > n1 > 0 and n8 % 256 == 0
+    assert lib.efunc_cosine_workspace_bytes(ctypes.byref(g), 0, 10) == 0
+    assert lib.efunc_cosine_workspace_bytes(ctypes.byref(g), 17, 10) == 0
+    assert lib.efunc_cosine_forward(ctypes.byref(g), 0, 4096, 8192, 16, 3, 12288, 1 << 30, 1 << 40, None) == 1
+    assert lib.efunc_cosine_forward(ctypes.byref(g), 4, 4096, 8192, 16, 3, 12288, 1 << 30, 100, None) == 3
+    assert lib.efunc_cosine_forward(ctypes.byref(g), 4, 4096, 8192, 0, 3, None, 1 << 30, 1 << 40, None) == 0
+    assert lib.efunc_cosine_backward(ctypes.byref(g), 4, 4096, 8192, 16, 3, None, 4096, 1 << 30, 1 << 40,
+                                     None) == 1
+    ad = B.Adam(1e-3, 0.9, 0.999, 1e-8, 0.0, 0)
+    assert lib.efunc_cosine_fit(ctypes.byref(g), 4, ctypes.byref(ad), 3, 16, 32, 48, 64, 10, 1, 1, 0, None, 1 << 30,
+                                1 << 40, None) == 1                                          # bad loss kind
+    assert lib.efunc_launch_count() == 0
+
+
 def test_profile_api_without_gpu(lib):
     ms, cnt = ctypes.c_double(1.0), ctypes.c_int64(1)
     lib.efunc_profile_reset()
