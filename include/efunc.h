@@ -126,6 +126,14 @@ const char *efunc_status_str(efunc_status s);
  * (the maximum over all calls).  0 if the grid is invalid. */
 size_t efunc_workspace_bytes(const efunc_grid *grid, int64_t J);
 
+/* Bytes of workspace with which efunc_fit pipelines its steps: the sort of
+ * batch s+1 runs on a library-owned stream, into a second sort buffer, while
+ * batch s is computed on the caller's stream (about 20 bytes per query more
+ * than efunc_workspace_bytes).  With less (but at least
+ * efunc_workspace_bytes) efunc_fit sorts each batch in line.  0 if the grid
+ * is invalid. */
+size_t efunc_fit_workspace_bytes(const efunc_grid *grid, int64_t J);
+
 /* ------------------------------------------------------------ entry points */
 
 /* Cell sort (hot-path step a1; not in the paper, whose Algorithm 1 visits
@@ -209,7 +217,12 @@ efunc_status efunc_adam_step(const efunc_adam *adam, int64_t n, float *params, f
  *            Eikonal term, mean |O - o|) of every step, evaluated at the
  *            parameters before that step's
  *            update.  If stats is host memory the call synchronises the
- *            stream before returning. */
+ *            stream before returning.
+ *   workspace  at least efunc_workspace_bytes; with efunc_fit_workspace_bytes
+ *            the sort of batch s+1 runs on a sort stream of the library
+ *            alongside batch s (the copy and sort streams and their events
+ *            are shared per device: calls of efunc_fit on one device must
+ *            not run concurrently from several host threads). */
 efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t loss, float eikonal_weight,
                        float *params, float *m, float *v, const float *qo, int64_t J, int32_t n_batches,
                        int32_t steps, int64_t step0, float *stats, void *workspace, size_t workspace_bytes,

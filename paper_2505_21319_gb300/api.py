@@ -58,8 +58,9 @@ class Workspace:
         self.device = torch.device(device or "cuda")
         self.buf = None
 
-    def get(self, grid: B.Grid, J: int) -> tuple[torch.Tensor, int]:
-        n = int(B.load().efunc_workspace_bytes(ctypes.byref(grid), int(J)))
+    def get(self, grid: B.Grid, J: int, fit: bool = False) -> tuple[torch.Tensor, int]:
+        query = B.load().efunc_fit_workspace_bytes if fit else B.load().efunc_workspace_bytes
+        n = int(query(ctypes.byref(grid), int(J)))
         if n == 0:
             raise ValueError("invalid grid or query count")
         if self.buf is None or self.buf.numel() < n:
@@ -413,7 +414,7 @@ def efunc_fit(params, m, v, qo, steps: int, J: int | None = None, n_batches: int
         raise ValueError("stats must be a contiguous float32 tensor of at least 2*steps")
     grid = make_grid(R, log_beta0)
     ad = make_adam(**adam_kw)
-    buf, n = _workspace(params.device, ws).get(grid, J)
+    buf, n = _workspace(params.device, ws).get(grid, J, fit=True)
     lk = {"l1": B.LOSS_L1, "mse": B.LOSS_MSE}[loss]
     B.check("efunc_fit", B.load().efunc_fit(ctypes.byref(grid), ctypes.byref(ad), lk, float(eikonal_weight),
                                             _ptr(params), _ptr(m), _ptr(v),

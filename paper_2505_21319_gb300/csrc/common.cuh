@@ -15,6 +15,9 @@ constexpr int kThreads = 128;     // threads of the fused kernel = keys per wind
 constexpr int kChunk = 256;       // queries per work item at most
 constexpr int kMaxR = 256;
 constexpr int kBrick = 4;         // cells per brick edge in the sort order
+constexpr int kSortThreads = 128; // block size of every sort kernel (small, so that the
+                                  // sort of the next batch fits beside the fit kernel)
+constexpr int kScanSegment = 512; // bins per scan block
 
 // Work item: one window-base cell and a contiguous slice of its sorted queries.
 //   x = first sorted row, y = number of rows (1..kChunk),
@@ -35,13 +38,17 @@ struct Layout {
     int64_t nbins;      // P^3 * 64
     int64_t nscan_blocks;
     int64_t max_items;
-    size_t ctrl, hist, blocksum, rank, sorted, perm, items, keys, grad, stage, total;
+    size_t ctrl, hist, blocksum, rank, sorted, perm, items, keys, grad, stage;
+    // second sort buffer (the fit sorts batch s+1 while batch s is computed)
+    size_t ctrl2, hist2, blocksum2, rank2, sorted2, items2;
+    bool two_sort_buffers;
+    size_t total;
 };
 
 // Workspace layout for R^3 centres and J queries; key_records (float4) and
 // channels (floats) per centre size the key-record and gradient regions
 // (the default model: 4 and 13; the ablation variants need other sizes).
-Layout make_layout(int R, int64_t J, int key_records = 4, int channels = 13);
+Layout make_layout(int R, int64_t J, int key_records = 4, int channels = 13, bool two_sort_buffers = false);
 
 // Sort configuration passed to kernels.
 struct SortArgs {
@@ -181,11 +188,14 @@ void launch_end(int kid, cudaStream_t s);
 
 // Launchers (defined in sort.cu, fused.cu, adam.cu).  They return the CUDA
 // error of the launch.
-cudaError_t launch_sort(const SortArgs &a, cudaStream_t s);
+// narrow: bin and scatter with one block per SM (the pipelined fit runs them
+// beside the persistent fit kernel)
+cudaError_t launch_sort(const SortArgs &a, cudaStream_t s, bool narrow = false);
 cudaError_t launch_pack_keys(const PackArgs &a, cudaStream_t s);
 cudaError_t launch_forward(const FusedArgs &a, bool with_dq, int grid, cudaStream_t s);
 cudaError_t launch_fused_backward(const FusedArgs &a, bool with_gq, bool second_order, int grid, cudaStream_t s);
 cudaError_t launch_fused_fit(const FusedArgs &a, bool eikonal, int grid, cudaStream_t s);
+int fused_fit_grid_size(bool eikonal, bool leave_room);   // persistent grid of the fit kernel
 cudaError_t launch_adam(const AdamArgs &a, cudaStream_t s);
 cudaError_t launch_mean_shift(const MeanShiftArgs &a, cudaStream_t s);
 cudaError_t launch_variant_pack(const VariantArgs &a, cudaStream_t s);

@@ -91,12 +91,12 @@ void launch_end(int kid, cudaStream_t s)
 
 // ------------------------------------------------------------- layout
 
-Layout make_layout(int R, int64_t J, int key_records, int channels)
+Layout make_layout(int R, int64_t J, int key_records, int channels, bool two_sort_buffers)
 {
     Layout L{};
     L.P = (R + 1 + kBrick - 1) / kBrick;
     L.nbins = (int64_t)L.P * L.P * L.P * 64;
-    L.nscan_blocks = (L.nbins + 4095) / 4096;
+    L.nscan_blocks = (L.nbins + kScanSegment - 1) / kScanSegment;
     L.max_items = (J + kChunk - 1) / kChunk + (J < L.nbins ? J : L.nbins);
     const size_t A = 256;
     size_t off = 0;
@@ -110,6 +110,15 @@ Layout make_layout(int R, int64_t J, int key_records, int channels)
     L.keys = off;      off = align_up(off + (size_t)R * R * R * key_records * 16, A);
     L.grad = off;      off = align_up(off + (size_t)R * R * R * channels * 4, A);
     L.stage = off;     off = align_up(off + (size_t)J * 32, A);   // two host-batch staging buffers
+    L.two_sort_buffers = two_sort_buffers;
+    if (two_sort_buffers) {
+        L.ctrl2 = off;     off = align_up(off + sizeof(Ctrl), A);
+        L.hist2 = off;     off = align_up(off + (size_t)L.nbins * 4, A);
+        L.blocksum2 = off; off = align_up(off + (size_t)L.nscan_blocks * 8, A);
+        L.rank2 = off;     off = align_up(off + (size_t)J * 4, A);
+        L.sorted2 = off;   off = align_up(off + (size_t)J * 16, A);
+        L.items2 = off;    off = align_up(off + (size_t)L.max_items * 16, A);
+    }
     L.total = off;
     return L;
 }
@@ -154,6 +163,52 @@ struct Views {
     // staging buffer b (0 or 1) of a host batch: J rows of 4 floats each
     float4 *stage(int b, int64_t J) const { return reinterpret_cast<float4 *>(base + L.stage) + (size_t)b * (size_t)J; }
 };
+
+// One of the two sort buffers of a pipelined fit (buffer 0 is the one every
+// other call uses).
+struct SortBuf {
+    Ctrl *ctrl;
+    uint32_t *hist;
+    unsigned long long *blocksum;
+    uint32_t *rank;
+    float4 *sorted;
+    Item *items;
+};
+
+SortBuf sort_buf(const Views &v, int b)
+{
+    const Layout &L = v.L;
+    char *p = v.base;
+    if (b == 0)
+        return {v.ctrl(), v.hist(), v.blocksum(), v.rank(), v.sorted(), v.items()};
+    return {reinterpret_cast<Ctrl *>(p + L.ctrl2), reinterpret_cast<uint32_t *>(p + L.hist2),
+            reinterpret_cast<unsigned long long *>(p + L.blocksum2), reinterpret_cast<uint32_t *>(p + L.rank2),
+            reinterpret_cast<float4 *>(p + L.sorted2), reinterpret_cast<Item *>(p + L.items2)};
+}
+
+cudaError_t sort_into_buf(const SortBuf &b, const Layout &L, int R, const float *q, int64_t J, int q_stride,
+                          cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(b.ctrl, 0, sizeof(Ctrl), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(b.hist, 0, (size_t)L.nbins * 4, s);
+    if (e != cudaSuccess) return e;
+    SortArgs a{};
+    a.q = q;
+    a.J = J;
+    a.q_stride = q_stride;
+    a.R = R;
+    a.P = L.P;
+    a.nbins = L.nbins;
+    a.hist = b.hist;
+    a.blocksum = b.blocksum;
+    a.rank = b.rank;
+    a.sorted = b.sorted;
+    a.perm = nullptr;
+    a.items = b.items;
+    a.ctrl = b.ctrl;
+    return launch_sort(a, s, true);
+}
 
 // Clears the control block and histogram, then sorts q into the workspace
 // (or into the caller's sorted / perm buffers when given).
@@ -204,14 +259,18 @@ FusedArgs fused_args(const Views &v, const efunc_grid *g)
     return f;
 }
 
-// Per-device copy stream and events that overlap the host->device copy of
-// batch s+1 with the computation of batch s in efunc_fit.  Created on the
-// first fit from host memory on a device and kept for the process.
+// Per-device streams and events of efunc_fit: the copy stream overlaps the
+// host->device copy of batch s+1 with the computation of batch s; the sort
+// stream sorts batch s+1 into the other sort buffer meanwhile (pipelined
+// fit).  Created on the first fit on a device and kept for the process.
 struct CopyPipe {
     bool ready = false;
     cudaStream_t stream = nullptr;
+    cudaStream_t sort_stream = nullptr;
     cudaEvent_t copied[2] = {nullptr, nullptr};
     cudaEvent_t freed[2] = {nullptr, nullptr};
+    cudaEvent_t sorted[2] = {nullptr, nullptr};
+    cudaEvent_t consumed[2] = {nullptr, nullptr};
 };
 constexpr int kMaxPipes = 64;
 std::mutex g_pipe_mu;
@@ -227,9 +286,12 @@ cudaError_t copy_pipe(CopyPipe **out)
     CopyPipe &p = g_pipes[dev];
     if (!p.ready) {
         if ((e = cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithFlags(&p.sort_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
         for (int b = 0; b < 2; ++b) {
             if ((e = cudaEventCreateWithFlags(&p.copied[b], cudaEventDisableTiming)) != cudaSuccess) return e;
             if ((e = cudaEventCreateWithFlags(&p.freed[b], cudaEventDisableTiming)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&p.sorted[b], cudaEventDisableTiming)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&p.consumed[b], cudaEventDisableTiming)) != cudaSuccess) return e;
         }
         p.ready = true;
     }
@@ -356,6 +418,87 @@ AdamArgs adam_args(const efunc_adam *ad, int64_t n, float *p, float *g, float *m
     return a;
 }
 
+// efunc_fit with the sort of batch s+1 (on the library's sort stream, into
+// the second sort buffer) overlapped with pack / fused kernel / Adam of batch
+// s on the caller's stream.  The fused kernel's persistent grid leaves one
+// sort block's registers free on every SM so the two run side by side.
+// Events order the buffers: sorted[b] (sort done) before the fused kernel
+// that reads buffer b; consumed[b] (Adam of that step done, it reads the loss
+// sums in buffer b's control block) before the next sort into b.
+efunc_status fit_pipelined(const efunc_grid *grid, const efunc_adam *adam, int32_t loss, float eikonal_weight,
+                           float *params, float *m, float *v, const float *qo, int64_t J, int32_t n_batches,
+                           int32_t steps, int64_t step0, float *stats, void *workspace, cudaStream_t s)
+{
+    const int R = grid->R;
+    Views vw{make_layout(R, J, kKeyRecords, kSlots, true), static_cast<char *>(workspace)};
+    const bool q_host = is_host_pointer(qo);
+    const bool stats_host = stats && is_host_pointer(stats);
+    const int64_t n = (int64_t)R * R * R * kSlots;
+    float *grad = vw.grad();
+    CopyPipe *pipe = nullptr;
+    if (copy_pipe(&pipe) != cudaSuccess) return EFUNC_ERR_CUDA;
+    cudaStream_t ss = pipe->sort_stream;
+    const size_t batch_bytes = (size_t)J * 16;
+    auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * (size_t)J * 4; };
+    const bool eik = eikonal_weight > 0.f;
+    const int grid_blocks = fused_fit_grid_size(eik, true);
+
+    if (cudaMemsetAsync(grad, 0, (size_t)n * 4, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    // both sort buffers (and staging buffers) are free once the caller's earlier work is done
+    for (int b = 0; b < 2; ++b) {
+        if (cudaEventRecord(pipe->consumed[b], s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (q_host && cudaEventRecord(pipe->freed[b], s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    }
+    auto issue_sort = [&](int32_t k) -> bool {
+        const int b = k & 1;
+        const float *src = batch(k);
+        if (q_host) {
+            if (cudaStreamWaitEvent(pipe->stream, pipe->freed[b], 0) != cudaSuccess ||
+                cudaMemcpyAsync(vw.stage(b, J), src, batch_bytes, cudaMemcpyHostToDevice, pipe->stream) !=
+                    cudaSuccess ||
+                cudaEventRecord(pipe->copied[b], pipe->stream) != cudaSuccess ||
+                cudaStreamWaitEvent(ss, pipe->copied[b], 0) != cudaSuccess)
+                return false;
+            src = reinterpret_cast<const float *>(vw.stage(b, J));
+        }
+        if (cudaStreamWaitEvent(ss, pipe->consumed[b], 0) != cudaSuccess) return false;
+        if (sort_into_buf(sort_buf(vw, b), vw.L, R, src, J, 4, ss) != cudaSuccess) return false;
+        if (q_host && cudaEventRecord(pipe->freed[b], ss) != cudaSuccess) return false;
+        return cudaEventRecord(pipe->sorted[b], ss) == cudaSuccess;
+    };
+
+    if (!issue_sort(0)) return EFUNC_ERR_CUDA;
+    for (int32_t it = 0; it < steps; ++it) {
+        const int b = it & 1;
+        if (it + 1 < steps && !issue_sort(it + 1)) return EFUNC_ERR_CUDA;
+        const SortBuf sb = sort_buf(vw, b);
+        if (cudaStreamWaitEvent(s, pipe->sorted[b], 0) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (pack_keys(vw, grid, params, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        FusedArgs f = fused_args(vw, grid);
+        f.sorted = sb.sorted;
+        f.items = sb.items;
+        f.ctrl = sb.ctrl;
+        f.perm = nullptr;
+        f.grad = grad;
+        f.loss = loss;
+        f.inv_J = (float)(1.0 / (double)J);
+        f.eik_weight = eikonal_weight;
+        if (launch_fused_fit(f, eik, grid_blocks, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        float *stats_dev = reinterpret_cast<float *>(sb.ctrl) + 16;
+        AdamArgs a = adam_args(adam, n, params, grad, m, v, step0 + it + 1);
+        a.ctrl = sb.ctrl;
+        a.inv_J = f.inv_J;
+        a.stats = stats ? (stats_host ? stats_dev : stats + 2 * (size_t)it) : nullptr;
+        if (launch_adam(a, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (stats_host && cudaMemcpyAsync(stats + 2 * (size_t)it, stats_dev, 8, cudaMemcpyDeviceToHost, s) !=
+                              cudaSuccess)
+            return EFUNC_ERR_CUDA;
+        if (cudaEventRecord(pipe->consumed[b], s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    }
+    if (stats_host && cudaStreamSynchronize(s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    return EFUNC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -389,6 +532,12 @@ size_t efunc_workspace_bytes(const efunc_grid *grid, int64_t J)
 {
     if (!grid_ok(grid) || J < 0 || J > kMaxJ) return 0;
     return make_layout(grid->R, J).total;
+}
+
+size_t efunc_fit_workspace_bytes(const efunc_grid *grid, int64_t J)
+{
+    if (!grid_ok(grid) || J < 0 || J > kMaxJ) return 0;
+    return make_layout(grid->R, J, kKeyRecords, kSlots, true).total;
 }
 
 efunc_status efunc_cell_sort(const efunc_grid *grid, const float *q, int64_t J, int32_t q_stride, float *q_sorted,
@@ -498,6 +647,9 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
     if (!params || !m || !v || !qo) return EFUNC_ERR_ARG;
     if ((st = check_workspace(grid, J, workspace, workspace_bytes))) return st;
     if (steps == 0) return EFUNC_OK;
+    if (workspace_bytes >= make_layout(grid->R, J, kKeyRecords, kSlots, true).total)
+        return fit_pipelined(grid, adam, loss, eikonal_weight, params, m, v, qo, J, n_batches, steps, step0, stats,
+                             workspace, (cudaStream_t)stream);
     cudaStream_t s = (cudaStream_t)stream;
     Views vw{make_layout(grid->R, J), static_cast<char *>(workspace)};
     const bool q_host = is_host_pointer(qo);

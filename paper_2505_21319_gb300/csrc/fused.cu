@@ -522,7 +522,7 @@ __device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *
 }
 
 template <int MODE, bool DQ, bool GEIK>
-__global__ void __launch_bounds__(kThreads, GEIK ? 5 : 8) fused_kernel(FusedArgs a)
+__global__ void __launch_bounds__(kThreads, GEIK ? 5 : 9) fused_kernel(FusedArgs a)
 {
     __shared__ float4 s_rec[kCentres * kKeyRecords];          // key records of the window
     __shared__ float4 s_qt[kChunk];                           // query tile
@@ -672,6 +672,31 @@ int fused_grid_size()
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel<FIT, false, false>, kThreads, 0);
         if (per_sm <= 0) per_sm = 1;
+        g = sm_count() * per_sm;
+    }
+    return g;
+}
+
+int fused_fit_grid_size(bool eikonal, bool leave_room)
+{
+    static int cached[2][2] = {{0, 0}, {0, 0}};
+    int &g = cached[eikonal ? 1 : 0][leave_room ? 1 : 0];
+    if (!g) {
+        const void *k = eikonal ? reinterpret_cast<const void *>(fused_kernel<FIT, false, true>)
+                                : reinterpret_cast<const void *>(fused_kernel<FIT, false, false>);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, 0);
+        if (per_sm <= 0) per_sm = 1;
+        if (leave_room) {
+            // leave the registers of one sort block (kSortThreads x 32) free on every SM
+            cudaFuncAttributes fa{};
+            int dev = 0, regs_sm = 65536;
+            cudaFuncGetAttributes(&fa, k);
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+            const int per_cta = (fa.numRegs + 7) / 8 * 8 * kThreads;
+            while (per_sm > 1 && per_sm * per_cta > regs_sm - kSortThreads * 32) --per_sm;
+        }
         g = sm_count() * per_sm;
     }
     return g;

@@ -19,9 +19,14 @@ namespace efunc {
 
 namespace {
 
-constexpr int kScanThreads = 1024;
-constexpr int kScanPerThread = 4;
-constexpr int kScanSeg = kScanThreads * kScanPerThread;   // bins per scan block
+constexpr int kScanThreads = kSortThreads;
+constexpr int kScanPerThread = kScanSegment / kScanThreads;
+constexpr int kScanSeg = kScanSegment;   // bins per scan block
+constexpr int kWideThreads = 256;        // bin / scatter block size when the sort runs alone
+// at most 32 registers per thread, so that a kSortThreads block fits in the
+// registers the persistent fit kernel leaves free on each SM
+constexpr int kSortMinBlocks = 65536 / (kSortThreads * 32);
+constexpr int kWideMinBlocks = 65536 / (kWideThreads * 32);
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ void load_query(const float *q, int64_t j, int stride, bool vec4, float &x, float &y,
@@ -45,12 +50,31 @@ __device__ __forceinline__ uint32_t query_bin(float x, float y, float z, float h
     return bin_of(ux, uy, uz, P);
 }
 
+// Grid-stride loops take kUnroll queries per thread and iteration, so that a
+// small grid (one block per SM beside the fit kernel) still keeps several
+// loads and atomics in flight per thread.
+constexpr int kUnroll = 4;
+
 template <bool VEC4>
-__global__ void __launch_bounds__(256) bin_kernel(SortArgs a)
+__global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) bin_kernel(SortArgs a)
 {
     const float half_r = (float)a.R * 0.5f, rmax = (float)(a.R - 1);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.J; j += stride) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; j + (kUnroll - 1) * stride < a.J; j += kUnroll * stride) {
+        uint32_t bin[kUnroll], r[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            float x, y, z, w;
+            load_query(a.q, j + u * stride, a.q_stride, VEC4, x, y, z, w);
+            bin[u] = query_bin(x, y, z, half_r, rmax, a.P);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) r[u] = atomicAdd(&a.hist[bin[u]], 1u);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) a.rank[j + u * stride] = r[u];
+    }
+    for (; j < a.J; j += stride) {
         float x, y, z, w;
         load_query(a.q, j, a.q_stride, VEC4, x, y, z, w);
         a.rank[j] = atomicAdd(&a.hist[query_bin(x, y, z, half_r, rmax, a.P)], 1u);
@@ -93,7 +117,7 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long
     return prefix + x - v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(SortArgs a)
+__global__ void __launch_bounds__(kScanThreads, kSortMinBlocks) scan_reduce_kernel(SortArgs a)
 {
     const int64_t b0 = (int64_t)blockIdx.x * kScanSeg + (int64_t)threadIdx.x * kScanPerThread;
     unsigned long long s = 0;
@@ -105,7 +129,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(SortArgs a)
     if (threadIdx.x == 0) a.blocksum[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_top_kernel(SortArgs a, int64_t nblocks)
+__global__ void __launch_bounds__(kScanThreads, kSortMinBlocks) scan_top_kernel(SortArgs a, int64_t nblocks)
 {
     unsigned long long carry = 0;
     for (int64_t base = 0; base < nblocks; base += kScanThreads) {
@@ -119,7 +143,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_top_kernel(SortArgs a, int6
     if (threadIdx.x == 0) a.ctrl->n_items = (int)(carry >> 32);
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_emit_kernel(SortArgs a)
+__global__ void __launch_bounds__(kScanThreads, kSortMinBlocks) scan_emit_kernel(SortArgs a)
 {
     const int64_t b0 = (int64_t)blockIdx.x * kScanSeg + (int64_t)threadIdx.x * kScanPerThread;
     uint32_t cnt[kScanPerThread];
@@ -153,11 +177,28 @@ __global__ void __launch_bounds__(kScanThreads) scan_emit_kernel(SortArgs a)
 }
 
 template <bool VEC4>
-__global__ void __launch_bounds__(256) scatter_kernel(SortArgs a)
+__global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) scatter_kernel(SortArgs a)
 {
     const float half_r = (float)a.R * 0.5f, rmax = (float)(a.R - 1);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.J; j += stride) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; j + (kUnroll - 1) * stride < a.J; j += kUnroll * stride) {
+        float4 v[kUnroll];
+        uint32_t pos[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            load_query(a.q, j + u * stride, a.q_stride, VEC4, v[u].x, v[u].y, v[u].z, v[u].w);
+            pos[u] = a.rank[j + u * stride];
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) pos[u] += a.hist[query_bin(v[u].x, v[u].y, v[u].z, half_r, rmax, a.P)];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            a.sorted[pos[u]] = v[u];
+            if (a.perm) a.perm[pos[u]] = (int)(j + u * stride);
+        }
+    }
+    for (; j < a.J; j += stride) {
         float x, y, z, w;
         load_query(a.q, j, a.q_stride, VEC4, x, y, z, w);
         const uint32_t bin = query_bin(x, y, z, half_r, rmax, a.P);
@@ -167,7 +208,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(SortArgs a)
     }
 }
 
-int stream_grid(int64_t work, int threads)
+int stream_grid(int64_t work, int threads, int blocks_per_sm)
 {
     static int sms = 0;
     if (!sms) {
@@ -177,22 +218,24 @@ int stream_grid(int64_t work, int threads)
         if (sms <= 0) sms = 1;
     }
     int64_t blocks = (work + threads - 1) / threads;
-    int64_t cap = (int64_t)sms * 8;
+    int64_t cap = (int64_t)sms * blocks_per_sm;
     if (blocks > cap) blocks = cap;
     return (int)(blocks < 1 ? 1 : blocks);
 }
 
 }  // namespace
 
-cudaError_t launch_sort(const SortArgs &a, cudaStream_t s)
+cudaError_t launch_sort(const SortArgs &a, cudaStream_t s, bool narrow)
 {
     const bool vec4 = a.q_stride == 4 && (reinterpret_cast<uintptr_t>(a.q) & 15u) == 0;
-    const int g = stream_grid(a.J, 256);
+    // narrow: one block per SM, to run beside the persistent fit kernel
+    const int threads = narrow ? kSortThreads : kWideThreads;
+    const int g = stream_grid(a.J, threads, narrow ? 1 : 8);
     const int64_t nblocks = (a.nbins + kScanSeg - 1) / kScanSeg;
 
     launch_begin(K_BIN, s);
-    if (vec4) bin_kernel<true><<<g, 256, 0, s>>>(a);
-    else bin_kernel<false><<<g, 256, 0, s>>>(a);
+    if (vec4) bin_kernel<true><<<g, threads, 0, s>>>(a);
+    else bin_kernel<false><<<g, threads, 0, s>>>(a);
     launch_end(K_BIN, s);
 
     launch_begin(K_SCAN_REDUCE, s);
@@ -208,8 +251,8 @@ cudaError_t launch_sort(const SortArgs &a, cudaStream_t s)
     launch_end(K_SCAN_EMIT, s);
 
     launch_begin(K_SCATTER, s);
-    if (vec4) scatter_kernel<true><<<g, 256, 0, s>>>(a);
-    else scatter_kernel<false><<<g, 256, 0, s>>>(a);
+    if (vec4) scatter_kernel<true><<<g, threads, 0, s>>>(a);
+    else scatter_kernel<false><<<g, threads, 0, s>>>(a);
     launch_end(K_SCATTER, s);
     return cudaGetLastError();
 }
