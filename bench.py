@@ -310,6 +310,7 @@ def main():
     ap.add_argument("--mean-shift-reps", type=int, default=20)
     ap.add_argument("--variant-steps", type=int, default=50)
     ap.add_argument("--cosine-steps", type=int, default=50)
+    ap.add_argument("--isolated-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -391,6 +392,22 @@ def main():
     avg_fused = fused_ms / max(1, fused_n)
     achieved = ops_per_launch / (avg_fused * 1e-3) / 1e12
     clocks = clk.summary()
+
+    # ---- the fused kernel alone: the same fit with the sort in line (no
+    # sort of the next batch beside it), for the kernel's own roofline
+    iso = None
+    if args.isolated_steps > 0:
+        api.profile_reset()
+        api.profile(True)
+        api.efunc_fit(params, m, v, pool, steps=args.isolated_steps, J=J, n_batches=N_BATCHES, step0=4 * 10 ** 6,
+                      lr=LR, ws=ws_buf, pipelined=False)
+        torch.cuda.synchronize(dev)
+        api.profile(False)
+        im, icnt = api.profile_read("fused_fit")
+        iavg = im / max(1, icnt)
+        iach = ops_per_launch / (iavg * 1e-3) / 1e12
+        iso = {"avg_launch_ms": iavg, "achieved": iach, "frac": iach / peak, "steps": args.isolated_steps,
+               "note": "fused kernel of the same fit with the batch sorted in line: nothing runs beside it"}
 
     # ---- the same fit with the Eikonal term (NEXT-1: second-order fused
     # backward through dO/dq), timed the same way on a shorter run
@@ -546,7 +563,9 @@ def main():
             "roofline": {"bound": "alu", "kernel": "fused_fit", "achieved": achieved, "peak": peak,
                          "unit": "T FP32 op/s", "frac": achieved / peak, "traffic": fused_traffic(),
                          "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_fused,
-                         "peak_from": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz"},
+                         "peak_from": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz",
+                         "co_running": "the sort of the next batch runs beside the fused kernel (pipelined fit)",
+                         "isolated": iso},
             "kernel_ms": kernel_ms,
             "e2e": e2e,
             "eikonal_fit": eik,

@@ -47,6 +47,10 @@ def test_host_helpers(lib):
     assert n1 > n2 > 0 and n1 % 256 == 0
     assert lib.efunc_workspace_bytes(ctypes.byref(B.Grid(0, 2, 7.0)), 10) == 0
     assert lib.efunc_workspace_bytes(ctypes.byref(g), -1) == 0
+    # the pipelined fit's second sort buffer: about 20 bytes per query more
+    nf = lib.efunc_fit_workspace_bytes(ctypes.byref(g), 1 << 22)
+    assert nf > n1 and nf - n1 >= 20 * (1 << 22) and nf % 256 == 0
+    assert lib.efunc_fit_workspace_bytes(ctypes.byref(B.Grid(0, 2, 7.0)), 10) == 0
     assert lib.efunc_launch_count() == 0
 
 

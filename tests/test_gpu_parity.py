@@ -327,7 +327,28 @@ def test_fit_steps_match_oracle_trajectory():
     np.testing.assert_allclose(pd.cpu().numpy().reshape(-1)[solid], pr.reshape(-1)[solid], rtol=1e-4, atol=1e-6)
 
 
-def test_fit_from_host_memory_matches_device():
+@pytest.mark.parametrize("eikonal", [0.0, 0.5])
+def test_pipelined_fit_matches_inline_sort(eikonal):
+    """The pipelined fit (next batch sorted on the library's sort stream into
+    the second sort buffer) and the in-line sort take the same steps: losses
+    agree and parameters agree wherever the first moment is far from zero."""
+    R, J = 8, 30000
+    qo = to_dev(synth.sample_batch(synth.random_union(4), 3 * J, seed=4))
+    p0 = synth.init_params(R, seed=2)
+    out = {}
+    for pipe in (True, False):
+        pd, m, v = to_dev(p0), torch.zeros(p0.size, device=DEV), torch.zeros(p0.size, device=DEV)
+        stats = torch.zeros(14, device=DEV)
+        api.efunc_fit(pd, m, v, qo, steps=7, J=J, n_batches=3, loss="mse", stats=stats, lr=1e-3,
+                      log_beta0=lb32(R), eikonal_weight=eikonal, pipelined=pipe, ws=api.Workspace(DEV))
+        out[pipe] = (pd.cpu().numpy().reshape(-1), m.cpu().numpy().reshape(-1), stats.cpu().numpy())
+    np.testing.assert_allclose(out[True][2], out[False][2], rtol=1e-4)
+    solid = np.abs(out[False][1]) > 1e-2 * np.abs(out[False][1]).max()
+    np.testing.assert_allclose(out[True][0][solid], out[False][0][solid], rtol=1e-4, atol=1e-6)
+
+
+@pytest.mark.parametrize("pipelined", [True, False])
+def test_fit_from_host_memory_matches_device(pipelined):
     R, J = 8, 20000
     qo = synth.sample_batch(synth.random_union(1), 2 * J, seed=1)
     p0 = synth.init_params(R, seed=1)
@@ -336,7 +357,8 @@ def test_fit_from_host_memory_matches_device():
         pd, m, v = to_dev(p0), torch.zeros(p0.size, device=DEV), torch.zeros(p0.size, device=DEV)
         src = torch.from_numpy(qo).pin_memory() if host else to_dev(qo)
         stats = torch.zeros(6, device="cpu" if host else DEV)
-        api.efunc_fit(pd, m, v, src, steps=3, J=J, n_batches=2, loss="l1", stats=stats, lr=1e-3)
+        api.efunc_fit(pd, m, v, src, steps=3, J=J, n_batches=2, loss="l1", stats=stats, lr=1e-3,
+                      pipelined=pipelined, ws=api.Workspace(DEV))
         torch.cuda.synchronize()
         outs.append((pd.cpu().numpy(), stats.cpu().numpy()))
     np.testing.assert_allclose(outs[0][1], outs[1][1], rtol=1e-5)
