@@ -154,26 +154,120 @@ __device__ __forceinline__ Win window_of(const Item item, int R)
     return w;
 }
 
-// (e, m) of one query over the window's keys, exponents shifted by M2.
-template <int NS, int DEG>
-__device__ __forceinline__ void fwd_sums(const float4 *rec, int nk, float x, float y, float z, float M2, float &e,
-                                         float &m)
+constexpr int kClasses = 4;   // interleaved summation classes of the forward
+
+// Combines per-class partial sums of a query held by KQ lanes in the fixed
+// order ((c0 + c1) + (c2 + c3)); lane `part` holds classes part + KQ i.
+template <int KQ>
+__device__ __forceinline__ float combine_classes(const float *v)
+{
+    if (KQ == 1) return (v[0] + v[1]) + (v[2] + v[3]);
+    if (KQ == 2) {
+        const float lo = v[0] + __shfl_xor_sync(kFull, v[0], 1);
+        const float hi = v[1] + __shfl_xor_sync(kFull, v[1], 1);
+        return lo + hi;
+    }
+    const float s1 = v[0] + __shfl_xor_sync(kFull, v[0], 1);
+    return s1 + __shfl_xor_sync(kFull, s1, 2);
+}
+
+// (e, m) of one query over the window's keys, exponents shifted by M2.  Key k
+// goes to class k mod 4, summed in key order, the classes combined in a
+// fixed tree: the result does not depend on how many lanes share the query.
+template <int DEG, int KQ>
+__device__ __forceinline__ void fwd_sums(const float4 *rec, int nk, int part, float x, float y, float z, float M2,
+                                         float &e, float &m)
 {
     constexpr int NREC = nrec_of(DEG);
-    e = 0.f;
-    m = 0.f;
+    constexpr int CPL = kClasses / KQ;
+    float ev[CPL], mv[CPL];
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) ev[i] = mv[i] = 0.f;
 #pragma unroll 1
-    for (int k = 0; k < nk; ++k) {
-        const float4 *r = rec + k * NREC;
-        const float4 A = r[0];
-        const float rx = x - A.x, ry = y - A.y, rz = z - A.z;
-        const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-        const float l = ex2_approx(fmaf(A.w, d2, -M2));
-        float c[nv_of(DEG)], mo[nv_of(DEG)];
-        load_coefs<DEG>(r, c);
-        monomials<DEG>(rx, ry, rz, mo);
-        e += l;
-        m = fmaf(l, poly<DEG>(c, mo), m);
+    for (int base = 0; base < nk; base += kClasses) {
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) {
+            const int k = base + part + KQ * i;
+            if (k < nk) {
+                const float4 *r = rec + k * NREC;
+                const float4 A = r[0];
+                const float rx = x - A.x, ry = y - A.y, rz = z - A.z;
+                const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                const float l = ex2_approx(fmaf(A.w, d2, -M2));
+                float c[nv_of(DEG)], mo[nv_of(DEG)];
+                load_coefs<DEG>(r, c);
+                monomials<DEG>(rx, ry, rz, mo);
+                ev[i] += l;
+                mv[i] = fmaf(l, poly<DEG>(c, mo), mv[i]);
+            }
+        }
+    }
+    e = combine_classes<KQ>(ev);
+    m = combine_classes<KQ>(mv);
+}
+
+// Forward of the item's queries with KQ lanes per query; stores, for the
+// backward, (local q, lse2) and (O, dL/dO) per query.
+template <int MODE, int DEG, int KQ>
+__device__ __forceinline__ void forward_phase(const VariantArgs &a, const float4 *rec, float4 *qt, float2 *og,
+                                              int start, int n, int nk, float3 orig, float &loss_acc, float &abs_acc)
+{
+    constexpr int NREC = nrec_of(DEG);
+    constexpr int LG = KQ == 1 ? 0 : (KQ == 2 ? 1 : 2);
+    const int t = threadIdx.x;
+    const int part = t & (KQ - 1);
+    for (int base = 0; base < n; base += kThreads / KQ) {
+        const int qi = base + (t >> LG);
+        const bool valid = qi < n;
+        // lanes without a query evaluate the window origin (never stored)
+        const float4 q4 = valid ? qt[qi] : make_float4(orig.x, orig.y, orig.z, 0.f);
+        const float x = q4.x - orig.x, y = q4.y - orig.y, z = q4.z - orig.z;
+        float e, m, M2 = 0.f;
+        fwd_sums<DEG, KQ>(rec, nk, part, x, y, z, 0.f, e, m);
+        const bool tiny = !(e >= 0x1p-60f);   // the same in every lane of the group
+        if (__any_sync(kFull, tiny)) {        // every key far in units of its scale: shift by the largest exponent
+            float mx = -INFINITY;
+            for (int k = part; k < nk; k += KQ) {
+                const float4 A = rec[k * NREC];
+                const float rx = x - A.x, ry = y - A.y, rz = z - A.z;
+                mx = fmaxf(mx, A.w * fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
+            }
+#pragma unroll
+            for (int o = 1; o < KQ; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+            float e2, m2;
+            fwd_sums<DEG, KQ>(rec, nk, part, x, y, z, mx, e2, m2);
+            if (tiny) {
+                e = e2;
+                m = m2;
+                M2 = mx;
+            }
+        }
+        const float O = m / e, lse2 = M2 + lg2_approx(e);
+        float gO = 0.f;
+        if (MODE == VAR_FIT) {
+            const float diff = O - q4.w;
+            if (a.loss == EFUNC_LOSS_L1) gO = diff > 0.f ? a.inv_J : (diff < 0.f ? -a.inv_J : 0.f);
+            else gO = 2.f * diff * a.inv_J;
+            if (valid && part == 0) {
+                loss_acc += a.loss == EFUNC_LOSS_L1 ? fabsf(diff) : diff * diff;
+                abs_acc += fabsf(diff);
+            }
+        } else if (valid && part == 0) {
+            const int j = __ldg(a.perm + start + qi);
+            if (MODE == VAR_FORWARD) {
+                a.O[j] = O;
+                if (a.lse) a.lse[j] = lse2 * kLn2;
+            } else {
+                gO = __ldg(a.gO + j);
+            }
+        }
+        if (MODE != VAR_FORWARD) {
+            __syncwarp();   // every lane of the group has read its row of qt
+            if (valid && part == 0) {
+                qt[qi] = make_float4(x, y, z, lse2);
+                og[qi] = make_float2(O, gO);
+            }
+        }
     }
 }
 
@@ -223,44 +317,10 @@ __global__ void __launch_bounds__(kThreads, 4) variant_kernel(VariantArgs a)
         for (int qi = t; qi < n; qi += kThreads) s_qt[qi] = a.sorted[start + qi];
         __syncthreads();
 
-        // ---- 2. forward, one thread per query
-        for (int qi = t; qi < n; qi += kThreads) {
-            const float4 q4 = s_qt[qi];
-            const float x = q4.x - orig.x, y = q4.y - orig.y, z = q4.z - orig.z;
-            float e, m, M2 = 0.f;
-            fwd_sums<NS, DEG>(s_rec, nk, x, y, z, 0.f, e, m);
-            if (!(e >= 0x1p-60f)) {   // every key far in units of its scale: shift by the largest exponent
-                float mx = -INFINITY;
-                for (int k = 0; k < nk; ++k) {
-                    const float4 A = s_rec[k * NREC];
-                    const float rx = x - A.x, ry = y - A.y, rz = z - A.z;
-                    mx = fmaxf(mx, A.w * fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
-                }
-                M2 = mx;
-                fwd_sums<NS, DEG>(s_rec, nk, x, y, z, M2, e, m);
-            }
-            const float O = m / e, lse2 = M2 + lg2_approx(e);
-            float gO = 0.f;
-            if (MODE == VAR_FIT) {
-                const float diff = O - q4.w;
-                if (a.loss == EFUNC_LOSS_L1) gO = diff > 0.f ? a.inv_J : (diff < 0.f ? -a.inv_J : 0.f);
-                else gO = 2.f * diff * a.inv_J;
-                loss_acc += a.loss == EFUNC_LOSS_L1 ? fabsf(diff) : diff * diff;
-                abs_acc += fabsf(diff);
-            } else {
-                const int j = __ldg(a.perm + start + qi);
-                if (MODE == VAR_FORWARD) {
-                    a.O[j] = O;
-                    if (a.lse) a.lse[j] = lse2 * kLn2;
-                } else {
-                    gO = __ldg(a.gO + j);
-                }
-            }
-            if (MODE != VAR_FORWARD) {
-                s_qt[qi] = make_float4(x, y, z, lse2);
-                s_og[qi] = make_float2(O, gO);
-            }
-        }
+        // ---- 2. forward, 1, 2 or 4 lanes per query (sparse items use more)
+        if (n > 64) forward_phase<MODE, DEG, 1>(a, s_rec, s_qt, s_og, start, n, nk, orig, loss_acc, abs_acc);
+        else if (n > 32) forward_phase<MODE, DEG, 2>(a, s_rec, s_qt, s_og, start, n, nk, orig, loss_acc, abs_acc);
+        else forward_phase<MODE, DEG, 4>(a, s_rec, s_qt, s_og, start, n, nk, orig, loss_acc, abs_acc);
         if (MODE == VAR_FORWARD) continue;
 
         // ---- 3. backward, one thread per key (two threads per key, each
