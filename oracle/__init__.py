@@ -44,34 +44,75 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _configure(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    lib.ora_window_base.argtypes = [ctypes.c_float, i32]
+    lib.ora_window_base.restype = i32
+    lib.ora_forward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp, dp, dp]
+    lib.ora_backward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
+    lib.ora_forward_global.argtypes = [i32, f64, dp, dp, i64, i32, dp, dp]
+    lib.ora_backward_grad.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
+    lib.ora_mean_shift.argtypes = [i32, f64, dp, i64, dp]
+    lib.ora_variant_channels.argtypes = [i32, i32, i32]
+    lib.ora_variant_channels.restype = i32
+    lib.ora_variant_forward.argtypes = [i32, i32, f64, i32, i32, i32, dp, dp, i64, i32, dp, dp, dp, dp]
+    lib.ora_variant_backward.argtypes = [i32, i32, f64, i32, i32, i32, dp, dp, i64, i32, dp, dp]
+    lib.ora_cosine_forward.argtypes = [i32, i32, f64, i32, dp, dp, i64, i32, dp]
+    lib.ora_cosine_backward.argtypes = [i32, i32, f64, i32, dp, dp, i64, i32, dp, dp]
+    lib.ora_loss_grad.argtypes = [i32, dp, dp, i64, dp, dp, dp]
+    lib.ora_adam.argtypes = [i64, dp, dp, dp, dp, i64, f64, f64, f64, f64, f64, i32]
+    for fn in ("ora_forward", "ora_backward", "ora_forward_global", "ora_loss_grad", "ora_adam",
+               "ora_backward_grad", "ora_mean_shift", "ora_variant_forward", "ora_variant_backward",
+               "ora_cosine_forward", "ora_cosine_backward"):
+        getattr(lib, fn).restype = None
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_LIB_PATH)
-            dp = ctypes.POINTER(ctypes.c_double)
-            i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
-            lib.ora_window_base.argtypes = [ctypes.c_float, i32]
-            lib.ora_window_base.restype = i32
-            lib.ora_forward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp, dp, dp]
-            lib.ora_backward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
-            lib.ora_forward_global.argtypes = [i32, f64, dp, dp, i64, i32, dp, dp]
-            lib.ora_backward_grad.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
-            lib.ora_mean_shift.argtypes = [i32, f64, dp, i64, dp]
-            lib.ora_variant_channels.argtypes = [i32, i32, i32]
-            lib.ora_variant_channels.restype = i32
-            lib.ora_variant_forward.argtypes = [i32, i32, f64, i32, i32, i32, dp, dp, i64, i32, dp, dp, dp, dp]
-            lib.ora_variant_backward.argtypes = [i32, i32, f64, i32, i32, i32, dp, dp, i64, i32, dp, dp]
-            lib.ora_cosine_forward.argtypes = [i32, i32, f64, i32, dp, dp, i64, i32, dp]
-            lib.ora_cosine_backward.argtypes = [i32, i32, f64, i32, dp, dp, i64, i32, dp, dp]
-            lib.ora_loss_grad.argtypes = [i32, dp, dp, i64, dp, dp, dp]
-            lib.ora_adam.argtypes = [i64, dp, dp, dp, dp, i64, f64, f64, f64, f64, f64, i32]
-            for fn in ("ora_forward", "ora_backward", "ora_forward_global", "ora_loss_grad", "ora_adam",
-                       "ora_backward_grad", "ora_mean_shift"):
-                getattr(lib, fn).restype = None
-            _lib = lib
+            _lib = _configure(ctypes.CDLL(_LIB_PATH))
     return _lib
+
+
+def build_variant_source(text: str, name: str) -> str:
+    """Compile a modified copy of the oracle's C source (mutation tests of
+    the pins) into ``oracle/_build/<name>.so``; returns its path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    src = os.path.join(_BUILD, name + ".c")
+    out = os.path.join(_BUILD, name + ".so")
+    with open(src, "w") as f:
+        f.write(text)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+                    "-o", out, src, "-lm"], check=True)
+    return out
+
+
+class swapped_library:
+    """Context manager: every oracle function uses the library at ``path``
+    (a build of a modified source) until the block exits."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _load()
+        _lib = _configure(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def source_text() -> str:
+    with open(_SRC) as f:
+        return f.read()
 
 
 def _f64(a) -> np.ndarray:

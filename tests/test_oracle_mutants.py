@@ -1,0 +1,126 @@
+"""Mutation tests of the oracle's pins.
+
+Each case plants one plausible mistake in a copy of the oracle's C source (a
+dropped term, a flipped sign, an off-by-one window, swapped slots, a wrong
+Taylor factor, a different reading of a garbled formula), builds it, and
+checks that at least one pin of test_oracle_pins.py fails against it.  The
+mistakes are planted in the oracle only, on the CPU; the CUDA path is not
+involved.  A mutant that no pin catches would mean the pins leave that part
+of the oracle unchecked.
+"""
+import hashlib
+import inspect
+
+import pytest
+
+import oracle
+import test_oracle_pins as P
+
+# name -> (text in efunc_oracle.c, replacement); the text must occur exactly once
+MUTANTS = {
+    "offset key placed at the grid key (Delta dropped)": (
+        "        k.p[0] += th[0]; k.p[1] += th[1]; k.p[2] += th[2];\n        k.beta = exp(log_beta0 + th[4]);",
+        "        k.beta = exp(log_beta0 + th[4]);"),
+    "value without its linear term": (
+        "*f = k->o + k->d[0] * r[0] + k->d[1] * r[1] + k->d[2] * r[2];",
+        "*f = k->o;"),
+    "exponent without the scale beta": (
+        "*expo = -k->beta * (*d2);",
+        "*expo = -(*d2);"),
+    "grid key reads the offset key's log-scale": (
+        "        k.beta = exp(log_beta0 + th[3]);",
+        "        k.beta = exp(log_beta0 + th[4]);"),
+    "dO/dbeta with the wrong sign": (
+        "double dbeta = gl * (-d2 * (f - O));",
+        "double dbeta = gl * (d2 * (f - O));"),
+    "dO/dDelta without the -d term": (
+        "gr[x] += gl * (-k.d[x] + 2.0 * k.beta * r[x] * (f - O));",
+        "gr[x] += gl * (2.0 * k.beta * r[x] * (f - O));"),
+    "dO/dq without the 2 beta (q - p)(O - f) term": (
+        "g[x] += w * (k.d[x] + 2.0 * k.beta * r[x] * (O - f));",
+        "g[x] += w * k.d[x];"),
+    "window one centre low": (
+        "int l = c - W + 1, h = c + W;",
+        "int l = c - W, h = c + W - 1;"),
+    "window base without the half-cell shift": (
+        "float u = t - 0.5f;",
+        "float u = t;"),
+    "L1 gradient with sign(0) = 1": (
+        "(diff > 0.0 ? 1.0 : (diff < 0.0 ? -1.0 : 0.0))",
+        "(diff >= 0.0 ? 1.0 : -1.0)"),
+    "Adam without the first-moment bias correction": (
+        "double mhat = m[i] / bc1;",
+        "double mhat = m[i];"),
+    "second order: dG/dd without the + u term": (
+        "g_d[x] = w * (r[x] * e1 + u[x]) + go * w * r[x];",
+        "g_d[x] = w * (r[x] * e1) + go * w * r[x];"),
+    "variant: quadratic term without the 1/2": (
+        "v += 0.5 * S[a][b] * x[a] * x[b];",
+        "v += S[a][b] * x[a] * x[b];"),
+    "variant: cubic term with 1/2 instead of 1/6": (
+        "v += T[a][b][c] * x[a] * x[b] * x[c] / 6.0;",
+        "v += T[a][b][c] * x[a] * x[b] * x[c] / 2.0;"),
+    "variant: offset gradient without grad f": (
+        "k.grad_delta[i] += gl * (-g[i] + 2.0 * k.beta * x[i] * (f - O));",
+        "k.grad_delta[i] += gl * (2.0 * k.beta * x[i] * (f - O));"),
+    "variant: learnable-scale gradient without the chain factor beta": (
+        "if (k.grad_b) *k.grad_b += gl * k.beta * (-d2 * (f - O));",
+        "if (k.grad_b) *k.grad_b += gl * (-d2 * (f - O));"),
+    "mean shift returns the weighted mean, not the offset": (
+        "dl[x] = S[x] / Z - k[x];",
+        "dl[x] = S[x] / Z;"),
+    "cosine weight read as cos(b pi (x + y + z))": (
+        "return cos(b * pi * q[0]) * cos(b * pi * q[1]) * cos(b * pi * q[2]);",
+        "return cos(b * pi * (q[0] + q[1] + q[2]));"),
+}
+
+
+def pin_cases():
+    """Every pin of test_oracle_pins.py with its parametrisations expanded."""
+    for name, fn in sorted(inspect.getmembers(P, inspect.isfunction)):
+        if not name.startswith("test_"):
+            continue
+        combos = [{}]
+        for mark in getattr(fn, "pytestmark", []):
+            if mark.name != "parametrize":
+                continue
+            names = [n.strip() for n in mark.args[0].split(",")]
+            expanded = []
+            for c in combos:
+                for vals in mark.args[1]:
+                    vals = vals if len(names) > 1 else (vals,)
+                    d = dict(c)
+                    d.update(zip(names, vals))
+                    expanded.append(d)
+            combos = expanded
+        if set(inspect.signature(fn).parameters) - set(combos[0]):
+            continue   # needs a fixture: not a pure pin
+        for c in combos:
+            yield name, fn, c
+
+
+def first_failing_pin(path):
+    with oracle.swapped_library(path):
+        for name, fn, kw in pin_cases():
+            try:
+                fn(**kw)
+            except Exception:   # an assertion or an error: the pin suite fails
+                return name
+    return None
+
+
+def test_pins_pass_on_the_unmodified_source():
+    text = oracle.source_text()
+    path = oracle.build_variant_source(text, "unmodified_copy")
+    assert first_failing_pin(path) is None
+
+
+@pytest.mark.parametrize("mutant", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(mutant):
+    old, new = MUTANTS[mutant]
+    text = oracle.source_text()
+    assert text.count(old) == 1, f"mutation target not unique or missing: {old!r}"
+    tag = hashlib.sha1(mutant.encode()).hexdigest()[:10]
+    path = oracle.build_variant_source(text.replace(old, new), "mutant_" + tag)
+    caught = first_failing_pin(path)
+    assert caught is not None, f"no pin fails with the mistake: {mutant}"
