@@ -81,6 +81,40 @@ __global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) bin_kernel(SortA
     }
 }
 
+// Coarse grids (few bins, hundreds of queries per bin) make the global
+// histogram atomics contend.  There every block counts a contiguous slice of
+// queries in a shared-memory histogram first (local arrival ranks), then
+// reserves each non-empty bin's range with one global atomic, then adds the
+// reserved base to its queries' ranks.
+constexpr int kSmemBinsMax = 12288;   // 48 KB of counters
+
+template <bool VEC4>
+__global__ void __launch_bounds__(kWideThreads) bin_smem_kernel(SortArgs a, int64_t slice)
+{
+    extern __shared__ uint32_t s_hist[];
+    const float half_r = (float)a.R * 0.5f, rmax = (float)(a.R - 1);
+    const int nb = (int)a.nbins;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s_hist[i] = 0u;
+    __syncthreads();
+    const int64_t j0 = (int64_t)blockIdx.x * slice, j1 = min(a.J, j0 + slice);
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        float x, y, z, w;
+        load_query(a.q, j, a.q_stride, VEC4, x, y, z, w);
+        a.rank[j] = atomicAdd(&s_hist[query_bin(x, y, z, half_r, rmax, a.P)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const uint32_t c = s_hist[i];
+        if (c) s_hist[i] = atomicAdd(&a.hist[i], c);
+    }
+    __syncthreads();
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        float x, y, z, w;
+        load_query(a.q, j, a.q_stride, VEC4, x, y, z, w);
+        a.rank[j] += s_hist[query_bin(x, y, z, half_r, rmax, a.P)];
+    }
+}
+
 // Packed scan value: low 32 bits = query count, high 32 bits = work items.
 __device__ __forceinline__ unsigned long long pack(uint32_t count)
 {
@@ -234,8 +268,17 @@ cudaError_t launch_sort(const SortArgs &a, cudaStream_t s, bool narrow)
     const int64_t nblocks = (a.nbins + kScanSeg - 1) / kScanSeg;
 
     launch_begin(K_BIN, s);
-    if (vec4) bin_kernel<true><<<g, threads, 0, s>>>(a);
-    else bin_kernel<false><<<g, threads, 0, s>>>(a);
+    if (!narrow && a.nbins <= kSmemBinsMax) {
+        // one slice per block, two blocks per SM
+        const int64_t blocks = stream_grid(a.J, kWideThreads, 2);
+        const int64_t slice = (a.J + blocks - 1) / blocks;
+        const size_t smem = (size_t)a.nbins * 4;
+        if (vec4) bin_smem_kernel<true><<<(unsigned)blocks, kWideThreads, smem, s>>>(a, slice);
+        else bin_smem_kernel<false><<<(unsigned)blocks, kWideThreads, smem, s>>>(a, slice);
+    } else {
+        if (vec4) bin_kernel<true><<<g, threads, 0, s>>>(a);
+        else bin_kernel<false><<<g, threads, 0, s>>>(a);
+    }
     launch_end(K_BIN, s);
 
     launch_begin(K_SCAN_REDUCE, s);
