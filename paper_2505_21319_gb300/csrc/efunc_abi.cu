@@ -271,6 +271,7 @@ struct CopyPipe {
     cudaEvent_t freed[2] = {nullptr, nullptr};
     cudaEvent_t sorted[2] = {nullptr, nullptr};
     cudaEvent_t consumed[2] = {nullptr, nullptr};
+    cudaEvent_t packed = nullptr;
 };
 constexpr int kMaxPipes = 64;
 std::mutex g_pipe_mu;
@@ -293,6 +294,7 @@ cudaError_t copy_pipe(CopyPipe **out)
             if ((e = cudaEventCreateWithFlags(&p.sorted[b], cudaEventDisableTiming)) != cudaSuccess) return e;
             if ((e = cudaEventCreateWithFlags(&p.consumed[b], cudaEventDisableTiming)) != cudaSuccess) return e;
         }
+        if ((e = cudaEventCreateWithFlags(&p.packed, cudaEventDisableTiming)) != cudaSuccess) return e;
         p.ready = true;
     }
     *out = &p;
@@ -419,12 +421,16 @@ AdamArgs adam_args(const efunc_adam *ad, int64_t n, float *p, float *g, float *m
 }
 
 // efunc_fit with the sort of batch s+1 (on the library's sort stream, into
-// the second sort buffer) overlapped with pack / fused kernel / Adam of batch
+// the second sort buffer) overlapped with the fused kernel and Adam of batch
 // s on the caller's stream.  The fused kernel's persistent grid leaves one
 // sort block's registers free on every SM so the two run side by side.
 // Events order the buffers: sorted[b] (sort done) before the fused kernel
 // that reads buffer b; consumed[b] (Adam of that step done, it reads the loss
-// sums in buffer b's control block) before the next sort into b.
+// sums in buffer b's control block) before the next sort into b; packed (the
+// key pack of step s done) before the sort of s+1, so that the sort starts
+// together with the fused kernel instead of ahead of it (started earlier it
+// runs at full speed and takes memory bandwidth from the fused kernel's
+// first items; started with it, it trickles along on its one block per SM).
 efunc_status fit_pipelined(const efunc_grid *grid, const efunc_adam *adam, int32_t loss, float eikonal_weight,
                            float *params, float *m, float *v, const float *qo, int64_t J, int32_t n_batches,
                            int32_t steps, int64_t step0, float *stats, void *workspace, cudaStream_t s)
@@ -470,10 +476,15 @@ efunc_status fit_pipelined(const efunc_grid *grid, const efunc_adam *adam, int32
     if (!issue_sort(0)) return EFUNC_ERR_CUDA;
     for (int32_t it = 0; it < steps; ++it) {
         const int b = it & 1;
-        if (it + 1 < steps && !issue_sort(it + 1)) return EFUNC_ERR_CUDA;
         const SortBuf sb = sort_buf(vw, b);
         if (cudaStreamWaitEvent(s, pipe->sorted[b], 0) != cudaSuccess) return EFUNC_ERR_CUDA;
         if (pack_keys(vw, grid, params, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        // the next sort starts once this step's fused kernel is about to start
+        if (it + 1 < steps) {
+            if (cudaEventRecord(pipe->packed, s) != cudaSuccess ||
+                cudaStreamWaitEvent(ss, pipe->packed, 0) != cudaSuccess || !issue_sort(it + 1))
+                return EFUNC_ERR_CUDA;
+        }
         FusedArgs f = fused_args(vw, grid);
         f.sorted = sb.sorted;
         f.items = sb.items;
