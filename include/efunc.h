@@ -269,8 +269,10 @@ efunc_status efunc_mean_shift_init(const efunc_grid *grid, const float *pts, int
  * an invalid description. */
 int32_t efunc_variant_channels(const efunc_variant *variant);
 
-/* Workspace bytes of every variant call below for J queries; 0 if the grid
- * or the variant is invalid. */
+/* Workspace bytes of every variant call below for J queries (the fit sorts
+ * the next batch into a second sort buffer on a library stream while the
+ * current one is computed, and needs all of it; forward and backward need
+ * less); 0 if the grid or the variant is invalid. */
 size_t efunc_variant_workspace_bytes(const efunc_grid *grid, const efunc_variant *variant, int64_t J);
 
 /* Forward of a variant (Algorithm 1 over the windowed keys of its key sets,
@@ -291,8 +293,10 @@ efunc_status efunc_variant_backward(const efunc_grid *grid, const efunc_variant 
 
 /* Fitting loop of a variant (Sec. 3.4), as efunc_fit without the Eikonal
  * term: per step sort, pack, fused forward + loss + backward, Adam on
- * R^3 x channels floats.  qo and stats must be device memory (a host pointer
- * returns EFUNC_ERR_ARG). */
+ * R^3 x channels floats, with the sort of batch s+1 beside batch s (as
+ * efunc_fit with efunc_fit_workspace_bytes).  qo and stats must be device
+ * memory (a host pointer returns EFUNC_ERR_ARG); workspace_bytes at least
+ * efunc_variant_workspace_bytes. */
 efunc_status efunc_variant_fit(const efunc_grid *grid, const efunc_variant *variant, const efunc_adam *adam,
                                int32_t loss, float *params, float *m, float *v, const float *qo, int64_t J,
                                int32_t n_batches, int32_t steps, int64_t step0, float *stats, void *workspace,
@@ -310,7 +314,7 @@ efunc_status efunc_variant_fit(const efunc_grid *grid, const efunc_variant *vari
  * is Config-G-6).  bands in [1, 16].
  *   params  [device] B x R^3 x 5 floats, band-major
  * Workspace: efunc_cosine_workspace_bytes (0 for an invalid grid, band count
- * or J). */
+ * or J; the fit needs all of it, forward and backward less). */
 size_t efunc_cosine_workspace_bytes(const efunc_grid *grid, int32_t bands, int64_t J);
 
 /* S at J queries (caller's order), arguments as efunc_forward. */
@@ -325,7 +329,8 @@ efunc_status efunc_cosine_backward(const efunc_grid *grid, int32_t bands, const 
                                    size_t workspace_bytes, efunc_stream_t stream);
 
 /* Fitting loop of S (Sec. 4.4 optimises S as in Eq. loss), as
- * efunc_variant_fit: device batches and statistics only. */
+ * efunc_variant_fit (sort of the next batch beside the current one; device
+ * batches and statistics only). */
 efunc_status efunc_cosine_fit(const efunc_grid *grid, int32_t bands, const efunc_adam *adam, int32_t loss,
                               float *params, float *m, float *v, const float *qo, int64_t J, int32_t n_batches,
                               int32_t steps, int64_t step0, float *stats, void *workspace, size_t workspace_bytes,

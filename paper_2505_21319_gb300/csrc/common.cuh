@@ -152,6 +152,7 @@ struct VariantArgs {
     float *grad;         // R^3 x channels, accumulated
     int loss;            // fit
     float inv_J;
+    int leave_room;      // persistent grid leaves room for the next batch's sort (pipelined fit)
 };
 
 enum VariantMode { VAR_FORWARD = 0, VAR_BACKWARD = 1, VAR_FIT = 2 };
@@ -175,6 +176,7 @@ struct CosineArgs {
     float *grad;         // B x R^3 x 5, accumulated
     int loss;
     float inv_J;
+    int leave_room;      // persistent grid leaves room for the next batch's sort (pipelined fit)
 };
 
 // Kernel identifiers for the profiler.
@@ -196,6 +198,9 @@ cudaError_t launch_forward(const FusedArgs &a, bool with_dq, int grid, cudaStrea
 cudaError_t launch_fused_backward(const FusedArgs &a, bool with_gq, bool second_order, int grid, cudaStream_t s);
 cudaError_t launch_fused_fit(const FusedArgs &a, bool eikonal, int grid, cudaStream_t s);
 int fused_fit_grid_size(bool eikonal, bool leave_room);   // persistent grid of the fit kernel
+// CTAs per SM of a persistent kernel reduced until the registers of one
+// sort block (kSortThreads x 32) stay free on every SM
+int leave_sort_room(const void *kernel, int per_sm);
 cudaError_t launch_adam(const AdamArgs &a, cudaStream_t s);
 cudaError_t launch_mean_shift(const MeanShiftArgs &a, cudaStream_t s);
 cudaError_t launch_variant_pack(const VariantArgs &a, cudaStream_t s);

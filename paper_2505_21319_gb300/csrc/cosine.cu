@@ -239,6 +239,7 @@ cudaError_t launch_mode(const CosineArgs &a, int kid, cudaStream_t s)
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cosine_kernel<MODE>, kThreads, smem);
     if (per_sm <= 0) per_sm = 1;
+    if (a.leave_room) per_sm = leave_sort_room(reinterpret_cast<const void *>(cosine_kernel<MODE>), per_sm);
     launch_begin(kid, s);
     cosine_kernel<MODE><<<cos_sm_count() * per_sm, kThreads, smem, s>>>(a);
     launch_end(kid, s);

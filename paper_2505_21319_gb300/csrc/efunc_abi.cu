@@ -341,9 +341,9 @@ int variant_channels_of(const efunc_variant *v)
     return ((v->sets & 2) ? 3 : 0) + v->learn_scale * ns + kVariantNV[v->degree] * ns;
 }
 
-Layout variant_layout(const efunc_grid *g, const efunc_variant *v, int64_t J)
+Layout variant_layout(const efunc_grid *g, const efunc_variant *v, int64_t J, bool two_sort_buffers = false)
 {
-    return make_layout(g->R, J, variant_key_records(v->sets, v->degree), variant_channels_of(v));
+    return make_layout(g->R, J, variant_key_records(v->sets, v->degree), variant_channels_of(v), two_sort_buffers);
 }
 
 efunc_status check_variant_workspace(const efunc_grid *g, const efunc_variant *v, int64_t J, const void *ws,
@@ -376,7 +376,10 @@ VariantArgs variant_args(const Views &vw, const efunc_grid *g, const efunc_varia
 
 bool bands_ok(int32_t B) { return B >= 1 && B <= kMaxBands; }
 
-Layout cosine_layout(const efunc_grid *g, int32_t B, int64_t J) { return make_layout(g->R, J, 2 * B, 5 * B); }
+Layout cosine_layout(const efunc_grid *g, int32_t B, int64_t J, bool two_sort_buffers = false)
+{
+    return make_layout(g->R, J, 2 * B, 5 * B, two_sort_buffers);
+}
 
 efunc_status check_cosine_workspace(const efunc_grid *g, int32_t B, int64_t J, const void *ws, size_t ws_bytes)
 {
@@ -447,7 +450,10 @@ efunc_status fit_pipelined(const efunc_grid *grid, const efunc_adam *adam, int32
     const size_t batch_bytes = (size_t)J * 16;
     auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * (size_t)J * 4; };
     const bool eik = eikonal_weight > 0.f;
-    const int grid_blocks = fused_fit_grid_size(eik, true);
+    // the second-order kernel (5 CTAs/SM) loses more at 4 CTAs/SM than the
+    // overlap gains (1.93 vs 1.91 ms/step): it keeps its full grid and the
+    // sort runs between its launches
+    const int grid_blocks = fused_fit_grid_size(eik, !eik);
 
     if (cudaMemsetAsync(grad, 0, (size_t)n * 4, s) != cudaSuccess) return EFUNC_ERR_CUDA;
     // both sort buffers (and staging buffers) are free once the caller's earlier work is done
@@ -507,6 +513,41 @@ efunc_status fit_pipelined(const efunc_grid *grid, const efunc_adam *adam, int32
         if (cudaEventRecord(pipe->consumed[b], s) != cudaSuccess) return EFUNC_ERR_CUDA;
     }
     if (stats_host && cudaStreamSynchronize(s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    return EFUNC_OK;
+}
+
+// The sort-ahead schedule of fit_pipelined for device batches, shared by the
+// variant and cosine fits: pack(stream) issues a step's key pack,
+// compute(step, sort buffer, stream) its fused kernel and Adam step.
+template <class Pack, class Compute>
+efunc_status pipelined_device_fit(const Views &vw, int R, const float *qo, int64_t J, int32_t n_batches,
+                                  int32_t steps, cudaStream_t s, Pack pack, Compute compute)
+{
+    CopyPipe *pipe = nullptr;
+    if (copy_pipe(&pipe) != cudaSuccess) return EFUNC_ERR_CUDA;
+    cudaStream_t ss = pipe->sort_stream;
+    auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * (size_t)J * 4; };
+    for (int b = 0; b < 2; ++b)
+        if (cudaEventRecord(pipe->consumed[b], s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    auto issue_sort = [&](int32_t k) -> bool {
+        const int b = k & 1;
+        if (cudaStreamWaitEvent(ss, pipe->consumed[b], 0) != cudaSuccess) return false;
+        if (sort_into_buf(sort_buf(vw, b), vw.L, R, batch(k), J, 4, ss) != cudaSuccess) return false;
+        return cudaEventRecord(pipe->sorted[b], ss) == cudaSuccess;
+    };
+    if (!issue_sort(0)) return EFUNC_ERR_CUDA;
+    for (int32_t it = 0; it < steps; ++it) {
+        const int b = it & 1;
+        if (cudaStreamWaitEvent(s, pipe->sorted[b], 0) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (pack(s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (it + 1 < steps) {
+            if (cudaEventRecord(pipe->packed, s) != cudaSuccess ||
+                cudaStreamWaitEvent(ss, pipe->packed, 0) != cudaSuccess || !issue_sort(it + 1))
+                return EFUNC_ERR_CUDA;
+        }
+        if (compute(it, sort_buf(vw, b), s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (cudaEventRecord(pipe->consumed[b], s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    }
     return EFUNC_OK;
 }
 
@@ -755,7 +796,7 @@ int32_t efunc_variant_channels(const efunc_variant *variant)
 size_t efunc_variant_workspace_bytes(const efunc_grid *grid, const efunc_variant *variant, int64_t J)
 {
     if (!grid_ok(grid) || !variant_ok(variant) || J < 0 || J > kMaxJ) return 0;
-    return variant_layout(grid, variant, J).total;
+    return variant_layout(grid, variant, J, true).total;
 }
 
 efunc_status efunc_variant_forward(const efunc_grid *grid, const efunc_variant *variant, const float *params,
@@ -814,37 +855,46 @@ efunc_status efunc_variant_fit(const efunc_grid *grid, const efunc_variant *vari
     if (loss != EFUNC_LOSS_L1 && loss != EFUNC_LOSS_MSE) return EFUNC_ERR_ARG;
     if (J < 1 || J > kMaxJ || n_batches < 1 || steps < 0 || step0 < 0) return EFUNC_ERR_ARG;
     if (!params || !m || !v || !qo) return EFUNC_ERR_ARG;
-    if ((st = check_variant_workspace(grid, variant, J, workspace, workspace_bytes))) return st;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u) ||
+        workspace_bytes < variant_layout(grid, variant, J, true).total)
+        return EFUNC_ERR_WORKSPACE;
     if (steps == 0) return EFUNC_OK;
     if (is_host_pointer(qo) || (stats && is_host_pointer(stats))) return EFUNC_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    Views vw{variant_layout(grid, variant, J), static_cast<char *>(workspace)};
     const int64_t n = (int64_t)grid->R * grid->R * grid->R * efunc_variant_channels(variant);
-    float *grad = vw.grad();
-    if (cudaMemsetAsync(grad, 0, (size_t)n * 4, s) != cudaSuccess) return EFUNC_ERR_CUDA;
-    for (int32_t it = 0; it < steps; ++it) {
-        const float *qdev = qo + (size_t)(it % n_batches) * (size_t)J * 4;
-        cudaError_t e = sort_into(vw, grid->R, qdev, J, 4, vw.sorted(), nullptr, s);
-        VariantArgs a = variant_args(vw, grid, variant, params);
-        if (e == cudaSuccess) e = launch_variant_pack(a, s);
-        if (e != cudaSuccess) return EFUNC_ERR_CUDA;
-        a.grad = grad;
-        a.loss = loss;
-        a.inv_J = (float)(1.0 / (double)J);
-        if (launch_variant(a, VAR_FIT, s) != cudaSuccess) return EFUNC_ERR_CUDA;
-        AdamArgs ad = adam_args(adam, n, params, grad, m, v, step0 + it + 1);
-        ad.ctrl = vw.ctrl();
-        ad.inv_J = a.inv_J;
-        ad.stats = stats ? stats + 2 * (size_t)it : nullptr;
-        if (launch_adam(ad, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    const float inv_J = (float)(1.0 / (double)J);
+    {
+        Views vp{variant_layout(grid, variant, J, true), static_cast<char *>(workspace)};
+        float *gp = vp.grad();
+        if (cudaMemsetAsync(gp, 0, (size_t)n * 4, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        return pipelined_device_fit(
+            vp, grid->R, qo, J, n_batches, steps, s,
+            [&](cudaStream_t st) { return launch_variant_pack(variant_args(vp, grid, variant, params), st); },
+            [&](int32_t it, const SortBuf &sb, cudaStream_t st) {
+                VariantArgs a = variant_args(vp, grid, variant, params);
+                a.sorted = sb.sorted;
+                a.items = sb.items;
+                a.ctrl = sb.ctrl;
+                a.perm = nullptr;
+                a.grad = gp;
+                a.loss = loss;
+                a.inv_J = inv_J;
+                a.leave_room = 1;
+                cudaError_t e = launch_variant(a, VAR_FIT, st);
+                if (e != cudaSuccess) return e;
+                AdamArgs ad = adam_args(adam, n, params, gp, m, v, step0 + it + 1);
+                ad.ctrl = sb.ctrl;
+                ad.inv_J = inv_J;
+                ad.stats = stats ? stats + 2 * (size_t)it : nullptr;
+                return launch_adam(ad, st);
+            });
     }
-    return EFUNC_OK;
 }
 
 size_t efunc_cosine_workspace_bytes(const efunc_grid *grid, int32_t bands, int64_t J)
 {
     if (!grid_ok(grid) || !bands_ok(bands) || J < 0 || J > kMaxJ) return 0;
-    return cosine_layout(grid, bands, J).total;
+    return cosine_layout(grid, bands, J, true).total;
 }
 
 efunc_status efunc_cosine_forward(const efunc_grid *grid, int32_t bands, const float *params, const float *q,
@@ -902,31 +952,40 @@ efunc_status efunc_cosine_fit(const efunc_grid *grid, int32_t bands, const efunc
     if (loss != EFUNC_LOSS_L1 && loss != EFUNC_LOSS_MSE) return EFUNC_ERR_ARG;
     if (J < 1 || J > kMaxJ || n_batches < 1 || steps < 0 || step0 < 0) return EFUNC_ERR_ARG;
     if (!params || !m || !v || !qo) return EFUNC_ERR_ARG;
-    if ((st = check_cosine_workspace(grid, bands, J, workspace, workspace_bytes))) return st;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u) ||
+        workspace_bytes < cosine_layout(grid, bands, J, true).total)
+        return EFUNC_ERR_WORKSPACE;
     if (steps == 0) return EFUNC_OK;
     if (is_host_pointer(qo) || (stats && is_host_pointer(stats))) return EFUNC_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    Views vw{cosine_layout(grid, bands, J), static_cast<char *>(workspace)};
     const int64_t n = (int64_t)grid->R * grid->R * grid->R * 5 * bands;
-    float *grad = vw.grad();
-    if (cudaMemsetAsync(grad, 0, (size_t)n * 4, s) != cudaSuccess) return EFUNC_ERR_CUDA;
-    for (int32_t it = 0; it < steps; ++it) {
-        const float *qdev = qo + (size_t)(it % n_batches) * (size_t)J * 4;
-        cudaError_t e = sort_into(vw, grid->R, qdev, J, 4, vw.sorted(), nullptr, s);
-        CosineArgs a = cosine_args(vw, grid, bands, params);
-        if (e == cudaSuccess) e = launch_cosine_pack(a, s);
-        if (e != cudaSuccess) return EFUNC_ERR_CUDA;
-        a.grad = grad;
-        a.loss = loss;
-        a.inv_J = (float)(1.0 / (double)J);
-        if (launch_cosine(a, VAR_FIT, s) != cudaSuccess) return EFUNC_ERR_CUDA;
-        AdamArgs ad = adam_args(adam, n, params, grad, m, v, step0 + it + 1);
-        ad.ctrl = vw.ctrl();
-        ad.inv_J = a.inv_J;
-        ad.stats = stats ? stats + 2 * (size_t)it : nullptr;
-        if (launch_adam(ad, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    const float inv_J = (float)(1.0 / (double)J);
+    {
+        Views vp{cosine_layout(grid, bands, J, true), static_cast<char *>(workspace)};
+        float *gp = vp.grad();
+        if (cudaMemsetAsync(gp, 0, (size_t)n * 4, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        return pipelined_device_fit(
+            vp, grid->R, qo, J, n_batches, steps, s,
+            [&](cudaStream_t st) { return launch_cosine_pack(cosine_args(vp, grid, bands, params), st); },
+            [&](int32_t it, const SortBuf &sb, cudaStream_t st) {
+                CosineArgs a = cosine_args(vp, grid, bands, params);
+                a.sorted = sb.sorted;
+                a.items = sb.items;
+                a.ctrl = sb.ctrl;
+                a.perm = nullptr;
+                a.grad = gp;
+                a.loss = loss;
+                a.inv_J = inv_J;
+                a.leave_room = 1;
+                cudaError_t e = launch_cosine(a, VAR_FIT, st);
+                if (e != cudaSuccess) return e;
+                AdamArgs ad = adam_args(adam, n, params, gp, m, v, step0 + it + 1);
+                ad.ctrl = sb.ctrl;
+                ad.inv_J = inv_J;
+                ad.stats = stats ? stats + 2 * (size_t)it : nullptr;
+                return launch_adam(ad, st);
+            });
     }
-    return EFUNC_OK;
 }
 
 void efunc_profile_enable(int32_t enable)

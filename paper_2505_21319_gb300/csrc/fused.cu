@@ -687,19 +687,24 @@ int fused_fit_grid_size(bool eikonal, bool leave_room)
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, 0);
         if (per_sm <= 0) per_sm = 1;
-        if (leave_room) {
-            // leave the registers of one sort block (kSortThreads x 32) free on every SM
-            cudaFuncAttributes fa{};
-            int dev = 0, regs_sm = 65536;
-            cudaFuncGetAttributes(&fa, k);
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-            const int per_cta = (fa.numRegs + 7) / 8 * 8 * kThreads;
-            while (per_sm > 1 && per_sm * per_cta > regs_sm - kSortThreads * 32) --per_sm;
-        }
+        if (leave_room) per_sm = leave_sort_room(k, per_sm);
         g = sm_count() * per_sm;
     }
     return g;
+}
+
+int leave_sort_room(const void *kernel, int per_sm)
+{
+    cudaFuncAttributes fa{};
+    int dev = 0, regs_sm = 65536;
+    cudaFuncGetAttributes(&fa, kernel);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    const int per_cta = (fa.numRegs + 7) / 8 * 8 * kThreads;
+    // exactly one block's worth left free was not enough on the GPU: the sort
+    // then waited for the persistent kernel to finish; leave two
+    while (per_sm > 1 && per_sm * per_cta > regs_sm - 2 * kSortThreads * 32) --per_sm;
+    return per_sm;
 }
 
 cudaError_t launch_pack_keys(const PackArgs &a, cudaStream_t s)

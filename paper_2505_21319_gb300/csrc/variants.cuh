@@ -419,16 +419,19 @@ __global__ void __launch_bounds__(kThreads, 4) variant_kernel(VariantArgs a)
 int sm_count();
 
 template <int MODE, int SETS, int DEG>
-int persistent_grid()
+int persistent_grid(bool leave_room)
 {
-    static int g = 0;
-    if (!g) {
+    static int g[2] = {0, 0};
+    int &v = g[leave_room ? 1 : 0];
+    if (!v) {
+        const void *k = reinterpret_cast<const void *>(variant_kernel<MODE, SETS, DEG>);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, variant_kernel<MODE, SETS, DEG>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, 0);
         if (per_sm <= 0) per_sm = 1;
-        g = sm_count() * per_sm;
+        if (leave_room) per_sm = leave_sort_room(k, per_sm);
+        v = sm_count() * per_sm;
     }
-    return g;
+    return v;
 }
 
 template <int SETS, int DEG>
@@ -436,15 +439,15 @@ cudaError_t launch_sets_deg(const VariantArgs &a, int mode, cudaStream_t s)
 {
     if (mode == VAR_FORWARD) {
         launch_begin(K_VAR_FORWARD, s);
-        variant_kernel<VAR_FORWARD, SETS, DEG><<<persistent_grid<VAR_FORWARD, SETS, DEG>(), kThreads, 0, s>>>(a);
+        variant_kernel<VAR_FORWARD, SETS, DEG><<<persistent_grid<VAR_FORWARD, SETS, DEG>(a.leave_room), kThreads, 0, s>>>(a);
         launch_end(K_VAR_FORWARD, s);
     } else if (mode == VAR_BACKWARD) {
         launch_begin(K_VAR_BACKWARD, s);
-        variant_kernel<VAR_BACKWARD, SETS, DEG><<<persistent_grid<VAR_BACKWARD, SETS, DEG>(), kThreads, 0, s>>>(a);
+        variant_kernel<VAR_BACKWARD, SETS, DEG><<<persistent_grid<VAR_BACKWARD, SETS, DEG>(a.leave_room), kThreads, 0, s>>>(a);
         launch_end(K_VAR_BACKWARD, s);
     } else {
         launch_begin(K_VAR_FIT, s);
-        variant_kernel<VAR_FIT, SETS, DEG><<<persistent_grid<VAR_FIT, SETS, DEG>(), kThreads, 0, s>>>(a);
+        variant_kernel<VAR_FIT, SETS, DEG><<<persistent_grid<VAR_FIT, SETS, DEG>(a.leave_room), kThreads, 0, s>>>(a);
         launch_end(K_VAR_FIT, s);
     }
     return cudaGetLastError();
