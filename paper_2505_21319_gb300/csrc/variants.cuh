@@ -272,7 +272,7 @@ __device__ __forceinline__ void forward_phase(const VariantArgs &a, const float4
 }
 
 template <int MODE, int SETS, int DEG>
-__global__ void __launch_bounds__(kThreads, 4) variant_kernel(VariantArgs a)
+__global__ void __launch_bounds__(kThreads, DEG <= 1 ? 7 : (DEG == 2 ? 5 : 4)) variant_kernel(VariantArgs a)
 {
     constexpr int NV = nv_of(DEG), NREC = nrec_of(DEG), NS = nsets_of(SETS);
     __shared__ float4 s_rec[kCentres * NS * NREC];   // window key records, key-major
