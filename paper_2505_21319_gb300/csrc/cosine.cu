@@ -8,8 +8,8 @@
 // query evaluates the B softmaxes (forward thread-per-query) and the weighted
 // sum.  The backward loops thread-per-(key, band) over the item's queries with
 // the band's upstream gS_j w_b(q_j), one atomic per parameter per item.  The
-// band weights are formed in FP64 (b q_x exact, cospi correctly rounded to
-// well below FP32 precision) and rounded once.
+// band weights are formed in FP32 from the exact split of b q (cos_factor);
+// FP64 cospi, exact but slow on this GPU, cost a third of the one-band kernel.
 #include "common.cuh"
 
 namespace efunc {
@@ -50,6 +50,19 @@ __device__ __forceinline__ CWin cwindow_of(const Item item, int R)
     w.nz = min(w.cz + kW, R - 1) - w.loz + 1;
     w.nc = w.nx * w.ny * w.nz;
     return w;
+}
+
+// cos(b pi x) in FP32 from the exact split b x = hi + lo (lo = fma(b, x, -hi),
+// |lo| <= ulp(hi) / 2): cos(pi hi) - pi lo sin(pi hi), the neglected terms
+// O(lo^2) far below FP32 rounding; sincospif is accurate to about one ulp.
+__device__ __forceinline__ float cos_factor(int b, float x)
+{
+    const float fb = (float)b;
+    const float hi = fb * x;
+    const float lo = fmaf(fb, x, -hi);
+    float s, c;
+    sincospif(hi, &s, &c);
+    return fmaf(-3.14159265358979f * lo, s, c);
 }
 
 // (e, m) of one query over one band's window keys, exponents shifted by M2.
@@ -137,8 +150,7 @@ __global__ void __launch_bounds__(kThreads) cosine_kernel(CosineArgs a)
                     band_sums(rec, nc, x, y, z, M2, e, m);
                 }
                 const float O = m / e;
-                const float wb = (float)(cospi((double)b * (double)q4.x) * cospi((double)b * (double)q4.y) *
-                                         cospi((double)b * (double)q4.z));
+                const float wb = cos_factor(b, q4.x) * cos_factor(b, q4.y) * cos_factor(b, q4.z);
                 S = fmaf(wb, O, S);
                 if (MODE != VAR_FORWARD) s_qb[qi * B + b] = make_float4(M2 + lg2_approx(e), O, wb, 0.f);
             }
@@ -161,14 +173,19 @@ __global__ void __launch_bounds__(kThreads) cosine_kernel(CosineArgs a)
         }
         if (MODE == VAR_FORWARD) continue;
 
-        // ---- 3. backward: thread per (key, band) over the item's queries
+        // ---- 3. backward: thread per (key, band) over the item's queries;
+        //         with at most 64 keys (one band) two threads share a key,
+        //         each over every second query
         __syncthreads();
-        for (int k = t; k < nc * B; k += kThreads) {
+        const int nkeys = nc * B;
+        const int split = nkeys <= kThreads / 2 ? 2 : 1;
+        for (int kk = t; kk < nkeys * split; kk += kThreads) {
+            const int k = kk / split, part = kk - k * split;
             const int c = k % nc, b = k / nc;
             const float4 A = s_rec[(b * kCentres + c) * 2], V = s_rec[(b * kCentres + c) * 2 + 1];
             float ao = 0.f, adx = 0.f, ady = 0.f, adz = 0.f, ab = 0.f;
 #pragma unroll 2
-            for (int j = 0; j < n; ++j) {
+            for (int j = part; j < n; j += split) {
                 const float4 Q = s_qt[j], P = s_qb[j * B + b];
                 const float rx = Q.x - A.x, ry = Q.y - A.y, rz = Q.z - A.z;
                 const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) bin_kernel(SortA
 constexpr int kSmemBinsMax = 12288;   // 48 KB of counters
 
 template <bool VEC4>
-__global__ void __launch_bounds__(kWideThreads) bin_smem_kernel(SortArgs a, int64_t slice)
+__global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) bin_smem_kernel(SortArgs a, int64_t slice)
 {
     extern __shared__ uint32_t s_hist[];
     const float half_r = (float)a.R * 0.5f, rmax = (float)(a.R - 1);
@@ -269,7 +269,8 @@ cudaError_t launch_sort(const SortArgs &a, cudaStream_t s, bool narrow)
 
     launch_begin(K_BIN, s);
     if (!narrow && a.nbins <= kSmemBinsMax) {
-        // one slice per block, two blocks per SM
+        // one slice per block, two blocks per SM (beside a fit kernel, with one
+        // block per SM, the slices are too long: the global atomics win there)
         const int64_t blocks = stream_grid(a.J, kWideThreads, 2);
         const int64_t slice = (a.J + blocks - 1) / blocks;
         const size_t smem = (size_t)a.nbins * 4;
