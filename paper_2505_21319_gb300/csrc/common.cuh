@@ -198,9 +198,12 @@ cudaError_t launch_forward(const FusedArgs &a, bool with_dq, int grid, cudaStrea
 cudaError_t launch_fused_backward(const FusedArgs &a, bool with_gq, bool second_order, int grid, cudaStream_t s);
 cudaError_t launch_fused_fit(const FusedArgs &a, bool eikonal, int grid, cudaStream_t s);
 int fused_fit_grid_size(bool eikonal, bool leave_room);   // persistent grid of the fit kernel
-// CTAs per SM of a persistent kernel reduced until the registers of one
-// sort block (kSortThreads x 32) stay free on every SM
-int leave_sort_room(const void *kernel, int per_sm);
+// CTAs per SM of a persistent kernel reduced until the registers of
+// sort_blocks sort blocks (kSortThreads x 32 each) stay free on every SM.
+// Two by default: with exactly one block's worth free, a sort started
+// together with the persistent kernel did not fit beside it (variant and
+// second-order fits measured: the sort ran after the kernel).
+int leave_sort_room(const void *kernel, int per_sm, int sort_blocks = 2);
 cudaError_t launch_adam(const AdamArgs &a, cudaStream_t s);
 cudaError_t launch_mean_shift(const MeanShiftArgs &a, cudaStream_t s);
 cudaError_t launch_variant_pack(const VariantArgs &a, cudaStream_t s);

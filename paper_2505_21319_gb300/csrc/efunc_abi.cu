@@ -450,10 +450,7 @@ efunc_status fit_pipelined(const efunc_grid *grid, const efunc_adam *adam, int32
     const size_t batch_bytes = (size_t)J * 16;
     auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * (size_t)J * 4; };
     const bool eik = eikonal_weight > 0.f;
-    // the second-order kernel (5 CTAs/SM) loses more at 4 CTAs/SM than the
-    // overlap gains (1.93 vs 1.91 ms/step): it keeps its full grid and the
-    // sort runs between its launches
-    const int grid_blocks = fused_fit_grid_size(eik, !eik);
+    const int grid_blocks = fused_fit_grid_size(eik, true);
 
     if (cudaMemsetAsync(grad, 0, (size_t)n * 4, s) != cudaSuccess) return EFUNC_ERR_CUDA;
     // both sort buffers (and staging buffers) are free once the caller's earlier work is done

@@ -693,7 +693,7 @@ int fused_fit_grid_size(bool eikonal, bool leave_room)
     return g;
 }
 
-int leave_sort_room(const void *kernel, int per_sm)
+int leave_sort_room(const void *kernel, int per_sm, int sort_blocks)
 {
     cudaFuncAttributes fa{};
     int dev = 0, regs_sm = 65536;
@@ -701,9 +701,7 @@ int leave_sort_room(const void *kernel, int per_sm)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
     const int per_cta = (fa.numRegs + 7) / 8 * 8 * kThreads;
-    // exactly one block's worth left free was not enough on the GPU: the sort
-    // then waited for the persistent kernel to finish; leave two
-    while (per_sm > 1 && per_sm * per_cta > regs_sm - 2 * kSortThreads * 32) --per_sm;
+    while (per_sm > 1 && per_sm * per_cta > regs_sm - sort_blocks * kSortThreads * 32) --per_sm;
     return per_sm;
 }
 
