@@ -206,11 +206,57 @@ __device__ __forceinline__ void fwd_sums(const float4 *rec, int nk, int part, fl
     m = combine_classes<KQ>(mv);
 }
 
+// (e, m) over a full window (64 centres) of grid keys only: the keys sit on
+// the lattice (i - c) h, so the per-axis differences and squares are formed
+// once per query and axis and d2 = (x2 + y2) + z2.  Key k = 16 ox + 4 oy + oz
+// is in class oz, summed in the same key order as fwd_sums.
+template <int DEG, int KQ>
+__device__ __forceinline__ void fwd_sums_lattice(const float4 *rec, int part, float h, float x, float y, float z,
+                                                 float &e, float &m)
+{
+    constexpr int NREC = nrec_of(DEG);
+    constexpr int CPL = kClasses / KQ;
+    float ev[CPL], mv[CPL], ry[4], y2[4], rz[CPL], z2[CPL];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        ry[b] = y - (float)(b - 1) * h;
+        y2[b] = ry[b] * ry[b];
+    }
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) {
+        rz[i] = z - (float)(part + KQ * i - 1) * h;
+        z2[i] = rz[i] * rz[i];
+        ev[i] = mv[i] = 0.f;
+    }
+#pragma unroll 1
+    for (int ox = 0; ox < 4; ++ox) {
+        const float rx = x - (float)(ox - 1) * h;
+        const float x2 = rx * rx;
+#pragma unroll
+        for (int oy = 0; oy < 4; ++oy) {
+            const float xy = x2 + y2[oy];
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                const float4 *r = rec + (16 * ox + 4 * oy + part + KQ * i) * NREC;
+                const float l = ex2_approx(r[0].w * (xy + z2[i]));
+                float c[nv_of(DEG)], mo[nv_of(DEG)];
+                load_coefs<DEG>(r, c);
+                monomials<DEG>(rx, ry[oy], rz[i], mo);
+                ev[i] += l;
+                mv[i] = fmaf(l, poly<DEG>(c, mo), mv[i]);
+            }
+        }
+    }
+    e = combine_classes<KQ>(ev);
+    m = combine_classes<KQ>(mv);
+}
+
 // Forward of the item's queries with KQ lanes per query; stores, for the
 // backward, (local q, lse2) and (O, dL/dO) per query.
-template <int MODE, int DEG, int KQ>
+template <int MODE, int DEG, int KQ, bool LATTICE>
 __device__ __forceinline__ void forward_phase(const VariantArgs &a, const float4 *rec, float4 *qt, float2 *og,
-                                              int start, int n, int nk, float3 orig, float &loss_acc, float &abs_acc)
+                                              int start, int n, int nk, float3 orig, float h, float &loss_acc,
+                                              float &abs_acc)
 {
     constexpr int NREC = nrec_of(DEG);
     constexpr int LG = KQ == 1 ? 0 : (KQ == 2 ? 1 : 2);
@@ -223,7 +269,8 @@ __device__ __forceinline__ void forward_phase(const VariantArgs &a, const float4
         const float4 q4 = valid ? qt[qi] : make_float4(orig.x, orig.y, orig.z, 0.f);
         const float x = q4.x - orig.x, y = q4.y - orig.y, z = q4.z - orig.z;
         float e, m, M2 = 0.f;
-        fwd_sums<DEG, KQ>(rec, nk, part, x, y, z, 0.f, e, m);
+        if (LATTICE) fwd_sums_lattice<DEG, KQ>(rec, part, h, x, y, z, e, m);
+        else fwd_sums<DEG, KQ>(rec, nk, part, x, y, z, 0.f, e, m);
         const bool tiny = !(e >= 0x1p-60f);   // the same in every lane of the group
         if (__any_sync(kFull, tiny)) {        // every key far in units of its scale: shift by the largest exponent
             float mx = -INFINITY;
@@ -318,9 +365,19 @@ __global__ void __launch_bounds__(kThreads, DEG <= 1 ? 7 : (DEG == 2 ? 5 : 4)) v
         __syncthreads();
 
         // ---- 2. forward, 1, 2 or 4 lanes per query (sparse items use more)
-        if (n > 64) forward_phase<MODE, DEG, 1>(a, s_rec, s_qt, s_og, start, n, nk, orig, loss_acc, abs_acc);
-        else if (n > 32) forward_phase<MODE, DEG, 2>(a, s_rec, s_qt, s_og, start, n, nk, orig, loss_acc, abs_acc);
-        else forward_phase<MODE, DEG, 4>(a, s_rec, s_qt, s_og, start, n, nk, orig, loss_acc, abs_acc);
+        //         (grid keys of a full window, degree <= 1: lattice distances;
+        //         for higher degrees the per-axis arrays cost more registers
+        //         than the distances save)
+        const float h = 2.f * invR;
+        if (SETS == 1 && DEG <= 1 && nc == kCentres) {
+            if (n > 64) forward_phase<MODE, DEG, 1, true>(a, s_rec, s_qt, s_og, start, n, nk, orig, h, loss_acc, abs_acc);
+            else if (n > 32) forward_phase<MODE, DEG, 2, true>(a, s_rec, s_qt, s_og, start, n, nk, orig, h, loss_acc, abs_acc);
+            else forward_phase<MODE, DEG, 4, true>(a, s_rec, s_qt, s_og, start, n, nk, orig, h, loss_acc, abs_acc);
+        } else {
+            if (n > 64) forward_phase<MODE, DEG, 1, false>(a, s_rec, s_qt, s_og, start, n, nk, orig, h, loss_acc, abs_acc);
+            else if (n > 32) forward_phase<MODE, DEG, 2, false>(a, s_rec, s_qt, s_og, start, n, nk, orig, h, loss_acc, abs_acc);
+            else forward_phase<MODE, DEG, 4, false>(a, s_rec, s_qt, s_og, start, n, nk, orig, h, loss_acc, abs_acc);
+        }
         if (MODE == VAR_FORWARD) continue;
 
         // ---- 3. backward, one thread per key (two threads per key, each
