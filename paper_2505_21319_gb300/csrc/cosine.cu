@@ -82,6 +82,35 @@ __device__ __forceinline__ void band_sums(const float4 *rec, int nc, float x, fl
     }
 }
 
+// band_sums over a full window (64 centres): the grid keys sit on the lattice
+// (i - c) h, so d2 = (x2 + y2) + z2 from per-axis terms formed once per query
+// (ry, y2, rz, z2 for the four offsets of each axis); same key order.
+__device__ __forceinline__ void band_sums_lattice(const float4 *rec, float h, float x, const float (&ry)[4],
+                                                  const float (&y2)[4], const float (&rz)[4], const float (&z2)[4],
+                                                  float &e, float &m)
+{
+    e = 0.f;
+    m = 0.f;
+#pragma unroll 1
+    for (int ox = 0; ox < 4; ++ox) {
+        const float rx = x - (float)(ox - 1) * h;
+        const float x2 = rx * rx;
+#pragma unroll
+        for (int oy = 0; oy < 4; ++oy) {
+            const float xy = x2 + y2[oy];
+#pragma unroll
+            for (int oz = 0; oz < 4; ++oz) {
+                const int c = 16 * ox + 4 * oy + oz;
+                const float nbl = rec[2 * c].w;
+                const float4 V = rec[2 * c + 1];
+                const float l = ex2_approx(nbl * (xy + z2[oz]));
+                e += l;
+                m = fmaf(l, fmaf(V.y, rx, fmaf(V.z, ry[oy], fmaf(V.w, rz[oz], V.x))), m);
+            }
+        }
+    }
+}
+
 size_t cos_smem_bytes(int B, int mode)
 {
     return (size_t)(B * kCentres * 2 + kChunk + (mode == VAR_FORWARD ? 0 : kChunk * B)) * sizeof(float4);
@@ -131,14 +160,26 @@ __global__ void __launch_bounds__(kThreads) cosine_kernel(CosineArgs a)
         __syncthreads();
 
         // ---- 2. forward: B softmaxes and the cosine-weighted sum per query
+        //         (full windows: lattice distances, per-axis terms shared by the bands)
+        const bool full = nc == kCentres;
+        const float h = 2.f * invR;
         for (int qi = t; qi < n; qi += kThreads) {
             const float4 q4 = s_qt[qi];
             const float x = q4.x - orig.x, y = q4.y - orig.y, z = q4.z - orig.z;
+            float ry[4], y2[4], rz[4], z2[4];
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                ry[o] = y - (float)(o - 1) * h;
+                y2[o] = ry[o] * ry[o];
+                rz[o] = z - (float)(o - 1) * h;
+                z2[o] = rz[o] * rz[o];
+            }
             float S = 0.f;
             for (int b = 0; b < B; ++b) {
                 const float4 *rec = s_rec + b * kCentres * 2;
                 float e, m, M2 = 0.f;
-                band_sums(rec, nc, x, y, z, 0.f, e, m);
+                if (full) band_sums_lattice(rec, h, x, ry, y2, rz, z2, e, m);
+                else band_sums(rec, nc, x, y, z, 0.f, e, m);
                 if (!(e >= 0x1p-60f)) {   // every key far in units of its scale: shift by the largest exponent
                     float mx = -INFINITY;
                     for (int c = 0; c < nc; ++c) {
