@@ -190,9 +190,9 @@ void launch_end(int kid, cudaStream_t s);
 
 // Launchers (defined in sort.cu, fused.cu, adam.cu).  They return the CUDA
 // error of the launch.
-// narrow: bin and scatter with one block per SM (the pipelined fit runs them
-// beside the persistent fit kernel)
-cudaError_t launch_sort(const SortArgs &a, cudaStream_t s, bool narrow = false);
+// narrow_blocks > 0: bin and scatter with that many 128-thread blocks per SM
+// (the pipelined fits run them beside a persistent fit kernel); 0: wide grids
+cudaError_t launch_sort(const SortArgs &a, cudaStream_t s, int narrow_blocks = 0);
 cudaError_t launch_pack_keys(const PackArgs &a, cudaStream_t s);
 cudaError_t launch_forward(const FusedArgs &a, bool with_dq, int grid, cudaStream_t s);
 cudaError_t launch_fused_backward(const FusedArgs &a, bool with_gq, bool second_order, int grid, cudaStream_t s);

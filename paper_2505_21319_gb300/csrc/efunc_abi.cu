@@ -187,7 +187,7 @@ SortBuf sort_buf(const Views &v, int b)
 }
 
 cudaError_t sort_into_buf(const SortBuf &b, const Layout &L, int R, const float *q, int64_t J, int q_stride,
-                          cudaStream_t s)
+                          cudaStream_t s, int narrow_blocks)
 {
     cudaError_t e = cudaMemsetAsync(b.ctrl, 0, sizeof(Ctrl), s);
     if (e != cudaSuccess) return e;
@@ -207,7 +207,7 @@ cudaError_t sort_into_buf(const SortBuf &b, const Layout &L, int R, const float 
     a.perm = nullptr;
     a.items = b.items;
     a.ctrl = b.ctrl;
-    return launch_sort(a, s, true);
+    return launch_sort(a, s, narrow_blocks);
 }
 
 // Clears the control block and histogram, then sorts q into the workspace
@@ -471,7 +471,9 @@ efunc_status fit_pipelined(const efunc_grid *grid, const efunc_adam *adam, int32
             src = reinterpret_cast<const float *>(vw.stage(b, J));
         }
         if (cudaStreamWaitEvent(ss, pipe->consumed[b], 0) != cudaSuccess) return false;
-        if (sort_into_buf(sort_buf(vw, b), vw.L, R, src, J, 4, ss) != cudaSuccess) return false;
+        // one sort block per SM: the default kernel's steps are long enough to
+        // hide it, and more sort traffic slows the kernel beside it
+        if (sort_into_buf(sort_buf(vw, b), vw.L, R, src, J, 4, ss, 1) != cudaSuccess) return false;
         if (q_host && cudaEventRecord(pipe->freed[b], ss) != cudaSuccess) return false;
         return cudaEventRecord(pipe->sorted[b], ss) == cudaSuccess;
     };
@@ -529,7 +531,9 @@ efunc_status pipelined_device_fit(const Views &vw, int R, const float *qo, int64
     auto issue_sort = [&](int32_t k) -> bool {
         const int b = k & 1;
         if (cudaStreamWaitEvent(ss, pipe->consumed[b], 0) != cudaSuccess) return false;
-        if (sort_into_buf(sort_buf(vw, b), vw.L, R, batch(k), J, 4, ss) != cudaSuccess) return false;
+        // two sort blocks per SM (the room the persistent grids leave): the
+        // variant and cosine kernels are shorter than the default one
+        if (sort_into_buf(sort_buf(vw, b), vw.L, R, batch(k), J, 4, ss, 2) != cudaSuccess) return false;
         return cudaEventRecord(pipe->sorted[b], ss) == cudaSuccess;
     };
     if (!issue_sort(0)) return EFUNC_ERR_CUDA;

@@ -259,12 +259,13 @@ int stream_grid(int64_t work, int threads, int blocks_per_sm)
 
 }  // namespace
 
-cudaError_t launch_sort(const SortArgs &a, cudaStream_t s, bool narrow)
+cudaError_t launch_sort(const SortArgs &a, cudaStream_t s, int narrow_blocks)
 {
     const bool vec4 = a.q_stride == 4 && (reinterpret_cast<uintptr_t>(a.q) & 15u) == 0;
-    // narrow: one block per SM, to run beside the persistent fit kernel
+    // narrow: narrow_blocks small blocks per SM, to run beside a persistent fit kernel
+    const bool narrow = narrow_blocks > 0;
     const int threads = narrow ? kSortThreads : kWideThreads;
-    const int g = stream_grid(a.J, threads, narrow ? 1 : 8);
+    const int g = stream_grid(a.J, threads, narrow ? narrow_blocks : 8);
     const int64_t nblocks = (a.nbins + kScanSeg - 1) / kScanSeg;
 
     launch_begin(K_BIN, s);
