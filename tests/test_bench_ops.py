@@ -1,0 +1,39 @@
+"""Consistency of bench.py's algorithmic operation counts (host logic, CPU):
+the variant formula reproduces the default model's per-centre counts, and the
+window sizes follow the FP32 window rule."""
+import numpy as np
+
+import bench
+
+
+def test_variant_counts_reproduce_the_default_model():
+    # degree 1, both key sets, learnable scales is the 13-float model: forward
+    # 12 per key, backward 18 (grid key) and 21 (offset key)
+    grid = bench.variant_ops_per_key(1, 1, False)
+    offset = bench.variant_ops_per_key(1, 1, True)
+    assert grid == 12 + 18 and offset == 12 + 21
+    assert grid + offset == bench.OPS_PER_CENTRE
+    # the lattice form saves 5 operations per grid key in the forward
+    assert bench.OPS_PER_CENTRE - bench.OPS_PER_CENTRE_FULL == 12 - 7
+
+
+def test_variant_counts_grow_with_degree_and_features():
+    for deg in range(3):
+        for learn in (0, 1):
+            for off in (False, True):
+                assert bench.variant_ops_per_key(deg + 1, learn, off) > bench.variant_ops_per_key(deg, learn, off)
+    assert bench.variant_ops_per_key(1, 0, False) < bench.variant_ops_per_key(1, 1, False)
+    assert bench.variant_ops_per_key(2, 1, True) > bench.variant_ops_per_key(2, 1, False)
+
+
+def test_window_sizes():
+    R = 8
+    h = 2.0 / R
+    q = np.array([[0.0, 0.0, 0.0, 0.0],                       # interior: full 4x4x4 window
+                  [-1.0 + 0.1 * h, 0.0, 0.0, 0.0],            # base c = -1 along x: centres 0, 1
+                  [-1.5, -1.5, -1.5, 0.0],                    # far outside: 2 per axis
+                  [0.999, 0.999, 0.999, 0.0]], np.float32)    # last cell: 2 per axis
+    nc = bench.centres_per_query(q, R)
+    assert list(nc) == [64, 32, 8, 8]
+    ops = bench.variant_algorithmic_ops(q, R, 1, 1, 1)
+    assert ops == nc.sum() * bench.variant_ops_per_key(1, 1, False)

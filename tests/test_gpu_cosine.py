@@ -131,3 +131,15 @@ def test_cosine_full_size_sampled():
     ref = oracle.cosine_forward(p, qo[idx, :3], R, B, log_beta0=lb)
     lim = S_tolerance(p, qo[idx, :3].astype(np.float64), R, B, lb)
     assert np.all(np.abs(S[idx] - ref) <= lim)
+
+
+def test_cosine_forward_is_deterministic_and_order_independent():
+    R, B, J = 8, 3, 30000
+    p = to_dev(band_params(R, B, seed=7)).reshape(-1)
+    qo = mixed_queries(R, J, seed=7)
+    a = api.efunc_cosine_forward(B, p, to_dev(qo)).cpu().numpy()
+    b = api.efunc_cosine_forward(B, p, to_dev(qo)).cpu().numpy()
+    perm = synth.rng(3).permutation(J)
+    c = api.efunc_cosine_forward(B, p, to_dev(qo[perm])).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(a[perm], c)

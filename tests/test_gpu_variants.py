@@ -219,3 +219,20 @@ def test_variant_empty_and_single_query():
     O = api.efunc_variant_forward("G-8", pd, to_dev(q), log_beta0=lb32(R)).cpu().numpy()
     ref, _, kap, fab = oracle.variant_forward(p, q[:, :3], R, *var, log_beta0=lb32(R), want_diag=True)
     assert np.all(np.abs(O - ref) <= variant_tol(ref, kap, fab, 3))
+
+
+@pytest.mark.parametrize("name", ["G-6", "G-8", "Full-3"])
+def test_variant_forward_is_deterministic_and_order_independent(name):
+    """Four summation classes combined in a fixed tree: a query's O does not
+    depend on how many lanes share it or on the batch order (G-6 takes the
+    lattice path in full windows, G-8 and Full-3 the generic one)."""
+    var = api.VARIANTS[name]
+    R, J = 8, 30000
+    p = to_dev(make_params(var, R, seed=4)).reshape(-1)
+    qo = mixed_queries(R, J, seed=6)
+    a = api.efunc_variant_forward(name, p, to_dev(qo)).cpu().numpy()
+    b = api.efunc_variant_forward(name, p, to_dev(qo)).cpu().numpy()
+    perm = synth.rng(2).permutation(J)
+    c = api.efunc_variant_forward(name, p, to_dev(qo[perm])).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(a[perm], c)
