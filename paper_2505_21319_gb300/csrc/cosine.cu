@@ -287,12 +287,18 @@ template <int MODE>
 cudaError_t launch_mode(const CosineArgs &a, int kid, cudaStream_t s)
 {
     const size_t smem = cos_smem_bytes(a.B, MODE);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(cosine_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)cos_smem_bytes(kMaxBands, VAR_FIT));
+    // the dynamic shared-memory limit is a per-device attribute of the kernel
+    constexpr int kMaxDevices = 64;
+    static bool attr[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
+        e = cudaFuncSetAttribute(cosine_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cos_smem_bytes(kMaxBands, VAR_FIT));
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[dev] = true;
     }
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cosine_kernel<MODE>, kThreads, smem);
