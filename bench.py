@@ -408,6 +408,22 @@ def main():
         iach = ops_per_launch / (iavg * 1e-3) / 1e12
         iso = {"avg_launch_ms": iavg, "achieved": iach, "frac": iach / peak, "steps": args.isolated_steps,
                "note": "fused kernel of the same fit with the batch sorted in line: nothing runs beside it"}
+        # the memory-bound kernels of the same in-line run against the measured copy bandwidth:
+        # algorithmic bytes per launch (bin: query row read + rank written; scatter: row and
+        # rank read, row written; adam: p, g, m, v read and p, m, v, g written)
+        try:
+            hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+            hbm_from = "measured copy bandwidth"
+        except (OSError, ValueError, KeyError):
+            hbm, hbm_from = 6800.0, "fallback"
+        n_par = R ** 3 * 13
+        for kname, nbytes in (("bin", J * 20), ("scatter", J * 36), ("adam", n_par * 32)):
+            km, kc = api.profile_read(kname)
+            kavg = km / max(1, kc)
+            gbs = nbytes / (kavg * 1e-3) / 1e9
+            iso.setdefault("memory_bound", {})[kname] = {
+                "avg_launch_ms": kavg, "bytes": nbytes, "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                "frac": gbs / hbm, "peak_from": hbm_from}
 
     # ---- the same fit with the Eikonal term (NEXT-1: second-order fused
     # backward through dO/dq), timed the same way on a shorter run
