@@ -241,9 +241,18 @@ def cpu_baseline(qo: np.ndarray, R: int, lb: float, seconds: float = 12.0):
         grad = oracle_step(pool, params, qo[:n], R, lb, cores)
         oracle.adam(params, grad, m, v, 1, lr=LR)
         dt = time.perf_counter() - t0
+    # the same step single-threaded, on a sample of about two seconds
+    n1 = int(min(len(qo), max(256, (n / dt) / cores * 2.0)))
+    t0 = time.perf_counter()
+    O, _ = oracle.forward(params, qo[:n1], R, 2, lb)
+    gO, _, _ = oracle.loss_grad(O, qo[:n1, 3].astype(np.float64), oracle.L1)
+    grad1 = oracle.backward(params, qo[:n1], gO, R, 2, lb)
+    oracle.adam(params, grad1, m, v, 2, lr=LR)
+    dt1 = time.perf_counter() - t0
     return {"value": n / dt, "unit": "query-pts/s", "cores": cores, "kind": "oracle",
             "sample": f"one fit step (forward, L1 gradient, backward, Adam) on the first {n} queries of the "
-                      f"2^22 batch at 32^3, FP64, {cores} spawn processes"}
+                      f"2^22 batch at 32^3, FP64, {cores} spawn processes",
+            "single_thread": {"value": n1 / dt1, "unit": "query-pts/s", "sample": f"the first {n1} queries"}}
 
 
 # ------------------------------------------------------------------ main
