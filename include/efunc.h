@@ -30,8 +30,10 @@
  *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
  *     default stream) unless stated otherwise.
  *   - Work memory comes from the caller: `workspace` [device] of at least
- *     efunc_workspace_bytes(grid, J) bytes, 256-byte aligned.  Concurrent calls
- *     must not share a workspace.  The library allocates no device memory.
+ *     efunc_workspace_bytes(grid, J) bytes (or the variant / cosine / fit sizes
+ *     below), 256-byte aligned.  Concurrent calls must not share a workspace.
+ *     The library allocates no device memory; it creates, once per device,
+ *     the copy and sort streams and events of efunc_fit.
  *   - Arguments are validated on the host before anything is launched; an
  *     invalid argument returns EFUNC_ERR_ARG (or _WORKSPACE / _NONFINITE /
  *     _UNSUPPORTED) and enqueues nothing.  A failing CUDA call returns
@@ -122,8 +124,10 @@ float efunc_default_log_beta0(int32_t R);
 /* Static description of a status code.  Never NULL. */
 const char *efunc_status_str(efunc_status s);
 
-/* Bytes of workspace every call below needs for J queries on this grid
- * (the maximum over all calls).  0 if the grid is invalid. */
+/* Bytes of workspace that suffice for every call of the default model below
+ * for J queries on this grid (efunc_fit can use more, see
+ * efunc_fit_workspace_bytes; the variant and cosine calls have their own
+ * sizes).  0 if the grid is invalid. */
 size_t efunc_workspace_bytes(const efunc_grid *grid, int64_t J);
 
 /* Bytes of workspace with which efunc_fit pipelines its steps: the sort of
