@@ -138,6 +138,13 @@ def test_variant_helpers_and_validation(lib):
     ad = B.Adam(1e-3, 0.9, 0.999, 1e-8, 0.0, 0)
     assert lib.efunc_variant_fit(ctypes.byref(g), ctypes.byref(v), ctypes.byref(ad), 0, 16, 32, 48, 64, 10, 0, 1, 0,
                                  None, 1 << 30, 1 << 40, None) == 1                          # no batches
+    # the variant fit needs its whole workspace (second sort buffer) and device batches
+    v1 = B.Variant(1, 1, 1)
+    wsv = lib.efunc_variant_workspace_bytes(ctypes.byref(g), ctypes.byref(v1), 16)
+    assert lib.efunc_variant_fit(ctypes.byref(g), ctypes.byref(v1), ctypes.byref(ad), 0, 16, 32, 48, 64, 16, 1, 1, 0,
+                                 None, 1 << 30, wsv - 256, None) == 3
+    assert lib.efunc_variant_fit(ctypes.byref(g), ctypes.byref(v1), ctypes.byref(ad), 0, 16, 32, 48, 64, 16, 1, 1, 0,
+                                 None, 1 << 30, wsv, None) == 1                              # not device memory
     assert lib.efunc_launch_count() == 0
 
 
@@ -156,6 +163,9 @@ def test_cosine_helpers_and_validation(lib):
     ad = B.Adam(1e-3, 0.9, 0.999, 1e-8, 0.0, 0)
     assert lib.efunc_cosine_fit(ctypes.byref(g), 4, ctypes.byref(ad), 3, 16, 32, 48, 64, 10, 1, 1, 0, None, 1 << 30,
                                 1 << 40, None) == 1                                          # bad loss kind
+    wsc = lib.efunc_cosine_workspace_bytes(ctypes.byref(g), 4, 16)
+    assert lib.efunc_cosine_fit(ctypes.byref(g), 4, ctypes.byref(ad), 0, 16, 32, 48, 64, 16, 1, 1, 0, None, 1 << 30,
+                                wsc - 256, None) == 3                                        # workspace too small
     assert lib.efunc_launch_count() == 0
 
 
