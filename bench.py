@@ -55,6 +55,18 @@ OPS_PER_CENTRE = 12 + 12 + 18 + 21
 OPS_PER_CENTRE_FULL = 7 + 12 + 18 + 21
 OPS_PER_QUERY_FULL_SETUP = 24
 EX2_PER_CENTRE = 4
+# The fit step with the Eikonal term (backward through dO/dq), per (query,
+# centre), adds to the counts above: a second forward pass forming dO/dq
+# and V = sum w beta (q - key), 24 per key (difference 3, squared distance 3,
+# exponent 1, value 3, w beta 2, 2 beta w (O - f) 3, dO/dq 6, V 3); and in the
+# backward the derivative of u . dO/dq, 23 per grid key (u.r 3, u.t 1, u.d 3,
+# h 1, w (u.t - T) 2, (h - H) - dlt T 2, 7 sums, log-scale term 4) and 8 more
+# for an offset key (its 6 position sums and 2 products).  Per-query terms
+# (residual, u, H, T) are left out.
+EIK_GV_PER_KEY = 24
+EIK_BWD_GRID_EXTRA = 23
+EIK_BWD_OFFSET_EXTRA = 23 + 8
+EIK_EXTRA_PER_CENTRE = 2 * EIK_GV_PER_KEY + EIK_BWD_GRID_EXTRA + EIK_BWD_OFFSET_EXTRA
 FP32_LANES_PER_SM = 128
 # FP32-pipe operations of one (centre, point) pair of the mean-shift
 # initialisation: 3 differences, 3 for the squared norm, 1 scale, 1 compare,
@@ -111,6 +123,13 @@ def algorithmic_ops(q: np.ndarray, R: int) -> float:
     full = nc == 64
     return float(full.sum()) * (64 * OPS_PER_CENTRE_FULL + OPS_PER_QUERY_FULL_SETUP) + \
         float(nc[~full].sum()) * OPS_PER_CENTRE
+
+
+def eikonal_algorithmic_ops(q: np.ndarray, R: int) -> float:
+    """Exact algorithmic FP32 operations of one fused fit launch with the
+    Eikonal term: the plain fit's count plus the second-order terms of every
+    (query, centre) pair."""
+    return algorithmic_ops(q, R) + float(centres_per_query(q, R).sum()) * EIK_EXTRA_PER_CENTRE
 
 
 def variant_ops_per_key(deg: int, learn: int, offset: bool) -> int:
@@ -452,8 +471,12 @@ def main():
         api.profile(False)
         ems = max_over_ranks(e0.elapsed_time(e1) / args.eikonal_steps, dev)
         fm, fn = api.profile_read("fused_fit")
+        eops = sum(eikonal_algorithmic_ops(pool_np[b * J:(b + 1) * J], R) for b in range(N_BATCHES)) / N_BATCHES
+        eavg = fm / max(1, fn)
+        each = eops / (eavg * 1e-3) / 1e12
         eik = {"value": J * ws / (ems * 1e-3), "unit": "query-pts/s", "ms_per_step": ems,
-               "fused_ms": fm / max(1, fn), "steps": args.eikonal_steps, "eikonal_weight": 0.1}
+               "fused_ms": eavg, "achieved": each, "peak": peak, "unit_roofline": "T FP32 op/s",
+               "frac": each / peak, "ops_per_launch": eops, "steps": args.eikonal_steps, "eikonal_weight": 0.1}
 
     # ---- mean-shift offset initialisation (Sec. 3.3): R^3 centres x 16384
     # surface points, 13 FP32-pipe operations and one ex2 per pair

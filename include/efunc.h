@@ -39,7 +39,9 @@
  *     _UNSUPPORTED) and enqueues nothing.  A failing CUDA call returns
  *     EFUNC_ERR_CUDA.  Nothing aborts the process.
  *   - Queries: q holds J rows of q_stride floats (q_stride 3 or 4), x,y,z
- *     first.  Outputs indexed by query are in the caller's query order.
+ *     first, J in [0, 2^30] (J = 0 enqueues nothing and returns EFUNC_OK;
+ *     the fitting loops need J >= 1).  Outputs indexed by query are in the
+ *     caller's query order.
  *   - Non-finite parameters or queries give non-finite outputs; they are not
  *     checked.
  */
@@ -261,8 +263,10 @@ efunc_status efunc_forward_noalloc(const efunc_grid *grid, const float *params, 
  * into params slots 0..2 (the other slots are left as they are), with the
  * largest exponent subtracted so that centres far from every point still get
  * a defined offset.  The paper uses bw = 100 and N = 16384 surface points.
- *   pts      [device] N x 3 floats
- *   params   [device] R^3*13 floats, slots 0..2 written */
+ *   pts      [device] N x 3 floats, N in [1, 2^30] (N = 0 is EFUNC_ERR_ARG:
+ *            the offset is undefined without points)
+ *   params   [device] R^3*13 floats, slots 0..2 written
+ *   bandwidth > 0 and finite */
 efunc_status efunc_mean_shift_init(const efunc_grid *grid, const float *pts, int64_t N, float bandwidth,
                                    float *params, efunc_stream_t stream);
 

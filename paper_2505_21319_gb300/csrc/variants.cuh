@@ -311,8 +311,13 @@ __device__ __forceinline__ void forward_phase(const VariantArgs &a, const float4
         if (MODE != VAR_FORWARD) {
             __syncwarp();   // every lane of the group has read its row of qt
             if (valid && part == 0) {
-                qt[qi] = make_float4(x, y, z, lse2);
+                const float4 row = make_float4(x, y, z, lse2);
+                qt[qi] = row;
                 og[qi] = make_float2(O, gO);
+                if (qi == n - 1 && (n & 1)) {   // pad the last pair: the same query without gradient
+                    qt[n] = row;
+                    og[n] = make_float2(O, 0.f);
+                }
             }
         }
     }
@@ -324,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, DEG <= 1 ? 7 : (DEG == 2 ? 5 : 4)) v
     constexpr int NV = nv_of(DEG), NREC = nrec_of(DEG), NS = nsets_of(SETS);
     __shared__ float4 s_rec[kCentres * NS * NREC];   // window key records, key-major
     __shared__ float4 s_qt[kChunk];                   // queries: (x, y, z, target), then (local q, lse2)
-    __shared__ float2 s_og[kChunk];                   // (O, dL/dO) per query
+    __shared__ float4 s_og[kChunk / 2];               // (O, dL/dO) of query pairs 2i, 2i + 1
     __shared__ int s_item;
     __shared__ float s_red[2][kThreads / 32];
 
@@ -369,19 +374,22 @@ __global__ void __launch_bounds__(kThreads, DEG <= 1 ? 7 : (DEG == 2 ? 5 : 4)) v
         //         for higher degrees the per-axis arrays cost more registers
         //         than the distances save)
         const float h = 2.f * invR;
+        float2 *og2 = reinterpret_cast<float2 *>(s_og);
         if (SETS == 1 && DEG <= 1 && nc == kCentres) {
-            if (n > 64) forward_phase<MODE, DEG, 1, true>(a, s_rec, s_qt, s_og, start, n, nk, orig, h, loss_acc, abs_acc);
-            else if (n > 32) forward_phase<MODE, DEG, 2, true>(a, s_rec, s_qt, s_og, start, n, nk, orig, h, loss_acc, abs_acc);
-            else forward_phase<MODE, DEG, 4, true>(a, s_rec, s_qt, s_og, start, n, nk, orig, h, loss_acc, abs_acc);
+            if (n > 64) forward_phase<MODE, DEG, 1, true>(a, s_rec, s_qt, og2, start, n, nk, orig, h, loss_acc, abs_acc);
+            else if (n > 32) forward_phase<MODE, DEG, 2, true>(a, s_rec, s_qt, og2, start, n, nk, orig, h, loss_acc, abs_acc);
+            else forward_phase<MODE, DEG, 4, true>(a, s_rec, s_qt, og2, start, n, nk, orig, h, loss_acc, abs_acc);
         } else {
-            if (n > 64) forward_phase<MODE, DEG, 1, false>(a, s_rec, s_qt, s_og, start, n, nk, orig, h, loss_acc, abs_acc);
-            else if (n > 32) forward_phase<MODE, DEG, 2, false>(a, s_rec, s_qt, s_og, start, n, nk, orig, h, loss_acc, abs_acc);
-            else forward_phase<MODE, DEG, 4, false>(a, s_rec, s_qt, s_og, start, n, nk, orig, h, loss_acc, abs_acc);
+            if (n > 64) forward_phase<MODE, DEG, 1, false>(a, s_rec, s_qt, og2, start, n, nk, orig, h, loss_acc, abs_acc);
+            else if (n > 32) forward_phase<MODE, DEG, 2, false>(a, s_rec, s_qt, og2, start, n, nk, orig, h, loss_acc, abs_acc);
+            else forward_phase<MODE, DEG, 4, false>(a, s_rec, s_qt, og2, start, n, nk, orig, h, loss_acc, abs_acc);
         }
         if (MODE == VAR_FORWARD) continue;
 
         // ---- 3. backward, one thread per key (two threads per key, each
-        //         over half of the queries, when there is one key set)
+        //         over every second pair of queries, when there is one key
+        //         set); a pair's two query rows and its (O, dL/dO) float4 are
+        //         loaded together
         __syncthreads();
         const int kk = NS == 2 ? t : (t & (kCentres - 1));
         const int half = NS == 2 ? 0 : (t >> 6);
@@ -399,19 +407,17 @@ __global__ void __launch_bounds__(kThreads, DEG <= 1 ? 7 : (DEG == 2 ? 5 : 4)) v
 #pragma unroll
             for (int i = 0; i < NV; ++i) acc[i] = 0.f;
             float ab = 0.f, adx = 0.f, ady = 0.f, adz = 0.f, agx = 0.f, agy = 0.f, agz = 0.f;
-#pragma unroll 1
-            for (int j = half; j < n; j += qstep) {
-                const float4 Q = s_qt[j];
-                const float2 og = s_og[j];
+            // one query: Q = (local q, lse2), O and dL/dO
+            auto one = [&](const float4 Q, float O, float gO) {
                 const float rx = Q.x - A.x, ry = Q.y - A.y, rz = Q.z - A.z;
                 const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                const float g = ex2_approx(fmaf(A.w, d2, -Q.w)) * og.y;
+                const float g = ex2_approx(fmaf(A.w, d2, -Q.w)) * gO;
                 float mo[NV];
                 monomials<DEG>(rx, ry, rz, mo);
 #pragma unroll
                 for (int i = 0; i < NV; ++i) acc[i] = fmaf(g, mo[i], acc[i]);
                 if (a.learn || offset) {
-                    const float gd = g * (poly<DEG>(c, mo) - og.x);
+                    const float gd = g * (poly<DEG>(c, mo) - O);
                     ab = fmaf(gd, d2, ab);
                     if (offset) {
                         adx = fmaf(gd, rx, adx);
@@ -426,6 +432,13 @@ __global__ void __launch_bounds__(kThreads, DEG <= 1 ? 7 : (DEG == 2 ? 5 : 4)) v
                         }
                     }
                 }
+            };
+            const int pairs = (n + 1) >> 1;
+#pragma unroll 1
+            for (int jp = half; jp < pairs; jp += qstep) {
+                const float4 Q0 = s_qt[2 * jp], Q1 = s_qt[2 * jp + 1], G = s_og[jp];
+                one(Q0, G.x, G.y);
+                one(Q1, G.z, G.w);
             }
             const int oz = cidx % w.nz, oy = (cidx / w.nz) % w.ny, ox = cidx / (w.ny * w.nz);
             float *gr = a.grad + (((size_t)(w.lox + ox) * R + (w.loy + oy)) * R + (w.loz + oz)) * a.channels;

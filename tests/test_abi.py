@@ -72,6 +72,7 @@ def test_argument_validation_enqueues_nothing(lib):
     assert _fwd(lib, B.Grid(8, 2, float("nan"))) == 4
     assert _fwd(lib, B.Grid(8, 2, float("inf"))) == 4
     assert _fwd(lib, ok, J=-1) == 1
+    assert _fwd(lib, ok, J=(1 << 30) + 1) == 1
     assert _fwd(lib, ok, stride=2) == 1
     assert _fwd(lib, ok, params=None) == 1
     assert _fwd(lib, ok, q=None) == 1
@@ -103,6 +104,7 @@ def test_argument_validation_enqueues_nothing(lib):
     assert lib.efunc_backward_grad(ctypes.byref(ok), 4096, 8192, 16, 3, None, None, 4096, 1 << 30, 1 << 40,
                                    None) == 1                                               # neither gO nor gG
     assert lib.efunc_mean_shift_init(ctypes.byref(ok), 4096, 0, 100.0, 8192, None) == 1       # no points
+    assert lib.efunc_mean_shift_init(ctypes.byref(ok), 4096, (1 << 30) + 1, 100.0, 8192, None) == 1
     assert lib.efunc_mean_shift_init(ctypes.byref(ok), 4096, 10, 0.0, 8192, None) == 1        # bandwidth 0
     assert lib.efunc_mean_shift_init(ctypes.byref(ok), 4096, 10, -1.0, 8192, None) == 1
     assert lib.efunc_mean_shift_init(ctypes.byref(ok), 4096, 10, float("inf"), 8192, None) == 4

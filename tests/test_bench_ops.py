@@ -37,3 +37,16 @@ def test_window_sizes():
     assert list(nc) == [64, 32, 8, 8]
     ops = bench.variant_algorithmic_ops(q, R, 1, 1, 1)
     assert ops == nc.sum() * bench.variant_ops_per_key(1, 1, False)
+
+
+def test_eikonal_counts_add_the_second_order_terms():
+    # per centre: the plain 63 (12 + 12 forward, 18 + 21 backward), the
+    # dO/dq-and-V pass over both keys (2 x 24), the second-order backward of
+    # the grid key (23) and of the offset key (31)
+    assert bench.EIK_EXTRA_PER_CENTRE == 2 * 24 + 23 + 31
+    q = np.array([[0.0, 0.0, 0.0, 0.0], [-1.5, -1.5, -1.5, 0.0]], np.float32)
+    R = 8
+    nc = bench.centres_per_query(q, R)
+    plain = bench.algorithmic_ops(q, R)
+    assert plain == 64 * bench.OPS_PER_CENTRE_FULL + bench.OPS_PER_QUERY_FULL_SETUP + 8 * bench.OPS_PER_CENTRE
+    assert bench.eikonal_algorithmic_ops(q, R) == plain + nc.sum() * bench.EIK_EXTRA_PER_CENTRE

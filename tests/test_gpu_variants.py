@@ -53,13 +53,26 @@ def groups(sets, deg, learn):
     return out
 
 
-def assert_variant_grad_close(gpu, ref, var, what, rtol=1e-4):
+def assert_variant_grad_close(gpu, ref, var, what, rtol=1e-4, floors=None):
+    """floors: group name -> absolute bound added to the relative one (for a
+    group whose exact gradient vanishes and whose kernel value is rounding)."""
     ch = ref.shape[1]
     gpu = np.asarray(gpu, dtype=np.float64).reshape(-1, ch)
     for name, cols in groups(*var).items():
         scale = np.abs(ref[:, cols]).max()
         err = np.abs(gpu[:, cols] - ref[:, cols]).max()
-        assert err <= rtol * scale + 1e-30, f"{what} {name}: max err {err:.3e} vs scale {scale:.3e}"
+        floor = (floors or {}).get(name, 0.0)
+        assert err <= rtol * scale + floor + 1e-30, f"{what} {name}: max err {err:.3e} vs scale {scale:.3e}"
+
+
+def lone_key_scale_bound(gO, q, beta, f, fabs, nv):
+    """Bound on the log-scale gradient when every query sees one key (R = 1,
+    one key set): the softmax is 1, O = f and the exact dO/db is 0; the
+    kernel's value is beta |q - key|^2 (f - O) per query, with f - O the
+    rounding of f (evaluated in FP32, (nv + 3) u fabs on each of the forward
+    and backward evaluations) and of O = (l f) / l (2u |f|), weight 1 + O(u)."""
+    d2 = np.sum(np.asarray(q, np.float64) ** 2, axis=1)   # the one centre sits at the origin
+    return 1.01 * np.sum(np.abs(gO) * beta * d2 * (2 * (nv + 3) * U32 * fabs + 4 * U32 * np.abs(f)))
 
 
 def variant_tol(ref, kappa, fabs, deg):
@@ -236,3 +249,28 @@ def test_variant_forward_is_deterministic_and_order_independent(name):
     c = api.efunc_variant_forward(name, p, to_dev(qo[perm])).cpu().numpy()
     np.testing.assert_array_equal(a, b)
     np.testing.assert_array_equal(a[perm], c)
+
+
+@pytest.mark.parametrize("name", ["G-6", "G-8", "Full-3"])
+@pytest.mark.parametrize("R", [1, 2, 3])
+def test_variant_tiny_grids(name, R):
+    """Grids of 1, 2 or 3 centres per axis (every window clipped): forward
+    and backward against the oracle."""
+    var = api.VARIANTS[name]
+    J = 3001
+    p = make_params(var, R, seed=20 + R)
+    qo = mixed_queries(R, J, seed=30 + R)
+    lb = lb32(R)
+    pd = to_dev(p).reshape(-1)
+    O = api.efunc_variant_forward(name, pd, to_dev(qo), log_beta0=lb).cpu().numpy()
+    ref, _, kap, fab = oracle.variant_forward(p, qo[:, :3], R, *var, log_beta0=lb, want_diag=True)
+    bad = np.flatnonzero(~(np.abs(O - ref) <= variant_tol(ref, kap, fab, var[1])))
+    assert bad.size == 0, f"{name} R={R}: {bad.size} of {J}; idx {bad[:5]} gpu {O[bad[:5]]} ref {ref[bad[:5]]}"
+    gO = (synth.rng(R).standard_normal(J) / J).astype(np.float32)
+    grad = api.efunc_variant_backward(name, pd, to_dev(qo), to_dev(gO), log_beta0=lb)
+    g_ref = oracle.variant_backward(p, qo[:, :3], gO, R, *var, log_beta0=lb)
+    floors = None
+    if R == 1 and var[0] == 1:   # one key per query: dO/db vanishes
+        beta = np.exp(lb + np.float64(p[0, 0]))
+        floors = {"b grid": lone_key_scale_bound(gO, qo[:, :3], beta, ref, fab, NV[var[1]])}
+    assert_variant_grad_close(grad.cpu().numpy(), g_ref, var, f"{name} R={R}", floors=floors)
