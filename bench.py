@@ -339,6 +339,7 @@ def main():
     ap.add_argument("--variant-steps", type=int, default=50)
     ap.add_argument("--cosine-steps", type=int, default=50)
     ap.add_argument("--isolated-steps", type=int, default=50)
+    ap.add_argument("--graph-steps", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -570,6 +571,46 @@ def main():
                                  "steps": args.cosine_steps}
             del cp, cm, cv, cws
 
+    # ---- the fit replayed from a CUDA graph (efunc_fit_graph): the same
+    # 32^3 x 2^22 workload, and the small 16^3 x 65,536-query configuration
+    # (1 MiB batches, L2-resident) whose steps are shorter than the host's
+    # time to launch them one by one; the stream-issued fit beside it
+    graph_fit = None
+    if args.graph_steps > 0:
+        def timed_fit(p_, m_, v_, pool_, Jg, steps, step0, graph, wsp):
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if ws > 1:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            g0.record(stream)
+            api.efunc_fit(p_, m_, v_, pool_, steps=steps, J=Jg, n_batches=N_BATCHES, step0=step0, lr=LR, ws=wsp,
+                          graph=graph)
+            g1.record(stream)
+            torch.cuda.synchronize(dev)
+            return max_over_ranks(g0.elapsed_time(g1) / steps, dev)
+
+        api.efunc_fit(params, m, v, pool, steps=3, J=J, n_batches=N_BATCHES, step0=7 * 10 ** 6, lr=LR, ws=ws_buf,
+                      graph=True)
+        gms = timed_fit(params, m, v, pool, J, args.graph_steps, 8 * 10 ** 6, True, ws_buf)
+        Rs, Js = 16, 65536
+        small = torch.from_numpy(make_pool(Rs, Js, N_BATCHES, rank)).to(dev)
+        sp = torch.from_numpy(synth.init_params(Rs, seed=rank)).to(dev)
+        sm_, sv_ = torch.zeros_like(sp), torch.zeros_like(sp)
+        sws = api.Workspace(dev)
+        small_ms = {}
+        for graph in (False, True):
+            api.efunc_fit(sp, sm_, sv_, small, steps=6, J=Js, n_batches=N_BATCHES, lr=LR, ws=sws, graph=graph)
+            small_ms[graph] = timed_fit(sp, sm_, sv_, small, Js, 4 * args.graph_steps, 100, graph, sws)
+        graph_fit = {
+            "32^3 x 2^22": {"value": J * ws / (gms * 1e-3), "unit": "query-pts/s", "ms_per_step": gms,
+                            "stream_ms_per_step": ms, "steps": args.graph_steps},
+            "16^3 x 65536": {"value": Js * ws / (small_ms[True] * 1e-3), "unit": "query-pts/s",
+                             "ms_per_step": small_ms[True], "stream_value": Js * ws / (small_ms[False] * 1e-3),
+                             "stream_ms_per_step": small_ms[False], "steps": 4 * args.graph_steps,
+                             "l2": "1 MiB batches: L2-resident"},
+            "note": "CUDA events around the whole call: graph capture and instantiation included"}
+        del small, sp, sm_, sv_, sws
+
     # ---- end to end through the C ABI with host buffers: the batch pool in
     # pinned host memory, every step copies its 64 MiB batch to the device
     # (overlapped with the previous step's compute by the library) and copies
@@ -620,6 +661,7 @@ def main():
             "mean_shift_init": ms_init,
             "variants": variants,
             "cosine_series": cosine,
+            "graph_fit": graph_fit,
             "cpu_baseline": cpu_line,
             "clocks": clocks,
             "gpu_launches": launches,

@@ -234,6 +234,31 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
                        int32_t steps, int64_t step0, float *stats, void *workspace, size_t workspace_bytes,
                        efunc_stream_t stream);
 
+/* efunc_fit replayed from a CUDA graph (Sec. 3.4 as efunc_fit; same
+ * arguments and results).  The schedule of efunc_fit with the second sort
+ * buffer repeats every P = lcm(2, n_batches) steps, apart from Adam's step
+ * number; here that number and the bias corrections 1 - beta^t live in
+ * device memory (in the workspace) and advance on the GPU, so the call
+ * captures one period of P steps (sort of the next batch, key pack, fused
+ * kernel, Adam) into a graph, launches it (steps - 1) / P times and issues
+ * the remaining steps one by one.  It removes the per-step host launch cost,
+ * which exceeds the GPU time for small batches (tens of thousands of
+ * queries); for large batches it matches efunc_fit.
+ *   qo, stats  [device] only (stats may be NULL; a host pointer returns
+ *              EFUNC_ERR_ARG); n_batches in [1, 64]
+ *   workspace  at least efunc_fit_workspace_bytes(grid, J)
+ *   - The graph is built and destroyed inside the call (its instantiation
+ *     costs about a few steps' host time).  The call itself must not be made
+ *     while `stream` is being captured (EFUNC_ERR_ARG).
+ *   - efunc_launch_count counts every kernel the replays run; the event
+ *     profiler (efunc_profile_*) times only the steps issued one by one.
+ *   - Bias corrections come from running products beta^t in FP64 instead
+ *     of pow: they agree with efunc_fit's to FP64 rounding. */
+efunc_status efunc_fit_graph(const efunc_grid *grid, const efunc_adam *adam, int32_t loss, float eikonal_weight,
+                             float *params, float *m, float *v, const float *qo, int64_t J, int32_t n_batches,
+                             int32_t steps, int64_t step0, float *stats, void *workspace, size_t workspace_bytes,
+                             efunc_stream_t stream);
+
 /* Forward without any device allocation by the caller.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory themselves, for example code running inside a host
@@ -365,6 +390,15 @@ void efunc_profile_reset(void);
 
 /* Kernels launched by this library since it was loaded. */
 int64_t efunc_launch_count(void);
+
+/* The cudaError_t of the CUDA call behind the calling thread's most recent
+ * EFUNC_ERR_CUDA (0 before any).  The library clears the runtime's pending
+ * error when it reports one, so a failure never resurfaces in a later call. */
+int32_t efunc_last_cuda_error(void);
+
+/* Name of a cudaError_t value ("cudaErrorInvalidValue", ...); a static
+ * string owned by the CUDA runtime. */
+const char *efunc_cuda_error_name(int32_t code);
 
 #ifdef __cplusplus
 }

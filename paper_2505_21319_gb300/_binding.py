@@ -56,6 +56,11 @@ SIGNATURES = {
     "efunc_fit": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Adam), c_int32, c_float, c_void_p, c_void_p,
                             c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int64, c_void_p, c_void_p, c_size_t,
                             c_void_p]),
+    "efunc_last_cuda_error": (c_int32, []),
+    "efunc_cuda_error_name": (ctypes.c_char_p, [c_int32]),
+    "efunc_fit_graph": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Adam), c_int32, c_float, c_void_p, c_void_p,
+                                  c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int64, c_void_p, c_void_p,
+                                  c_size_t, c_void_p]),
     "efunc_forward_noalloc": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_void_p, c_int64, c_int32, c_void_p,
                                         c_void_p, c_void_p, c_void_p]),
     "efunc_mean_shift_init": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_int64, c_float, c_void_p, c_void_p]),
@@ -106,7 +111,12 @@ def load(build: bool = True) -> ctypes.CDLL:
 
 class EfuncError(RuntimeError):
     def __init__(self, fn: str, code: int):
-        msg = load().efunc_status_str(code).decode()
+        lib = load()
+        msg = lib.efunc_status_str(code).decode()
+        self.cuda_error = None
+        if code == 2:   # EFUNC_ERR_CUDA: name the CUDA error behind it
+            self.cuda_error = int(lib.efunc_last_cuda_error())
+            msg += ": " + (lib.efunc_cuda_error_name(self.cuda_error) or b"?").decode()
         super().__init__(f"{fn} failed: {STATUS.get(code, code)} ({msg})")
         self.code = code
 

@@ -395,14 +395,17 @@ def efunc_adam_step(params, grad, m, v, step: int, **adam_kw):
 
 def efunc_fit(params, m, v, qo, steps: int, J: int | None = None, n_batches: int = 1, step0: int = 0,
               loss: str = "l1", stats=None, log_beta0: float | None = None, ws: Workspace | None = None,
-              eikonal_weight: float = 0.0, pipelined: bool = True, **adam_kw):
+              eikonal_weight: float = 0.0, pipelined: bool = True, graph: bool = False, **adam_kw):
     """Fitting loop (Sec. 3.4) on batches of (x, y, z, target) rows.
 
     ``qo`` is a CUDA tensor or a (pinned) CPU tensor of n_batches*J rows of 4
     floats; ``stats`` (optional, CUDA or CPU float32 tensor of steps*2) gets
     (loss, MAE) per step.  ``pipelined`` sizes the workspace for the sort of
     the next batch to run beside the current one (else batches are sorted in
-    line)."""
+    line).  ``graph`` replays the pipelined schedule from a CUDA graph
+    (efunc_fit_graph: device batches and statistics only)."""
+    if graph and not pipelined:
+        raise ValueError("the graph-replayed fit is the pipelined schedule")
     R = resolution_of(params)
     for t, nm in ((params, "params"), (m, "m"), (v, "v")):
         _need(t, nm, params.numel())
@@ -420,10 +423,11 @@ def efunc_fit(params, m, v, qo, steps: int, J: int | None = None, n_batches: int
     if not pipelined:
         n = int(B.load().efunc_workspace_bytes(ctypes.byref(grid), int(J)))
     lk = {"l1": B.LOSS_L1, "mse": B.LOSS_MSE}[loss]
-    B.check("efunc_fit", B.load().efunc_fit(ctypes.byref(grid), ctypes.byref(ad), lk, float(eikonal_weight),
-                                            _ptr(params), _ptr(m), _ptr(v),
-                                            _ptr(qo), J, n_batches, steps, step0, _ptr(stats), _ptr(buf), n,
-                                            _stream(params.device)))
+    name = "efunc_fit_graph" if graph else "efunc_fit"
+    B.check(name, getattr(B.load(), name)(ctypes.byref(grid), ctypes.byref(ad), lk, float(eikonal_weight),
+                                          _ptr(params), _ptr(m), _ptr(v),
+                                          _ptr(qo), J, n_batches, steps, step0, _ptr(stats), _ptr(buf), n,
+                                          _stream(params.device)))
 
 
 class EfuncFn(torch.autograd.Function):

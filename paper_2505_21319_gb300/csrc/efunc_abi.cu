@@ -6,9 +6,12 @@
 #include <string.h>
 #include <vector>
 
+#include "adam_clock.cuh"
 #include "common.cuh"
 
 namespace efunc {
+
+efunc_status cuda_fail(cudaError_t e = cudaSuccess);
 
 namespace {
 
@@ -28,6 +31,8 @@ std::vector<cudaEvent_t> g_free_events;
 double g_ms[K_COUNT];
 int64_t g_count[K_COUNT];
 int64_t g_launches = 0;
+// set while this thread captures a CUDA graph: launches are counted, not timed
+thread_local bool g_in_capture = false;
 
 const char *const kKernelNames[K_COUNT] = {"bin",       "scan_reduce", "scan_top",       "scan_emit", "scatter",
                                            "pack_keys", "forward",     "fused_backward", "fused_fit", "adam",
@@ -74,7 +79,7 @@ void launch_begin(int kid, cudaStream_t s)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     ++g_launches;
-    if (!g_prof_on) return;
+    if (!g_prof_on || g_in_capture) return;
     Pending p{kid, take_event(), nullptr};
     if (p.start) cudaEventRecord(p.start, s);
     g_pending.push_back(p);
@@ -83,7 +88,8 @@ void launch_begin(int kid, cudaStream_t s)
 void launch_end(int kid, cudaStream_t s)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    if (!g_prof_on || g_pending.empty() || g_pending.back().kid != kid || g_pending.back().stop) return;
+    if (!g_prof_on || g_in_capture || g_pending.empty() || g_pending.back().kid != kid || g_pending.back().stop)
+        return;
     cudaEvent_t e = take_event();
     if (e) cudaEventRecord(e, s);
     g_pending.back().stop = e;
@@ -130,6 +136,7 @@ using namespace efunc;
 namespace {
 
 constexpr int64_t kMaxJ = (int64_t)1 << 30;
+constexpr int32_t kMaxGraphBatches = 64;   // a captured period holds lcm(2, n_batches) steps
 
 bool grid_ok(const efunc_grid *g) { return g && g->R >= 1 && g->R <= kMaxR; }
 
@@ -272,6 +279,8 @@ struct CopyPipe {
     cudaEvent_t sorted[2] = {nullptr, nullptr};
     cudaEvent_t consumed[2] = {nullptr, nullptr};
     cudaEvent_t packed = nullptr;
+    cudaEvent_t joined = nullptr;   // the sort stream's end of a captured period
+    cudaStream_t capture_stream = nullptr;   // origin of graph captures (the caller's may be the legacy stream)
 };
 constexpr int kMaxPipes = 64;
 std::mutex g_pipe_mu;
@@ -295,6 +304,8 @@ cudaError_t copy_pipe(CopyPipe **out)
             if ((e = cudaEventCreateWithFlags(&p.consumed[b], cudaEventDisableTiming)) != cudaSuccess) return e;
         }
         if ((e = cudaEventCreateWithFlags(&p.packed, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&p.joined, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithFlags(&p.capture_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
         p.ready = true;
     }
     *out = &p;
@@ -311,7 +322,28 @@ bool is_host_pointer(const void *p)
     return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
 }
 
-efunc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? EFUNC_OK : EFUNC_ERR_CUDA; }
+}  // namespace
+
+namespace efunc {
+
+// the CUDA error behind this thread's last EFUNC_ERR_CUDA (efunc_last_cuda_error)
+thread_local int g_last_cuda = 0;
+
+// Records and clears the runtime's pending error of a failed CUDA call (so it
+// cannot surface in a later call's launch check) and returns EFUNC_ERR_CUDA.
+efunc_status cuda_fail(cudaError_t e)
+{
+    const cudaError_t pending = cudaGetLastError();
+    if (e == cudaSuccess) e = pending;
+    g_last_cuda = e == cudaSuccess ? (int)cudaErrorUnknown : (int)e;
+    return EFUNC_ERR_CUDA;
+}
+
+}  // namespace efunc
+
+namespace {
+
+efunc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? EFUNC_OK : cuda_fail(e); }
 
 efunc_status check_adam(const efunc_adam *a)
 {
@@ -445,18 +477,18 @@ efunc_status fit_pipelined(const efunc_grid *grid, const efunc_adam *adam, int32
     const int64_t n = (int64_t)R * R * R * kSlots;
     float *grad = vw.grad();
     CopyPipe *pipe = nullptr;
-    if (copy_pipe(&pipe) != cudaSuccess) return EFUNC_ERR_CUDA;
+    if (copy_pipe(&pipe) != cudaSuccess) return cuda_fail();
     cudaStream_t ss = pipe->sort_stream;
     const size_t batch_bytes = (size_t)J * 16;
     auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * (size_t)J * 4; };
     const bool eik = eikonal_weight > 0.f;
     const int grid_blocks = fused_fit_grid_size(eik, true);
 
-    if (cudaMemsetAsync(grad, 0, (size_t)n * 4, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    if (cudaMemsetAsync(grad, 0, (size_t)n * 4, s) != cudaSuccess) return cuda_fail();
     // both sort buffers (and staging buffers) are free once the caller's earlier work is done
     for (int b = 0; b < 2; ++b) {
-        if (cudaEventRecord(pipe->consumed[b], s) != cudaSuccess) return EFUNC_ERR_CUDA;
-        if (q_host && cudaEventRecord(pipe->freed[b], s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (cudaEventRecord(pipe->consumed[b], s) != cudaSuccess) return cuda_fail();
+        if (q_host && cudaEventRecord(pipe->freed[b], s) != cudaSuccess) return cuda_fail();
     }
     auto issue_sort = [&](int32_t k) -> bool {
         const int b = k & 1;
@@ -478,17 +510,17 @@ efunc_status fit_pipelined(const efunc_grid *grid, const efunc_adam *adam, int32
         return cudaEventRecord(pipe->sorted[b], ss) == cudaSuccess;
     };
 
-    if (!issue_sort(0)) return EFUNC_ERR_CUDA;
+    if (!issue_sort(0)) return cuda_fail();
     for (int32_t it = 0; it < steps; ++it) {
         const int b = it & 1;
         const SortBuf sb = sort_buf(vw, b);
-        if (cudaStreamWaitEvent(s, pipe->sorted[b], 0) != cudaSuccess) return EFUNC_ERR_CUDA;
-        if (pack_keys(vw, grid, params, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (cudaStreamWaitEvent(s, pipe->sorted[b], 0) != cudaSuccess) return cuda_fail();
+        if (pack_keys(vw, grid, params, s) != cudaSuccess) return cuda_fail();
         // the next sort starts once this step's fused kernel is about to start
         if (it + 1 < steps) {
             if (cudaEventRecord(pipe->packed, s) != cudaSuccess ||
                 cudaStreamWaitEvent(ss, pipe->packed, 0) != cudaSuccess || !issue_sort(it + 1))
-                return EFUNC_ERR_CUDA;
+                return cuda_fail();
         }
         FusedArgs f = fused_args(vw, grid);
         f.sorted = sb.sorted;
@@ -499,19 +531,136 @@ efunc_status fit_pipelined(const efunc_grid *grid, const efunc_adam *adam, int32
         f.loss = loss;
         f.inv_J = (float)(1.0 / (double)J);
         f.eik_weight = eikonal_weight;
-        if (launch_fused_fit(f, eik, grid_blocks, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (launch_fused_fit(f, eik, grid_blocks, s) != cudaSuccess) return cuda_fail();
         float *stats_dev = reinterpret_cast<float *>(sb.ctrl) + 16;
         AdamArgs a = adam_args(adam, n, params, grad, m, v, step0 + it + 1);
         a.ctrl = sb.ctrl;
         a.inv_J = f.inv_J;
         a.stats = stats ? (stats_host ? stats_dev : stats + 2 * (size_t)it) : nullptr;
-        if (launch_adam(a, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (launch_adam(a, s) != cudaSuccess) return cuda_fail();
         if (stats_host && cudaMemcpyAsync(stats + 2 * (size_t)it, stats_dev, 8, cudaMemcpyDeviceToHost, s) !=
                               cudaSuccess)
-            return EFUNC_ERR_CUDA;
-        if (cudaEventRecord(pipe->consumed[b], s) != cudaSuccess) return EFUNC_ERR_CUDA;
+            return cuda_fail();
+        if (cudaEventRecord(pipe->consumed[b], s) != cudaSuccess) return cuda_fail();
     }
-    if (stats_host && cudaStreamSynchronize(s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    if (stats_host && cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail();
+    return EFUNC_OK;
+}
+
+// fit_pipelined's schedule replayed from a CUDA graph.  One period of
+// P = lcm(2, n_batches) steps repeats exactly (sort buffer it & 1, batch
+// it % n_batches, the same kernels and arguments) except for Adam's step
+// number, which lives in device memory (AdamClock in the first sort
+// buffer's control block, past the loss sums and the statistics slot).  The
+// call seeds the clock, sorts batch 0, captures one period on a library
+// stream (its last step sorts batch P = batch 0 into buffer 0 for the next
+// replay), launches the graph on the caller's stream (steps - 1) / P times
+// and issues the remaining 1..P steps one by one.
+// Inside the captured period the first step waits for nothing: the sort of
+// its batch ran before the graph launch on the same stream (or inside the
+// previous replay), and both sort buffers are free when a replay starts.
+efunc_status fit_graph(const efunc_grid *grid, const efunc_adam *adam, int32_t loss, float eikonal_weight,
+                       float *params, float *m, float *v, const float *qo, int64_t J, int32_t n_batches,
+                       int32_t steps, int64_t step0, float *stats, void *workspace, cudaStream_t s)
+{
+    const int R = grid->R;
+    Views vw{make_layout(R, J, kKeyRecords, kSlots, true), static_cast<char *>(workspace)};
+    const int64_t n = (int64_t)R * R * R * kSlots;
+    float *grad = vw.grad();
+    CopyPipe *pipe = nullptr;
+    if (copy_pipe(&pipe) != cudaSuccess) return cuda_fail();
+    cudaStream_t ss = pipe->sort_stream;
+    auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * (size_t)J * 4; };
+    const bool eik = eikonal_weight > 0.f;
+    const int grid_blocks = fused_fit_grid_size(eik, true);
+    const int32_t period = (n_batches % 2 == 0) ? n_batches : 2 * n_batches;
+    static_assert(sizeof(Ctrl) <= 64 && sizeof(AdamClock) <= 128, "control block layout");
+    AdamClock *clk = reinterpret_cast<AdamClock *>(reinterpret_cast<char *>(vw.ctrl()) + 128);
+    const AdamArgs base = adam_args(adam, n, params, grad, m, v, step0 + 1);
+
+    if (cudaMemsetAsync(grad, 0, (size_t)n * 4, s) != cudaSuccess) return cuda_fail();
+    if (launch_adam_clock_seed(clk, adam_clock_init(adam->lr, adam->beta1, adam->beta2, step0 + 1), s) !=
+        cudaSuccess)
+        return cuda_fail();
+    for (int b = 0; b < 2; ++b)
+        if (cudaEventRecord(pipe->consumed[b], s) != cudaSuccess) return cuda_fail();
+    auto issue_sort = [&](int32_t k, bool wait_consumed) -> bool {
+        const int b = k & 1;
+        if (wait_consumed && cudaStreamWaitEvent(ss, pipe->consumed[b], 0) != cudaSuccess) return false;
+        if (sort_into_buf(sort_buf(vw, b), vw.L, R, batch(k), J, 4, ss, 1) != cudaSuccess) return false;
+        return cudaEventRecord(pipe->sorted[b], ss) == cudaSuccess;
+    };
+    // one step on stream st; `head` marks the first step of a captured period
+    auto issue_step = [&](int32_t it, bool head, bool sort_next, cudaStream_t st) -> bool {
+        const int b = it & 1;
+        const SortBuf sb = sort_buf(vw, b);
+        if (!head && cudaStreamWaitEvent(st, pipe->sorted[b], 0) != cudaSuccess) return false;
+        if (pack_keys(vw, grid, params, st) != cudaSuccess) return false;
+        if (sort_next) {
+            if (cudaEventRecord(pipe->packed, st) != cudaSuccess ||
+                cudaStreamWaitEvent(ss, pipe->packed, 0) != cudaSuccess || !issue_sort(it + 1, !head))
+                return false;
+        }
+        FusedArgs f = fused_args(vw, grid);
+        f.sorted = sb.sorted;
+        f.items = sb.items;
+        f.ctrl = sb.ctrl;
+        f.perm = nullptr;
+        f.grad = grad;
+        f.loss = loss;
+        f.inv_J = (float)(1.0 / (double)J);
+        f.eik_weight = eikonal_weight;
+        if (launch_fused_fit(f, eik, grid_blocks, st) != cudaSuccess) return false;
+        AdamArgs a = base;
+        a.ctrl = sb.ctrl;
+        a.inv_J = f.inv_J;
+        a.stats = stats;
+        if (launch_adam_clocked(a, clk, st) != cudaSuccess) return false;
+        return cudaEventRecord(pipe->consumed[b], st) == cudaSuccess;
+    };
+
+    if (!issue_sort(0, true) || cudaStreamWaitEvent(s, pipe->sorted[0], 0) != cudaSuccess) return cuda_fail();
+    const int32_t replays = (steps - 1) / period;
+    if (replays > 0) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        int64_t before = 0, captured = 0;
+        {
+            std::lock_guard<std::mutex> lk(g_prof_mu);
+            before = g_launches;
+        }
+        cudaStream_t cs = pipe->capture_stream;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_fail();
+        g_in_capture = true;
+        bool ok = true;
+        for (int32_t it = 0; it < period && ok; ++it) ok = issue_step(it, it == 0, true, cs);
+        // the sort stream rejoins the capturing stream
+        ok = ok && cudaEventRecord(pipe->joined, ss) == cudaSuccess &&
+             cudaStreamWaitEvent(cs, pipe->joined, 0) == cudaSuccess;
+        g_in_capture = false;
+        const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        {
+            std::lock_guard<std::mutex> lk(g_prof_mu);
+            captured = g_launches - before;
+            g_launches = before;   // captured launches run once per replay
+        }
+        cudaError_t e = ce;
+        if (ok && e == cudaSuccess && graph) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        for (int32_t r = 0; ok && exec && r < replays && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, s);
+        if (exec) cudaGraphExecDestroy(exec);   // deferred by the driver until the launches complete
+        // the events recorded during the capture stand for graph nodes, not
+        // for work on a stream: record them again after the replays, on the
+        // caller's stream, before anything outside the graph waits for them
+        for (cudaEvent_t ev : {pipe->sorted[0], pipe->sorted[1], pipe->consumed[0], pipe->consumed[1], pipe->packed,
+                               pipe->joined})
+            if (cudaEventRecord(ev, s) != cudaSuccess && e == cudaSuccess) e = cudaErrorUnknown;
+        if (!ok || e != cudaSuccess) return cuda_fail(ok ? e : cudaSuccess);
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_launches += captured * replays;
+    }
+    for (int32_t it = replays * period; it < steps; ++it)
+        if (!issue_step(it, false, it + 1 < steps, s)) return cuda_fail();
     return EFUNC_OK;
 }
 
@@ -523,11 +672,11 @@ efunc_status pipelined_device_fit(const Views &vw, int R, const float *qo, int64
                                   int32_t steps, cudaStream_t s, Pack pack, Compute compute)
 {
     CopyPipe *pipe = nullptr;
-    if (copy_pipe(&pipe) != cudaSuccess) return EFUNC_ERR_CUDA;
+    if (copy_pipe(&pipe) != cudaSuccess) return cuda_fail();
     cudaStream_t ss = pipe->sort_stream;
     auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * (size_t)J * 4; };
     for (int b = 0; b < 2; ++b)
-        if (cudaEventRecord(pipe->consumed[b], s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (cudaEventRecord(pipe->consumed[b], s) != cudaSuccess) return cuda_fail();
     auto issue_sort = [&](int32_t k) -> bool {
         const int b = k & 1;
         if (cudaStreamWaitEvent(ss, pipe->consumed[b], 0) != cudaSuccess) return false;
@@ -536,18 +685,18 @@ efunc_status pipelined_device_fit(const Views &vw, int R, const float *qo, int64
         if (sort_into_buf(sort_buf(vw, b), vw.L, R, batch(k), J, 4, ss, 2) != cudaSuccess) return false;
         return cudaEventRecord(pipe->sorted[b], ss) == cudaSuccess;
     };
-    if (!issue_sort(0)) return EFUNC_ERR_CUDA;
+    if (!issue_sort(0)) return cuda_fail();
     for (int32_t it = 0; it < steps; ++it) {
         const int b = it & 1;
-        if (cudaStreamWaitEvent(s, pipe->sorted[b], 0) != cudaSuccess) return EFUNC_ERR_CUDA;
-        if (pack(s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (cudaStreamWaitEvent(s, pipe->sorted[b], 0) != cudaSuccess) return cuda_fail();
+        if (pack(s) != cudaSuccess) return cuda_fail();
         if (it + 1 < steps) {
             if (cudaEventRecord(pipe->packed, s) != cudaSuccess ||
                 cudaStreamWaitEvent(ss, pipe->packed, 0) != cudaSuccess || !issue_sort(it + 1))
-                return EFUNC_ERR_CUDA;
+                return cuda_fail();
         }
-        if (compute(it, sort_buf(vw, b), s) != cudaSuccess) return EFUNC_ERR_CUDA;
-        if (cudaEventRecord(pipe->consumed[b], s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (compute(it, sort_buf(vw, b), s) != cudaSuccess) return cuda_fail();
+        if (cudaEventRecord(pipe->consumed[b], s) != cudaSuccess) return cuda_fail();
     }
     return EFUNC_OK;
 }
@@ -621,7 +770,7 @@ efunc_status efunc_forward(const efunc_grid *grid, const float *params, const fl
     Views v{make_layout(grid->R, J), static_cast<char *>(workspace)};
     cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
     if (e == cudaSuccess) e = pack_keys(v, grid, params, s);
-    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_fail();
     FusedArgs f = fused_args(v, grid);
     f.O = O;
     f.lse = lse;
@@ -643,7 +792,7 @@ efunc_status efunc_backward(const efunc_grid *grid, const float *params, const f
     Views v{make_layout(grid->R, J), static_cast<char *>(workspace)};
     cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
     if (e == cudaSuccess) e = pack_keys(v, grid, params, s);
-    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_fail();
     FusedArgs f = fused_args(v, grid);
     f.gO = gO;
     f.grad = grad;
@@ -665,7 +814,7 @@ efunc_status efunc_backward_grad(const efunc_grid *grid, const float *params, co
     Views v{make_layout(grid->R, J), static_cast<char *>(workspace)};
     cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
     if (e == cudaSuccess) e = pack_keys(v, grid, params, s);
-    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_fail();
     FusedArgs f = fused_args(v, grid);
     f.gO = gO;
     f.gG = gG;
@@ -714,7 +863,7 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
     static_assert(sizeof(Ctrl) <= 64, "control block must leave room for the statistics slot");
 
     cudaError_t e = cudaMemsetAsync(grad, 0, (size_t)n * 4, s);
-    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_fail();
     const int grid_blocks = fused_grid_size();
     const size_t batch_bytes = (size_t)J * 16;
     auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * (size_t)J * 4; };
@@ -723,13 +872,13 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
     // buffers, batch it+1 landing while batch it is computed.
     CopyPipe *pipe = nullptr;
     if (q_host) {
-        if (copy_pipe(&pipe) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (copy_pipe(&pipe) != cudaSuccess) return cuda_fail();
         for (int b = 0; b < 2; ++b)   // buffers free once the caller's earlier work is done
-            if (cudaEventRecord(pipe->freed[b], s) != cudaSuccess) return EFUNC_ERR_CUDA;
+            if (cudaEventRecord(pipe->freed[b], s) != cudaSuccess) return cuda_fail();
         if (cudaStreamWaitEvent(pipe->stream, pipe->freed[0], 0) != cudaSuccess ||
             cudaMemcpyAsync(vw.stage(0, J), batch(0), batch_bytes, cudaMemcpyHostToDevice, pipe->stream) != cudaSuccess ||
             cudaEventRecord(pipe->copied[0], pipe->stream) != cudaSuccess)
-            return EFUNC_ERR_CUDA;
+            return cuda_fail();
     }
     for (int32_t it = 0; it < steps; ++it) {
         const int b = it & 1;
@@ -740,35 +889,61 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
                  cudaMemcpyAsync(vw.stage(b ^ 1, J), batch(it + 1), batch_bytes, cudaMemcpyHostToDevice,
                                  pipe->stream) != cudaSuccess ||
                  cudaEventRecord(pipe->copied[b ^ 1], pipe->stream) != cudaSuccess))
-                return EFUNC_ERR_CUDA;
-            if (cudaStreamWaitEvent(s, pipe->copied[b], 0) != cudaSuccess) return EFUNC_ERR_CUDA;
+                return cuda_fail();
+            if (cudaStreamWaitEvent(s, pipe->copied[b], 0) != cudaSuccess) return cuda_fail();
             qdev = reinterpret_cast<const float *>(vw.stage(b, J));
         }
         // the fit reduces over queries: no permutation back to the caller's order
         e = sort_into(vw, grid->R, qdev, J, 4, vw.sorted(), nullptr, s);
         if (e == cudaSuccess && q_host) e = cudaEventRecord(pipe->freed[b], s);   // staging buffer consumed
         if (e == cudaSuccess) e = pack_keys(vw, grid, params, s);
-        if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (e != cudaSuccess) return cuda_fail();
         FusedArgs f = fused_args(vw, grid);
         f.grad = grad;
         f.loss = loss;
         f.inv_J = (float)(1.0 / (double)J);
         f.eik_weight = eikonal_weight;
         e = launch_fused_fit(f, eikonal_weight > 0.f, grid_blocks, s);
-        if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (e != cudaSuccess) return cuda_fail();
         AdamArgs a = adam_args(adam, n, params, grad, m, v, step0 + it + 1);
         a.ctrl = vw.ctrl();
         a.inv_J = f.inv_J;
         a.stats = stats ? (stats_host ? stats_dev : stats + 2 * (size_t)it) : nullptr;
         e = launch_adam(a, s);
-        if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (e != cudaSuccess) return cuda_fail();
         if (stats_host) {
             e = cudaMemcpyAsync(stats + 2 * (size_t)it, stats_dev, 8, cudaMemcpyDeviceToHost, s);
-            if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+            if (e != cudaSuccess) return cuda_fail();
         }
     }
-    if (stats_host && cudaStreamSynchronize(s) != cudaSuccess) return EFUNC_ERR_CUDA;
+    if (stats_host && cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail();
     return EFUNC_OK;
+}
+
+efunc_status efunc_fit_graph(const efunc_grid *grid, const efunc_adam *adam, int32_t loss, float eikonal_weight,
+                             float *params, float *m, float *v, const float *qo, int64_t J, int32_t n_batches,
+                             int32_t steps, int64_t step0, float *stats, void *workspace, size_t workspace_bytes,
+                             efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if ((st = check_adam(adam))) return st;
+    if (loss != EFUNC_LOSS_L1 && loss != EFUNC_LOSS_MSE) return EFUNC_ERR_ARG;
+    if (!isfinite(eikonal_weight)) return EFUNC_ERR_NONFINITE;
+    if (eikonal_weight < 0.f) return EFUNC_ERR_ARG;
+    if (J < 1 || J > kMaxJ || n_batches < 1 || n_batches > kMaxGraphBatches || steps < 0 || step0 < 0)
+        return EFUNC_ERR_ARG;
+    if (!params || !m || !v || !qo) return EFUNC_ERR_ARG;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u) ||
+        workspace_bytes < make_layout(grid->R, J, kKeyRecords, kSlots, true).total)
+        return EFUNC_ERR_WORKSPACE;
+    if (steps == 0) return EFUNC_OK;
+    if (is_host_pointer(qo) || (stats && is_host_pointer(stats))) return EFUNC_ERR_ARG;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) return cuda_fail();
+    if (cs != cudaStreamCaptureStatusNone) return EFUNC_ERR_ARG;
+    return fit_graph(grid, adam, loss, eikonal_weight, params, m, v, qo, J, n_batches, steps, step0, stats,
+                     workspace, (cudaStream_t)stream);
 }
 
 efunc_status efunc_mean_shift_init(const efunc_grid *grid, const float *pts, int64_t N, float bandwidth,
@@ -816,7 +991,7 @@ efunc_status efunc_variant_forward(const efunc_grid *grid, const efunc_variant *
     cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
     VariantArgs a = variant_args(v, grid, variant, params);
     if (e == cudaSuccess) e = launch_variant_pack(a, s);
-    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_fail();
     a.O = O;
     a.lse = lse;
     return cuda_status(launch_variant(a, VAR_FORWARD, s));
@@ -838,7 +1013,7 @@ efunc_status efunc_variant_backward(const efunc_grid *grid, const efunc_variant 
     cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
     VariantArgs a = variant_args(v, grid, variant, params);
     if (e == cudaSuccess) e = launch_variant_pack(a, s);
-    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_fail();
     a.gO = gO;
     a.grad = grad;
     return cuda_status(launch_variant(a, VAR_BACKWARD, s));
@@ -867,7 +1042,7 @@ efunc_status efunc_variant_fit(const efunc_grid *grid, const efunc_variant *vari
     {
         Views vp{variant_layout(grid, variant, J, true), static_cast<char *>(workspace)};
         float *gp = vp.grad();
-        if (cudaMemsetAsync(gp, 0, (size_t)n * 4, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (cudaMemsetAsync(gp, 0, (size_t)n * 4, s) != cudaSuccess) return cuda_fail();
         return pipelined_device_fit(
             vp, grid->R, qo, J, n_batches, steps, s,
             [&](cudaStream_t st) { return launch_variant_pack(variant_args(vp, grid, variant, params), st); },
@@ -914,7 +1089,7 @@ efunc_status efunc_cosine_forward(const efunc_grid *grid, int32_t bands, const f
     cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
     CosineArgs a = cosine_args(v, grid, bands, params);
     if (e == cudaSuccess) e = launch_cosine_pack(a, s);
-    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_fail();
     a.S = S;
     return cuda_status(launch_cosine(a, VAR_FORWARD, s));
 }
@@ -935,7 +1110,7 @@ efunc_status efunc_cosine_backward(const efunc_grid *grid, int32_t bands, const 
     cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
     CosineArgs a = cosine_args(v, grid, bands, params);
     if (e == cudaSuccess) e = launch_cosine_pack(a, s);
-    if (e != cudaSuccess) return EFUNC_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_fail();
     a.gS = gS;
     a.grad = grad;
     return cuda_status(launch_cosine(a, VAR_BACKWARD, s));
@@ -964,7 +1139,7 @@ efunc_status efunc_cosine_fit(const efunc_grid *grid, int32_t bands, const efunc
     {
         Views vp{cosine_layout(grid, bands, J, true), static_cast<char *>(workspace)};
         float *gp = vp.grad();
-        if (cudaMemsetAsync(gp, 0, (size_t)n * 4, s) != cudaSuccess) return EFUNC_ERR_CUDA;
+        if (cudaMemsetAsync(gp, 0, (size_t)n * 4, s) != cudaSuccess) return cuda_fail();
         return pipelined_device_fit(
             vp, grid->R, qo, J, n_batches, steps, s,
             [&](cudaStream_t st) { return launch_cosine_pack(cosine_args(vp, grid, bands, params), st); },
@@ -1023,6 +1198,10 @@ void efunc_profile_reset(void)
         g_count[k] = 0;
     }
 }
+
+int32_t efunc_last_cuda_error(void) { return g_last_cuda; }
+
+const char *efunc_cuda_error_name(int32_t code) { return cudaGetErrorName((cudaError_t)code); }
 
 int64_t efunc_launch_count(void)
 {

@@ -40,6 +40,10 @@ cudaError_t noalloc_scratch(void **out)
 
 }  // namespace
 
+namespace efunc {
+efunc_status cuda_fail(cudaError_t e);   // records the error for efunc_last_cuda_error
+}
+
 extern "C" {
 
 efunc_status efunc_forward_noalloc(const efunc_grid *grid, const float *params, const float *q, int64_t J,
@@ -53,7 +57,8 @@ efunc_status efunc_forward_noalloc(const efunc_grid *grid, const float *params, 
     if (need == 0) return EFUNC_ERR_ARG;
     if (need > kNoAllocScratchBytes) return EFUNC_ERR_WORKSPACE;   // beyond the fixed scratch
     void *scratch = nullptr;
-    if (noalloc_scratch(&scratch) != cudaSuccess) return EFUNC_ERR_CUDA;
+    const cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) return efunc::cuda_fail(e);
     // efunc_forward clears the control block and histogram it reads before
     // use, so the previous call's contents of the shared array do not leak in
     return efunc_forward(grid, params, q, J, q_stride, O, lse, dOdq, scratch, kNoAllocScratchBytes, stream);

@@ -34,6 +34,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_host_helpers(lib):
+    n0 = lib.efunc_launch_count()   # launches of earlier tests in this process
     assert lib.efunc_param_count(32) == 32 ** 3 * 13 == 425984
     assert lib.efunc_param_count(0) == -1 and lib.efunc_param_count(257) == -1
     assert abs(lib.efunc_default_log_beta0(32) - 7.0) < 1e-6
@@ -41,6 +42,8 @@ def test_host_helpers(lib):
     for code in range(6):
         assert lib.efunc_status_str(code)
     assert lib.efunc_status_str(99) == b"unknown status"
+    assert lib.efunc_last_cuda_error() == 0
+    assert lib.efunc_cuda_error_name(1) == b"cudaErrorInvalidValue"
     g = B.Grid(32, 2, 7.0)
     n1 = lib.efunc_workspace_bytes(ctypes.byref(g), 1 << 22)
     n2 = lib.efunc_workspace_bytes(ctypes.byref(g), 1 << 10)
@@ -51,7 +54,7 @@ def test_host_helpers(lib):
     nf = lib.efunc_fit_workspace_bytes(ctypes.byref(g), 1 << 22)
     assert nf > n1 and nf - n1 >= 20 * (1 << 22) and nf % 256 == 0
     assert lib.efunc_fit_workspace_bytes(ctypes.byref(B.Grid(0, 2, 7.0)), 10) == 0
-    assert lib.efunc_launch_count() == 0
+    assert lib.efunc_launch_count() == n0
 
 
 def _fwd(lib, grid, J=16, stride=3, ws=1 << 30, ws_bytes=None, params=4096, q=8192, O=12288):
@@ -64,6 +67,7 @@ def _fwd(lib, grid, J=16, stride=3, ws=1 << 30, ws_bytes=None, params=4096, q=81
 def test_argument_validation_enqueues_nothing(lib):
     """Invalid arguments are rejected on the host (fake, never dereferenced
     pointers are enough to reach every check)."""
+    n0 = lib.efunc_launch_count()   # launches of earlier tests in this process
     ok = B.Grid(8, 2, 7.0)
     assert _fwd(lib, None) == 1
     assert _fwd(lib, B.Grid(0, 2, 7.0)) == 1
@@ -80,7 +84,7 @@ def test_argument_validation_enqueues_nothing(lib):
     assert _fwd(lib, ok, ws=(1 << 30) + 8) == 3          # misaligned
     assert _fwd(lib, ok, ws_bytes=100) == 3              # too small
     assert _fwd(lib, ok, J=0) == 0                       # empty batch: nothing to do
-    assert lib.efunc_launch_count() == 0
+    assert lib.efunc_launch_count() == n0
     # backward, cell sort, Adam, fit
     assert lib.efunc_backward(ctypes.byref(ok), 4096, 8192, 16, 3, 4096, None, None, 1 << 30, 1 << 40, None) == 1
     assert lib.efunc_backward(ctypes.byref(ok), 4096, 8192, 0, 3, None, 4096, None, 1 << 30, 1 << 40, None) == 0
@@ -103,6 +107,25 @@ def test_argument_validation_enqueues_nothing(lib):
                          1 << 40, None) == 0                                                # zero steps
     assert lib.efunc_backward_grad(ctypes.byref(ok), 4096, 8192, 16, 3, None, None, 4096, 1 << 30, 1 << 40,
                                    None) == 1                                               # neither gO nor gG
+    # the graph-replayed fit: the same checks, its whole workspace, device batches, at most 64 batches
+    fg = lib.efunc_fit_graph
+    wsf = lib.efunc_fit_workspace_bytes(ctypes.byref(ok), 16)
+    assert fg(ctypes.byref(ok), ctypes.byref(ad), 2, 0.0, 16, 32, 48, 64, 16, 1, 1, 0, None, 1 << 30, wsf,
+              None) == 1                                                                    # bad loss kind
+    assert fg(ctypes.byref(ok), ctypes.byref(ad), 0, float("inf"), 16, 32, 48, 64, 16, 1, 1, 0, None, 1 << 30, wsf,
+              None) == 4
+    assert fg(ctypes.byref(ok), ctypes.byref(ad), 0, 0.0, 16, 32, 48, 64, 16, 0, 1, 0, None, 1 << 30, wsf,
+              None) == 1                                                                    # no batches
+    assert fg(ctypes.byref(ok), ctypes.byref(ad), 0, 0.0, 16, 32, 48, 64, 16, 65, 1, 0, None, 1 << 30, wsf,
+              None) == 1                                                                    # period too long
+    assert fg(ctypes.byref(ok), ctypes.byref(ad), 0, 0.0, 16, 32, 48, 64, 16, 1, 1, 0, None, 1 << 30, wsf - 256,
+              None) == 3                                                                    # no second sort buffer
+    assert fg(ctypes.byref(ok), ctypes.byref(ad), 0, 0.0, 16, 32, 48, 64, 16, 1, 1, 0, None, (1 << 30) + 64, wsf,
+              None) == 3                                                                    # misaligned
+    assert fg(ctypes.byref(ok), ctypes.byref(ad), 0, 0.0, 16, 32, 48, 64, 16, 1, 0, 0, None, 1 << 30, wsf,
+              None) == 0                                                                    # zero steps
+    assert fg(ctypes.byref(ok), ctypes.byref(ad), 0, 0.0, 16, 32, 48, 64, 16, 1, 1, 0, None, 1 << 30, wsf,
+              None) == 1                                                                    # not device memory
     assert lib.efunc_mean_shift_init(ctypes.byref(ok), 4096, 0, 100.0, 8192, None) == 1       # no points
     assert lib.efunc_mean_shift_init(ctypes.byref(ok), 4096, (1 << 30) + 1, 100.0, 8192, None) == 1
     assert lib.efunc_mean_shift_init(ctypes.byref(ok), 4096, 10, 0.0, 8192, None) == 1        # bandwidth 0
@@ -110,12 +133,13 @@ def test_argument_validation_enqueues_nothing(lib):
     assert lib.efunc_mean_shift_init(ctypes.byref(ok), 4096, 10, float("inf"), 8192, None) == 4
     assert lib.efunc_mean_shift_init(ctypes.byref(ok), None, 10, 100.0, 8192, None) == 1
     assert lib.efunc_mean_shift_init(ctypes.byref(B.Grid(0, 2, 7.0)), 4096, 10, 100.0, 8192, None) == 1
-    assert lib.efunc_launch_count() == 0
+    assert lib.efunc_launch_count() == n0
 
 
 def test_variant_helpers_and_validation(lib):
     """Channel counts of the ablation variants and host-side rejection of
     invalid variant requests (nothing launches)."""
+    n0 = lib.efunc_launch_count()   # launches of earlier tests in this process
     from paper_2505_21319_gb300 import api
     for name, (sets, deg, learn) in api.VARIANTS.items():
         ch = lib.efunc_variant_channels(ctypes.byref(B.Variant(sets, deg, learn)))
@@ -147,10 +171,11 @@ def test_variant_helpers_and_validation(lib):
                                  None, 1 << 30, wsv - 256, None) == 3
     assert lib.efunc_variant_fit(ctypes.byref(g), ctypes.byref(v1), ctypes.byref(ad), 0, 16, 32, 48, 64, 16, 1, 1, 0,
                                  None, 1 << 30, wsv, None) == 1                              # not device memory
-    assert lib.efunc_launch_count() == 0
+    assert lib.efunc_launch_count() == n0
 
 
 def test_cosine_helpers_and_validation(lib):
+    n0 = lib.efunc_launch_count()   # launches of earlier tests in this process
     g = B.Grid(16, 2, 7.0)
     n1 = lib.efunc_cosine_workspace_bytes(ctypes.byref(g), 1, 1 << 16)
     n8 = lib.efunc_cosine_workspace_bytes(ctypes.byref(g), 8, 1 << 16)
@@ -168,7 +193,7 @@ def test_cosine_helpers_and_validation(lib):
     wsc = lib.efunc_cosine_workspace_bytes(ctypes.byref(g), 4, 16)
     assert lib.efunc_cosine_fit(ctypes.byref(g), 4, ctypes.byref(ad), 0, 16, 32, 48, 64, 16, 1, 1, 0, None, 1 << 30,
                                 wsc - 256, None) == 3                                        # workspace too small
-    assert lib.efunc_launch_count() == 0
+    assert lib.efunc_launch_count() == n0
 
 
 def test_profile_api_without_gpu(lib):

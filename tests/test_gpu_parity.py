@@ -347,6 +347,79 @@ def test_pipelined_fit_matches_inline_sort(eikonal):
     np.testing.assert_allclose(out[True][0][solid], out[False][0][solid], rtol=1e-4, atol=1e-6)
 
 
+@pytest.mark.parametrize("n_batches,steps,side", [(3, 14, False), (3, 14, True), (1, 3, False), (2, 2, False),
+                                                  (1, 1, False)])
+def test_graph_fit_matches_oracle_trajectory(n_batches, steps, side):
+    """The graph-replayed fit against the oracle's loop over the same batch
+    sequence: with 3 batches the period is 6 steps, so 14 steps are 2 replays
+    and 2 steps issued one by one (the step number and the statistics row
+    advance on the device across replays); the shorter runs have one replay
+    or none.  `side`: on a non-default stream of the caller."""
+    R, J = 4, 4000
+    qo = synth.sample_batch(synth.sphere(0.5), n_batches * J, seed=5)
+    p0 = synth.init_params(R, seed=3)
+    pd, m, v = to_dev(p0), torch.zeros(p0.size, device=DEV), torch.zeros(p0.size, device=DEV)
+    stats = torch.zeros(2 * steps, device=DEV)
+    qd = to_dev(qo)
+    st = torch.cuda.Stream() if side else torch.cuda.current_stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        api.efunc_fit(pd, m, v, qd, steps=steps, J=J, n_batches=n_batches, step0=7, loss="mse", stats=stats,
+                      lr=1e-3, log_beta0=lb32(R), graph=True, ws=api.Workspace(DEV))
+    st.synchronize()
+    pr, mr, vr = p0.astype(np.float64), np.zeros_like(p0, dtype=np.float64), np.zeros_like(p0, dtype=np.float64)
+    losses, maes = [], []
+    for it in range(steps):
+        b = it % n_batches
+        pr, mr, vr, L, mae = oracle.fit_step(pr, mr, vr, 8 + it, qo[b * J:(b + 1) * J], R, loss=oracle.MSE, lr=1e-3,
+                                             log_beta0=lb32(R))
+        losses.append(L)
+        maes.append(mae)
+    s = stats.cpu().numpy().reshape(steps, 2)
+    np.testing.assert_allclose(s[:, 0], losses, rtol=1e-4)
+    np.testing.assert_allclose(s[:, 1], maes, rtol=1e-4)
+    solid = np.abs(mr.reshape(-1)) > 1e-3 * np.abs(mr).max()
+    np.testing.assert_allclose(pd.cpu().numpy().reshape(-1)[solid], pr.reshape(-1)[solid], rtol=1e-4, atol=1e-6)
+
+
+@pytest.mark.parametrize("eikonal", [0.0, 0.5])
+def test_graph_fit_matches_stream_fit(eikonal):
+    """efunc_fit_graph and efunc_fit take the same steps (losses, parameters
+    where the first moment is far from zero) and launch the same kernels,
+    plus the one that seeds the device step counter."""
+    R, J, steps = 16, 65536, 9
+    qo = to_dev(synth.sample_batch(synth.random_union(6), 2 * J, seed=6))
+    p0 = synth.init_params(R, seed=4)
+    out, launches = {}, {}
+    for graph in (False, True):
+        pd, m, v = to_dev(p0), torch.zeros(p0.size, device=DEV), torch.zeros(p0.size, device=DEV)
+        stats = torch.zeros(2 * steps, device=DEV)
+        ws = api.Workspace(DEV)
+        torch.cuda.synchronize()
+        n0 = api.launch_count()
+        api.efunc_fit(pd, m, v, qo, steps=steps, J=J, n_batches=2, loss="mse", stats=stats, lr=1e-3,
+                      log_beta0=lb32(R), eikonal_weight=eikonal, graph=graph, ws=ws)
+        torch.cuda.synchronize()
+        launches[graph] = api.launch_count() - n0
+        out[graph] = (pd.cpu().numpy().reshape(-1), m.cpu().numpy().reshape(-1), stats.cpu().numpy())
+    assert launches[True] == launches[False] + 1
+    np.testing.assert_allclose(out[True][2], out[False][2], rtol=1e-5)
+    solid = np.abs(out[False][1]) > 1e-2 * np.abs(out[False][1]).max()
+    np.testing.assert_allclose(out[True][0][solid], out[False][0][solid], rtol=1e-4, atol=1e-6)
+
+
+def test_graph_fit_rejects_host_memory_and_capture():
+    R, J = 4, 1000
+    qo = synth.sample_batch(synth.sphere(0.5), J, seed=1)
+    p0 = synth.init_params(R, seed=1)
+    pd, m, v = to_dev(p0), torch.zeros(p0.size, device=DEV), torch.zeros(p0.size, device=DEV)
+    with pytest.raises(RuntimeError):
+        api.efunc_fit(pd, m, v, torch.from_numpy(qo).pin_memory(), steps=2, graph=True)
+    with pytest.raises(RuntimeError):
+        api.efunc_fit(pd, m, v, to_dev(qo), steps=2, stats=torch.zeros(4), graph=True)
+    np.testing.assert_array_equal(pd.cpu().numpy(), p0)
+
+
 @pytest.mark.parametrize("pipelined", [True, False])
 def test_fit_from_host_memory_matches_device(pipelined):
     R, J = 8, 20000
