@@ -68,6 +68,10 @@ EIK_BWD_GRID_EXTRA = 23
 EIK_BWD_OFFSET_EXTRA = 23 + 8
 EIK_EXTRA_PER_CENTRE = 2 * EIK_GV_PER_KEY + EIK_BWD_GRID_EXTRA + EIK_BWD_OFFSET_EXTRA
 FP32_LANES_PER_SM = 128
+# steps of one whole fit: 2000 at 32^3 x 2^22 queries, 100 at 16^3 x 65,536
+# (fits/s = 1 / (steps x time per step))
+FIT_STEPS_32 = 2000
+FIT_STEPS_16 = 100
 # FP32-pipe operations of one (centre, point) pair of the mean-shift
 # initialisation: 3 differences, 3 for the squared norm, 1 scale, 1 compare,
 # 1 exponent difference, 1 add to Z, 3 FMAs into S (the ex2 runs on the MUFU)
@@ -605,6 +609,7 @@ def main():
             "32^3 x 2^22": {"value": J * ws / (gms * 1e-3), "unit": "query-pts/s", "ms_per_step": gms,
                             "stream_ms_per_step": ms, "steps": args.graph_steps},
             "16^3 x 65536": {"value": Js * ws / (small_ms[True] * 1e-3), "unit": "query-pts/s",
+                             "fits_per_s": 1e3 / (FIT_STEPS_16 * small_ms[True]) * ws, "steps_per_fit": FIT_STEPS_16,
                              "ms_per_step": small_ms[True], "stream_value": Js * ws / (small_ms[False] * 1e-3),
                              "stream_ms_per_step": small_ms[False], "steps": 4 * args.graph_steps,
                              "l2": "1 MiB batches: L2-resident"},
@@ -666,7 +671,8 @@ def main():
             "clocks": clocks,
             "gpu_launches": launches,
             "fit": {"steps_total": args.warmup + args.steps, "loss_first_timed": float(st[0, 0]),
-                    "mae_first_timed": float(st[0, 1]), "mae_last": float(st[-1, 1])},
+                    "mae_first_timed": float(st[0, 1]), "mae_last": float(st[-1, 1]),
+                    "fits_per_s": 1e3 / (FIT_STEPS_32 * ms) * ws, "steps_per_fit": FIT_STEPS_32},
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
