@@ -344,6 +344,7 @@ def main():
     ap.add_argument("--cosine-steps", type=int, default=50)
     ap.add_argument("--isolated-steps", type=int, default=50)
     ap.add_argument("--graph-steps", type=int, default=500)
+    ap.add_argument("--large-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -482,6 +483,41 @@ def main():
         eik = {"value": J * ws / (ems * 1e-3), "unit": "query-pts/s", "ms_per_step": ems,
                "fused_ms": eavg, "achieved": each, "peak": peak, "unit_roofline": "T FP32 op/s",
                "frac": each / peak, "ops_per_launch": eops, "steps": args.eikonal_steps, "eikonal_weight": 0.1}
+
+    # ---- the largest configuration, 64^3 x 13 with 2^24 queries per step
+    # (one 256 MiB batch, larger than L2: the three 2^22 batches of the pool
+    # and a fourth drawn the same way), same fit and roofline accounting
+    large = None
+    if args.large_steps > 0:
+        RL, JL = 64, 1 << 24
+        big_np = np.concatenate([pool_np, synth.sample_batch(synth.random_union(0), J, seed=1000 * rank + N_BATCHES)])
+        assert big_np.shape[0] == JL
+        big = torch.from_numpy(big_np).to(dev)
+        lp = torch.from_numpy(synth.init_params(RL, seed=rank)).to(dev)
+        lm, lv = torch.zeros_like(lp), torch.zeros_like(lp)
+        lws = api.Workspace(dev)
+        api.efunc_fit(lp, lm, lv, big, steps=3, J=JL, lr=LR, ws=lws)
+        torch.cuda.synchronize(dev)
+        api.profile_reset()
+        api.profile(True)
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if ws > 1:
+            dist.barrier()
+        l0.record(stream)
+        api.efunc_fit(lp, lm, lv, big, steps=args.large_steps, J=JL, step0=3, lr=LR, ws=lws)
+        l1.record(stream)
+        torch.cuda.synchronize(dev)
+        api.profile(False)
+        lms = max_over_ranks(l0.elapsed_time(l1) / args.large_steps, dev)
+        fm, fn = api.profile_read("fused_fit")
+        lavg = fm / max(1, fn)
+        lops = algorithmic_ops(big_np, RL)
+        lach = lops / (lavg * 1e-3) / 1e12
+        large = {"R": RL, "J_per_step": JL, "value": JL * ws / (lms * 1e-3), "unit": "query-pts/s",
+                 "ms_per_step": lms, "fused_ms": lavg, "achieved": lach, "peak": peak,
+                 "unit_roofline": "T FP32 op/s", "frac": lach / peak, "ops_per_launch": lops,
+                 "steps": args.large_steps, "l2": "one 256 MiB batch, larger than L2"}
+        del big, big_np, lp, lm, lv, lws
 
     # ---- mean-shift offset initialisation (Sec. 3.3): R^3 centres x 16384
     # surface points, 13 FP32-pipe operations and one ex2 per pair
@@ -667,6 +703,7 @@ def main():
             "variants": variants,
             "cosine_series": cosine,
             "graph_fit": graph_fit,
+            "fit_64cubed_2p24": large,
             "cpu_baseline": cpu_line,
             "clocks": clocks,
             "gpu_launches": launches,

@@ -227,8 +227,8 @@ efunc_status efunc_adam_step(const efunc_adam *adam, int64_t n, float *params, f
  *   workspace  at least efunc_workspace_bytes; with efunc_fit_workspace_bytes
  *            the sort of batch s+1 runs on a sort stream of the library
  *            alongside batch s (the copy and sort streams and their events
- *            are shared per device: calls of efunc_fit on one device must
- *            not run concurrently from several host threads). */
+ *            are shared per device; fits called on one device from several
+ *            host threads enqueue their steps one call at a time). */
 efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t loss, float eikonal_weight,
                        float *params, float *m, float *v, const float *qo, int64_t J, int32_t n_batches,
                        int32_t steps, int64_t step0, float *stats, void *workspace, size_t workspace_bytes,

@@ -31,8 +31,10 @@ std::vector<cudaEvent_t> g_free_events;
 double g_ms[K_COUNT];
 int64_t g_count[K_COUNT];
 int64_t g_launches = 0;
-// set while this thread captures a CUDA graph: launches are counted, not timed
+// set while this thread captures a CUDA graph: its launches are counted in
+// g_captured (they run once per replay), not timed
 thread_local bool g_in_capture = false;
+thread_local int64_t g_captured = 0;
 
 const char *const kKernelNames[K_COUNT] = {"bin",       "scan_reduce", "scan_top",       "scan_emit", "scatter",
                                            "pack_keys", "forward",     "fused_backward", "fused_fit", "adam",
@@ -77,9 +79,13 @@ int drain_pending()
 
 void launch_begin(int kid, cudaStream_t s)
 {
+    if (g_in_capture) {
+        ++g_captured;
+        return;
+    }
     std::lock_guard<std::mutex> lk(g_prof_mu);
     ++g_launches;
-    if (!g_prof_on || g_in_capture) return;
+    if (!g_prof_on) return;
     Pending p{kid, take_event(), nullptr};
     if (p.start) cudaEventRecord(p.start, s);
     g_pending.push_back(p);
@@ -280,6 +286,7 @@ struct CopyPipe {
     cudaEvent_t consumed[2] = {nullptr, nullptr};
     cudaEvent_t packed = nullptr;
     cudaEvent_t joined = nullptr;   // the sort stream's end of a captured period
+    std::mutex mu;                  // held by a fit while it enqueues its steps
     cudaStream_t capture_stream = nullptr;   // origin of graph captures (the caller's may be the legacy stream)
 };
 constexpr int kMaxPipes = 64;
@@ -478,6 +485,7 @@ efunc_status fit_pipelined(const efunc_grid *grid, const efunc_adam *adam, int32
     float *grad = vw.grad();
     CopyPipe *pipe = nullptr;
     if (copy_pipe(&pipe) != cudaSuccess) return cuda_fail();
+    std::lock_guard<std::mutex> pipe_lock(pipe->mu);   // fits on one device enqueue one at a time
     cudaStream_t ss = pipe->sort_stream;
     const size_t batch_bytes = (size_t)J * 16;
     auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * (size_t)J * 4; };
@@ -569,6 +577,7 @@ efunc_status fit_graph(const efunc_grid *grid, const efunc_adam *adam, int32_t l
     float *grad = vw.grad();
     CopyPipe *pipe = nullptr;
     if (copy_pipe(&pipe) != cudaSuccess) return cuda_fail();
+    std::lock_guard<std::mutex> pipe_lock(pipe->mu);   // fits on one device enqueue one at a time
     cudaStream_t ss = pipe->sort_stream;
     auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * (size_t)J * 4; };
     const bool eik = eikonal_weight > 0.f;
@@ -624,13 +633,9 @@ efunc_status fit_graph(const efunc_grid *grid, const efunc_adam *adam, int32_t l
     if (replays > 0) {
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
-        int64_t before = 0, captured = 0;
-        {
-            std::lock_guard<std::mutex> lk(g_prof_mu);
-            before = g_launches;
-        }
         cudaStream_t cs = pipe->capture_stream;
         if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_fail();
+        g_captured = 0;
         g_in_capture = true;
         bool ok = true;
         for (int32_t it = 0; it < period && ok; ++it) ok = issue_step(it, it == 0, true, cs);
@@ -639,11 +644,7 @@ efunc_status fit_graph(const efunc_grid *grid, const efunc_adam *adam, int32_t l
              cudaStreamWaitEvent(cs, pipe->joined, 0) == cudaSuccess;
         g_in_capture = false;
         const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
-        {
-            std::lock_guard<std::mutex> lk(g_prof_mu);
-            captured = g_launches - before;
-            g_launches = before;   // captured launches run once per replay
-        }
+        const int64_t captured = g_captured;
         cudaError_t e = ce;
         if (ok && e == cudaSuccess && graph) e = cudaGraphInstantiate(&exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
@@ -673,6 +674,7 @@ efunc_status pipelined_device_fit(const Views &vw, int R, const float *qo, int64
 {
     CopyPipe *pipe = nullptr;
     if (copy_pipe(&pipe) != cudaSuccess) return cuda_fail();
+    std::lock_guard<std::mutex> pipe_lock(pipe->mu);   // fits on one device enqueue one at a time
     cudaStream_t ss = pipe->sort_stream;
     auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * (size_t)J * 4; };
     for (int b = 0; b < 2; ++b)
@@ -871,8 +873,10 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
     // Host batches: copies run on the library's copy stream into two staging
     // buffers, batch it+1 landing while batch it is computed.
     CopyPipe *pipe = nullptr;
+    std::unique_lock<std::mutex> pipe_lock;
     if (q_host) {
         if (copy_pipe(&pipe) != cudaSuccess) return cuda_fail();
+        pipe_lock = std::unique_lock<std::mutex>(pipe->mu);   // fits on one device enqueue one at a time
         for (int b = 0; b < 2; ++b)   // buffers free once the caller's earlier work is done
             if (cudaEventRecord(pipe->freed[b], s) != cudaSuccess) return cuda_fail();
         if (cudaStreamWaitEvent(pipe->stream, pipe->freed[0], 0) != cudaSuccess ||

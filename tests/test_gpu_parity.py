@@ -408,6 +408,42 @@ def test_graph_fit_matches_stream_fit(eikonal):
     np.testing.assert_allclose(out[True][0][solid], out[False][0][solid], rtol=1e-4, atol=1e-6)
 
 
+def test_fits_from_two_host_threads():
+    """Two host threads fitting their own grids on their own streams (one
+    stream-issued, one graph-replayed, sharing the library's per-device sort
+    stream and events) take the same steps as the same fits run one after
+    the other."""
+    import threading
+    R, J, steps = 8, 30000, 9
+    qo = to_dev(synth.sample_batch(synth.random_union(8), 3 * J, seed=8))
+
+    def run(seed, graph, out, key):
+        p0 = synth.init_params(R, seed=seed)
+        pd, m, v = to_dev(p0), torch.zeros(p0.size, device=DEV), torch.zeros(p0.size, device=DEV)
+        stats = torch.zeros(2 * steps, device=DEV)
+        st = torch.cuda.Stream()
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            api.efunc_fit(pd, m, v, qo, steps=steps, J=J, n_batches=3, loss="mse", stats=stats, lr=1e-3,
+                          log_beta0=lb32(R), graph=graph, ws=api.Workspace(DEV))
+        st.synchronize()
+        out[key] = (pd.cpu().numpy().reshape(-1), m.cpu().numpy().reshape(-1), stats.cpu().numpy())
+
+    alone, together = {}, {}
+    for key, (seed, graph) in {"a": (1, False), "b": (2, True)}.items():
+        run(seed, graph, alone, key)
+    threads = [threading.Thread(target=run, args=(seed, graph, together, key))
+               for key, (seed, graph) in {"a": (1, False), "b": (2, True)}.items()]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for key in ("a", "b"):
+        np.testing.assert_allclose(together[key][2], alone[key][2], rtol=1e-5)
+        solid = np.abs(alone[key][1]) > 1e-2 * np.abs(alone[key][1]).max()
+        np.testing.assert_allclose(together[key][0][solid], alone[key][0][solid], rtol=1e-4, atol=1e-6)
+
+
 def test_graph_fit_rejects_host_memory_and_capture():
     R, J = 4, 1000
     qo = synth.sample_batch(synth.sphere(0.5), J, seed=1)
