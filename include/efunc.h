@@ -270,7 +270,7 @@ efunc_status efunc_fit_graph(const efunc_grid *grid, const efunc_adam *adam, int
  * keeps it until the process exits).
  *   - Limit: requests whose efunc_workspace_bytes(grid, J) exceeds 32 MiB
  *     return EFUNC_ERR_WORKSPACE with nothing enqueued.  That admits up to
- *     514,048 queries at R = 32, 587,168 at R = 16 and 26,112 at R = 64;
+ *     514,048 queries at R = 32, 585,456 at R = 16 and 26,112 at R = 64;
  *     larger grids need efunc_forward with a caller workspace.
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device current); make that first call before

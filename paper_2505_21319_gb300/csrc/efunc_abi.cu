@@ -8,6 +8,7 @@
 
 #include "adam_clock.cuh"
 #include "common.cuh"
+#include "sort_copies.cuh"
 
 namespace efunc {
 
@@ -113,7 +114,7 @@ Layout make_layout(int R, int64_t J, int key_records, int channels, bool two_sor
     const size_t A = 256;
     size_t off = 0;
     L.ctrl = off;      off = align_up(off + sizeof(Ctrl), A);
-    L.hist = off;      off = align_up(off + (size_t)L.nbins * 4, A);
+    L.hist = off;      off = align_up(off + (size_t)hist_entries(L.nbins) * 4, A);
     L.blocksum = off;  off = align_up(off + (size_t)L.nscan_blocks * 8, A);
     L.rank = off;      off = align_up(off + (size_t)J * 4, A);
     L.sorted = off;    off = align_up(off + (size_t)J * 16, A);
@@ -125,7 +126,7 @@ Layout make_layout(int R, int64_t J, int key_records, int channels, bool two_sor
     L.two_sort_buffers = two_sort_buffers;
     if (two_sort_buffers) {
         L.ctrl2 = off;     off = align_up(off + sizeof(Ctrl), A);
-        L.hist2 = off;     off = align_up(off + (size_t)L.nbins * 4, A);
+        L.hist2 = off;     off = align_up(off + (size_t)hist_entries(L.nbins) * 4, A);
         L.blocksum2 = off; off = align_up(off + (size_t)L.nscan_blocks * 8, A);
         L.rank2 = off;     off = align_up(off + (size_t)J * 4, A);
         L.sorted2 = off;   off = align_up(off + (size_t)J * 16, A);
@@ -204,7 +205,7 @@ cudaError_t sort_into_buf(const SortBuf &b, const Layout &L, int R, const float 
 {
     cudaError_t e = cudaMemsetAsync(b.ctrl, 0, sizeof(Ctrl), s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(b.hist, 0, (size_t)L.nbins * 4, s);
+    e = cudaMemsetAsync(b.hist, 0, (size_t)hist_entries(L.nbins) * 4, s);
     if (e != cudaSuccess) return e;
     SortArgs a{};
     a.q = q;
@@ -230,7 +231,7 @@ cudaError_t sort_into(const Views &v, int R, const float *q, int64_t J, int q_st
 {
     cudaError_t e = cudaMemsetAsync(v.ctrl(), 0, sizeof(Ctrl), s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(v.hist(), 0, (size_t)v.L.nbins * 4, s);
+    e = cudaMemsetAsync(v.hist(), 0, (size_t)hist_entries(v.L.nbins) * 4, s);
     if (e != cudaSuccess) return e;
     SortArgs a{};
     a.q = q;

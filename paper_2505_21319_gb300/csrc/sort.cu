@@ -12,8 +12,11 @@
 //   scatter  query -> position offset[bin] + rank: float4 row + permutation
 //            (the permutation only when a caller needs outputs in its order)
 // The scan also emits the work items of the fused kernel: every non-empty bin
-// yields ceil(count / kChunk) slices of at most kChunk sorted queries.
+// yields ceil(count / kChunk) slices of at most kChunk sorted queries.  On
+// coarse grids the histogram has several copies (sort_copies.cuh); the
+// kernels take the copy count K as a template argument.
 #include "common.cuh"
+#include "sort_copies.cuh"
 
 namespace efunc {
 
@@ -55,7 +58,15 @@ __device__ __forceinline__ uint32_t query_bin(float x, float y, float z, float h
 // loads and atomics in flight per thread.
 constexpr int kUnroll = 4;
 
-template <bool VEC4>
+// The histogram copy of query j (K copies): the 32 queries of a warp's
+// coalesced load share one, consecutive warps cycle through them.
+template <int K>
+__device__ __forceinline__ uint32_t copy_of(int64_t j)
+{
+    return K == 1 ? 0u : (uint32_t)(j >> 5) & (uint32_t)(K - 1);
+}
+
+template <bool VEC4, int K>
 __global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) bin_kernel(SortArgs a)
 {
     const float half_r = (float)a.R * 0.5f, rmax = (float)(a.R - 1);
@@ -70,25 +81,28 @@ __global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) bin_kernel(SortA
             bin[u] = query_bin(x, y, z, half_r, rmax, a.P);
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) r[u] = atomicAdd(&a.hist[bin[u]], 1u);
+        for (int u = 0; u < kUnroll; ++u)
+            r[u] = atomicAdd(&a.hist[(int64_t)copy_of<K>(j + u * stride) * a.nbins + bin[u]], 1u);
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) a.rank[j + u * stride] = r[u];
+        for (int u = 0; u < kUnroll; ++u) a.rank[j + u * stride] = (copy_of<K>(j + u * stride) << kRankBits) | r[u];
     }
     for (; j < a.J; j += stride) {
         float x, y, z, w;
         load_query(a.q, j, a.q_stride, VEC4, x, y, z, w);
-        a.rank[j] = atomicAdd(&a.hist[query_bin(x, y, z, half_r, rmax, a.P)], 1u);
+        const uint32_t c = copy_of<K>(j);
+        a.rank[j] = (c << kRankBits) |
+                    atomicAdd(&a.hist[(int64_t)c * a.nbins + query_bin(x, y, z, half_r, rmax, a.P)], 1u);
     }
 }
 
 // Coarse grids (few bins, hundreds of queries per bin) make the global
 // histogram atomics contend.  There every block counts a contiguous slice of
 // queries in a shared-memory histogram first (local arrival ranks), then
-// reserves each non-empty bin's range with one global atomic, then adds the
-// reserved base to its queries' ranks.
-constexpr int kSmemBinsMax = 12288;   // 48 KB of counters
+// reserves each non-empty bin's range with one global atomic (in histogram
+// copy blockIdx mod K), then adds the reserved base to its queries' ranks.
+constexpr int kSmemBinsMax = (int)kCoarseBins;   // 48 KB of counters
 
-template <bool VEC4>
+template <bool VEC4, int K>
 __global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) bin_smem_kernel(SortArgs a, int64_t slice)
 {
     extern __shared__ uint32_t s_hist[];
@@ -103,15 +117,17 @@ __global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) bin_smem_kernel(
         a.rank[j] = atomicAdd(&s_hist[query_bin(x, y, z, half_r, rmax, a.P)], 1u);
     }
     __syncthreads();
+    const uint32_t copy = K == 1 ? 0u : blockIdx.x & (uint32_t)(K - 1);
+    uint32_t *h = a.hist + (int64_t)copy * a.nbins;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         const uint32_t c = s_hist[i];
-        if (c) s_hist[i] = atomicAdd(&a.hist[i], c);
+        if (c) s_hist[i] = atomicAdd(&h[i], c);
     }
     __syncthreads();
     for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         float x, y, z, w;
         load_query(a.q, j, a.q_stride, VEC4, x, y, z, w);
-        a.rank[j] += s_hist[query_bin(x, y, z, half_r, rmax, a.P)];
+        a.rank[j] = (copy << kRankBits) | (a.rank[j] + s_hist[query_bin(x, y, z, half_r, rmax, a.P)]);
     }
 }
 
@@ -151,13 +167,24 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long
     return prefix + x - v;
 }
 
+// A bin's count: the sum of its K histogram copies.
+template <int K>
+__device__ __forceinline__ uint32_t bin_count(const SortArgs &a, int64_t b)
+{
+    uint32_t c = a.hist[b];
+#pragma unroll
+    for (int k = 1; k < K; ++k) c += a.hist[k * a.nbins + b];
+    return c;
+}
+
+template <int K>
 __global__ void __launch_bounds__(kScanThreads, kSortMinBlocks) scan_reduce_kernel(SortArgs a)
 {
     const int64_t b0 = (int64_t)blockIdx.x * kScanSeg + (int64_t)threadIdx.x * kScanPerThread;
     unsigned long long s = 0;
 #pragma unroll
     for (int k = 0; k < kScanPerThread; ++k)
-        if (b0 + k < a.nbins) s += pack(a.hist[b0 + k]);
+        if (b0 + k < a.nbins) s += pack(bin_count<K>(a, b0 + k));
     unsigned long long total;
     block_exclusive_scan(s, total);
     if (threadIdx.x == 0) a.blocksum[blockIdx.x] = total;
@@ -177,6 +204,7 @@ __global__ void __launch_bounds__(kScanThreads, kSortMinBlocks) scan_top_kernel(
     if (threadIdx.x == 0) a.ctrl->n_items = (int)(carry >> 32);
 }
 
+template <int K>
 __global__ void __launch_bounds__(kScanThreads, kSortMinBlocks) scan_emit_kernel(SortArgs a)
 {
     const int64_t b0 = (int64_t)blockIdx.x * kScanSeg + (int64_t)threadIdx.x * kScanPerThread;
@@ -184,7 +212,7 @@ __global__ void __launch_bounds__(kScanThreads, kSortMinBlocks) scan_emit_kernel
     unsigned long long s = 0;
 #pragma unroll
     for (int k = 0; k < kScanPerThread; ++k) {
-        cnt[k] = b0 + k < a.nbins ? a.hist[b0 + k] : 0u;
+        cnt[k] = b0 + k < a.nbins ? bin_count<K>(a, b0 + k) : 0u;
         s += pack(cnt[k]);
     }
     unsigned long long total;
@@ -194,7 +222,19 @@ __global__ void __launch_bounds__(kScanThreads, kSortMinBlocks) scan_emit_kernel
         if (b0 + k >= a.nbins) break;
         const uint32_t start = (uint32_t)(run & 0xffffffffull);
         const uint32_t item0 = (uint32_t)(run >> 32);
-        a.hist[b0 + k] = start;   // counts become exclusive offsets, in place
+        // counts become exclusive offsets, in place: a bin's copies take
+        // consecutive ranges from its start
+        if (K == 1) {
+            a.hist[b0 + k] = start;
+        } else {
+            uint32_t off = start;
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                const uint32_t n = a.hist[c * a.nbins + b0 + k];
+                a.hist[c * a.nbins + b0 + k] = off;
+                off += n;
+            }
+        }
         if (cnt[k]) {
             int ux, uy, uz;
             cell_of_bin((uint32_t)(b0 + k), a.P, ux, uy, uz);
@@ -210,7 +250,7 @@ __global__ void __launch_bounds__(kScanThreads, kSortMinBlocks) scan_emit_kernel
     }
 }
 
-template <bool VEC4>
+template <bool VEC4, int K>
 __global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) scatter_kernel(SortArgs a)
 {
     const float half_r = (float)a.R * 0.5f, rmax = (float)(a.R - 1);
@@ -225,7 +265,11 @@ __global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) scatter_kernel(S
             pos[u] = a.rank[j + u * stride];
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) pos[u] += a.hist[query_bin(v[u].x, v[u].y, v[u].z, half_r, rmax, a.P)];
+        for (int u = 0; u < kUnroll; ++u) {
+            const uint32_t rk = pos[u];   // (copy, rank in the copy)
+            const uint32_t bin = query_bin(v[u].x, v[u].y, v[u].z, half_r, rmax, a.P);
+            pos[u] = K == 1 ? a.hist[bin] + rk : a.hist[(int64_t)(rk >> kRankBits) * a.nbins + bin] + (rk & kRankMask);
+        }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             a.sorted[pos[u]] = v[u];
@@ -236,7 +280,9 @@ __global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) scatter_kernel(S
         float x, y, z, w;
         load_query(a.q, j, a.q_stride, VEC4, x, y, z, w);
         const uint32_t bin = query_bin(x, y, z, half_r, rmax, a.P);
-        const uint32_t pos = a.hist[bin] + a.rank[j];
+        const uint32_t rk = a.rank[j];
+        const uint32_t pos =
+            K == 1 ? a.hist[bin] + rk : a.hist[(int64_t)(rk >> kRankBits) * a.nbins + bin] + (rk & kRankMask);
         a.sorted[pos] = make_float4(x, y, z, w);
         if (a.perm) a.perm[pos] = (int)j;
     }
@@ -257,9 +303,9 @@ int stream_grid(int64_t work, int threads, int blocks_per_sm)
     return (int)(blocks < 1 ? 1 : blocks);
 }
 
-}  // namespace
-
-cudaError_t launch_sort(const SortArgs &a, cudaStream_t s, int narrow_blocks)
+// The five launches of one sort, with K histogram copies.
+template <int K>
+cudaError_t launch_sort_k(const SortArgs &a, cudaStream_t s, int narrow_blocks)
 {
     const bool vec4 = a.q_stride == 4 && (reinterpret_cast<uintptr_t>(a.q) & 15u) == 0;
     // narrow: narrow_blocks small blocks per SM, to run beside a persistent fit kernel
@@ -275,16 +321,16 @@ cudaError_t launch_sort(const SortArgs &a, cudaStream_t s, int narrow_blocks)
         const int64_t blocks = stream_grid(a.J, kWideThreads, 2);
         const int64_t slice = (a.J + blocks - 1) / blocks;
         const size_t smem = (size_t)a.nbins * 4;
-        if (vec4) bin_smem_kernel<true><<<(unsigned)blocks, kWideThreads, smem, s>>>(a, slice);
-        else bin_smem_kernel<false><<<(unsigned)blocks, kWideThreads, smem, s>>>(a, slice);
+        if (vec4) bin_smem_kernel<true, K><<<(unsigned)blocks, kWideThreads, smem, s>>>(a, slice);
+        else bin_smem_kernel<false, K><<<(unsigned)blocks, kWideThreads, smem, s>>>(a, slice);
     } else {
-        if (vec4) bin_kernel<true><<<g, threads, 0, s>>>(a);
-        else bin_kernel<false><<<g, threads, 0, s>>>(a);
+        if (vec4) bin_kernel<true, K><<<g, threads, 0, s>>>(a);
+        else bin_kernel<false, K><<<g, threads, 0, s>>>(a);
     }
     launch_end(K_BIN, s);
 
     launch_begin(K_SCAN_REDUCE, s);
-    scan_reduce_kernel<<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
+    scan_reduce_kernel<K><<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
     launch_end(K_SCAN_REDUCE, s);
 
     launch_begin(K_SCAN_TOP, s);
@@ -292,14 +338,22 @@ cudaError_t launch_sort(const SortArgs &a, cudaStream_t s, int narrow_blocks)
     launch_end(K_SCAN_TOP, s);
 
     launch_begin(K_SCAN_EMIT, s);
-    scan_emit_kernel<<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
+    scan_emit_kernel<K><<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
     launch_end(K_SCAN_EMIT, s);
 
     launch_begin(K_SCATTER, s);
-    if (vec4) scatter_kernel<true><<<g, threads, 0, s>>>(a);
-    else scatter_kernel<false><<<g, threads, 0, s>>>(a);
+    if (vec4) scatter_kernel<true, K><<<g, threads, 0, s>>>(a);
+    else scatter_kernel<false, K><<<g, threads, 0, s>>>(a);
     launch_end(K_SCATTER, s);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sort(const SortArgs &a, cudaStream_t s, int narrow_blocks)
+{
+    return hist_copies(a.nbins) == 1 ? launch_sort_k<1>(a, s, narrow_blocks)
+                                     : launch_sort_k<kCoarseCopies>(a, s, narrow_blocks);
 }
 
 }  // namespace efunc
