@@ -46,3 +46,14 @@ def test_status_codes_raise_with_their_description():
     with pytest.raises(B.EfuncError, match="invalid argument"):
         B.check("efunc_forward", 1)
     B.check("efunc_forward", 0)
+    # a CUDA failure names the CUDA error behind it (none recorded here)
+    with pytest.raises(B.EfuncError, match="CUDA runtime error: cudaSuccess") as info:
+        B.check("efunc_fit", 2)
+    assert info.value.cuda_error == 0 and info.value.code == 2
+
+
+def test_graph_fit_is_the_pipelined_schedule():
+    p = torch.zeros(8 ** 3 * 13)
+    with pytest.raises(ValueError):
+        api.efunc_fit(p, p, p, torch.zeros(10, 4), steps=1, graph=True, pipelined=False)
+    assert api.launch_count() == 0
