@@ -72,6 +72,53 @@ MUTANTS = {
     "cosine weight read as cos(b pi (x + y + z))": (
         "return cos(b * pi * q[0]) * cos(b * pi * q[1]) * cos(b * pi * q[2]);",
         "return cos(b * pi * (q[0] + q[1] + q[2]));"),
+    "window upper clamp at R instead of R - 1": (
+        "float lo = -1.0f, hi = (float)(R - 1);",
+        "float lo = -1.0f, hi = (float)R;"),
+    "centres at cell corners": (
+        "return -1.0 + ((double)idx + 0.5) * (2.0 / (double)R);",
+        "return -1.0 + ((double)idx) * (2.0 / (double)R);"),
+    "global brute force over grid keys only": (
+        "            for (int s = 0; s < 2; ++s) {\n                key_t_ k = make_key(params, R, log_beta0, a, b, c, s);\n"
+        "                double r[3], d2;",
+        "            for (int s = 0; s < 1; ++s) {\n                key_t_ k = make_key(params, R, log_beta0, a, b, c, s);\n"
+        "                double r[3], d2;"),
+    "second order: T without its factor -2": (
+        "const double T = -2.0 * (u[0] * V[0] + u[1] * V[1] + u[2] * V[2]);",
+        "const double T = (u[0] * V[0] + u[1] * V[1] + u[2] * V[2]);"),
+    "second order: dG/dbeta without the -2 dlt u.r term": (
+        "const double g_beta = w * (-d2 * hH - 2.0 * dlt * ur) + go * w * (-d2 * dlt);",
+        "const double g_beta = w * (-d2 * hH) + go * w * (-d2 * dlt);"),
+    "second order: dG/dDelta without 2 beta dlt u": (
+        "g_p[x] = w * (2.0 * k.beta * r[x] * hH - k.d[x] * e1 + 2.0 * k.beta * dlt * u[x]) +",
+        "g_p[x] = w * (2.0 * k.beta * r[x] * hH - k.d[x] * e1) +"),
+    "mean shift without the largest-exponent shift": (
+        "const double w = exp(-bw * d2 - M);",
+        "const double w = exp(-bw * d2);"),
+    "variant: quadratic gradient with a 1/2": (
+        "g[a] += S[a][b] * x[b];",
+        "g[a] += 0.5 * S[a][b] * x[b];"),
+    "variant: cubic gradient with 1/6 instead of 1/2": (
+        "g[a] += 0.5 * T[a][b][c] * x[b] * x[c];",
+        "g[a] += T[a][b][c] * x[b] * x[c] / 6.0;"),
+    "variant: S_xy stored on one side only": (
+        "S[0][1] = S[1][0] = phi[7];",
+        "S[0][1] = phi[7];"),
+    "cosine backward without the band weight": (
+        "variant_one(params + b * band, grad + b * band, gS[j] * cosine_weight(b, qj), R, W, log_beta0, 1, 1, 1,",
+        "variant_one(params + b * band, grad + b * band, gS[j], R, W, log_beta0, 1, 1, 1,"),
+    "cosine bands counted from 1": (
+        "s += cosine_weight(b, qj) * O;",
+        "s += cosine_weight(b + 1, qj) * O;"),
+    "MSE gradient without the factor 2": (
+        "gO[j] = 2.0 * diff / (double)J;",
+        "gO[j] = diff / (double)J;"),
+    "AdamW decay and Adam L2 penalty swapped": (
+        "        if (decoupled)\n            p[i] *= 1.0 - lr * wd;",
+        "        if (!decoupled)\n            p[i] *= 1.0 - lr * wd;"),
+    "Adam eps inside the square root": (
+        "p[i] -= lr * mhat / (sqrt(vhat) + eps);",
+        "p[i] -= lr * mhat / sqrt(vhat + eps);"),
 }
 
 
