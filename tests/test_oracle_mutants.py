@@ -119,6 +119,15 @@ MUTANTS = {
     "Adam eps inside the square root": (
         "p[i] -= lr * mhat / (sqrt(vhat) + eps);",
         "p[i] -= lr * mhat / sqrt(vhat + eps);"),
+    "tolerance diagnostic: kappa without the weights' own rounding": (
+        "k_sum += exp(expo - M) / e * (fabs(expo) + 1.0) * fabs(f - O);",
+        "k_sum += exp(expo - M) / e * fabs(expo) * fabs(f - O);"),
+    "tolerance diagnostic: dO/dq sensitivity without its factor 2": (
+        "*dq_sens = 2.0 * sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);",
+        "*dq_sens = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);"),
+    "tolerance diagnostic: variant fabs as |f| instead of its terms": (
+        "fa += fabs(k.phi[i] * fu);",
+        "fa += k.phi[i] * fu;"),
 }
 
 

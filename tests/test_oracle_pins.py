@@ -693,3 +693,83 @@ def test_cosine_series_gradients_match_central_differences():
                       / (2 * hstep))
             an.append(flat[i, s])
     np.testing.assert_allclose(np.array(an), np.array(fd), rtol=2e-6, atol=2e-8 * max(1.0, np.abs(an).max()))
+
+
+# ------------------------------------------------- tolerance diagnostics
+
+def test_kappa_is_the_attained_first_order_sensitivity():
+    """kappa, from which the FP32 forward tolerance is derived, is the first
+    order worst case of O under relative perturbations of size eps of every
+    key's exponent and weight: the adversarial perturbation (exponent by
+    eps sign((f - O) expo), weight by eps sign(f - O)) moves O by eps kappa,
+    and random perturbations of the same size by less."""
+    R, lb, eps = 3, 2.0, 1e-7
+    p = synth.random_params(R, seed=77, delta_scale=0.6, b_scale=0.6).astype(np.float64)
+    q = queries(78, 16)
+    O, _, kappa = oracle.forward(p, q, R, W=R, log_beta0=lb, want_kappa=True)
+    pos, beta, o, d = keys_of(p, R, lb)
+    rng = synth.rng(79)
+
+    def blend(ex, w, f):
+        lw = np.exp(ex - ex.max()) * w
+        return (lw * f).sum() / lw.sum()
+
+    for j in range(q.shape[0]):
+        r = q[j] - pos
+        expo = -beta * (r ** 2).sum(1)
+        f = o + (d * r).sum(1)
+        s = np.sign(f - O[j])
+        worst = blend(expo * (1 + eps * s * np.sign(expo)), 1 + eps * s, f)
+        assert abs(abs(worst - O[j]) / eps - kappa[j]) <= 1e-5 * kappa[j] + 1e-8
+        for _ in range(3):
+            rnd = blend(expo * (1 + eps * rng.uniform(-1, 1, expo.size)), 1 + eps * rng.uniform(-1, 1, expo.size), f)
+            assert abs(rnd - O[j]) <= eps * kappa[j] * (1 + 1e-5) + 1e-15
+
+
+def test_dq_sensitivity_is_the_norm_of_the_lse_gradient():
+    """dq_sens = 2 ||sum softmax beta (q - key)||, the factor by which an
+    error in O enters dO/dq, equals ||grad_q lse|| (lse = log sum
+    exp(-beta ||q - key||^2)): central differences of the oracle's lse."""
+    R, lb, h = 3, 2.0, 1e-6
+    p = synth.random_params(R, seed=81, delta_scale=0.6, b_scale=0.6).astype(np.float64)
+    q = queries(82, 12)
+    _, _, sens = oracle.forward(p, q, R, W=R, log_beta0=lb, want_dq_sens=True)
+    grad = np.zeros((q.shape[0], 3))
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        _, lp = oracle.forward(p, q + e, R, W=R, log_beta0=lb)
+        _, lm = oracle.forward(p, q - e, R, W=R, log_beta0=lb)
+        grad[:, a] = (lp - lm) / (2 * h)
+    np.testing.assert_allclose(sens, np.linalg.norm(grad, axis=1), rtol=1e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2, 3])
+def test_variant_fabs_of_a_single_key_is_the_sum_of_its_taylor_terms(deg):
+    """fabs, from which the variant tolerance is derived, is for a single key
+    (R = 1, grid keys only: softmax 1) the sum of the absolute values of the
+    distinct Taylor terms of f at x = q - key: |o|, |d_a x_a|, |S_aa x_a^2| / 2,
+    |S_ab x_a x_b| (a < b), |T_aaa x_a^3| / 6, |T_aab x_a^2 x_b| / 2 (a != b),
+    |T_xyz x y z|, with the channel order of Eq. func-offset's tuple."""
+    rng = synth.rng(90 + deg)
+    nv = [1, 4, 10, 20][deg]
+    for _ in range(5):
+        phi = rng.uniform(-2, 2, nv)
+        p = np.concatenate([[rng.uniform(-1, 1)], phi])[None, :]   # (b, phi)
+        x = rng.uniform(-0.8, 0.8, (4, 3))
+        _, _, kap, fab = oracle.variant_forward(p, x, 1, 1, deg, 1, log_beta0=1.0, want_diag=True)
+        for j in range(4):
+            X, Y, Z = x[j]
+            terms = [phi[0]]
+            if deg >= 1:
+                terms += [phi[1] * X, phi[2] * Y, phi[3] * Z]
+            if deg >= 2:
+                terms += [phi[4] * X * X / 2, phi[5] * Y * Y / 2, phi[6] * Z * Z / 2,
+                          phi[7] * X * Y, phi[8] * X * Z, phi[9] * Y * Z]
+            if deg >= 3:
+                terms += [phi[10] * X ** 3 / 6, phi[11] * Y ** 3 / 6, phi[12] * Z ** 3 / 6,
+                          phi[13] * X * X * Y / 2, phi[14] * X * X * Z / 2, phi[15] * X * Y * Y / 2,
+                          phi[16] * Y * Y * Z / 2, phi[17] * X * Z * Z / 2, phi[18] * Y * Z * Z / 2,
+                          phi[19] * X * Y * Z]
+            assert abs(fab[j] - np.abs(terms).sum()) <= 1e-12 * (1 + np.abs(terms).sum())
+            assert abs(kap[j]) <= 1e-12   # one key: f - O = 0
