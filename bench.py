@@ -300,7 +300,7 @@ def run_reference(args, ws, rank):
     m = np.zeros_like(params)
     v = np.zeros_like(params)
     qo = synth.sample_batch(synth.random_union(0), 1 << 18, seed=0)
-    budget = 150.0   # seconds for warm-up + timed steps
+    budget = float(args.reference_seconds)   # seconds for warm-up + timed steps
     with ctx.Pool(cores) as pool:
         n = 256 * cores
         t0 = time.perf_counter()
@@ -346,6 +346,8 @@ def main():
     ap.add_argument("--graph-steps", type=int, default=500)
     ap.add_argument("--large-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reference-seconds", type=float, default=150.0,
+                    help="--impl reference: seconds of oracle work over warm-up and timed steps")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

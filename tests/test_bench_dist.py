@@ -38,3 +38,26 @@ def test_max_over_ranks_gloo_two_processes():
 def test_max_over_ranks_single_process_is_identity():
     import bench
     assert bench.max_over_ranks(3.25) == 3.25
+
+
+def test_reference_arm_prints_the_oracle_line(tmp_path):
+    """bench.py --impl reference times the FP64 oracle on the host cores (a
+    bounded sample per step) and prints one JSON line with impl=reference;
+    ranks other than 0 print nothing and exit 0."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "3",
+           "--reference-seconds", "1"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "query-pts/s"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=root, env=env)
+    assert r.returncode == 0 and r.stdout.strip() == ""
