@@ -63,7 +63,8 @@ typedef enum {
     EFUNC_ERR_CUDA = 2,        /* a CUDA runtime call failed */
     EFUNC_ERR_WORKSPACE = 3,   /* workspace NULL, misaligned or too small */
     EFUNC_ERR_NONFINITE = 4,   /* a hyper-parameter is NaN or infinite */
-    EFUNC_ERR_UNSUPPORTED = 5  /* valid request outside the implemented set */
+    EFUNC_ERR_UNSUPPORTED = 5, /* valid request outside the implemented set */
+    EFUNC_ERR_IO = 6           /* checkpoint file missing, unwritable, short or corrupt */
 } efunc_status;
 
 /* Grid description.  R in [1, 256]; W must be 2; log_beta0 is the log-scale
@@ -368,6 +369,48 @@ efunc_status efunc_cosine_fit(const efunc_grid *grid, int32_t bands, const efunc
                               float *params, float *m, float *v, const float *qo, int64_t J, int32_t n_batches,
                               int32_t steps, int64_t step0, float *stats, void *workspace, size_t workspace_bytes,
                               efunc_stream_t stream);
+
+/* ---------------------------------------------------- checkpoint / resume */
+
+/* A fit's state is its parameter grid, Adam's two moments and the number of
+ * steps taken (the representation is its own checkpoint: 13 R^3 floats,
+ * Sec. 3.1); with the configuration below, a later efunc_fit with
+ * step0 = step continues the same trajectory (up to the order of the FP32
+ * gradient atomics).  The file is flat and little-endian: a 128-byte header
+ * (magic "EFUNCCKP", format version 1, these fields, an FNV-1a 64 checksum of
+ * the header), params, m, v as n floats each, and an FNV-1a 64 checksum of
+ * those 12 n bytes.  Host code only: the arrays are HOST memory. */
+typedef struct {
+    int32_t R;          /* grid resolution */
+    int32_t W;          /* window half-width */
+    float log_beta0;
+    int32_t channels;   /* floats per centre: 13, efunc_variant_channels, or 5 B for B cosine bands */
+    int64_t n;          /* floats per array: R^3 * channels */
+    int64_t step;       /* Adam steps taken */
+    uint64_t seed;      /* the caller's sampling seed, stored as given */
+    int32_t loss;       /* efunc_loss */
+    efunc_adam adam;
+} efunc_checkpoint_info;
+
+/* Writes params, m, v ([host], info->n floats each) and info to path, through
+ * a temporary file renamed over path once complete (an interrupted save
+ * leaves the previous file).  EFUNC_ERR_ARG for an inconsistent info
+ * (n != R^3 * channels, step < 0, ...), EFUNC_ERR_IO if the file cannot be
+ * written. */
+efunc_status efunc_checkpoint_save(const char *path, const efunc_checkpoint_info *info, const float *params,
+                                   const float *m, const float *v);
+
+/* Reads and checks the header only (to size the arrays of a load).
+ * EFUNC_ERR_IO if the file is missing or its header is not a valid
+ * version-1 header (magic, sizes, checksum). */
+efunc_status efunc_checkpoint_info_read(const char *path, efunc_checkpoint_info *info);
+
+/* Reads a checkpoint into params, m, v ([host], capacity floats each) and
+ * info.  EFUNC_ERR_ARG if capacity < n; EFUNC_ERR_IO if the file is
+ * missing, short, longer than its contents, or a checksum does not match
+ * (the arrays' contents are then unspecified and info is not written). */
+efunc_status efunc_checkpoint_load(const char *path, efunc_checkpoint_info *info, float *params, float *m, float *v,
+                                   int64_t capacity);
 
 /* ------------------------------------------------------------ measurement */
 

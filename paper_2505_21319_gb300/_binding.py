@@ -17,7 +17,7 @@ c_size_t, c_void_p, c_char_p = ctypes.c_size_t, ctypes.c_void_p, ctypes.c_char_p
 P_float = ctypes.POINTER(ctypes.c_float)
 
 STATUS = {0: "EFUNC_OK", 1: "EFUNC_ERR_ARG", 2: "EFUNC_ERR_CUDA", 3: "EFUNC_ERR_WORKSPACE",
-          4: "EFUNC_ERR_NONFINITE", 5: "EFUNC_ERR_UNSUPPORTED"}
+          4: "EFUNC_ERR_NONFINITE", 5: "EFUNC_ERR_UNSUPPORTED", 6: "EFUNC_ERR_IO"}
 LOSS_L1, LOSS_MSE = 0, 1
 
 
@@ -32,6 +32,11 @@ class Adam(ctypes.Structure):
 
 class Variant(ctypes.Structure):
     _fields_ = [("sets", c_int32), ("degree", c_int32), ("learn_scale", c_int32)]
+
+
+class CheckpointInfo(ctypes.Structure):
+    _fields_ = [("R", c_int32), ("W", c_int32), ("log_beta0", c_float), ("channels", c_int32), ("n", c_int64),
+                ("step", c_int64), ("seed", ctypes.c_uint64), ("loss", c_int32), ("adam", Adam)]
 
 
 KEYS_GRID, KEYS_OFFSET, KEYS_BOTH = 1, 2, 3
@@ -56,6 +61,10 @@ SIGNATURES = {
     "efunc_fit": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Adam), c_int32, c_float, c_void_p, c_void_p,
                             c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int64, c_void_p, c_void_p, c_size_t,
                             c_void_p]),
+    "efunc_checkpoint_save": (c_int32, [c_char_p, ctypes.POINTER(CheckpointInfo), c_void_p, c_void_p, c_void_p]),
+    "efunc_checkpoint_info_read": (c_int32, [c_char_p, ctypes.POINTER(CheckpointInfo)]),
+    "efunc_checkpoint_load": (c_int32, [c_char_p, ctypes.POINTER(CheckpointInfo), c_void_p, c_void_p, c_void_p,
+                                        c_int64]),
     "efunc_last_cuda_error": (c_int32, []),
     "efunc_cuda_error_name": (ctypes.c_char_p, [c_int32]),
     "efunc_fit_graph": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Adam), c_int32, c_float, c_void_p, c_void_p,

@@ -384,6 +384,51 @@ def make_adam(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, decou
     return B.Adam(lr, beta1, beta2, eps, weight_decay, int(bool(decoupled)))
 
 
+def _host_f32(t: torch.Tensor, n: int, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or t.numel() != n:
+        raise ValueError(f"{name} must be a tensor of {n} floats")
+    return t.detach().to("cpu", torch.float32).contiguous()
+
+
+def save_checkpoint(path: str, params: torch.Tensor, m: torch.Tensor, v: torch.Tensor, step: int,
+                    channels: int = 13, log_beta0: float | None = None, W: int = 2, seed: int = 0,
+                    loss: str = "l1", **adam_kw) -> None:
+    """Write a fit's state (efunc_checkpoint_save): params, m, v (CUDA or CPU
+    tensors of R^3 * channels floats), the number of Adam steps taken and the
+    fit's configuration; efunc_fit(..., step0=step) continues it."""
+    n = params.numel()
+    if channels < 1 or n % channels:
+        raise ValueError("params must hold R^3 * channels floats")
+    R = round((n // channels) ** (1.0 / 3.0))
+    if R ** 3 * channels != n:
+        raise ValueError("params must hold R^3 * channels floats")
+    hp, hm, hv = (_host_f32(t, n, nm) for t, nm in ((params, "params"), (m, "m"), (v, "v")))
+    info = B.CheckpointInfo(R, W, default_log_beta0(R) if log_beta0 is None else float(log_beta0), channels, n,
+                            int(step), int(seed), {"l1": B.LOSS_L1, "mse": B.LOSS_MSE}[loss], make_adam(**adam_kw))
+    B.check("efunc_checkpoint_save", B.load().efunc_checkpoint_save(
+        str(path).encode(), ctypes.byref(info), _ptr(hp), _ptr(hm), _ptr(hv)))
+
+
+def load_checkpoint(path: str, device="cuda") -> dict:
+    """Read a checkpoint written by save_checkpoint (efunc_checkpoint_load):
+    params, m, v on ``device`` and the stored step, seed, loss, grid and Adam
+    settings.  A missing, short or corrupt file raises EfuncError
+    (EFUNC_ERR_IO)."""
+    lib = B.load()
+    info = B.CheckpointInfo()
+    B.check("efunc_checkpoint_info_read", lib.efunc_checkpoint_info_read(str(path).encode(), ctypes.byref(info)))
+    n = int(info.n)
+    arrays = [torch.empty(n, dtype=torch.float32) for _ in range(3)]
+    B.check("efunc_checkpoint_load", lib.efunc_checkpoint_load(
+        str(path).encode(), ctypes.byref(info), *(_ptr(a) for a in arrays), n))
+    a = info.adam
+    return {"params": arrays[0].to(device), "m": arrays[1].to(device), "v": arrays[2].to(device),
+            "step": int(info.step), "seed": int(info.seed), "loss": {B.LOSS_L1: "l1", B.LOSS_MSE: "mse"}[info.loss],
+            "R": int(info.R), "W": int(info.W), "log_beta0": float(info.log_beta0), "channels": int(info.channels),
+            "adam": {"lr": a.lr, "beta1": a.beta1, "beta2": a.beta2, "eps": a.eps, "weight_decay": a.weight_decay,
+                     "decoupled": bool(a.decoupled)}}
+
+
 def efunc_adam_step(params, grad, m, v, step: int, **adam_kw):
     """One Adam/AdamW step in place; grad is zeroed."""
     for t, nm in ((params, "params"), (grad, "grad"), (m, "m"), (v, "v")):

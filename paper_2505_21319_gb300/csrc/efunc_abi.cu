@@ -726,6 +726,7 @@ const char *efunc_status_str(efunc_status s)
     case EFUNC_OK: return "ok";
     case EFUNC_ERR_ARG: return "invalid argument";
     case EFUNC_ERR_CUDA: return "CUDA runtime error";
+    case EFUNC_ERR_IO: return "checkpoint file missing, unwritable, short or corrupt";
     case EFUNC_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
     case EFUNC_ERR_NONFINITE: return "non-finite hyper-parameter";
     case EFUNC_ERR_UNSUPPORTED: return "unsupported configuration";

@@ -444,6 +444,34 @@ def test_fits_from_two_host_threads():
         np.testing.assert_allclose(together[key][0][solid], alone[key][0][solid], rtol=1e-4, atol=1e-6)
 
 
+def test_fit_resumes_from_a_checkpoint(tmp_path):
+    """Eight fit steps in one call against four, a checkpoint (saved from and
+    loaded back to the device) and four more continuing at step0 = 4 with the
+    batch cycle rotated to where the first call left it: the same losses and
+    parameters up to the order of the FP32 gradient atomics."""
+    R, J = 8, 30000
+    qo = synth.sample_batch(synth.random_union(9), 3 * J, seed=9)
+    p0 = synth.init_params(R, seed=9)
+    lb = lb32(R)
+    zeros = lambda: torch.zeros(p0.size, device=DEV)
+    pd, m, v, st = to_dev(p0), zeros(), zeros(), torch.zeros(16, device=DEV)
+    api.efunc_fit(pd, m, v, to_dev(qo), steps=8, J=J, n_batches=3, loss="mse", stats=st, lr=1e-3, log_beta0=lb)
+    p1, m1, v1, s1 = to_dev(p0), zeros(), zeros(), torch.zeros(8, device=DEV)
+    api.efunc_fit(p1, m1, v1, to_dev(qo), steps=4, J=J, n_batches=3, loss="mse", stats=s1, lr=1e-3, log_beta0=lb)
+    path = tmp_path / "fit.ckp"
+    api.save_checkpoint(path, p1, m1, v1, step=4, log_beta0=lb, loss="mse", lr=1e-3)
+    c = api.load_checkpoint(path, device=DEV)
+    rot = np.concatenate([qo[J:2 * J], qo[2 * J:], qo[:J]])   # step 4 takes batch 4 mod 3 = 1
+    s2 = torch.zeros(8, device=DEV)
+    api.efunc_fit(c["params"], c["m"], c["v"], to_dev(rot), steps=4, J=J, n_batches=3, step0=c["step"],
+                  loss=c["loss"], stats=s2, lr=c["adam"]["lr"], log_beta0=c["log_beta0"])
+    np.testing.assert_allclose(torch.cat([s1, s2]).cpu().numpy(), st.cpu().numpy(), rtol=1e-5)
+    mref = m.cpu().numpy().reshape(-1)
+    solid = np.abs(mref) > 1e-2 * np.abs(mref).max()
+    np.testing.assert_allclose(c["params"].cpu().numpy().reshape(-1)[solid], pd.cpu().numpy().reshape(-1)[solid],
+                               rtol=1e-4, atol=1e-6)
+
+
 def test_graph_fit_rejects_host_memory_and_capture():
     R, J = 4, 1000
     qo = synth.sample_batch(synth.sphere(0.5), J, seed=1)
