@@ -30,8 +30,9 @@
  *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
  *     default stream) unless stated otherwise.
  *   - Work memory comes from the caller: `workspace` [device] of at least
- *     efunc_workspace_bytes(grid, J) bytes (or the variant / cosine / fit sizes
- *     below), 256-byte aligned.  Concurrent calls must not share a workspace.
+ *     efunc_eval_workspace_bytes(grid, J) bytes for the sort, forward and
+ *     backward, efunc_workspace_bytes(grid, J) for efunc_fit (or the
+ *     variant / cosine / pipelined-fit sizes below), 256-byte aligned.  Concurrent calls must not share a workspace.
  *     The library allocates no device memory; it creates, once per device,
  *     the copy and sort streams and events of efunc_fit.
  *   - Arguments are validated on the host before anything is launched; an
@@ -128,10 +129,19 @@ float efunc_default_log_beta0(int32_t R);
 const char *efunc_status_str(efunc_status s);
 
 /* Bytes of workspace that suffice for every call of the default model below
- * for J queries on this grid (efunc_fit can use more, see
- * efunc_fit_workspace_bytes; the variant and cosine calls have their own
- * sizes).  0 if the grid is invalid. */
+ * for J queries on this grid, including the in-line efunc_fit (efunc_fit can
+ * use more, see efunc_fit_workspace_bytes; the sort, forward and backward
+ * need only efunc_eval_workspace_bytes; the variant and cosine calls have
+ * their own sizes).  0 if the grid is invalid. */
 size_t efunc_workspace_bytes(const efunc_grid *grid, int64_t J);
+
+/* Bytes of workspace that suffice for efunc_cell_sort, efunc_forward,
+ * efunc_backward and efunc_backward_grad for J queries on this grid: the
+ * sort buffers and key records, without the gradient grid and host-batch
+ * staging buffers that only efunc_fit uses (about 32 bytes per query and
+ * 52 R^3 bytes less than efunc_workspace_bytes).  0 if the grid is
+ * invalid. */
+size_t efunc_eval_workspace_bytes(const efunc_grid *grid, int64_t J);
 
 /* Bytes of workspace with which efunc_fit pipelines its steps: the sort of
  * batch s+1 runs on a library-owned stream, into a second sort buffer, while
@@ -269,10 +279,10 @@ efunc_status efunc_fit_graph(const efunc_grid *grid, const efunc_adam *adam, int
  * computes, with the same arguments minus the workspace: the scratch is a
  * fixed 32 MiB array inside this library (every GPU that loads the library
  * keeps it until the process exits).
- *   - Limit: requests whose efunc_workspace_bytes(grid, J) exceeds 32 MiB
- *     return EFUNC_ERR_WORKSPACE with nothing enqueued.  That admits up to
- *     514,048 queries at R = 32, 585,456 at R = 16 and 26,112 at R = 64;
- *     larger grids need efunc_forward with a caller workspace.
+ *   - Limit: requests whose efunc_eval_workspace_bytes(grid, J) exceeds
+ *     32 MiB return EFUNC_ERR_WORKSPACE with nothing enqueued.  That admits
+ *     up to 1,268,480 queries at R = 32, 1,372,896 at R = 16 and 435,648 at
+ *     R = 64; larger requests need efunc_forward with a caller workspace.
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device current); make that first call before
  *     any stream capture.

@@ -47,6 +47,7 @@ SIGNATURES = {
     "efunc_default_log_beta0": (c_float, [c_int32]),
     "efunc_status_str": (c_char_p, [c_int32]),
     "efunc_workspace_bytes": (c_size_t, [ctypes.POINTER(Grid), c_int64]),
+    "efunc_eval_workspace_bytes": (c_size_t, [ctypes.POINTER(Grid), c_int64]),
     "efunc_fit_workspace_bytes": (c_size_t, [ctypes.POINTER(Grid), c_int64]),
     "efunc_cell_sort": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_int64, c_int32, c_void_p, c_void_p,
                                   c_void_p, c_size_t, c_void_p]),

@@ -58,8 +58,12 @@ class Workspace:
         self.device = torch.device(device or "cuda")
         self.buf = None
 
-    def get(self, grid: B.Grid, J: int, fit: bool = False) -> tuple[torch.Tensor, int]:
-        query = B.load().efunc_fit_workspace_bytes if fit else B.load().efunc_workspace_bytes
+    def get(self, grid: B.Grid, J: int, fit: bool = False, eval_only: bool = False) -> tuple[torch.Tensor, int]:
+        """fit: the pipelined fit's size; eval_only: the sort / forward /
+        backward size; neither: the in-line fit's size."""
+        lib = B.load()
+        query = (lib.efunc_fit_workspace_bytes if fit else
+                 lib.efunc_eval_workspace_bytes if eval_only else lib.efunc_workspace_bytes)
         n = int(query(ctypes.byref(grid), int(J)))
         if n == 0:
             raise ValueError("invalid grid or query count")
@@ -93,7 +97,7 @@ def efunc_cell_sort(q: torch.Tensor, R: int, ws: Workspace | None = None):
     grid = make_grid(R)
     out = torch.empty((J, 4), dtype=torch.float32, device=q.device)
     perm = torch.empty(J, dtype=torch.int32, device=q.device)
-    buf, n = _workspace(q.device, ws).get(grid, J)
+    buf, n = _workspace(q.device, ws).get(grid, J, eval_only=True)
     B.check("efunc_cell_sort", B.load().efunc_cell_sort(ctypes.byref(grid), _ptr(q), J, stride, _ptr(out),
                                                         _ptr(perm), _ptr(buf), n, _stream(q.device)))
     return out, perm
@@ -109,7 +113,7 @@ def efunc_forward(params: torch.Tensor, q: torch.Tensor, log_beta0: float | None
     O = torch.empty(J, dtype=torch.float32, device=q.device)
     lse = torch.empty(J, dtype=torch.float32, device=q.device) if want_lse else None
     dq = torch.empty((J, 3), dtype=torch.float32, device=q.device) if want_dq else None
-    buf, n = _workspace(q.device, ws).get(grid, J)
+    buf, n = _workspace(q.device, ws).get(grid, J, eval_only=True)
     B.check("efunc_forward", B.load().efunc_forward(ctypes.byref(grid), _ptr(params), _ptr(q), J, stride, _ptr(O),
                                                     _ptr(lse), _ptr(dq), _ptr(buf), n, _stream(q.device)))
     out = [O]
@@ -132,7 +136,7 @@ def efunc_backward(params: torch.Tensor, q: torch.Tensor, gO: torch.Tensor, grad
     _need(grad, "grad", params.numel())
     gq = torch.empty((J, 3), dtype=torch.float32, device=q.device) if want_gq else None
     grid = make_grid(R, log_beta0)
-    buf, n = _workspace(q.device, ws).get(grid, J)
+    buf, n = _workspace(q.device, ws).get(grid, J, eval_only=True)
     B.check("efunc_backward", B.load().efunc_backward(ctypes.byref(grid), _ptr(params), _ptr(q), J, stride,
                                                       _ptr(gO), _ptr(grad), _ptr(gq), _ptr(buf), n,
                                                       _stream(q.device)))
@@ -155,7 +159,7 @@ def efunc_backward_grad(params: torch.Tensor, q: torch.Tensor, gO: torch.Tensor 
         grad = torch.zeros_like(params)
     _need(grad, "grad", params.numel())
     grid = make_grid(R, log_beta0)
-    buf, n = _workspace(q.device, ws).get(grid, J)
+    buf, n = _workspace(q.device, ws).get(grid, J, eval_only=True)
     B.check("efunc_backward_grad", B.load().efunc_backward_grad(ctypes.byref(grid), _ptr(params), _ptr(q), J, stride,
                                                                 _ptr(gO), _ptr(gG), _ptr(grad), _ptr(buf), n,
                                                                 _stream(q.device)))

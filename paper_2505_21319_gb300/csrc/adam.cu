@@ -98,13 +98,7 @@ __global__ void adam_clock_seed_kernel(AdamClock *clk, AdamClock init) { *clk = 
 
 int adam_blocks(const AdamArgs &a, bool &vec)
 {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+    const int sms = device_sm_count();
     const uintptr_t mis = reinterpret_cast<uintptr_t>(a.p) | reinterpret_cast<uintptr_t>(a.g) |
                           reinterpret_cast<uintptr_t>(a.m) | reinterpret_cast<uintptr_t>(a.v);
     vec = (mis & 15u) == 0;

@@ -18,13 +18,17 @@
 //          128  params, m, v                     float32 x 3n
 //   128 + 12n  FNV-1a 64 of the 12n payload bytes  uint64
 //
-// The file is written to a temporary name beside the target and renamed over
-// it once complete, so a crash mid-write leaves the previous checkpoint.
+// The file is written to a temporary name beside the target (unique per
+// process and call), flushed to the storage device, renamed over the target
+// and the directory entry flushed as well, so a crash or power loss at any
+// point leaves either the previous checkpoint or the complete new one.
+#include <fcntl.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 #include <unistd.h>
 
+#include <atomic>
 #include <string>
 
 #include "common.cuh"
@@ -154,7 +158,9 @@ efunc_status efunc_checkpoint_save(const char *path, const efunc_checkpoint_info
     if (!path || !*path || !info_ok(info) || !params || !m || !v) return EFUNC_ERR_ARG;
     unsigned char h[kHeaderBytes];
     encode_header(info, h);
-    const std::string tmp = std::string(path) + ".tmp" + std::to_string((long)getpid());
+    static std::atomic<unsigned long long> calls{0};   // two saves in one process never share a temporary
+    const std::string tmp = std::string(path) + ".tmp" + std::to_string((long)getpid()) + "." +
+                            std::to_string(calls.fetch_add(1));
     Fnv sum;
     {
         File out(fopen(tmp.c_str(), "wb"));
@@ -169,6 +175,7 @@ efunc_status efunc_checkpoint_save(const char *path, const efunc_checkpoint_info
         put<uint64_t>(t, 0, sum.h);
         ok = ok && fwrite(t, 1, 8, out.f) == 8;
         ok = ok && fflush(out.f) == 0;
+        ok = ok && fsync(fileno(out.f)) == 0;   // the data is on the device before the rename
         const int rc = fclose(out.f);
         out.f = nullptr;
         if (!ok || rc != 0) {
@@ -180,7 +187,16 @@ efunc_status efunc_checkpoint_save(const char *path, const efunc_checkpoint_info
         remove(tmp.c_str());
         return EFUNC_ERR_IO;
     }
-    return EFUNC_OK;
+    // the rename itself lives in the directory: flush it too
+    const std::string p(path);
+    const size_t slash = p.find_last_of('/');
+    const std::string dir = slash == std::string::npos ? std::string(".") : (slash == 0 ? std::string("/")
+                                                                                           : p.substr(0, slash));
+    const int dfd = open(dir.c_str(), O_RDONLY | O_DIRECTORY);
+    if (dfd < 0) return EFUNC_ERR_IO;
+    const int drc = fsync(dfd);
+    close(dfd);
+    return drc == 0 ? EFUNC_OK : EFUNC_ERR_IO;
 }
 
 efunc_status efunc_checkpoint_info_read(const char *path, efunc_checkpoint_info *info)

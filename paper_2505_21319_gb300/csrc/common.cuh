@@ -4,9 +4,34 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "efunc.h"
 
 namespace efunc {
+
+constexpr int kMaxDevices = 64;
+
+// Device ordinal of the calling thread's current device (0 if the runtime
+// cannot tell).
+int current_device();
+// Multiprocessor count of the current device, looked up once per device.
+int device_sm_count();
+// Values derived from a device's properties (occupancy, persistent grid
+// sizes, kernel attributes) are cached per (device, key, tag): the first
+// call on a device runs compute() under one process-wide lock, so threads
+// and devices never see each other's values.  A result <= 0 is not cached.
+std::recursive_mutex &device_cache_mutex();
+int &device_cache_slot(int dev, const void *key, int tag);   // caller holds the lock
+template <class F>
+int per_device_cached(const void *key, int tag, F compute)
+{
+    const int dev = current_device();
+    std::lock_guard<std::recursive_mutex> lk(device_cache_mutex());
+    int &v = device_cache_slot(dev, key, tag);
+    if (v <= 0) v = compute();
+    return v;
+}
 
 constexpr int kSlots = 13;        // floats per centre (Eq. func-offset, f^1)
 constexpr int kW = 2;             // window half-width
@@ -48,7 +73,12 @@ struct Layout {
 // Workspace layout for R^3 centres and J queries; key_records (float4) and
 // channels (floats) per centre size the key-record and gradient regions
 // (the default model: 4 and 13; the ablation variants need other sizes).
-Layout make_layout(int R, int64_t J, int key_records = 4, int channels = 13, bool two_sort_buffers = false);
+// fit_regions = false leaves out what only the fits use (the gradient grid
+// and the two host-batch staging buffers): the layout of the sort, forward
+// and backward calls.
+Layout make_layout(int R, int64_t J, int key_records = 4, int channels = 13, bool two_sort_buffers = false,
+                   bool fit_regions = true);
+inline Layout eval_layout(int R, int64_t J) { return make_layout(R, J, 4, 13, false, false); }
 
 // Sort configuration passed to kernels.
 struct SortArgs {

@@ -271,35 +271,20 @@ __global__ void __launch_bounds__(kThreads) cosine_kernel(CosineArgs a)
     }
 }
 
-int cos_sm_count()
-{
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return sms;
-}
+int cos_sm_count() { return device_sm_count(); }
 
 template <int MODE>
 cudaError_t launch_mode(const CosineArgs &a, int kid, cudaStream_t s)
 {
     const size_t smem = cos_smem_bytes(a.B, MODE);
     // the dynamic shared-memory limit is a per-device attribute of the kernel
-    constexpr int kMaxDevices = 64;
-    static bool attr[kMaxDevices] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!attr[dev]) {
+    cudaError_t e = cudaSuccess;
+    per_device_cached(reinterpret_cast<const void *>(cosine_kernel<MODE>), 0, [&e] {
         e = cudaFuncSetAttribute(cosine_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)cos_smem_bytes(kMaxBands, VAR_FIT));
-        if (e != cudaSuccess) return e;
-        attr[dev] = true;
-    }
+        return e == cudaSuccess ? 1 : 0;   // a failure is not cached
+    });
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cosine_kernel<MODE>, kThreads, smem);
     if (per_sm <= 0) per_sm = 1;

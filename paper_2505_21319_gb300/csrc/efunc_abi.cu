@@ -2,8 +2,10 @@
 // order of the hot path, and the launch counter / event profiler.
 #include <math.h>
 #include <stddef.h>
+#include <map>
 #include <mutex>
 #include <string.h>
+#include <tuple>
 #include <vector>
 
 #include "adam_clock.cuh"
@@ -102,9 +104,46 @@ void launch_end(int kid, cudaStream_t s)
     g_pending.back().stop = e;
 }
 
+// ------------------------------------------------ per-device property cache
+
+int current_device()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return dev;
+}
+
+std::recursive_mutex &device_cache_mutex()
+{
+    static std::recursive_mutex mu;
+    return mu;
+}
+
+int &device_cache_slot(int dev, const void *key, int tag)
+{
+    static std::map<std::tuple<int, const void *, int>, int> slots;   // references stay valid on insertion
+    return slots[std::make_tuple(dev, key, tag)];
+}
+
+int device_sm_count()
+{
+    static const char key = 0;
+    return per_device_cached(&key, 0, [] {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, current_device()) != cudaSuccess) {
+            cudaGetLastError();
+            sms = 0;
+        }
+        return sms > 0 ? sms : 1;
+    });
+}
+
 // ------------------------------------------------------------- layout
 
-Layout make_layout(int R, int64_t J, int key_records, int channels, bool two_sort_buffers)
+Layout make_layout(int R, int64_t J, int key_records, int channels, bool two_sort_buffers, bool fit_regions)
 {
     Layout L{};
     L.P = (R + 1 + kBrick - 1) / kBrick;
@@ -121,8 +160,10 @@ Layout make_layout(int R, int64_t J, int key_records, int channels, bool two_sor
     L.perm = off;      off = align_up(off + (size_t)J * 4, A);
     L.items = off;     off = align_up(off + (size_t)L.max_items * 16, A);
     L.keys = off;      off = align_up(off + (size_t)R * R * R * key_records * 16, A);
-    L.grad = off;      off = align_up(off + (size_t)R * R * R * channels * 4, A);
-    L.stage = off;     off = align_up(off + (size_t)J * 32, A);   // two host-batch staging buffers
+    if (fit_regions) {
+        L.grad = off;  off = align_up(off + (size_t)R * R * R * channels * 4, A);
+        L.stage = off; off = align_up(off + (size_t)J * 32, A);   // two host-batch staging buffers
+    }
     L.two_sort_buffers = two_sort_buffers;
     if (two_sort_buffers) {
         L.ctrl2 = off;     off = align_up(off + sizeof(Ctrl), A);
@@ -155,10 +196,11 @@ efunc_status check_grid(const efunc_grid *g)
     return EFUNC_OK;
 }
 
-efunc_status check_workspace(const efunc_grid *g, int64_t J, const void *ws, size_t ws_bytes)
+// fit: the in-line fit needs the gradient and staging regions too
+efunc_status check_workspace(const efunc_grid *g, int64_t J, const void *ws, size_t ws_bytes, bool fit = false)
 {
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return EFUNC_ERR_WORKSPACE;
-    if (ws_bytes < make_layout(g->R, J).total) return EFUNC_ERR_WORKSPACE;
+    if (ws_bytes < (fit ? make_layout(g->R, J) : eval_layout(g->R, J)).total) return EFUNC_ERR_WORKSPACE;
     return EFUNC_OK;
 }
 
@@ -740,6 +782,12 @@ size_t efunc_workspace_bytes(const efunc_grid *grid, int64_t J)
     return make_layout(grid->R, J).total;
 }
 
+size_t efunc_eval_workspace_bytes(const efunc_grid *grid, int64_t J)
+{
+    if (!grid_ok(grid) || J < 0 || J > kMaxJ) return 0;
+    return eval_layout(grid->R, J).total;
+}
+
 size_t efunc_fit_workspace_bytes(const efunc_grid *grid, int64_t J)
 {
     if (!grid_ok(grid) || J < 0 || J > kMaxJ) return 0;
@@ -755,7 +803,7 @@ efunc_status efunc_cell_sort(const efunc_grid *grid, const float *q, int64_t J, 
     if (J == 0) return EFUNC_OK;
     if (!q || !q_sorted || !perm || (reinterpret_cast<uintptr_t>(q_sorted) & 15u)) return EFUNC_ERR_ARG;
     if ((st = check_workspace(grid, J, workspace, workspace_bytes))) return st;
-    Views v{make_layout(grid->R, J), static_cast<char *>(workspace)};
+    Views v{eval_layout(grid->R, J), static_cast<char *>(workspace)};
     return cuda_status(sort_into(v, grid->R, q, J, q_stride, reinterpret_cast<float4 *>(q_sorted), perm,
                                  (cudaStream_t)stream));
 }
@@ -771,7 +819,7 @@ efunc_status efunc_forward(const efunc_grid *grid, const float *params, const fl
     if (!q || !O) return EFUNC_ERR_ARG;
     if ((st = check_workspace(grid, J, workspace, workspace_bytes))) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    Views v{make_layout(grid->R, J), static_cast<char *>(workspace)};
+    Views v{eval_layout(grid->R, J), static_cast<char *>(workspace)};
     cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
     if (e == cudaSuccess) e = pack_keys(v, grid, params, s);
     if (e != cudaSuccess) return cuda_fail();
@@ -793,7 +841,7 @@ efunc_status efunc_backward(const efunc_grid *grid, const float *params, const f
     if (!q || !gO) return EFUNC_ERR_ARG;
     if ((st = check_workspace(grid, J, workspace, workspace_bytes))) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    Views v{make_layout(grid->R, J), static_cast<char *>(workspace)};
+    Views v{eval_layout(grid->R, J), static_cast<char *>(workspace)};
     cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
     if (e == cudaSuccess) e = pack_keys(v, grid, params, s);
     if (e != cudaSuccess) return cuda_fail();
@@ -815,7 +863,7 @@ efunc_status efunc_backward_grad(const efunc_grid *grid, const float *params, co
     if (!q || (!gO && !gG)) return EFUNC_ERR_ARG;
     if ((st = check_workspace(grid, J, workspace, workspace_bytes))) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    Views v{make_layout(grid->R, J), static_cast<char *>(workspace)};
+    Views v{eval_layout(grid->R, J), static_cast<char *>(workspace)};
     cudaError_t e = sort_into(v, grid->R, q, J, q_stride, v.sorted(), v.perm(), s);
     if (e == cudaSuccess) e = pack_keys(v, grid, params, s);
     if (e != cudaSuccess) return cuda_fail();
@@ -851,7 +899,7 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
     if (eikonal_weight < 0.f) return EFUNC_ERR_ARG;
     if (J < 1 || J > kMaxJ || n_batches < 1 || steps < 0 || step0 < 0) return EFUNC_ERR_ARG;
     if (!params || !m || !v || !qo) return EFUNC_ERR_ARG;
-    if ((st = check_workspace(grid, J, workspace, workspace_bytes))) return st;
+    if ((st = check_workspace(grid, J, workspace, workspace_bytes, true))) return st;
     if (steps == 0) return EFUNC_OK;
     if (workspace_bytes >= make_layout(grid->R, J, kKeyRecords, kSlots, true).total)
         return fit_pipelined(grid, adam, loss, eikonal_weight, params, m, v, qo, J, n_batches, steps, step0, stats,

@@ -651,46 +651,32 @@ __global__ void __launch_bounds__(kThreads, GEIK ? 5 : 9) fused_kernel(FusedArgs
     }
 }
 
-int sm_count()
-{
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return sms;
-}
+int sm_count() { return device_sm_count(); }
 
 }  // namespace
 
 int fused_grid_size()
 {
-    static int g = 0;
-    if (!g) {
+    const void *k = reinterpret_cast<const void *>(fused_kernel<FIT, false, false>);
+    return per_device_cached(k, 0, [k] {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel<FIT, false, false>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, 0);
         if (per_sm <= 0) per_sm = 1;
-        g = sm_count() * per_sm;
-    }
-    return g;
+        return sm_count() * per_sm;
+    });
 }
 
 int fused_fit_grid_size(bool eikonal, bool leave_room)
 {
-    static int cached[2][2] = {{0, 0}, {0, 0}};
-    int &g = cached[eikonal ? 1 : 0][leave_room ? 1 : 0];
-    if (!g) {
-        const void *k = eikonal ? reinterpret_cast<const void *>(fused_kernel<FIT, false, true>)
-                                : reinterpret_cast<const void *>(fused_kernel<FIT, false, false>);
+    const void *k = eikonal ? reinterpret_cast<const void *>(fused_kernel<FIT, false, true>)
+                            : reinterpret_cast<const void *>(fused_kernel<FIT, false, false>);
+    return per_device_cached(k, leave_room ? 2 : 1, [k, leave_room] {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, 0);
         if (per_sm <= 0) per_sm = 1;
         if (leave_room) per_sm = leave_sort_room(k, per_sm);
-        g = sm_count() * per_sm;
-    }
-    return g;
+        return sm_count() * per_sm;
+    });
 }
 
 int leave_sort_room(const void *kernel, int per_sm, int sort_blocks)

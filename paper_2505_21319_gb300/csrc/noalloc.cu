@@ -53,7 +53,7 @@ efunc_status efunc_forward_noalloc(const efunc_grid *grid, const float *params, 
     if (!grid || grid->R < 1 || grid->R > efunc::kMaxR) return EFUNC_ERR_ARG;
     if (J < 0) return EFUNC_ERR_ARG;
     if (J == 0) return efunc_forward(grid, params, q, J, q_stride, O, lse, dOdq, nullptr, 0, stream);
-    const size_t need = efunc_workspace_bytes(grid, J);
+    const size_t need = efunc_eval_workspace_bytes(grid, J);
     if (need == 0) return EFUNC_ERR_ARG;
     if (need > kNoAllocScratchBytes) return EFUNC_ERR_WORKSPACE;   // beyond the fixed scratch
     void *scratch = nullptr;

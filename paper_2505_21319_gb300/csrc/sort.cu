@@ -290,13 +290,7 @@ __global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) scatter_kernel(S
 
 int stream_grid(int64_t work, int threads, int blocks_per_sm)
 {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+    const int sms = device_sm_count();
     int64_t blocks = (work + threads - 1) / threads;
     int64_t cap = (int64_t)sms * blocks_per_sm;
     if (blocks > cap) blocks = cap;

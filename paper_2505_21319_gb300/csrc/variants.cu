@@ -4,17 +4,7 @@
 namespace efunc {
 namespace variant {
 
-int sm_count()
-{
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return sms;
-}
+int sm_count() { return device_sm_count(); }
 
 }  // namespace variant
 

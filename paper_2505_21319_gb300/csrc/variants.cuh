@@ -491,17 +491,14 @@ int sm_count();
 template <int MODE, int SETS, int DEG>
 int persistent_grid(bool leave_room)
 {
-    static int g[2] = {0, 0};
-    int &v = g[leave_room ? 1 : 0];
-    if (!v) {
-        const void *k = reinterpret_cast<const void *>(variant_kernel<MODE, SETS, DEG>);
+    const void *k = reinterpret_cast<const void *>(variant_kernel<MODE, SETS, DEG>);
+    return per_device_cached(k, leave_room ? 2 : 1, [k, leave_room] {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, 0);
         if (per_sm <= 0) per_sm = 1;
         if (leave_room) per_sm = leave_sort_room(k, per_sm);
-        v = sm_count() * per_sm;
-    }
-    return v;
+        return sm_count() * per_sm;
+    });
 }
 
 template <int SETS, int DEG>

@@ -6,8 +6,15 @@ import os
 import re
 
 import pytest
+import torch
 
 from paper_2505_21319_gb300 import _binding as B
+
+# Tests that pass made-up device addresses to reach the host-side checks run
+# only where no CUDA device is visible: if a check ever regressed, the call
+# would enqueue work on those addresses, which must never happen on a GPU.
+fake_pointers = pytest.mark.skipif(torch.cuda.is_available(),
+                                   reason="made-up device pointers are only passed where no GPU is visible")
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "efunc.h")
@@ -54,6 +61,12 @@ def test_host_helpers(lib):
     nf = lib.efunc_fit_workspace_bytes(ctypes.byref(g), 1 << 22)
     assert nf > n1 and nf - n1 >= 20 * (1 << 22) and nf % 256 == 0
     assert lib.efunc_fit_workspace_bytes(ctypes.byref(B.Grid(0, 2, 7.0)), 10) == 0
+    # the sort / forward / backward layout leaves out the gradient grid and
+    # the two host-batch staging buffers (32 bytes per query, 52 R^3 bytes)
+    ne = lib.efunc_eval_workspace_bytes(ctypes.byref(g), 1 << 22)
+    assert 0 < ne < n1 and n1 - ne >= 32 * (1 << 22) + 52 * 32 ** 3 and ne % 256 == 0
+    assert lib.efunc_eval_workspace_bytes(ctypes.byref(B.Grid(0, 2, 7.0)), 10) == 0
+    assert lib.efunc_eval_workspace_bytes(ctypes.byref(g), -1) == 0
     assert lib.efunc_launch_count() == n0
 
 
@@ -64,6 +77,7 @@ def _fwd(lib, grid, J=16, stride=3, ws=1 << 30, ws_bytes=None, params=4096, q=81
     return lib.efunc_forward(g, params, q, J, stride, O, None, None, ws, ws_bytes, None)
 
 
+@fake_pointers
 def test_argument_validation_enqueues_nothing(lib):
     """Invalid arguments are rejected on the host (fake, never dereferenced
     pointers are enough to reach every check)."""
@@ -83,6 +97,8 @@ def test_argument_validation_enqueues_nothing(lib):
     assert _fwd(lib, ok, ws=None) == 3
     assert _fwd(lib, ok, ws=(1 << 30) + 8) == 3          # misaligned
     assert _fwd(lib, ok, ws_bytes=100) == 3              # too small
+    ne = lib.efunc_eval_workspace_bytes(ctypes.byref(ok), 16)
+    assert _fwd(lib, ok, ws_bytes=ne - 256) == 3         # one region short of the forward's layout
     assert _fwd(lib, ok, J=0) == 0                       # empty batch: nothing to do
     assert lib.efunc_launch_count() == n0
     # backward, cell sort, Adam, fit
@@ -105,6 +121,8 @@ def test_argument_validation_enqueues_nothing(lib):
                          1 << 30, 1 << 40, None) == 4                                       # non-finite weight
     assert lib.efunc_fit(ctypes.byref(ok), ctypes.byref(ad), 0, 0.0, 16, 32, 48, 64, 10, 1, 0, 0, None, 1 << 30,
                          1 << 40, None) == 0                                                # zero steps
+    assert lib.efunc_fit(ctypes.byref(ok), ctypes.byref(ad), 0, 0.0, 16, 32, 48, 64, 10, 1, 1, 0, None, 1 << 30,
+                         lib.efunc_eval_workspace_bytes(ctypes.byref(ok), 10), None) == 3   # no gradient region
     assert lib.efunc_backward_grad(ctypes.byref(ok), 4096, 8192, 16, 3, None, None, 4096, 1 << 30, 1 << 40,
                                    None) == 1                                               # neither gO nor gG
     # the graph-replayed fit: the same checks, its whole workspace, device batches, at most 64 batches
@@ -136,6 +154,7 @@ def test_argument_validation_enqueues_nothing(lib):
     assert lib.efunc_launch_count() == n0
 
 
+@fake_pointers
 def test_variant_helpers_and_validation(lib):
     """Channel counts of the ablation variants and host-side rejection of
     invalid variant requests (nothing launches)."""
@@ -174,6 +193,7 @@ def test_variant_helpers_and_validation(lib):
     assert lib.efunc_launch_count() == n0
 
 
+@fake_pointers
 def test_cosine_helpers_and_validation(lib):
     n0 = lib.efunc_launch_count()   # launches of earlier tests in this process
     g = B.Grid(16, 2, 7.0)

@@ -132,3 +132,33 @@ def test_resumed_oracle_fit_follows_the_uninterrupted_trajectory(tmp_path):
     np.testing.assert_array_equal(mr, ma)
     np.testing.assert_array_equal(vr, va)
     assert lb1 + lb2 == la
+
+
+def test_concurrent_saves_to_one_path_leave_one_complete_file(tmp_path):
+    """Threads of one process saving to the same path at once use distinct
+    temporary names: every save succeeds, the file left is one of the
+    complete checkpoints, and no temporary file remains."""
+    import threading
+    n = 8 ** 3 * 13
+    states = [_state(n, 100 + k) for k in range(6)]
+    path = tmp_path / "same.ckp"
+    errors = []
+
+    def save(k):
+        try:
+            for _ in range(5):
+                api.save_checkpoint(path, *states[k], step=k)
+        except Exception as e:   # noqa: BLE001 - reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=save, args=(k,)) for k in range(len(states))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    c = api.load_checkpoint(path, device="cpu")
+    k = c["step"]
+    for name, t in zip(("params", "m", "v"), states[k]):
+        assert torch.equal(c[name], t)
+    assert sorted(os.listdir(tmp_path)) == ["same.ckp"]

@@ -8,10 +8,12 @@ Tolerances (FP32 kernels vs FP64 oracle):
                   exponents (FP32 cannot do better than ~u kappa; inside the
                   domain at the paper's scales kappa < 3 and the first term
                   governs; queries outside the domain reach kappa ~ 30)
-  dO/dq, dL/dq    |gpu - ref| <= 1e-4 |ref| + 1e-5 max|ref| + sens * tol_O,
+  dO/dq, dL/dq    |gpu - ref| <= 1e-4 |ref| + 1e-5 max|ref| + sens * 4 u kappa,
                   sens = 2 ||sum softmax beta (q - key)|| the factor by which
-                  O's own rounding enters dO/dq (about 2 beta h ~ 10^2 inside
-                  the domain, ~10^3 for queries 0.5 outside it)
+                  an error of O enters dO/dq through the (O - f) terms of
+                  Eq. func-normal (about 2 beta h ~ 10^2 inside the domain,
+                  ~10^3 for queries 0.5 outside it) and 4 u kappa O's own
+                  FP32 error bound (not its tolerance)
   dL/dparams      per slot type, |gpu - ref| <= 1e-4 max_slot_type |ref|
                   (FP32 atomics: the summation order is not deterministic)
   Adam            |gpu - ref| <= 1e-6 + 1e-5 |ref|
@@ -24,6 +26,7 @@ import numpy as np
 import pytest
 import torch
 
+import margins
 import oracle
 from paper_2505_21319_gb300 import api, synth
 
@@ -56,6 +59,7 @@ def assert_close(gpu, ref, rtol, atol, what):
     gpu = np.asarray(gpu, dtype=np.float64)
     err = np.abs(gpu - ref)
     lim = atol + rtol * np.abs(ref)
+    margins.record(what, err, lim)
     bad = np.flatnonzero(~(err <= lim))
     assert bad.size == 0, (f"{what}: {bad.size} of {err.size} outside tolerance; worst idx {bad[:5]} "
                            f"gpu {gpu.ravel()[bad[:5]]} ref {ref.ravel()[bad[:5]]}")
@@ -68,20 +72,25 @@ def assert_O_close(gpu, ref, kappa, what):
     gpu = np.asarray(gpu, dtype=np.float64)
     err = np.abs(gpu - ref)
     lim = np.maximum(1e-6 + 1e-5 * np.abs(ref), 4 * U32 * kappa)
+    margins.record(what, err, lim)
     bad = np.flatnonzero(~(err <= lim))
     assert bad.size == 0, (f"{what}: {bad.size} of {err.size} outside tolerance; idx {bad[:5]} "
                            f"gpu {gpu[bad[:5]]} ref {ref[bad[:5]]} kappa {kappa[bad[:5]]}")
 
 
-def O_tol(ref, kappa):
-    return np.maximum(1e-6 + 1e-5 * np.abs(ref), 4 * U32 * kappa)
+def O_err_bound(kappa):
+    """O's FP32 error bound: 4 u kappa (relative rounding of every exponent
+    and weight, kappa from the oracle)."""
+    return 4 * U32 * kappa
 
 
-def assert_dq_close(gpu, ref, sens, tolO, what, scale=None):
-    """dq (J, 3) against the oracle; scale multiplies the O-induced term (gO for dL/dq)."""
+def assert_dq_close(gpu, ref, sens, errO, what, scale=None):
+    """dq (J, 3) against the oracle; errO is O's FP32 error bound, which
+    enters dq amplified by sens; scale multiplies it (gO for dL/dq)."""
     gpu = np.asarray(gpu, dtype=np.float64)
-    extra = sens * tolO if scale is None else sens * tolO * np.abs(scale)
+    extra = sens * errO if scale is None else sens * errO * np.abs(scale)
     lim = 1e-4 * np.abs(ref) + 1e-5 * np.abs(ref).max() + extra[:, None]
+    margins.record(what, np.abs(gpu - ref), lim)
     bad = np.flatnonzero(~(np.abs(gpu - ref) <= lim))
     assert bad.size == 0, (f"{what}: {bad.size} of {ref.size} outside tolerance; idx {bad[:5]} "
                            f"gpu {gpu.ravel()[bad[:5]]} ref {ref.ravel()[bad[:5]]}")
@@ -93,6 +102,7 @@ def assert_grad_close(gpu, ref, what, rtol=1e-4):
     for name, cols in SLOT_TYPES.items():
         scale = np.abs(ref[:, cols]).max()
         err = np.abs(gpu[:, cols] - ref[:, cols]).max()
+        margins.record(f"{what} [{name}]", err, rtol * scale + 1e-30)
         assert err <= rtol * scale + 1e-30, f"{what} slot {name}: max err {err:.3e} vs scale {scale:.3e}"
 
 
@@ -155,10 +165,15 @@ def test_forward_matches_oracle(R, J, pkind):
     O_ref, lse_ref, dq_ref, kappa, sens = oracle.forward(p.astype(np.float64), qo.astype(np.float64), R, 2, lb,
                                                          want_dq=True, want_kappa=True, want_dq_sens=True)
     inside = np.all(np.abs(qo[:, :3]) <= 1, axis=1)
-    assert kappa[inside].max() < 8
+    # inside the domain the kappa floor never exceeds the absolute 1e-6 (so
+    # 1e-5 rel / 1e-6 abs governs O there), and grids shaped like fitted
+    # ones (sdf, init) stay at kappa < 3; the rough stress grid reaches ~3.6
+    assert 4 * U32 * kappa[inside].max() < 1e-6
+    if pkind != "random":
+        assert kappa[inside].max() < 3
     assert_O_close(O.cpu().numpy(), O_ref, kappa, "O")
     assert_close(lse.cpu().numpy(), lse_ref, 1e-5, 1e-6, "lse")
-    assert_dq_close(dq.cpu().numpy(), dq_ref, sens, O_tol(O_ref, kappa), "dO/dq")
+    assert_dq_close(dq.cpu().numpy(), dq_ref, sens, O_err_bound(kappa), "dO/dq")
 
 
 def test_forward_is_deterministic_and_order_independent():
@@ -233,7 +248,7 @@ def test_backward_matches_oracle(R, J, pkind):
     O_ref, _, kappa, sens = oracle.forward(p.astype(np.float64), qo.astype(np.float64), R, 2, lb, want_kappa=True,
                                            want_dq_sens=True)
     assert_grad_close(grad.cpu().numpy(), g_ref, f"R={R}")
-    assert_dq_close(gq.cpu().numpy(), gq_ref, sens, O_tol(O_ref, kappa), "dL/dq", scale=gO32)
+    assert_dq_close(gq.cpu().numpy(), gq_ref, sens, O_err_bound(kappa), "dL/dq", scale=gO32)
 
 
 def test_backward_accumulates_and_is_linear():
@@ -586,7 +601,7 @@ def test_autograd_function_matches_oracle():
     O_ref, _, kappa, sens = oracle.forward(p.astype(np.float64), q.astype(np.float64), R, 2, lb32(R), want_kappa=True,
                                            want_dq_sens=True)
     assert_grad_close(pd.grad.cpu().numpy(), g_ref, "autograd params")
-    assert_dq_close(qd.grad.cpu().numpy(), gq_ref, sens, O_tol(O_ref, kappa), "autograd q", scale=w32)
+    assert_dq_close(qd.grad.cpu().numpy(), gq_ref, sens, O_err_bound(kappa), "autograd q", scale=w32)
 
 
 # ------------------------------------------- backward through dO/dq (NEXT-1)
@@ -627,6 +642,11 @@ def test_backward_through_query_gradient_outside_the_domain():
     grad = api.efunc_backward_grad(to_dev(p), to_dev(qo), to_dev(gO), to_dev(gG), log_beta0=lb32(R))
     g_ref = oracle.backward_grad(p.astype(np.float64), qo.astype(np.float64), gO.astype(np.float64),
                                  gG.astype(np.float64), R, 2, lb32(R))
+    # the measured headroom at the in-domain bound, recorded beside the check
+    gg, gr = grad.cpu().numpy().astype(np.float64).reshape(-1, 13), g_ref.reshape(-1, 13)
+    for name, cols in SLOT_TYPES.items():
+        margins.record(f"second order, queries outside, at 1e-4 [{name}]", np.abs(gg[:, cols] - gr[:, cols]).max(),
+                       1e-4 * np.abs(gr[:, cols]).max())
     assert_grad_close(grad.cpu().numpy(), g_ref, "second order, queries outside", rtol=2e-3)
 
 
