@@ -72,6 +72,13 @@ FP32_LANES_PER_SM = 128
 # (fits/s = 1 / (steps x time per step))
 FIT_STEPS_32 = 2000
 FIT_STEPS_16 = 100
+# plain fits to the MAE target: held-out points (half uniform, half near the
+# surface), the target of the metric, and the steps between evaluations
+HELDOUT = 1 << 20
+TARGET_MAE = 1e-3
+TARGET_CHUNK = 50
+# batched fit: shapes fitted together
+BATCH_SHAPES = 256
 # FP32-pipe operations of one (centre, point) pair of the mean-shift
 # initialisation: 3 differences, 3 for the squared norm, 1 scale, 1 compare,
 # 1 exponent difference, 1 add to Z, 3 FMAs into S (the ex2 runs on the MUFU)
@@ -331,6 +338,143 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def algorithmic_ops_torch(q, R: int) -> float:
+    """algorithmic_ops for a device tensor of rows (the same FP32 window rule)."""
+    import torch
+    u = (q[:, :3] + 1.0) * (R * 0.5) - 0.5
+    c = torch.floor(torch.clamp(u, -1.0, float(R - 1))).to(torch.int64)
+    n = (torch.clamp(c + 2, max=R - 1) - torch.clamp(c - 1, min=0) + 1).prod(dim=1)
+    full = n == 64
+    return float(full.sum().item()) * (64 * OPS_PER_CENTRE_FULL + OPS_PER_QUERY_FULL_SETUP) + \
+        float(n[~full].sum().item()) * OPS_PER_CENTRE
+
+
+def bench_batched(api, dev, stream, rank, steps, peak, ws=1):
+    """Many shapes fitted together (efunc_fit_batched): 256 unions of 4-16
+    random primitives, grid resolution drawn from {16, 32, 64}, queries per
+    shape log-uniform in [2^14, 2^20]; two batches per shape drawn on the
+    device; the launch configuration chosen by efunc_tune_batched; the
+    steps replayed from a CUDA graph (one period = two steps)."""
+    import torch
+    from paper_2505_21319_gb300 import synth
+    g = synth.rng(7000 + rank)
+    S = BATCH_SHAPES
+    Rs = [int(x) for x in g.choice([16, 32, 64], size=S)]
+    Js = [int(round(2.0 ** x)) for x in g.uniform(14.0, 20.0, size=S)]
+    prims = [int(x) for x in g.integers(4, 17, size=S)]
+    t0 = time.perf_counter()
+    shapes = [synth.random_union(8000 + 1000 * rank + s, n_prims=prims[s]) for s in range(S)]
+    b = api.Batch(Rs, Js, device=dev)
+    qo = torch.cat([synth.sample_batch_torch(shapes[s], Js[s], seed=(rank * 2 + k) * 100003 + s, device=dev)
+                    for k in range(2) for s in range(S)])
+    params = torch.cat([torch.from_numpy(synth.init_params(R, seed=s).reshape(-1)) for s, R in enumerate(Rs)]).to(dev)
+    m, v = torch.zeros_like(params), torch.zeros_like(params)
+    torch.cuda.synchronize(dev)
+    gen_s = time.perf_counter() - t0
+    # default configuration, a few steps issued one by one
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b.fit(params, m, v, qo, steps=2, n_batches=2, lr=LR, graph=False)
+    d0.record(stream)
+    b.fit(params, m, v, qo, steps=4, n_batches=2, lr=LR, graph=False)
+    d1.record(stream)
+    torch.cuda.synchronize(dev)
+    default_ms = d0.elapsed_time(d1) / 4
+    tuning, tuned_ms = b.tune(params, m, v, qo, n_batches=2, trial_steps=3)
+    params = torch.cat([torch.from_numpy(synth.init_params(R, seed=s).reshape(-1)) for s, R in enumerate(Rs)]).to(dev)
+    # the fused kernel's launch time (profiled steps issued one by one)
+    b.fit(params, m, v, qo, steps=3, n_batches=2, lr=LR, graph=False)
+    torch.cuda.synchronize(dev)
+    api.profile_reset()
+    api.profile(True)
+    b.fit(params, m, v, qo, steps=4, n_batches=2, step0=3, lr=LR, graph=False)
+    torch.cuda.synchronize(dev)
+    api.profile(False)
+    fk_ms, fk_n = api.profile_read("batched")
+    fk = fk_ms / max(1, fk_n)
+    # timed: the whole graph-replayed loop
+    params = torch.cat([torch.from_numpy(synth.init_params(R, seed=s).reshape(-1)) for s, R in enumerate(Rs)]).to(dev)
+    m.zero_()
+    v.zero_()
+    stats = torch.zeros(steps * S * 2, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    b.fit(params, m, v, qo, steps=steps, n_batches=2, stats=stats, lr=LR, graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, dev)
+    st = stats.view(steps, S, 2)
+    ops = 0.0
+    for k in range(2):
+        for s in range(S):
+            lo = k * b.n_queries + b.query_offsets[s]
+            ops += algorithmic_ops_torch(qo[lo:lo + Js[s]], Rs[s])
+    ops /= 2
+    ach = ops / (fk * 1e-3) / 1e12
+    return {"shapes": S, "grids": {str(R): Rs.count(R) for R in (16, 32, 64)}, "queries_per_step": b.n_queries,
+            "params": b.n_params, "steps": steps, "ms_per_step": ms,
+            "value": b.n_queries * ws / (ms * 1e-3), "unit": "query-pts/s",
+            "fits_per_s": S * ws / (steps * ms * 1e-3), "fits_unit": f"shapes per second ({steps}-step fits)",
+            "tuning": tuning, "tuned_ms_per_step": tuned_ms, "default_ms_per_step": default_ms,
+            "fused_ms": fk, "ops_per_launch": ops, "achieved": ach, "peak": peak, "unit_roofline": "T FP32 op/s",
+            "frac": ach / peak,
+            "mae_first": float(st[0, :, 1].mean()), "mae_last": float(st[-1, :, 1].mean()),
+            "generation_s": gen_s, "graph": "one period of 2 steps captured, replayed",
+            "timing": "CUDA events around the whole efunc_fit_batched call (capture and instantiation included)"}
+
+
+def fit_to_target(api, dev, stream, R, J, pool, held, rank, max_steps, chunk, target, ws=1, params0=None):
+    """A plain fit from the N(0, 1e-3) initialisation (or params0) in chunks of
+    ``chunk`` steps, the held-out MAE (volume, near-surface, and the two
+    together) after every chunk.  Returns the MAE curve, the first step count
+    at which the joint held-out MAE is <= target (if any), the fit's own
+    CUDA-event seconds up to there, and fits/s = 1 / those seconds."""
+    import torch
+    from paper_2505_21319_gb300 import synth
+    p = params0.clone() if params0 is not None else torch.from_numpy(synth.init_params(R, seed=rank)).to(dev)
+    m, v = torch.zeros_like(p), torch.zeros_like(p)
+    wsb = api.Workspace(dev)
+    nb = pool.shape[0] // J
+
+    def heldout():
+        outs = {k: api.efunc_eval_loss(p, q, ws=wsb) for k, q in held.items()}
+        mae = {k: float(o[1]) for k, o in outs.items()}
+        mae["all"] = (mae["volume"] + mae["near"]) / 2.0   # equal halves
+        return mae
+
+    curve = [{"step": 0, "seconds": 0.0, **heldout()}]
+    secs, step, reached = 0.0, 0, None
+    while step < max_steps:
+        n = min(chunk, max_steps - step)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        api.efunc_fit(p, m, v, pool, steps=n, J=J, n_batches=nb, step0=step, lr=LR, ws=wsb)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        secs += e0.elapsed_time(e1) * 1e-3
+        step += n
+        mae = heldout()
+        curve.append({"step": step, "seconds": secs, **mae})
+        if reached is None and mae["all"] <= target:
+            reached = {"steps": step, "seconds": secs}
+    final = curve[-1]
+    tgt, how = target, f"held-out MAE <= {target:g}"
+    if reached is None:   # the plain fit's final MAE stands in for the target
+        tgt, how = final["all"], "the plain fit's final held-out MAE (1e-3 not reached)"
+        reached = {"steps": final["step"], "seconds": final["seconds"]}
+    out = {"R": R, "J_per_step": J, "target": tgt, "target_rule": how, "steps_to_target": reached["steps"],
+           "seconds_to_target": reached["seconds"], "fits_per_s": ws / reached["seconds"],
+           "final_mae": {k: final[k] for k in ("volume", "near", "all")}, "steps": final["step"],
+           "seconds_per_step": final["seconds"] / max(1, final["step"]), "chunk": chunk,
+           "heldout_points": {k: int(q.shape[0]) for k, q in held.items()}, "curve": curve,
+           "timing": "CUDA events around each chunk's efunc_fit; held-out evaluation between chunks not timed"}
+    out["summary"] = (f"MAE {final['all']:.3e} after {final['step']} steps (volume {final['volume']:.3e}, "
+                      f"near {final['near']:.3e}); target {tgt:.3e} at step {reached['steps']}, "
+                      f"{reached['seconds']:.3f} s")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,6 +489,10 @@ def main():
     ap.add_argument("--isolated-steps", type=int, default=50)
     ap.add_argument("--graph-steps", type=int, default=500)
     ap.add_argument("--large-steps", type=int, default=20)
+    ap.add_argument("--batched-steps", type=int, default=1000,
+                    help="steps of the batched fit of 256 shapes (0 skips it)")
+    ap.add_argument("--target-steps", type=int, default=2000,
+                    help="steps of the plain fits to the MAE target (0 skips them)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-seconds", type=float, default=150.0,
                     help="--impl reference: seconds of oracle work over warm-up and timed steps")
@@ -654,6 +802,36 @@ def main():
             "note": "CUDA events around the whole call: graph capture and instantiation included"}
         del small, sp, sm_, sv_, sws
 
+    # ---- plain fits to an MAE target (the plain half of the metric): the
+    # fit runs in chunks of steps (CUDA events around each chunk's
+    # efunc_fit); between chunks efunc_eval_loss evaluates the held-out MAE
+    # on the device (not timed): 2^19 uniform + 2^19 near-surface points
+    # drawn apart from the training pool, the paper's volume / near-surface
+    # split of its AE metrics (Sec. 4.1)
+    to_target = None
+    if args.target_steps > 0:
+        to_target = {}
+        for cname, (Rt, Jt, shape_t, seed_t) in (("C2 32^3 union of 8", (R, J, synth.random_union(0), 0)),
+                                                 ("C1 16^3 sphere", (16, 65536, synth.sphere(0.5), 1))):
+            if Rt == R and Jt == J:
+                pool_t = pool
+            else:
+                pool_t = torch.from_numpy(np.concatenate([synth.sample_batch(shape_t, Jt, seed=500 + b)
+                                                          for b in range(N_BATCHES)])).to(dev)
+            held = {k: torch.from_numpy(synth.sample_batch(shape_t, HELDOUT // 2, seed=900 + seed_t, near_frac=f))
+                    .to(dev) for k, f in (("volume", 0.0), ("near", 1.0))}
+            to_target[cname] = fit_to_target(api, dev, stream, Rt, Jt, pool_t, held, rank, args.target_steps,
+                                             TARGET_CHUNK, TARGET_MAE, ws)
+            log(f"[bench] {cname}: {to_target[cname]['summary']}")
+            del pool_t, held
+
+    # ---- batched fit of many shapes of uneven size (efunc_fit_batched)
+    batched = None
+    if args.batched_steps > 0:
+        batched = bench_batched(api, dev, stream, rank, args.batched_steps, peak, ws)
+        log(f"[bench] batched: {batched['ms_per_step']:.3f} ms/step, {batched['value']:.3e} q/s, "
+            f"frac {batched['frac']:.3f}, tuning {batched['tuning']}")
+
     # ---- end to end through the C ABI with host buffers: the batch pool in
     # pinned host memory, every step copies its 64 MiB batch to the device
     # (overlapped with the previous step's compute by the library) and copies
@@ -709,6 +887,8 @@ def main():
             "cpu_baseline": cpu_line,
             "clocks": clocks,
             "gpu_launches": launches,
+            "fits_to_target": to_target,
+            "batched_fit": batched,
             "fit": {"steps_total": args.warmup + args.steps, "loss_first_timed": float(st[0, 0]),
                     "mae_first_timed": float(st[0, 1]), "mae_last": float(st[-1, 1]),
                     "fits_per_s": 1e3 / (FIT_STEPS_32 * ms) * ws, "steps_per_fit": FIT_STEPS_32},

@@ -208,6 +208,41 @@ efunc_status efunc_backward_grad(const efunc_grid *grid, const float *params, co
                                  int32_t q_stride, const float *gO, const float *gG, float *grad, void *workspace,
                                  size_t workspace_bytes, efunc_stream_t stream);
 
+/* Loss of the representation on a batch of J rows (x, y, z, target SDF),
+ * without any gradient: the forward of Algorithm 1 at every row, then
+ *   out[0] = mean_j (O_j - o_j)^2     (Eq. loss)
+ *   out[1] = mean_j |O_j - o_j|       (the absolute error the paper reports
+ *                                      as its AE metrics, Sec. 4.1)
+ * summed in FP64 and written as FP32.  For held-out error curves of a fit.
+ *   qo       [device] J x 4 floats, J >= 1
+ *   out      [device] 2 floats
+ *   workspace  at least efunc_eval_workspace_bytes(grid, J) */
+efunc_status efunc_eval_loss(const efunc_grid *grid, const float *params, const float *qo, int64_t J, float *out,
+                             void *workspace, size_t workspace_bytes, efunc_stream_t stream);
+
+/* ------------------------------------------------------------- FP64 path */
+
+/* The forward and backward above in FP64 (Algorithm 1, Algorithm 2, Eq.
+ * func-normal), for finite-difference checks of the implementation: the same
+ * fused kernels instantiated for double, with exp2 / log2 in double instead
+ * of the SFU approximations.  The window of a query is chosen, as in the
+ * FP32 path, from its coordinates rounded to FP32; everything after that is
+ * FP64.  Not a hot path (FP64 runs far below the FP32 rate on this GPU).
+ *   params   [device] R^3*13 doubles; q [device] J rows of q_stride doubles;
+ *   O, lse, dOdq, gO, grad, gq as efunc_forward / efunc_backward, in double
+ *   workspace  at least efunc_f64_workspace_bytes(grid, J) */
+size_t efunc_f64_workspace_bytes(const efunc_grid *grid, int64_t J);
+
+efunc_status efunc_forward_f64(const efunc_grid *grid, const double *params, const double *q, int64_t J,
+                               int32_t q_stride, double *O, double *lse, double *dOdq, void *workspace,
+                               size_t workspace_bytes, efunc_stream_t stream);
+
+/* ACCUMULATES grad[i*13 + s] += sum_j gO_j dO(q_j)/dtheta_{i,s} (double
+ * atomics); gq (or NULL) is written with gO_j dO/dq_j. */
+efunc_status efunc_backward_f64(const efunc_grid *grid, const double *params, const double *q, int64_t J,
+                                int32_t q_stride, const double *gO, double *grad, double *gq, void *workspace,
+                                size_t workspace_bytes, efunc_stream_t stream);
+
 /* One Adam/AdamW step over n floats (Sec. 3.4), step is 1-based (bias
  * correction).  params, m, v are updated in place; grad is read and then
  * zeroed.  All four [device], n >= 0. */
@@ -380,6 +415,97 @@ efunc_status efunc_cosine_fit(const efunc_grid *grid, int32_t bands, const efunc
                               int32_t steps, int64_t step0, float *stats, void *workspace, size_t workspace_bytes,
                               efunc_stream_t stream);
 
+/* ------------------------------------------------------------ batched fit */
+
+/* Many shapes of uneven grid resolution and query count fitted together.
+ * The paper fits one shape in about 20 minutes (Sec. 5, limitations); this
+ * call fits S shapes at once, every step one launch of each kernel for all
+ * of them: the cell sort of all shapes' queries (a shape's queries binned
+ * on its own grid), the key pack of all grids, the fused forward + loss +
+ * backward over the work items of every shape (an item's shape selects its
+ * grid), per-shape loss statistics, and one Adam step over the concatenated
+ * grids (Sec. 3.4 for each shape; one shared step count and learning rate).
+ *
+ * Shape s has an R_s^3 grid (13 floats per centre, layout of efunc_forward)
+ * stored at float offset 13 * sum_{s' < s} R_s'^3 of params / m / v, and J_s
+ * queries per batch; a batch holds the rows (x, y, z, target SDF) of every
+ * shape in shape order, sum_s J_s rows.  S in [1, 1024], J_s >= 1,
+ * sum_s J_s <= 2^30. */
+typedef struct {
+    int32_t R;           /* grid resolution, [1, 256] */
+    float log_beta0;     /* log-scale of b = 0 (efunc_default_log_beta0(R) by default) */
+    int64_t J;           /* queries per batch */
+} efunc_shape;
+
+/* Launch configuration of the batched fit, chosen by efunc_tune_batched:
+ *   chunk        queries per work item at most, [32, 256]
+ *   lanes2_max   work items of at most this many queries take 2 lanes per
+ *   lanes4_max   query in the forward, of at most lanes4_max 4 lanes
+ *                (lanes4_max <= lanes2_max <= 256)
+ *   sort_blocks  blocks per SM of the sort's bin and scatter kernels, [1, 16] */
+typedef struct {
+    int32_t chunk;
+    int32_t lanes2_max;
+    int32_t lanes4_max;
+    int32_t sort_blocks;
+} efunc_tuning;
+
+/* The configuration used when none is given: {256, 64, 32, 8}. */
+void efunc_default_tuning(efunc_tuning *out);
+
+/* Floats per array (params, m, v) of S shapes, sum 13 R_s^3; -1 if a shape
+ * is invalid. */
+int64_t efunc_batched_param_count(const efunc_shape *shapes, int32_t S);
+
+/* Rows of one batch, sum J_s; -1 if a shape is invalid. */
+int64_t efunc_batched_query_count(const efunc_shape *shapes, int32_t S);
+
+/* Workspace bytes of efunc_fit_batched / efunc_eval_batched /
+ * efunc_tune_batched for these shapes (any tuning); 0 if a shape is invalid. */
+size_t efunc_batched_workspace_bytes(const efunc_shape *shapes, int32_t S);
+
+/* Batched fitting loop: for it in [0, steps), batch (it mod n_batches) of
+ * qo, the step above, with Adam step number step0 + it + 1.
+ *   shapes   [host] S shape descriptions
+ *   params, m, v  [device] efunc_batched_param_count floats each, updated
+ *   qo       [device] n_batches * efunc_batched_query_count rows of 4 floats
+ *   stats    [device] steps x S x 2 floats or NULL: (loss, MAE) of every
+ *            shape at every step, at the parameters before the step
+ *   tuning   [host] or NULL (efunc_default_tuning)
+ *   graph    1: one period of n_batches steps is captured into a CUDA graph
+ *            and replayed (steps / n_batches) times, the rest issued one by
+ *            one (Adam's step number and the statistics row advance on the
+ *            device); 0: every step issued one by one.  With graph = 1 the
+ *            call must not be made while `stream` is being captured.
+ * n_batches in [1, 64].  The shape table is copied from host memory to the
+ * workspace at the start of the call (the call returns after that copy). */
+efunc_status efunc_fit_batched(const efunc_shape *shapes, int32_t S, const efunc_adam *adam, int32_t loss,
+                               float *params, float *m, float *v, const float *qo, int32_t n_batches, int32_t steps,
+                               int64_t step0, float *stats, const efunc_tuning *tuning, int32_t graph,
+                               void *workspace, size_t workspace_bytes, efunc_stream_t stream);
+
+/* Per-shape loss of S shapes on one batch (efunc_eval_loss for each shape,
+ * in one sort and one launch): out[2 s] = mean (O - o)^2 and
+ * out[2 s + 1] = mean |O - o| over shape s's rows.
+ *   qo  [device] efunc_batched_query_count rows of 4 floats
+ *   out [device] 2 S floats */
+efunc_status efunc_eval_batched(const efunc_shape *shapes, int32_t S, const float *params, const float *qo,
+                                float *out, const efunc_tuning *tuning, void *workspace, size_t workspace_bytes,
+                                efunc_stream_t stream);
+
+/* Autotuner of the batched fit: times trial_steps steps of efunc_fit_batched
+ * (after one untimed step) for each of 12 configurations (chunk 128 / 256,
+ * lane thresholds 64 / 32 and 96 / 48, 2 / 4 / 8 sort blocks per SM) on
+ * these shapes and batches, with CUDA events on `stream`, and writes the
+ * fastest to *best (and its milliseconds per step to *best_ms_per_step, or
+ * NULL).  The trial steps are Adam steps with learning rate 0: params are
+ * left as they are and m, v are zeroed at the end (tune before fitting).
+ * Synchronises the stream.  trial_steps in [1, 1000]. */
+efunc_status efunc_tune_batched(const efunc_shape *shapes, int32_t S, int32_t loss, float *params, float *m,
+                                float *v, const float *qo, int32_t n_batches, int32_t trial_steps,
+                                efunc_tuning *best, double *best_ms_per_step, void *workspace,
+                                size_t workspace_bytes, efunc_stream_t stream);
+
 /* ---------------------------------------------------- checkpoint / resume */
 
 /* A fit's state is its parameter grid, Adam's two moments and the number of
@@ -434,7 +560,10 @@ void efunc_profile_enable(int32_t enable);
  * "bin", "scan_reduce", "scan_top", "scan_emit", "scatter", "pack_keys",
  * "forward", "fused_backward", "fused_fit", "adam", "mean_shift", "variant_pack",
  * "variant_forward", "variant_backward", "variant_fit", "cosine_pack",
- * "cosine_forward", "cosine_backward", "cosine_fit").  Returns 0 on success, -1 for an
+ * "cosine_forward", "cosine_backward", "cosine_fit", "eval" (efunc_eval_loss,
+ * efunc_eval_batched), "f64" (every kernel of the FP64 calls), "batched"
+ * (the batched fit's fused kernel) or "batched_stats" (its per-shape
+ * statistics)).  Returns 0 on success, -1 for an
  * unknown name or a CUDA error. */
 int32_t efunc_profile_read(const char *name, double *total_ms, int64_t *launches);
 

@@ -51,6 +51,7 @@ def _configure(lib):
     lib.ora_window_base.restype = i32
     lib.ora_forward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp, dp, dp]
     lib.ora_backward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
+    lib.ora_forward_err_terms.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
     lib.ora_forward_global.argtypes = [i32, f64, dp, dp, i64, i32, dp, dp]
     lib.ora_backward_grad.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
     lib.ora_mean_shift.argtypes = [i32, f64, dp, i64, dp]
@@ -62,7 +63,7 @@ def _configure(lib):
     lib.ora_cosine_backward.argtypes = [i32, i32, f64, i32, dp, dp, i64, i32, dp, dp]
     lib.ora_loss_grad.argtypes = [i32, dp, dp, i64, dp, dp, dp]
     lib.ora_adam.argtypes = [i64, dp, dp, dp, dp, i64, f64, f64, f64, f64, f64, i32]
-    for fn in ("ora_forward", "ora_backward", "ora_forward_global", "ora_loss_grad", "ora_adam",
+    for fn in ("ora_forward", "ora_forward_err_terms", "ora_backward", "ora_forward_global", "ora_loss_grad", "ora_adam",
                "ora_backward_grad", "ora_mean_shift", "ora_variant_forward", "ora_variant_backward",
                "ora_cosine_forward", "ora_cosine_backward"):
         getattr(lib, fn).restype = None
@@ -176,6 +177,21 @@ def forward(params, q, R: int, W: int = 2, log_beta0: float | None = None, want_
         out.append(kappa)
     if want_dq_sens:
         out.append(sens)
+    return tuple(out)
+
+
+def dq_error_terms(params, q, R: int, W: int = 2, log_beta0: float | None = None):
+    """(kappa_G, fabs, gabs) per query, the error terms of G = dO/dq (Eq.
+    func-normal) under relative rounding, with g = d + 2 beta (q - key)(O - f)
+    a key's term of G:
+      kappa_G = sum softmax (|exponent| + 1) ||g - G||  (rounding of the weights)
+      fabs    = sum softmax (|o| + sum_a |d_a r_a|)      (rounding of the values f)
+      gabs    = sum softmax ||(|d_a| + 2 beta |r_a| |O - f|)_a||  (of G's terms)
+    Diagnostics used to derive the FP32 tolerance of dO/dq."""
+    lb = default_log_beta0(R) if log_beta0 is None else float(log_beta0)
+    params, q = _check(params, q, R)
+    out = [np.zeros(q.shape[0]) for _ in range(3)]
+    _load().ora_forward_err_terms(R, W, lb, _ptr(params), _ptr(q), q.shape[0], q.shape[1], *(_ptr(a) for a in out))
     return tuple(out)
 
 

@@ -226,6 +226,59 @@ void ora_forward(int R, int W, double log_beta0, const double *params, const dou
                     dq ? dq + 3 * j : NULL, kappa ? &kappa[j] : NULL, dq_sens ? &dq_sens[j] : NULL);
 }
 
+/* Error terms of dO/dq (Eq. func-normal) for its floating-point tolerance.
+ * With g_i = d_i + 2 beta_i (q - p_i)(O - f_i) the term of key i,
+ * G = dO/dq = sum softmax_i g_i:
+ *   kappa_G = sum softmax * (|expo| + 1) * ||g - G||
+ *     multiplying every weight by (1 + eps_i) moves G, to first order, by
+ *     sum softmax_i eps_i (g_i - G) (plus the change of O, which enters with
+ *     the factor dq_sens of forward_one): at most eps kappa_G when each
+ *     exponent and weight carries a relative error eps;
+ *   fabs = sum softmax * (|o| + |d_x r_x| + |d_y r_y| + |d_z r_z|)
+ *     relative errors eps in every term of every value f move O by at most
+ *     eps fabs;
+ *   gabs = sum softmax * ||(|d_a| + 2 beta |r_a| |O - f|)_a||
+ *     the same for the terms of G. */
+static void err_terms_one(const double *params, int R, int W, double log_beta0, const double *q, double *kappa_G,
+                          double *fabs_out, double *gabs_out)
+{
+    double O, lse, G[3];
+    forward_one(params, R, W, log_beta0, q, &O, &lse, G, NULL, NULL);
+    int lo[3], hi[3];
+    window_range(q, R, W, lo, hi);
+    double r[3], d2, expo, f, k_sum = 0.0, fa = 0.0, ga = 0.0;
+    for (int a = lo[0]; a <= hi[0]; ++a)
+        for (int b = lo[1]; b <= hi[1]; ++b)
+            for (int c = lo[2]; c <= hi[2]; ++c)
+                for (int s = 0; s < 2; ++s) {
+                    key_t_ k = make_key(params, R, log_beta0, a, b, c, s);
+                    eval_key(&k, q, r, &d2, &expo, &f);
+                    const double w = exp(expo - lse);
+                    double dev2 = 0.0, gab2 = 0.0;
+                    for (int x = 0; x < 3; ++x) {
+                        const double gx = k.d[x] + 2.0 * k.beta * r[x] * (O - f) - G[x];
+                        dev2 += gx * gx;
+                        const double ax = fabs(k.d[x]) + 2.0 * k.beta * fabs(r[x]) * fabs(O - f);
+                        gab2 += ax * ax;
+                    }
+                    k_sum += w * (fabs(expo) + 1.0) * sqrt(dev2);
+                    fa += w * (fabs(k.o) + fabs(k.d[0] * r[0]) + fabs(k.d[1] * r[1]) + fabs(k.d[2] * r[2]));
+                    ga += w * sqrt(gab2);
+                }
+    *kappa_G = k_sum;
+    *fabs_out = fa;
+    *gabs_out = ga;
+}
+
+/* The error terms of J queries (q: J rows of q_stride doubles); diagnostics
+ * for the floating-point tolerance of dO/dq. */
+void ora_forward_err_terms(int R, int W, double log_beta0, const double *params, const double *q, int64_t J,
+                           int q_stride, double *kappa_G, double *fabs_out, double *gabs_out)
+{
+    for (int64_t j = 0; j < J; ++j)
+        err_terms_one(params, R, W, log_beta0, q + j * q_stride, &kappa_G[j], &fabs_out[j], &gabs_out[j]);
+}
+
 /* -------------------------------------------------------------- backward */
 
 /* Algorithm 2 with the closed-form gradients of Sec. 3.6.  For every query j

@@ -39,6 +39,14 @@ class CheckpointInfo(ctypes.Structure):
                 ("step", c_int64), ("seed", ctypes.c_uint64), ("loss", c_int32), ("adam", Adam)]
 
 
+class Shape(ctypes.Structure):
+    _fields_ = [("R", c_int32), ("log_beta0", c_float), ("J", c_int64)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("chunk", c_int32), ("lanes2_max", c_int32), ("lanes4_max", c_int32), ("sort_blocks", c_int32)]
+
+
 KEYS_GRID, KEYS_OFFSET, KEYS_BOTH = 1, 2, 3
 
 # name -> (restype, argtypes); the order follows include/efunc.h
@@ -57,6 +65,13 @@ SIGNATURES = {
                                  c_void_p, c_void_p, c_size_t, c_void_p]),
     "efunc_backward_grad": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p,
                                       c_void_p, c_void_p, c_size_t, c_void_p]),
+    "efunc_eval_loss": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_size_t,
+                                  c_void_p]),
+    "efunc_f64_workspace_bytes": (c_size_t, [ctypes.POINTER(Grid), c_int64]),
+    "efunc_forward_f64": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_size_t, c_void_p]),
+    "efunc_backward_f64": (c_int32, [ctypes.POINTER(Grid), c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p,
+                                     c_void_p, c_void_p, c_size_t, c_void_p]),
     "efunc_adam_step": (c_int32, [ctypes.POINTER(Adam), c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,
                                   c_void_p]),
     "efunc_fit": (c_int32, [ctypes.POINTER(Grid), ctypes.POINTER(Adam), c_int32, c_float, c_void_p, c_void_p,
@@ -91,6 +106,18 @@ SIGNATURES = {
     "efunc_cosine_fit": (c_int32, [ctypes.POINTER(Grid), c_int32, ctypes.POINTER(Adam), c_int32, c_void_p, c_void_p,
                                    c_void_p, c_void_p, c_int64, c_int32, c_int32, c_int64, c_void_p, c_void_p,
                                    c_size_t, c_void_p]),
+    "efunc_default_tuning": (None, [ctypes.POINTER(Tuning)]),
+    "efunc_batched_param_count": (c_int64, [ctypes.POINTER(Shape), c_int32]),
+    "efunc_batched_query_count": (c_int64, [ctypes.POINTER(Shape), c_int32]),
+    "efunc_batched_workspace_bytes": (c_size_t, [ctypes.POINTER(Shape), c_int32]),
+    "efunc_fit_batched": (c_int32, [ctypes.POINTER(Shape), c_int32, ctypes.POINTER(Adam), c_int32, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_int32, c_int32, c_int64, c_void_p, ctypes.POINTER(Tuning),
+                                    c_int32, c_void_p, c_size_t, c_void_p]),
+    "efunc_eval_batched": (c_int32, [ctypes.POINTER(Shape), c_int32, c_void_p, c_void_p, c_void_p,
+                                     ctypes.POINTER(Tuning), c_void_p, c_size_t, c_void_p]),
+    "efunc_tune_batched": (c_int32, [ctypes.POINTER(Shape), c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                     c_int32, c_int32, ctypes.POINTER(Tuning), ctypes.POINTER(c_double), c_void_p,
+                                     c_size_t, c_void_p]),
     "efunc_profile_enable": (None, [c_int32]),
     "efunc_profile_read": (c_int32, [c_char_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     "efunc_profile_reset": (None, []),

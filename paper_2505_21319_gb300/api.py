@@ -24,11 +24,11 @@ def _stream(device):
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
-def _need(t: torch.Tensor, name: str, numel: int | None = None):
+def _need(t: torch.Tensor, name: str, numel: int | None = None, dtype=torch.float32):
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
-    if t.dtype != torch.float32:
-        raise TypeError(f"{name} must be float32, got {t.dtype}")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if numel is not None and t.numel() != numel:
@@ -84,8 +84,8 @@ def _workspace(device, ws: Workspace | None) -> Workspace:
     return _default_ws[key]
 
 
-def _queries(q: torch.Tensor):
-    _need(q, "q")
+def _queries(q: torch.Tensor, dtype=torch.float32):
+    _need(q, "q", dtype=dtype)
     if q.dim() != 2 or q.shape[1] not in (3, 4):
         raise ValueError("q must be (J, 3) or (J, 4)")
     return q.shape[0], q.shape[1]
@@ -164,6 +164,68 @@ def efunc_backward_grad(params: torch.Tensor, q: torch.Tensor, gO: torch.Tensor 
                                                                 _ptr(gO), _ptr(gG), _ptr(grad), _ptr(buf), n,
                                                                 _stream(q.device)))
     return grad
+
+
+def efunc_eval_loss(params: torch.Tensor, qo: torch.Tensor, log_beta0: float | None = None,
+                    ws: Workspace | None = None) -> torch.Tensor:
+    """(mean (O - o)^2, mean |O - o|) over rows (x, y, z, target) of ``qo``,
+    as a CUDA float32 tensor of 2 (no synchronisation)."""
+    R = resolution_of(params)
+    _need(params, "params")
+    _need(qo, "qo")
+    if qo.dim() != 2 or qo.shape[1] != 4 or qo.shape[0] < 1:
+        raise ValueError("qo must be (J, 4) with J >= 1")
+    J = qo.shape[0]
+    grid = make_grid(R, log_beta0)
+    out = torch.empty(2, dtype=torch.float32, device=qo.device)
+    buf, n = _workspace(qo.device, ws).get(grid, J, eval_only=True)
+    B.check("efunc_eval_loss", B.load().efunc_eval_loss(ctypes.byref(grid), _ptr(params), _ptr(qo), J, _ptr(out),
+                                                        _ptr(buf), n, _stream(qo.device)))
+    return out
+
+
+def _f64_workspace(device, grid, J):
+    n = int(B.load().efunc_f64_workspace_bytes(ctypes.byref(grid), int(J)))
+    if n == 0:
+        raise ValueError("invalid grid or query count")
+    return torch.empty(n, dtype=torch.uint8, device=device), n
+
+
+def efunc_forward_f64(params: torch.Tensor, q: torch.Tensor, log_beta0: float | None = None, want_lse: bool = False,
+                      want_dq: bool = False):
+    """The forward in FP64 (float64 params and queries): O, optionally lse and dO/dq."""
+    R = resolution_of(params)
+    _need(params, "params", dtype=torch.float64)
+    J, stride = _queries(q, torch.float64)
+    grid = make_grid(R, log_beta0)
+    O = torch.empty(J, dtype=torch.float64, device=q.device)
+    lse = torch.empty(J, dtype=torch.float64, device=q.device) if want_lse else None
+    dq = torch.empty((J, 3), dtype=torch.float64, device=q.device) if want_dq else None
+    buf, n = _f64_workspace(q.device, grid, J)
+    B.check("efunc_forward_f64", B.load().efunc_forward_f64(ctypes.byref(grid), _ptr(params), _ptr(q), J, stride,
+                                                            _ptr(O), _ptr(lse), _ptr(dq), _ptr(buf), n,
+                                                            _stream(q.device)))
+    out = [O] + ([lse] if want_lse else []) + ([dq] if want_dq else [])
+    return out[0] if len(out) == 1 else tuple(out)
+
+
+def efunc_backward_f64(params: torch.Tensor, q: torch.Tensor, gO: torch.Tensor, grad: torch.Tensor | None = None,
+                       want_gq: bool = False, log_beta0: float | None = None):
+    """The backward in FP64: accumulates dL/dparams into ``grad``; optionally dL/dq."""
+    R = resolution_of(params)
+    _need(params, "params", dtype=torch.float64)
+    J, stride = _queries(q, torch.float64)
+    _need(gO, "gO", J, dtype=torch.float64)
+    if grad is None:
+        grad = torch.zeros_like(params)
+    _need(grad, "grad", params.numel(), dtype=torch.float64)
+    gq = torch.empty((J, 3), dtype=torch.float64, device=q.device) if want_gq else None
+    grid = make_grid(R, log_beta0)
+    buf, n = _f64_workspace(q.device, grid, J)
+    B.check("efunc_backward_f64", B.load().efunc_backward_f64(ctypes.byref(grid), _ptr(params), _ptr(q), J, stride,
+                                                              _ptr(gO), _ptr(grad), _ptr(gq), _ptr(buf), n,
+                                                              _stream(q.device)))
+    return (grad, gq) if want_gq else grad
 
 
 def efunc_mean_shift_init(params: torch.Tensor, pts: torch.Tensor, bandwidth: float = 100.0):
@@ -483,24 +545,105 @@ class EfuncFn(torch.autograd.Function):
     """O = EfuncFn.apply(params, q): differentiable in params and q.
 
     Forward: Algorithm 1.  Backward: Algorithm 2 for dL/dparams and
-    Eq. func-normal for dL/dq, both recomputed from (params, q)."""
+    Eq. func-normal for dL/dq, both recomputed from (params, q).  float32
+    tensors run the hot-path kernels, float64 tensors their FP64
+    instantiation (for torch.autograd.gradcheck)."""
 
     @staticmethod
     def forward(ctx, params, q, log_beta0=None):
         ctx.save_for_backward(params, q)
         ctx.log_beta0 = log_beta0
-        return efunc_forward(params.detach().contiguous(), q.detach().contiguous(), log_beta0=log_beta0)
+        fwd = efunc_forward_f64 if params.dtype == torch.float64 else efunc_forward
+        return fwd(params.detach().contiguous(), q.detach().contiguous(), log_beta0=log_beta0)
 
     @staticmethod
     def backward(ctx, gO):
         params, q = ctx.saved_tensors
         need_q = ctx.needs_input_grad[1]
-        out = efunc_backward(params.detach().contiguous(), q.detach().contiguous(), gO.contiguous(),
-                             want_gq=need_q, log_beta0=ctx.log_beta0)
+        bwd = efunc_backward_f64 if params.dtype == torch.float64 else efunc_backward
+        out = bwd(params.detach().contiguous(), q.detach().contiguous(), gO.contiguous(),
+                  want_gq=need_q, log_beta0=ctx.log_beta0)
         gp, gq = (out if need_q else (out, None))
         if gq is not None and q.shape[1] == 4:
             gq = torch.cat([gq, torch.zeros_like(gq[:, :1])], 1)
         return (gp if ctx.needs_input_grad[0] else None), gq, None
+
+
+# ------------------------------------------------------------ batched fit
+
+class Batch:
+    """S shapes fitted together (efunc_fit_batched): ``Rs`` grid
+    resolutions, ``Js`` queries per batch of each shape.  Parameters of all
+    shapes live in one float32 tensor, shape s at offset 13 sum_{s'<s} R^3;
+    a batch is (sum J, 4) rows, the shapes' rows in order."""
+
+    def __init__(self, Rs, Js, log_beta0s=None, device="cuda"):
+        if len(Rs) != len(Js) or not Rs:
+            raise ValueError("Rs and Js must be non-empty and of equal length")
+        lbs = [default_log_beta0(R) for R in Rs] if log_beta0s is None else list(log_beta0s)
+        self.S = len(Rs)
+        self.Rs, self.Js = [int(r) for r in Rs], [int(j) for j in Js]
+        self.shapes = (B.Shape * self.S)(*[B.Shape(int(R), float(lb), int(J)) for R, lb, J in zip(Rs, lbs, Js)])
+        lib = B.load()
+        self.n_params = int(lib.efunc_batched_param_count(self.shapes, self.S))
+        self.n_queries = int(lib.efunc_batched_query_count(self.shapes, self.S))
+        if self.n_params < 0 or self.n_queries < 0:
+            raise ValueError("invalid shape list")
+        self.param_offsets = [0]
+        self.query_offsets = [0]
+        for R, J in zip(self.Rs, self.Js):
+            self.param_offsets.append(self.param_offsets[-1] + 13 * R ** 3)
+            self.query_offsets.append(self.query_offsets[-1] + J)
+        self.device = torch.device(device)
+        self.ws = torch.empty(int(lib.efunc_batched_workspace_bytes(self.shapes, self.S)), dtype=torch.uint8,
+                              device=self.device)
+        self.tuning = None
+
+    def params_of(self, t: torch.Tensor, s: int) -> torch.Tensor:
+        return t[self.param_offsets[s]:self.param_offsets[s + 1]]
+
+    def rows_of(self, batch: torch.Tensor, s: int) -> torch.Tensor:
+        return batch[self.query_offsets[s]:self.query_offsets[s + 1]]
+
+    def _tuning(self):
+        return ctypes.byref(self.tuning) if self.tuning is not None else None
+
+    def fit(self, params, m, v, qo, steps: int, n_batches: int = 1, step0: int = 0, loss: str = "l1", stats=None,
+            graph: bool = True, **adam_kw):
+        for t, nm in ((params, "params"), (m, "m"), (v, "v")):
+            _need(t, nm, self.n_params)
+        _need(qo, "qo", 4 * self.n_queries * n_batches)
+        if stats is not None:
+            _need(stats, "stats", 2 * self.S * steps)
+        ad = make_adam(**adam_kw)
+        lk = {"l1": B.LOSS_L1, "mse": B.LOSS_MSE}[loss]
+        B.check("efunc_fit_batched", B.load().efunc_fit_batched(
+            self.shapes, self.S, ctypes.byref(ad), lk, _ptr(params), _ptr(m), _ptr(v), _ptr(qo), n_batches, steps,
+            step0, _ptr(stats), self._tuning(), int(bool(graph)), _ptr(self.ws), self.ws.numel(),
+            _stream(self.device)))
+
+    def eval(self, params, qo) -> torch.Tensor:
+        """(S, 2): mean squared and mean absolute error of every shape on qo."""
+        _need(params, "params", self.n_params)
+        _need(qo, "qo", 4 * self.n_queries)
+        out = torch.empty((self.S, 2), dtype=torch.float32, device=self.device)
+        B.check("efunc_eval_batched", B.load().efunc_eval_batched(
+            self.shapes, self.S, _ptr(params), _ptr(qo), _ptr(out), self._tuning(), _ptr(self.ws), self.ws.numel(),
+            _stream(self.device)))
+        return out
+
+    def tune(self, params, m, v, qo, n_batches: int = 1, trial_steps: int = 3, loss: str = "l1"):
+        """Pick the fastest launch configuration (efunc_tune_batched); params
+        unchanged, m and v zeroed.  Returns (tuning dict, ms per step)."""
+        best = B.Tuning()
+        ms = ctypes.c_double(0)
+        lk = {"l1": B.LOSS_L1, "mse": B.LOSS_MSE}[loss]
+        B.check("efunc_tune_batched", B.load().efunc_tune_batched(
+            self.shapes, self.S, lk, _ptr(params), _ptr(m), _ptr(v), _ptr(qo), n_batches, trial_steps,
+            ctypes.byref(best), ctypes.byref(ms), _ptr(self.ws), self.ws.numel(), _stream(self.device)))
+        self.tuning = best
+        return ({"chunk": best.chunk, "lanes2_max": best.lanes2_max, "lanes4_max": best.lanes4_max,
+                 "sort_blocks": best.sort_blocks}, ms.value)
 
 
 def profile(enable: bool = True):

@@ -46,8 +46,24 @@ constexpr int kScanSegment = 512; // bins per scan block
 
 // Work item: one window-base cell and a contiguous slice of its sorted queries.
 //   x = first sorted row, y = number of rows (1..kChunk),
-//   z = packed cell (ux | uy << 10 | uz << 20) with u = c + 1 in [0, R].
+//   z = packed cell (ux | uy << 10 | uz << 20) with u = c + 1 in [0, R],
+//   w = shape of the item in a batched fit (0 otherwise).
 using Item = int4;
+
+// One shape of a batched fit (many grids of uneven resolution and query
+// count fitted together).  Its queries are rows [q_off, q_off + J) of every
+// batch, its histogram bins [bin_off, bin_off + P^3 * 64), its centres
+// [c_off, c_off + R^3) of the concatenated grids (key records at 4 c_off,
+// parameters and gradient at 13 c_off).
+struct BatchShape {
+    int R, P;
+    int64_t q_off, J;
+    int64_t bin_off, c_off;
+    double log_beta0;
+    float inv_J;
+    int pad;
+};
+constexpr int kMaxShapes = 1024;
 
 // Per-call control block at the start of the workspace.
 struct Ctrl {
@@ -95,7 +111,24 @@ struct SortArgs {
     int *perm;
     Item *items;
     Ctrl *ctrl;
+    // batched sort (shapes != NULL): S shapes, queries of shape s binned on
+    // its own grid into bins bin_off + [0, P^3 * 64); R / P above unused
+    const BatchShape *shapes;
+    int S;
+    int chunk;           // queries per work item at most (batched sort; kChunk otherwise)
 };
+
+// Four doubles in one 32-byte aligned record: the FP64 counterpart of a
+// float4 key record or query row.
+struct alignas(32) Double4 {
+    double x, y, z, w;
+};
+
+// Vector types of the scalar type a kernel computes in.
+template <typename T> struct VecOf;
+template <> struct VecOf<float> { using V4 = float4; using V2 = float2; };
+template <> struct VecOf<double> { using V4 = Double4; using V2 = double2; };
+template <typename T> using V4Of = typename VecOf<T>::V4;
 
 // Key records of one centre, 4 float4 (64 bytes), built once per call by the
 // pack kernel from the 13 parameters:
@@ -107,35 +140,44 @@ struct SortArgs {
 // no absolute position near +-1 is ever rounded.
 constexpr int kKeyRecords = 4;
 
-struct PackArgs {
-    const float *params;
-    float4 *keys;
+template <typename T>
+struct PackArgsT {
+    const T *params;
+    V4Of<T> *keys;
     int R;
     double log_beta0;
 };
+using PackArgs = PackArgsT<float>;
+using PackArgs64 = PackArgsT<double>;
 
-// Fused-kernel arguments.
-struct FusedArgs {
-    const float4 *keys;  // packed key records, R^3 * 4
+
+// Fused-kernel arguments, for the scalar type T of its arithmetic (float:
+// the hot path; double: the same kernels in FP64 for finite-difference
+// checks).
+template <typename T>
+struct FusedArgsT {
+    const V4Of<T> *keys;  // packed key records, R^3 * 4
     int R;
-    const float4 *sorted;
+    const V4Of<T> *sorted;
     const int *perm;
     const Item *items;
     Ctrl *ctrl;
     // forward outputs (user order)
-    float *O;
-    float *lse;
-    float *dq;
+    T *O;
+    T *lse;
+    T *dq;
     // backward inputs / outputs
-    const float *gO;     // user order, or NULL (no value term) in second-order mode
-    const float *gG;     // user order J x 3: dL/d(dO/dq) (second-order backward)
-    float *grad;
-    float *gq;           // user order
-    // fit
+    const T *gO;         // user order, or NULL (no value term) in second-order mode
+    const T *gG;         // user order J x 3: dL/d(dO/dq) (second-order backward)
+    T *grad;
+    T *gq;               // user order
+    // fit / evaluation
     int loss;
     float inv_J;
     float eik_weight;    // weight of the Eikonal term (|dO/dq|^2 - 1)^2 in the fit
 };
+using FusedArgs = FusedArgsT<float>;
+using FusedArgs64 = FusedArgsT<double>;
 
 struct AdamArgs {
     float *p, *g, *m, *v;
@@ -209,10 +251,38 @@ struct CosineArgs {
     int leave_room;      // persistent grid leaves room for the next batch's sort (pipelined fit)
 };
 
+// Extra arguments of the batched fused kernel (a second kernel parameter, so
+// that the other instantiations keep their argument layout): per-item shape
+// (Item.w) -> R, key records, gradient, 1/J; loss sums per shape in
+// shape_sums[2 s + {0, 1}]; lane thresholds of the forward (items of at most
+// lanes2_max / lanes4_max queries use 2 / 4 lanes per query).
+struct BatchArgs {
+    const BatchShape *shapes;
+    double *shape_sums;
+    int lanes2_max, lanes4_max;
+};
+
+// Batched fit (many shapes, one launch per kernel per step).
+struct BatchedPackArgs {
+    const float *params;   // concatenated grids, 13 floats per centre
+    float4 *keys;
+    const BatchShape *shapes;
+    int S;
+    int64_t n_centres;
+};
+struct BatchedStatsArgs {
+    const BatchShape *shapes;
+    int S;
+    double *sums;          // 2 S loss / |error| sums, zeroed after reading
+    float *stats;          // steps x S x 2 (loss, MAE) or NULL
+    const void *clk;       // AdamClock: statistics row t - t_first
+    float *out;            // S x 2 (mean squared, mean absolute error) of an evaluation, or NULL
+};
+
 // Kernel identifiers for the profiler.
 enum KernelId { K_BIN = 0, K_SCAN_REDUCE, K_SCAN_TOP, K_SCAN_EMIT, K_SCATTER, K_PACK_KEYS, K_FORWARD, K_FUSED_BWD,
                 K_FUSED_FIT, K_ADAM, K_MEAN_SHIFT, K_VAR_PACK, K_VAR_FORWARD, K_VAR_BACKWARD, K_VAR_FIT, K_COS_PACK, K_COS_FORWARD, K_COS_BACKWARD,
-                K_COS_FIT, K_COUNT };
+                K_COS_FIT, K_EVAL, K_F64, K_BATCHED, K_BATCHED_STATS, K_COUNT };
 
 // Launch bookkeeping (launch counter and optional CUDA-event profiling).
 void launch_begin(int kid, cudaStream_t s);
@@ -227,6 +297,29 @@ cudaError_t launch_pack_keys(const PackArgs &a, cudaStream_t s);
 cudaError_t launch_forward(const FusedArgs &a, bool with_dq, int grid, cudaStream_t s);
 cudaError_t launch_fused_backward(const FusedArgs &a, bool with_gq, bool second_order, int grid, cudaStream_t s);
 cudaError_t launch_fused_fit(const FusedArgs &a, bool eikonal, int grid, cudaStream_t s);
+// Forward over a batch of (x, y, z, target) rows that only sums the loss:
+// ctrl->loss_sum += sum (O - o)^2, ctrl->abs_sum += sum |O - o|.
+cudaError_t launch_fused_eval(const FusedArgs &a, int grid, cudaStream_t s);
+// out[0] = loss_sum * inv_J, out[1] = abs_sum * inv_J (FP32, device)
+cudaError_t launch_eval_finish(const Ctrl *ctrl, double inv_J, float *out, cudaStream_t s);
+// FP64 instantiations (no fast paths: exp2 / log2 in double) of the pack,
+// forward and backward kernels, and the gather of FP64 query rows in sorted
+// order (rows64[i] = q64[perm[i]], q_stride 3 or 4, w = 0 for stride 3).
+cudaError_t launch_pack_keys64(const PackArgs64 &a, cudaStream_t s);
+cudaError_t launch_forward64(const FusedArgs64 &a, bool with_dq, int grid, cudaStream_t s);
+cudaError_t launch_fused_backward64(const FusedArgs64 &a, bool with_gq, int grid, cudaStream_t s);
+cudaError_t launch_round_queries(const double *q64, int64_t J, int q_stride, float4 *rows32, cudaStream_t s);
+cudaError_t launch_gather_queries64(const double *q64, int64_t J, int q_stride, const int *perm, Double4 *rows64,
+                                    cudaStream_t s);
+int fused_grid_size64();
+// batched fit: sort of all shapes' queries (bins per shape), key pack over
+// all grids, fused fit / evaluation kernel with per-item shapes, per-shape
+// statistics
+cudaError_t launch_sort_batched(const SortArgs &a, cudaStream_t s, int blocks_per_sm);
+cudaError_t launch_pack_keys_batched(const BatchedPackArgs &a, cudaStream_t s);
+cudaError_t launch_fused_batched(const FusedArgs &a, const BatchArgs &b, bool eval, int grid, cudaStream_t s);
+cudaError_t launch_batched_stats(const BatchedStatsArgs &a, cudaStream_t s);
+int fused_batched_grid_size();
 int fused_fit_grid_size(bool eikonal, bool leave_room);   // persistent grid of the fit kernel
 // CTAs per SM of a persistent kernel reduced until the registers of
 // sort_blocks sort blocks (kSortThreads x 32 each) stay free on every SM.

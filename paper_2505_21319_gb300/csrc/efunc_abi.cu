@@ -43,7 +43,7 @@ const char *const kKernelNames[K_COUNT] = {"bin",       "scan_reduce", "scan_top
                                            "pack_keys", "forward",     "fused_backward", "fused_fit", "adam",
                                            "mean_shift", "variant_pack", "variant_forward", "variant_backward",
                                            "variant_fit", "cosine_pack", "cosine_forward", "cosine_backward",
-                                           "cosine_fit"};
+                                           "cosine_fit", "eval", "f64", "batched", "batched_stats"};
 
 cudaEvent_t take_event()
 {
@@ -202,6 +202,26 @@ efunc_status check_workspace(const efunc_grid *g, int64_t J, const void *ws, siz
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return EFUNC_ERR_WORKSPACE;
     if (ws_bytes < (fit ? make_layout(g->R, J) : eval_layout(g->R, J)).total) return EFUNC_ERR_WORKSPACE;
     return EFUNC_OK;
+}
+
+// FP64 calls: the forward's layout followed by the FP32 rows that choose
+// the windows (J x 16 B), the FP64 rows in sorted order (J x 32 B) and the
+// FP64 key records (R^3 x 4 x 32 B).
+struct Layout64 {
+    Layout L;
+    size_t rows32, rows64, keys64, total;
+};
+
+Layout64 layout64(int R, int64_t J)
+{
+    Layout64 X{};
+    X.L = eval_layout(R, J);
+    size_t off = X.L.total;
+    X.rows32 = off; off = align_up(off + (size_t)J * 16, 256);
+    X.rows64 = off; off = align_up(off + (size_t)J * 32, 256);
+    X.keys64 = off; off = align_up(off + (size_t)R * R * R * kKeyRecords * 32, 256);
+    X.total = off;
+    return X;
 }
 
 struct Views {
@@ -875,6 +895,109 @@ efunc_status efunc_backward_grad(const efunc_grid *grid, const float *params, co
     return cuda_status(launch_fused_backward(f, false, true, fused_grid_size(), s));
 }
 
+efunc_status efunc_eval_loss(const efunc_grid *grid, const float *params, const float *qo, int64_t J, float *out,
+                             void *workspace, size_t workspace_bytes, efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if (J < 1 || J > kMaxJ || !params || !qo || !out) return EFUNC_ERR_ARG;
+    if ((st = check_workspace(grid, J, workspace, workspace_bytes))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Views v{eval_layout(grid->R, J), static_cast<char *>(workspace)};
+    // a sum over queries: no permutation back to the caller's order
+    cudaError_t e = sort_into(v, grid->R, qo, J, 4, v.sorted(), nullptr, s);
+    if (e == cudaSuccess) e = pack_keys(v, grid, params, s);
+    if (e != cudaSuccess) return cuda_fail();
+    FusedArgs f = fused_args(v, grid);
+    f.perm = nullptr;
+    if ((e = launch_fused_eval(f, fused_grid_size(), s)) != cudaSuccess) return cuda_fail(e);
+    return cuda_status(launch_eval_finish(v.ctrl(), 1.0 / (double)J, out, s));
+}
+
+size_t efunc_f64_workspace_bytes(const efunc_grid *grid, int64_t J)
+{
+    if (!grid_ok(grid) || J < 0 || J > kMaxJ) return 0;
+    return layout64(grid->R, J).total;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The FP64 forward / backward: round the queries to FP32 rows (the windows
+// are chosen from them, as in the FP32 path), sort those rows with the
+// permutation, gather the FP64 rows in sorted order, pack FP64 key records,
+// then run the FP64 instantiation of the fused kernel.
+efunc_status run_f64(const efunc_grid *grid, const double *params, const double *q, int64_t J, int32_t q_stride,
+                     double *O, double *lse, double *dOdq, const double *gO, double *grad, double *gq,
+                     void *workspace, size_t workspace_bytes, cudaStream_t s, bool backward)
+{
+    const Layout64 X = layout64(grid->R, J);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u) || workspace_bytes < X.total)
+        return EFUNC_ERR_WORKSPACE;
+    char *base = static_cast<char *>(workspace);
+    Views v{X.L, base};
+    float4 *rows32 = reinterpret_cast<float4 *>(base + X.rows32);
+    Double4 *rows64 = reinterpret_cast<Double4 *>(base + X.rows64);
+    Double4 *keys64 = reinterpret_cast<Double4 *>(base + X.keys64);
+    cudaError_t e = launch_round_queries(q, J, q_stride, rows32, s);
+    if (e == cudaSuccess) e = sort_into(v, grid->R, reinterpret_cast<const float *>(rows32), J, 4, v.sorted(),
+                                        v.perm(), s);
+    if (e == cudaSuccess) e = launch_gather_queries64(q, J, q_stride, v.perm(), rows64, s);
+    PackArgs64 pk{};
+    pk.params = params;
+    pk.keys = keys64;
+    pk.R = grid->R;
+    pk.log_beta0 = (double)grid->log_beta0;
+    if (e == cudaSuccess) e = launch_pack_keys64(pk, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    FusedArgs64 f{};
+    f.keys = keys64;
+    f.R = grid->R;
+    f.sorted = rows64;
+    f.perm = v.perm();
+    f.items = v.items();
+    f.ctrl = v.ctrl();
+    f.O = O;
+    f.lse = lse;
+    f.dq = dOdq;
+    f.gO = gO;
+    f.grad = grad;
+    f.gq = gq;
+    if (backward) return cuda_status(launch_fused_backward64(f, gq != nullptr, fused_grid_size64(), s));
+    return cuda_status(launch_forward64(f, dOdq != nullptr, fused_grid_size64(), s));
+}
+
+}  // namespace
+
+extern "C" {
+
+efunc_status efunc_forward_f64(const efunc_grid *grid, const double *params, const double *q, int64_t J,
+                               int32_t q_stride, double *O, double *lse, double *dOdq, void *workspace,
+                               size_t workspace_bytes, efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if (J < 0 || J > kMaxJ || (q_stride != 3 && q_stride != 4) || !params) return EFUNC_ERR_ARG;
+    if (J == 0) return EFUNC_OK;
+    if (!q || !O) return EFUNC_ERR_ARG;
+    return run_f64(grid, params, q, J, q_stride, O, lse, dOdq, nullptr, nullptr, nullptr, workspace,
+                   workspace_bytes, (cudaStream_t)stream, false);
+}
+
+efunc_status efunc_backward_f64(const efunc_grid *grid, const double *params, const double *q, int64_t J,
+                                int32_t q_stride, const double *gO, double *grad, double *gq, void *workspace,
+                                size_t workspace_bytes, efunc_stream_t stream)
+{
+    efunc_status st = check_grid(grid);
+    if (st) return st;
+    if (J < 0 || J > kMaxJ || (q_stride != 3 && q_stride != 4) || !params || !grad) return EFUNC_ERR_ARG;
+    if (J == 0) return EFUNC_OK;
+    if (!q || !gO) return EFUNC_ERR_ARG;
+    return run_f64(grid, params, q, J, q_stride, nullptr, nullptr, nullptr, gO, grad, gq, workspace,
+                   workspace_bytes, (cudaStream_t)stream, true);
+}
+
 efunc_status efunc_adam_step(const efunc_adam *adam, int64_t n, float *params, float *grad, float *m, float *v,
                              int64_t step, efunc_stream_t stream)
 {
@@ -1216,6 +1339,345 @@ efunc_status efunc_cosine_fit(const efunc_grid *grid, int32_t bands, const efunc
                 return launch_adam(ad, st);
             });
     }
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ batched fit
+
+namespace {
+
+constexpr int kMinChunk = 32;
+
+bool shapes_ok(const efunc_shape *shapes, int32_t S)
+{
+    if (!shapes || S < 1 || S > kMaxShapes) return false;
+    int64_t jt = 0;
+    for (int32_t i = 0; i < S; ++i) {
+        if (shapes[i].R < 1 || shapes[i].R > kMaxR || shapes[i].J < 1 || !isfinite(shapes[i].log_beta0)) return false;
+        jt += shapes[i].J;
+        if (jt > kMaxJ) return false;
+    }
+    return true;
+}
+
+bool tuning_ok(const efunc_tuning &t)
+{
+    return t.chunk >= kMinChunk && t.chunk <= kChunk && t.lanes4_max >= 0 && t.lanes4_max <= t.lanes2_max &&
+           t.lanes2_max <= kChunk && t.sort_blocks >= 1 && t.sort_blocks <= 16;
+}
+
+efunc_tuning default_tuning() { return efunc_tuning{kChunk, 64, 32, 8}; }
+
+// Layout of a batched fit's workspace: control block (with the Adam clock
+// at +128), shape table, per-shape loss sums, the sort of one batch of all
+// shapes (histogram over every shape's bins), key records and gradient of the
+// concatenated grids.
+struct BatchedLayout {
+    int64_t Jt = 0, centres = 0, nbins = 0, nscan_blocks = 0, max_items = 0;
+    size_t ctrl, table, sums, hist, blocksum, rank, sorted, items, keys, grad, total;
+    std::vector<BatchShape> table_host;
+};
+
+BatchedLayout batched_layout(const efunc_shape *shapes, int32_t S)
+{
+    BatchedLayout L;
+    L.table_host.resize(S);
+    for (int32_t i = 0; i < S; ++i) {
+        const int R = shapes[i].R, P = (R + 1 + kBrick - 1) / kBrick;
+        const int64_t nb = (int64_t)P * P * P * 64;
+        BatchShape &b = L.table_host[i];
+        b.R = R;
+        b.P = P;
+        b.q_off = L.Jt;
+        b.J = shapes[i].J;
+        b.bin_off = L.nbins;
+        b.c_off = L.centres;
+        b.log_beta0 = (double)shapes[i].log_beta0;
+        b.inv_J = (float)(1.0 / (double)shapes[i].J);
+        b.pad = 0;
+        L.max_items += (shapes[i].J + kMinChunk - 1) / kMinChunk + (shapes[i].J < nb ? shapes[i].J : nb);
+        L.Jt += shapes[i].J;
+        L.nbins += nb;
+        L.centres += (int64_t)R * R * R;
+    }
+    L.nscan_blocks = (L.nbins + kScanSegment - 1) / kScanSegment;
+    const size_t A = 256;
+    size_t off = 0;
+    L.ctrl = off;     off = align_up(off + 256, A);   // Ctrl, then the AdamClock at +128
+    L.table = off;    off = align_up(off + (size_t)S * sizeof(BatchShape), A);
+    L.sums = off;     off = align_up(off + (size_t)S * 16, A);
+    L.hist = off;     off = align_up(off + (size_t)L.nbins * 4, A);
+    L.blocksum = off; off = align_up(off + (size_t)L.nscan_blocks * 8, A);
+    L.rank = off;     off = align_up(off + (size_t)L.Jt * 4, A);
+    L.sorted = off;   off = align_up(off + (size_t)L.Jt * 16, A);
+    L.items = off;    off = align_up(off + (size_t)L.max_items * 16, A);
+    L.keys = off;     off = align_up(off + (size_t)L.centres * kKeyRecords * 16, A);
+    L.grad = off;     off = align_up(off + (size_t)L.centres * kSlots * 4, A);
+    L.total = off;
+    return L;
+}
+
+struct BatchedRun {
+    const BatchedLayout *L;
+    char *base;
+    int32_t S;
+    efunc_tuning tune;
+    Ctrl *ctrl() const { return reinterpret_cast<Ctrl *>(base + L->ctrl); }
+    AdamClock *clock() const { return reinterpret_cast<AdamClock *>(base + L->ctrl + 128); }
+    BatchShape *table() const { return reinterpret_cast<BatchShape *>(base + L->table); }
+    double *sums() const { return reinterpret_cast<double *>(base + L->sums); }
+    float *grad() const { return reinterpret_cast<float *>(base + L->grad); }
+    float4 *keys() const { return reinterpret_cast<float4 *>(base + L->keys); }
+
+    // sort of one batch of every shape, key pack, fused kernel (FIT or EVAL)
+    cudaError_t forward_backward(const float *params, const float *q, int32_t loss, bool eval, cudaStream_t s) const
+    {
+        cudaError_t e = cudaMemsetAsync(ctrl(), 0, sizeof(Ctrl), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(base + L->hist, 0, (size_t)L->nbins * 4, s);
+        if (e != cudaSuccess) return e;
+        SortArgs a{};
+        a.q = q;
+        a.J = L->Jt;
+        a.q_stride = 4;
+        a.nbins = L->nbins;
+        a.hist = reinterpret_cast<uint32_t *>(base + L->hist);
+        a.blocksum = reinterpret_cast<unsigned long long *>(base + L->blocksum);
+        a.rank = reinterpret_cast<uint32_t *>(base + L->rank);
+        a.sorted = reinterpret_cast<float4 *>(base + L->sorted);
+        a.items = reinterpret_cast<Item *>(base + L->items);
+        a.ctrl = ctrl();
+        a.shapes = table();
+        a.S = S;
+        a.chunk = tune.chunk;
+        if ((e = launch_sort_batched(a, s, tune.sort_blocks)) != cudaSuccess) return e;
+        BatchedPackArgs pk{params, keys(), table(), S, L->centres};
+        if ((e = launch_pack_keys_batched(pk, s)) != cudaSuccess) return e;
+        FusedArgs f{};
+        f.keys = keys();
+        f.sorted = a.sorted;
+        f.items = a.items;
+        f.ctrl = ctrl();
+        f.grad = grad();
+        f.loss = loss;
+        BatchArgs b{table(), sums(), tune.lanes2_max, tune.lanes4_max};
+        return launch_fused_batched(f, b, eval, fused_batched_grid_size(), s);
+    }
+
+    cudaError_t step(const efunc_adam *adam, int32_t loss, float *params, float *m, float *v, const float *q,
+                     float *stats, cudaStream_t s) const
+    {
+        cudaError_t e = forward_backward(params, q, loss, false, s);
+        if (e != cudaSuccess) return e;
+        BatchedStatsArgs st{table(), S, sums(), stats, clock(), nullptr};
+        if ((e = launch_batched_stats(st, s)) != cudaSuccess) return e;
+        AdamArgs ad = adam_args(adam, L->centres * kSlots, params, grad(), m, v, 1);
+        return launch_adam_clocked(ad, clock(), s);
+    }
+};
+
+efunc_status check_batched(const efunc_shape *shapes, int32_t S, const efunc_tuning *tuning, void *workspace,
+                           size_t workspace_bytes, BatchedLayout &L, efunc_tuning &t)
+{
+    if (!shapes_ok(shapes, S)) return EFUNC_ERR_ARG;
+    t = tuning ? *tuning : default_tuning();
+    if (!tuning_ok(t)) return EFUNC_ERR_ARG;
+    L = batched_layout(shapes, S);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u) || workspace_bytes < L.total)
+        return EFUNC_ERR_WORKSPACE;
+    return EFUNC_OK;
+}
+
+// The batched fit's steps on stream s: seeds the Adam clock, uploads the
+// shape table, then issues the steps one by one or replays one period of
+// n_batches steps from a CUDA graph.
+efunc_status fit_batched(const BatchedRun &run, const efunc_adam *adam, int32_t loss, float *params, float *m,
+                         float *v, const float *qo, int32_t n_batches, int32_t steps, int64_t step0, float *stats,
+                         bool graph, cudaStream_t s)
+{
+    const BatchedLayout &L = *run.L;
+    const size_t batch_floats = (size_t)L.Jt * 4;
+    auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * batch_floats; };
+    if (cudaMemcpyAsync(run.table(), L.table_host.data(), L.table_host.size() * sizeof(BatchShape),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(run.sums(), 0, (size_t)run.S * 16, s) != cudaSuccess ||
+        cudaMemsetAsync(run.grad(), 0, (size_t)L.centres * kSlots * 4, s) != cudaSuccess ||
+        launch_adam_clock_seed(run.clock(), adam_clock_init(adam->lr, adam->beta1, adam->beta2, step0 + 1), s) !=
+            cudaSuccess)
+        return cuda_fail();
+    int32_t done = 0;
+    if (graph && steps > n_batches) {
+        CopyPipe *pipe = nullptr;
+        if (copy_pipe(&pipe) != cudaSuccess) return cuda_fail();
+        std::lock_guard<std::mutex> pipe_lock(pipe->mu);
+        cudaStream_t cs = pipe->capture_stream;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_fail();
+        g_captured = 0;
+        g_in_capture = true;
+        bool ok = true;
+        for (int32_t it = 0; it < n_batches && ok; ++it) ok = run.step(adam, loss, params, m, v, batch(it), stats, cs) == cudaSuccess;
+        g_in_capture = false;
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        const int64_t captured = g_captured;
+        if (ok && e == cudaSuccess && g) e = cudaGraphInstantiate(&exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        const int32_t replays = steps / n_batches;
+        for (int32_t r = 0; ok && exec && r < replays && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, s);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (!ok || e != cudaSuccess) return cuda_fail(ok ? e : cudaSuccess);
+        {
+            std::lock_guard<std::mutex> lk(g_prof_mu);
+            g_launches += captured * replays;
+        }
+        done = replays * n_batches;
+    }
+    for (int32_t it = done; it < steps; ++it)
+        if (run.step(adam, loss, params, m, v, batch(it), stats, s) != cudaSuccess) return cuda_fail();
+    return EFUNC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t efunc_batched_param_count(const efunc_shape *shapes, int32_t S)
+{
+    if (!shapes_ok(shapes, S)) return -1;
+    int64_t n = 0;
+    for (int32_t i = 0; i < S; ++i) n += (int64_t)shapes[i].R * shapes[i].R * shapes[i].R * kSlots;
+    return n;
+}
+
+int64_t efunc_batched_query_count(const efunc_shape *shapes, int32_t S)
+{
+    if (!shapes_ok(shapes, S)) return -1;
+    int64_t n = 0;
+    for (int32_t i = 0; i < S; ++i) n += shapes[i].J;
+    return n;
+}
+
+size_t efunc_batched_workspace_bytes(const efunc_shape *shapes, int32_t S)
+{
+    if (!shapes_ok(shapes, S)) return 0;
+    return batched_layout(shapes, S).total;
+}
+
+void efunc_default_tuning(efunc_tuning *out)
+{
+    if (out) *out = default_tuning();
+}
+
+efunc_status efunc_fit_batched(const efunc_shape *shapes, int32_t S, const efunc_adam *adam, int32_t loss,
+                               float *params, float *m, float *v, const float *qo, int32_t n_batches, int32_t steps,
+                               int64_t step0, float *stats, const efunc_tuning *tuning, int32_t graph,
+                               void *workspace, size_t workspace_bytes, efunc_stream_t stream)
+{
+    efunc_status st = check_adam(adam);
+    if (st) return st;
+    if (loss != EFUNC_LOSS_L1 && loss != EFUNC_LOSS_MSE) return EFUNC_ERR_ARG;
+    if (n_batches < 1 || n_batches > kMaxGraphBatches || steps < 0 || step0 < 0 || (graph != 0 && graph != 1))
+        return EFUNC_ERR_ARG;
+    if (!params || !m || !v || !qo) return EFUNC_ERR_ARG;
+    BatchedLayout L;
+    efunc_tuning t;
+    if ((st = check_batched(shapes, S, tuning, workspace, workspace_bytes, L, t))) return st;
+    if (steps == 0) return EFUNC_OK;
+    if (is_host_pointer(qo) || (stats && is_host_pointer(stats))) return EFUNC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (graph) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return cuda_fail();
+        if (cs != cudaStreamCaptureStatusNone) return EFUNC_ERR_ARG;
+    }
+    BatchedRun run{&L, static_cast<char *>(workspace), S, t};
+    return fit_batched(run, adam, loss, params, m, v, qo, n_batches, steps, step0, stats, graph != 0, s);
+}
+
+efunc_status efunc_eval_batched(const efunc_shape *shapes, int32_t S, const float *params, const float *qo,
+                                float *out, const efunc_tuning *tuning, void *workspace, size_t workspace_bytes,
+                                efunc_stream_t stream)
+{
+    if (!params || !qo || !out) return EFUNC_ERR_ARG;
+    BatchedLayout L;
+    efunc_tuning t;
+    efunc_status st = check_batched(shapes, S, tuning, workspace, workspace_bytes, L, t);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    BatchedRun run{&L, static_cast<char *>(workspace), S, t};
+    if (cudaMemcpyAsync(run.table(), L.table_host.data(), L.table_host.size() * sizeof(BatchShape),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(run.sums(), 0, (size_t)S * 16, s) != cudaSuccess)
+        return cuda_fail();
+    cudaError_t e = run.forward_backward(params, qo, EFUNC_LOSS_MSE, true, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    BatchedStatsArgs sa{run.table(), S, run.sums(), nullptr, nullptr, out};
+    return cuda_status(launch_batched_stats(sa, s));
+}
+
+efunc_status efunc_tune_batched(const efunc_shape *shapes, int32_t S, int32_t loss, float *params, float *m,
+                                float *v, const float *qo, int32_t n_batches, int32_t trial_steps,
+                                efunc_tuning *best, double *best_ms_per_step, void *workspace,
+                                size_t workspace_bytes, efunc_stream_t stream)
+{
+    if (!best || trial_steps < 1 || trial_steps > 1000 || n_batches < 1 || n_batches > kMaxGraphBatches)
+        return EFUNC_ERR_ARG;
+    if (loss != EFUNC_LOSS_L1 && loss != EFUNC_LOSS_MSE) return EFUNC_ERR_ARG;
+    if (!params || !m || !v || !qo) return EFUNC_ERR_ARG;
+    BatchedLayout L;
+    efunc_tuning t;
+    efunc_status st = check_batched(shapes, S, nullptr, workspace, workspace_bytes, L, t);
+    if (st) return st;
+    if (is_host_pointer(qo)) return EFUNC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    // trial steps take Adam steps with learning rate 0: the parameters stay
+    // as they are; the moments are cleared afterwards
+    const efunc_adam frozen{0.0, 0.9, 0.999, 1e-8, 0.0, 0};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail();
+    }
+    double best_ms = 1e300;
+    efunc_tuning best_t = default_tuning();
+    efunc_status rc = EFUNC_OK;
+    const int chunks[] = {128, 256};
+    const int lanes[][2] = {{64, 32}, {96, 48}};
+    const int sorts[] = {2, 4, 8};
+    for (int c : chunks)
+        for (const auto &ln : lanes)
+            for (int sb : sorts) {
+                BatchedRun run{&L, static_cast<char *>(workspace), S, efunc_tuning{c, ln[0], ln[1], sb}};
+                // one untimed step, then trial_steps timed
+                if ((rc = fit_batched(run, &frozen, loss, params, m, v, qo, n_batches, 1, 0, nullptr, false, s)))
+                    goto done;
+                if (cudaEventRecord(e0, s) != cudaSuccess) { rc = cuda_fail(); goto done; }
+                if ((rc = fit_batched(run, &frozen, loss, params, m, v, qo, n_batches, trial_steps, 1, nullptr,
+                                      false, s)))
+                    goto done;
+                float ms = 0.f;
+                if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    rc = cuda_fail();
+                    goto done;
+                }
+                if (ms / trial_steps < best_ms) {
+                    best_ms = ms / trial_steps;
+                    best_t = run.tune;
+                }
+            }
+    if (cudaMemsetAsync(m, 0, (size_t)L.centres * kSlots * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(v, 0, (size_t)L.centres * kSlots * 4, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        rc = cuda_fail();
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == EFUNC_OK) {
+        *best = best_t;
+        if (best_ms_per_step) *best_ms_per_step = best_ms;
+    }
+    return rc;
 }
 
 void efunc_profile_enable(int32_t enable)

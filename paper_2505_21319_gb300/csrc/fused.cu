@@ -25,6 +25,13 @@
 // No per-query intermediate leaves the CTA: the only outputs are O / lse /
 // dO/dq (forward), the gradient grid and dL/dq (backward), and the loss sums
 // (fit).
+//
+// Every function is templated on the scalar type T of the arithmetic.  The
+// hot path is T = float with the SFU's ex2.approx / lg2.approx; T = double
+// runs the same kernels (same staging, windows, summation classes and
+// branches) with exp2 / log2 in double, so that finite differences of the
+// FP64 results check the very code the FP32 path runs.
+#include "adam_clock.cuh"
 #include "common.cuh"
 
 namespace efunc {
@@ -32,17 +39,42 @@ namespace efunc {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr float kLn2 = 0.69314718055994531f;
 constexpr int kClasses = 4;   // interleaved summation classes of the forward
 
-enum Mode { FORWARD = 0, BACKWARD = 1, FIT = 2 };
+enum Mode { FORWARD = 0, BACKWARD = 1, FIT = 2, EVAL = 3 };
 
-// Shared key tile of one window: centre c holds 4 float4 records,
+// Scalar arithmetic of the kernels for T = float (fast SFU exponentials) and
+// T = double (exp2 / log2 in double).
+template <typename T> struct Num;
+template <> struct Num<float> {
+    using V4 = float4;
+    using V2 = float2;
+    static constexpr float kLn2 = 0.69314718055994531f;
+    __device__ static __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
+    __device__ static __forceinline__ float ex2(float x) { return ex2_approx(x); }
+    __device__ static __forceinline__ float lg2(float x) { return lg2_approx(x); }
+    __device__ static __forceinline__ float4 v4(float x, float y, float z, float w) { return make_float4(x, y, z, w); }
+    __device__ static __forceinline__ float2 v2(float x, float y) { return make_float2(x, y); }
+};
+template <> struct Num<double> {
+    using V4 = Double4;
+    using V2 = double2;
+    static constexpr double kLn2 = 0.69314718055994531;
+    __device__ static __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
+    __device__ static __forceinline__ double ex2(double x) { return exp2(x); }
+    __device__ static __forceinline__ double lg2(double x) { return log2(x); }
+    __device__ static __forceinline__ Double4 v4(double x, double y, double z, double w) { return {x, y, z, w}; }
+    __device__ static __forceinline__ double2 v2(double x, double y) { return make_double2(x, y); }
+};
+
+// Shared key tile of one window: centre c holds 4 records of 4 scalars,
 //   rec[4c + 0] = (grid key position, -beta log2 e)    rec[4c + 1] = (o, d)
 //   rec[4c + 2] = (offset key position, -beta' log2 e) rec[4c + 3] = (o', d')
 // with positions in window-local coordinates; set 0 = grid keys, 1 = offset keys.
-__device__ __forceinline__ float4 keyA(const float4 *rec, int set, int k) { return rec[4 * k + 2 * set]; }
-__device__ __forceinline__ float4 keyB(const float4 *rec, int set, int k) { return rec[4 * k + 2 * set + 1]; }
+template <typename V>
+__device__ __forceinline__ V keyA(const V *rec, int set, int k) { return rec[4 * k + 2 * set]; }
+template <typename V>
+__device__ __forceinline__ V keyB(const V *rec, int set, int k) { return rec[4 * k + 2 * set + 1]; }
 
 struct Window {
     int cx, cy, cz, lox, loy, loz, nx, ny, nz, nc;
@@ -66,70 +98,93 @@ __device__ __forceinline__ Window window_of(const Item item, int R)
 
 // --------------------------------------------------------------- pack
 
-__global__ void __launch_bounds__(256) pack_keys_kernel(PackArgs a)
+template <typename T>
+__global__ void __launch_bounds__(256) pack_keys_kernel(PackArgsT<T> a)
 {
+    using N = Num<T>;
     const int I = a.R * a.R * a.R;
     const double log2e = 1.4426950408889634;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I; i += gridDim.x * blockDim.x) {
-        const float *th = a.params + (size_t)i * kSlots;
-        float v[kSlots];
+        const T *th = a.params + (size_t)i * kSlots;
+        T v[kSlots];
 #pragma unroll
         for (int s = 0; s < kSlots; ++s) v[s] = __ldg(th + s);
-        const float nbl_g = (float)(-exp(a.log_beta0 + (double)v[3]) * log2e);
-        const float nbl_o = (float)(-exp(a.log_beta0 + (double)v[4]) * log2e);
-        float4 *k = a.keys + (size_t)i * kKeyRecords;
-        k[0] = make_float4(0.f, 0.f, 0.f, nbl_g);
-        k[1] = make_float4(v[5], v[6], v[7], v[8]);
-        k[2] = make_float4(v[0], v[1], v[2], nbl_o);
-        k[3] = make_float4(v[9], v[10], v[11], v[12]);
+        const T nbl_g = (T)(-exp(a.log_beta0 + (double)v[3]) * log2e);
+        const T nbl_o = (T)(-exp(a.log_beta0 + (double)v[4]) * log2e);
+        typename N::V4 *k = a.keys + (size_t)i * kKeyRecords;
+        k[0] = N::v4(T(0), T(0), T(0), nbl_g);
+        k[1] = N::v4(v[5], v[6], v[7], v[8]);
+        k[2] = N::v4(v[0], v[1], v[2], nbl_o);
+        k[3] = N::v4(v[9], v[10], v[11], v[12]);
+    }
+}
+
+// FP32 rows (x, y, z, 0) of FP64 queries: the rounding that picks windows.
+__global__ void __launch_bounds__(256) round_queries_kernel(const double *q64, int64_t J, int stride, float4 *rows)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < J; j += (int64_t)gridDim.x * blockDim.x) {
+        const double *r = q64 + j * stride;
+        rows[j] = make_float4((float)r[0], (float)r[1], (float)r[2], 0.f);
+    }
+}
+
+// FP64 query rows in sorted order: rows64[i] = q64[perm[i]].
+__global__ void __launch_bounds__(256) gather_queries64_kernel(const double *q64, int64_t J, int stride,
+                                                               const int *perm, Double4 *rows)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < J; i += (int64_t)gridDim.x * blockDim.x) {
+        const double *r = q64 + (int64_t)perm[i] * stride;
+        rows[i] = Double4{r[0], r[1], r[2], stride == 4 ? r[3] : 0.0};
     }
 }
 
 // ------------------------------------------------------------ forward
 
 // One key's contribution to (e, m) for a query at (x, y, z), shifted by M2.
-__device__ __forceinline__ void fwd_key(const float4 A, const float4 B, float x, float y, float z, float M2,
-                                        float &e, float &m)
+template <typename T, typename V>
+__device__ __forceinline__ void fwd_key(const V A, const V B, T x, T y, T z, T M2, T &e, T &m)
 {
-    const float rx = x - A.x, ry = y - A.y, rz = z - A.z;
-    const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-    const float l = ex2_approx(fmaf(A.w, d2, -M2));
-    const float f = fmaf(B.y, rx, fmaf(B.z, ry, fmaf(B.w, rz, B.x)));
+    using N = Num<T>;
+    const T rx = x - A.x, ry = y - A.y, rz = z - A.z;
+    const T d2 = N::fma(rx, rx, N::fma(ry, ry, rz * rz));
+    const T l = N::ex2(N::fma(A.w, d2, -M2));
+    const T f = N::fma(B.y, rx, N::fma(B.z, ry, N::fma(B.w, rz, B.x)));
     e += l;
-    m = fmaf(l, f, m);
+    m = N::fma(l, f, m);
 }
 
-__device__ __forceinline__ float key_exponent(const float4 A, float x, float y, float z)
+template <typename T, typename V>
+__device__ __forceinline__ T key_exponent(const V A, T x, T y, T z)
 {
-    const float rx = x - A.x, ry = y - A.y, rz = z - A.z;
-    return A.w * fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+    using N = Num<T>;
+    const T rx = x - A.x, ry = y - A.y, rz = z - A.z;
+    return A.w * N::fma(rx, rx, N::fma(ry, ry, rz * rz));
 }
 
 // Combines the per-class partial sums of a query held by KQ lanes in the
 // fixed order ((c0 + c1) + (c2 + c3)).  Lane `part` holds classes
 // part + KQ*i, i < 4/KQ.
-template <int KQ>
-__device__ __forceinline__ float combine_classes(const float *v)
+template <int KQ, typename T>
+__device__ __forceinline__ T combine_classes(const T *v)
 {
     if (KQ == 1) return (v[0] + v[1]) + (v[2] + v[3]);
     if (KQ == 2) {
-        const float lo = v[0] + __shfl_xor_sync(kFull, v[0], 1);
-        const float hi = v[1] + __shfl_xor_sync(kFull, v[1], 1);
+        const T lo = v[0] + __shfl_xor_sync(kFull, v[0], 1);
+        const T hi = v[1] + __shfl_xor_sync(kFull, v[1], 1);
         return lo + hi;
     }
-    const float s1 = v[0] + __shfl_xor_sync(kFull, v[0], 1);
+    const T s1 = v[0] + __shfl_xor_sync(kFull, v[0], 1);
     return s1 + __shfl_xor_sync(kFull, s1, 2);
 }
 
 // (e, m) of one query over the window's keys, classes as above.
-template <int KQ>
-__device__ __forceinline__ void fwd_sums(const float4 *rec, int nc, int part, float x, float y, float z, float M2,
-                                         float &e, float &m)
+template <int KQ, typename T, typename V>
+__device__ __forceinline__ void fwd_sums(const V *rec, int nc, int part, T x, T y, T z, T M2, T &e, T &m)
 {
     constexpr int CPL = kClasses / KQ;
-    float ev[CPL], mv[CPL];
+    T ev[CPL], mv[CPL];
 #pragma unroll
-    for (int i = 0; i < CPL; ++i) ev[i] = mv[i] = 0.f;
+    for (int i = 0; i < CPL; ++i) ev[i] = mv[i] = T(0);
 #pragma unroll
     for (int set = 0; set < 2; ++set) {
         for (int base = 0; base < nc; base += kClasses) {
@@ -149,42 +204,42 @@ __device__ __forceinline__ void fwd_sums(const float4 *rec, int nc, int part, fl
 // formed once per query and axis: d2 = (X2[ox] + Y2[oy]) + Z2[oz].  Offset
 // keys take the generic path.  Classes as in fwd_sums: class i of lane `part`
 // is the z offset oz = part + KQ i.
-template <int KQ>
-__device__ __forceinline__ void fwd_sums_full(const float4 *rec, int part, float h, float x, float y, float z,
-                                              float &e, float &m)
+template <int KQ, typename T, typename V>
+__device__ __forceinline__ void fwd_sums_full(const V *rec, int part, T h, T x, T y, T z, T &e, T &m)
 {
+    using N = Num<T>;
     constexpr int CPL = kClasses / KQ;
-    float ev[CPL], mv[CPL];
-    float ry[4], y2[4], rz[CPL], z2[CPL];
+    T ev[CPL], mv[CPL];
+    T ry[4], y2[4], rz[CPL], z2[CPL];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        ry[a] = y - (float)(a - 1) * h;
+        ry[a] = y - (T)(a - 1) * h;
         y2[a] = ry[a] * ry[a];
     }
 #pragma unroll
     for (int i = 0; i < CPL; ++i) {
-        rz[i] = z - (float)(part + KQ * i - 1) * h;
+        rz[i] = z - (T)(part + KQ * i - 1) * h;
         z2[i] = rz[i] * rz[i];
-        ev[i] = mv[i] = 0.f;
+        ev[i] = mv[i] = T(0);
     }
-    const float4 *P = rec + 4 * part;
+    const V *P = rec + 4 * part;
 #pragma unroll 1
     for (int ox = 0; ox < 4; ++ox) {
-        const float rx = x - (float)(ox - 1) * h;
-        const float x2 = rx * rx;
-        const float4 *Po = P + 4 * 16 * ox;
+        const T rx = x - (T)(ox - 1) * h;
+        const T x2 = rx * rx;
+        const V *Po = P + 4 * 16 * ox;
 #pragma unroll
         for (int oy = 0; oy < 4; ++oy) {
-            const float xy = x2 + y2[oy];
+            const T xy = x2 + y2[oy];
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
                 const int k = oy * 4 + KQ * i;
-                const float nbl = Po[4 * k].w;
-                const float4 b = Po[4 * k + 1];
-                const float l = ex2_approx(nbl * (xy + z2[i]));
-                const float f = fmaf(b.y, rx, fmaf(b.z, ry[oy], fmaf(b.w, rz[i], b.x)));
+                const T nbl = Po[4 * k].w;
+                const V b = Po[4 * k + 1];
+                const T l = N::ex2(nbl * (xy + z2[i]));
+                const T f = N::fma(b.y, rx, N::fma(b.z, ry[oy], N::fma(b.w, rz[i], b.x)));
                 ev[i] += l;
-                mv[i] = fmaf(l, f, mv[i]);
+                mv[i] = N::fma(l, f, mv[i]);
             }
         }
     }
@@ -195,7 +250,7 @@ __device__ __forceinline__ void fwd_sums_full(const float4 *rec, int part, float
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
                 const int k = k0 + kk + KQ * i;
-                fwd_key(P[4 * k + 2], P[4 * k + 3], x, y, z, 0.f, ev[i], mv[i]);
+                fwd_key(P[4 * k + 2], P[4 * k + 3], x, y, z, T(0), ev[i], mv[i]);
             }
         }
     }
@@ -204,14 +259,15 @@ __device__ __forceinline__ void fwd_sums_full(const float4 *rec, int part, float
 }
 
 // Eq. func-normal: dO/dq = sum w (d + 2 beta (q - key)(O - f)), same classes.
-template <int KQ>
-__device__ __forceinline__ void dq_sums(const float4 *rec, int nc, int part, float x, float y, float z, float lse2,
-                                        float O, float &gx, float &gy, float &gz)
+template <int KQ, typename T, typename V>
+__device__ __forceinline__ void dq_sums(const V *rec, int nc, int part, T x, T y, T z, T lse2, T O, T &gx, T &gy,
+                                        T &gz)
 {
+    using N = Num<T>;
     constexpr int CPL = kClasses / KQ;
-    float ax[CPL], ay[CPL], az[CPL];
+    T ax[CPL], ay[CPL], az[CPL];
 #pragma unroll
-    for (int i = 0; i < CPL; ++i) ax[i] = ay[i] = az[i] = 0.f;
+    for (int i = 0; i < CPL; ++i) ax[i] = ay[i] = az[i] = T(0);
 #pragma unroll
     for (int set = 0; set < 2; ++set) {
         for (int base = 0; base < nc; base += kClasses) {
@@ -219,15 +275,15 @@ __device__ __forceinline__ void dq_sums(const float4 *rec, int nc, int part, flo
             for (int i = 0; i < CPL; ++i) {
                 const int k = base + part + KQ * i;
                 if (k < nc) {
-                    const float4 a = keyA(rec, set, k), b = keyB(rec, set, k);
-                    const float rx = x - a.x, ry = y - a.y, rz = z - a.z;
-                    const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                    const float w = ex2_approx(fmaf(a.w, d2, -lse2));
-                    const float f = fmaf(b.y, rx, fmaf(b.z, ry, fmaf(b.w, rz, b.x)));
-                    const float c = w * (-2.f * kLn2) * a.w * (O - f);   // 2 beta w (O - f)
-                    ax[i] = fmaf(w, b.y, fmaf(c, rx, ax[i]));
-                    ay[i] = fmaf(w, b.z, fmaf(c, ry, ay[i]));
-                    az[i] = fmaf(w, b.w, fmaf(c, rz, az[i]));
+                    const V a = keyA(rec, set, k), b = keyB(rec, set, k);
+                    const T rx = x - a.x, ry = y - a.y, rz = z - a.z;
+                    const T d2 = N::fma(rx, rx, N::fma(ry, ry, rz * rz));
+                    const T w = N::ex2(N::fma(a.w, d2, -lse2));
+                    const T f = N::fma(b.y, rx, N::fma(b.z, ry, N::fma(b.w, rz, b.x)));
+                    const T c = w * (T(-2) * N::kLn2) * a.w * (O - f);   // 2 beta w (O - f)
+                    ax[i] = N::fma(w, b.y, N::fma(c, rx, ax[i]));
+                    ay[i] = N::fma(w, b.z, N::fma(c, ry, ay[i]));
+                    az[i] = N::fma(w, b.w, N::fma(c, rz, az[i]));
                 }
             }
         }
@@ -259,7 +315,7 @@ __device__ __forceinline__ void gv_sums(const float4 *rec, int nc, int part, flo
                     const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
                     const float w = ex2_approx(fmaf(a.w, d2, -lse2));
                     const float f = fmaf(b.y, rx, fmaf(b.z, ry, fmaf(b.w, rz, b.x)));
-                    const float wb = w * (-kLn2) * a.w;               // w beta
+                    const float wb = w * (-Num<float>::kLn2) * a.w;   // w beta
                     const float c = 2.f * wb * (O - f);                // 2 beta w (O - f)
                     ax[i] = fmaf(w, b.y, fmaf(c, rx, ax[i]));
                     ay[i] = fmaf(w, b.z, fmaf(c, ry, ay[i]));
@@ -279,30 +335,31 @@ __device__ __forceinline__ void gv_sums(const float4 *rec, int nc, int part, flo
     V[2] = combine_classes<KQ>(vz);
 }
 
+template <typename T>
 struct FwdOut {
-    float O, lse2;
+    T O, lse2;
 };
 
 // Forward of the query held by this lane group: fast path without shift,
 // shifted recomputation for groups whose sum underflowed.
-template <int KQ, bool FULL>
-__device__ __forceinline__ FwdOut forward_query(const float4 *rec, int nc, int part, float h, float4 q)
+template <int KQ, bool FULL, typename T, typename V>
+__device__ __forceinline__ FwdOut<T> forward_query(const V *rec, int nc, int part, T h, V q)
 {
-    float e, m;
+    T e, m;
     if (FULL) fwd_sums_full<KQ>(rec, part, h, q.x, q.y, q.z, e, m);
-    else fwd_sums<KQ>(rec, nc, part, q.x, q.y, q.z, 0.f, e, m);
-    float M2 = 0.f;
-    const bool tiny = !(e >= 0x1p-60f);   // identical in every lane of the group
+    else fwd_sums<KQ>(rec, nc, part, q.x, q.y, q.z, T(0), e, m);
+    T M2 = T(0);
+    const bool tiny = !(e >= T(0x1p-60));   // identical in every lane of the group
     if (__any_sync(kFull, tiny)) {
-        float mx = -INFINITY;
+        T mx = -INFINITY;
         for (int k = part; k < nc; k += KQ) {
-            mx = fmaxf(mx, key_exponent(keyA(rec, 0, k), q.x, q.y, q.z));
-            mx = fmaxf(mx, key_exponent(keyA(rec, 1, k), q.x, q.y, q.z));
+            mx = fmax(mx, key_exponent(keyA(rec, 0, k), q.x, q.y, q.z));
+            mx = fmax(mx, key_exponent(keyA(rec, 1, k), q.x, q.y, q.z));
         }
 #pragma unroll
-        for (int o = 1; o < KQ; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+        for (int o = 1; o < KQ; o <<= 1) mx = fmax(mx, __shfl_xor_sync(kFull, mx, o));
         // the shifted sums take the generic path in every window shape
-        float e2, m2;
+        T e2, m2;
         fwd_sums<KQ>(rec, nc, part, q.x, q.y, q.z, mx, e2, m2);
         if (tiny) {
             e = e2;
@@ -310,7 +367,7 @@ __device__ __forceinline__ FwdOut forward_query(const float4 *rec, int nc, int p
             M2 = mx;
         }
     }
-    return {m / e, M2 + lg2_approx(e)};
+    return {m / e, M2 + Num<T>::lg2(e)};
 }
 
 // ----------------------------------------------------------- backward
@@ -318,33 +375,34 @@ __device__ __forceinline__ FwdOut forward_query(const float4 *rec, int nc, int p
 // Thread-per-key loop over the item's queries, two queries per iteration:
 // sqA[j] = (q_j local, lse2_j), sqB[j/2] = (O_j, gO_j, O_j+1, gO_j+1); an odd
 // count is padded with a copy of the last query carrying dL/dO = 0.
-template <bool OFFSET>
-__device__ __forceinline__ void bwd_key_loop(const float4 A, const float4 B, const float4 *__restrict__ sqA,
-                                             const float4 *__restrict__ sqB, int n, float acc[8])
+template <bool OFFSET, typename T, typename V>
+__device__ __forceinline__ void bwd_key_loop(const V A, const V B, const V *__restrict__ sqA,
+                                             const V *__restrict__ sqB, int n, T acc[8])
 {
-    float ag = 0.f, arx = 0.f, ary = 0.f, arz = 0.f, ab = 0.f, adx = 0.f, ady = 0.f, adz = 0.f;
-    auto one = [&](const float4 Q, float O, float gO) {
-        const float rx = Q.x - A.x, ry = Q.y - A.y, rz = Q.z - A.z;
-        const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-        const float w = ex2_approx(fmaf(A.w, d2, -Q.w));
-        const float g = w * gO;
-        const float f = fmaf(B.y, rx, fmaf(B.z, ry, fmaf(B.w, rz, B.x)));
-        const float gd = g * (f - O);
+    using N = Num<T>;
+    T ag = 0, arx = 0, ary = 0, arz = 0, ab = 0, adx = 0, ady = 0, adz = 0;
+    auto one = [&](const V Q, T O, T gO) {
+        const T rx = Q.x - A.x, ry = Q.y - A.y, rz = Q.z - A.z;
+        const T d2 = N::fma(rx, rx, N::fma(ry, ry, rz * rz));
+        const T w = N::ex2(N::fma(A.w, d2, -Q.w));
+        const T g = w * gO;
+        const T f = N::fma(B.y, rx, N::fma(B.z, ry, N::fma(B.w, rz, B.x)));
+        const T gd = g * (f - O);
         ag += g;
-        arx = fmaf(g, rx, arx);
-        ary = fmaf(g, ry, ary);
-        arz = fmaf(g, rz, arz);
-        ab = fmaf(gd, d2, ab);
+        arx = N::fma(g, rx, arx);
+        ary = N::fma(g, ry, ary);
+        arz = N::fma(g, rz, arz);
+        ab = N::fma(gd, d2, ab);
         if (OFFSET) {
-            adx = fmaf(gd, rx, adx);
-            ady = fmaf(gd, ry, ady);
-            adz = fmaf(gd, rz, adz);
+            adx = N::fma(gd, rx, adx);
+            ady = N::fma(gd, ry, ady);
+            adz = N::fma(gd, rz, adz);
         }
     };
     const int pairs = (n + 1) >> 1;
 #pragma unroll 2
     for (int jp = 0; jp < pairs; ++jp) {
-        const float4 Q0 = sqA[2 * jp], Q1 = sqA[2 * jp + 1], S = sqB[jp];
+        const V Q0 = sqA[2 * jp], Q1 = sqA[2 * jp + 1], S = sqB[jp];
         one(Q0, S.x, S.y);
         one(Q1, S.z, S.w);
     }
@@ -369,7 +427,7 @@ __device__ __forceinline__ void bwd2_key_loop(const float4 A, const float4 B, co
                                               const float4 *__restrict__ sqE, const float4 *__restrict__ sqU, int n,
                                               float acc[19])
 {
-    const float beta = -A.w * kLn2;
+    const float beta = -A.w * Num<float>::kLn2;
     float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f, v6 = 0.f, v7 = 0.f;
     float e0 = 0.f, ex = 0.f, ey = 0.f, ez = 0.f, eb = 0.f, px = 0.f, py = 0.f, pz = 0.f, qx = 0.f, qy = 0.f,
           qz = 0.f;
@@ -426,11 +484,13 @@ __device__ __forceinline__ void bwd2_key_loop(const float4 A, const float4 B, co
 // Forward over the item's queries.  qt holds the raw query tile (x, y, z,
 // target); a query's row is rewritten in place with (local position, lse2)
 // by the lane that owns it, after every lane of its group has read it.
-template <int MODE, bool DQ, bool GEIK, int KQ, bool FULL>
-__device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *rec, float4 *qt, float4 *sqB,
-                                              float4 *sqE, float4 *sqU, int start, int n, int nc, float3 orig,
-                                              float h, float &loss_acc, float &abs_acc)
+template <int MODE, bool DQ, bool GEIK, int KQ, bool FULL, typename T>
+__device__ __forceinline__ void forward_phase(const FusedArgsT<T> &a, const V4Of<T> *rec, V4Of<T> *qt,
+                                              V4Of<T> *sqB, float4 *sqE, float4 *sqU, int start, int n, int nc,
+                                              V4Of<T> orig, T h, T &loss_acc, T &abs_acc)
 {
+    using N = Num<T>;
+    using V = V4Of<T>;
     constexpr int LG = KQ == 1 ? 0 : (KQ == 2 ? 1 : 2);
     const int t = threadIdx.x;
     const int part = t & (KQ - 1);
@@ -439,8 +499,8 @@ __device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *
         const int qi = base + (t >> LG);
         const bool valid = qi < n;
         int j_user = 0;
-        if (MODE != FIT) j_user = valid ? __ldg(a.perm + start + qi) : 0;   // issued before the long compute
-        float4 q;
+        if (MODE != FIT && MODE != EVAL) j_user = valid ? __ldg(a.perm + start + qi) : 0;   // issued before the long compute
+        V q;
         if (valid) {
             q = qt[qi];
             q.x -= orig.x;   // window-local coordinates
@@ -448,42 +508,49 @@ __device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *
             q.z -= orig.z;
         } else {
             // lanes without a query evaluate the window centre (never stored)
-            q = make_float4(0.5f * h, 0.5f * h, 0.5f * h, 0.f);
+            q = N::v4(T(0.5) * h, T(0.5) * h, T(0.5) * h, T(0));
         }
-        const FwdOut r = forward_query<KQ, FULL>(rec, nc, part, h, q);
-        const float O = r.O, lse2 = r.lse2;
+        const FwdOut<T> r = forward_query<KQ, FULL>(rec, nc, part, h, q);
+        const T O = r.O, lse2 = r.lse2;
 
-        float gO = 0.f;
+        T gO = T(0);
         if (MODE == FIT) {
-            const float diff = O - q.w;
-            if (a.loss == EFUNC_LOSS_L1) gO = diff > 0.f ? a.inv_J : (diff < 0.f ? -a.inv_J : 0.f);
-            else gO = 2.f * diff * a.inv_J;
+            const T diff = O - q.w;
+            if (a.loss == EFUNC_LOSS_L1) gO = diff > T(0) ? (T)a.inv_J : (diff < T(0) ? -(T)a.inv_J : T(0));
+            else gO = T(2) * diff * (T)a.inv_J;
             if (valid && part == 0) {
-                loss_acc += a.loss == EFUNC_LOSS_L1 ? fabsf(diff) : diff * diff;
-                abs_acc += fabsf(diff);
+                loss_acc += a.loss == EFUNC_LOSS_L1 ? fabs(diff) : diff * diff;
+                abs_acc += fabs(diff);
+            }
+        } else if (MODE == EVAL) {
+            const T diff = O - q.w;
+            if (valid && part == 0) {
+                loss_acc += diff * diff;
+                abs_acc += fabs(diff);
             }
         } else if (MODE == BACKWARD) {
-            gO = (valid && a.gO) ? __ldg(a.gO + j_user) : 0.f;
+            gO = (valid && a.gO) ? __ldg(a.gO + j_user) : T(0);
         } else if (valid && part == 0) {
             a.O[j_user] = O;
-            if (a.lse) a.lse[j_user] = lse2 * kLn2;
+            if (a.lse) a.lse[j_user] = lse2 * N::kLn2;
         }
         if (DQ) {
-            float gx, gy, gz;
+            T gx, gy, gz;
             dq_sums<KQ>(rec, nc, part, q.x, q.y, q.z, lse2, O, gx, gy, gz);
             if (valid && part == 0) {
-                float *dst = MODE == FORWARD ? a.dq : a.gq;
-                const float s = MODE == FORWARD ? 1.f : gO;
+                T *dst = MODE == FORWARD ? a.dq : a.gq;
+                const T s = MODE == FORWARD ? T(1) : gO;
                 dst[3 * (size_t)j_user + 0] = s * gx;
                 dst[3 * (size_t)j_user + 1] = s * gy;
                 dst[3 * (size_t)j_user + 2] = s * gz;
             }
         }
-        float4 rowE = make_float4(O, gO, 0.f, 0.f), rowU = make_float4(0.f, 0.f, 0.f, 0.f);
         if (GEIK) {
-            // second order: u = dL/d(dO/dq), H = u . dO/dq, T = -2 u . sum w beta (q - key)
-            float G[3], V[3];
-            gv_sums<KQ>(rec, nc, part, q.x, q.y, q.z, lse2, O, G, V);
+            // second order (FP32 only): u = dL/d(dO/dq), H = u . dO/dq,
+            // T = -2 u . sum w beta (q - key)
+            float G[3], Vs[3];
+            gv_sums<KQ>(reinterpret_cast<const float4 *>(rec), nc, part, (float)q.x, (float)q.y, (float)q.z,
+                        (float)lse2, (float)O, G, Vs);
             float u0 = 0.f, u1 = 0.f, u2 = 0.f;
             if (MODE == FIT) {
                 // Eikonal term of Sec. 3.2 in the squared form: weight (|G|^2 - 1)^2 / J
@@ -497,47 +564,154 @@ __device__ __forceinline__ void forward_phase(const FusedArgs &a, const float4 *
                 u2 = __ldg(a.gG + 3 * (size_t)j_user + 2);
             }
             const float H = fmaf(u0, G[0], fmaf(u1, G[1], u2 * G[2]));
-            const float T = -2.f * fmaf(u0, V[0], fmaf(u1, V[1], u2 * V[2]));
-            rowE = make_float4(O, gO, H, T);
-            rowU = make_float4(u0, u1, u2, 0.f);
+            const float Tt = -2.f * fmaf(u0, Vs[0], fmaf(u1, Vs[1], u2 * Vs[2]));
+            if (valid && part == 0) {
+                sqE[qi] = make_float4((float)O, (float)gO, H, Tt);
+                sqU[qi] = make_float4(u0, u1, u2, 0.f);
+            }
         }
-        if (GEIK && valid && part == 0) {
-            sqE[qi] = rowE;
-            sqU[qi] = rowU;
-        }
-        if (MODE != FORWARD) {
+        if (MODE == BACKWARD || MODE == FIT) {
             __syncwarp();   // every lane of the group has read its row of qt
             if (valid && part == 0) {
-                const float4 qa = make_float4(q.x, q.y, q.z, lse2);
-                float2 *sqB2 = reinterpret_cast<float2 *>(sqB);
+                const V qa = N::v4(q.x, q.y, q.z, lse2);
+                typename N::V2 *sqB2 = reinterpret_cast<typename N::V2 *>(sqB);
                 qt[qi] = qa;
-                sqB2[qi] = make_float2(O, gO);
+                sqB2[qi] = N::v2(O, gO);
                 if (qi == n - 1 && (n & 1)) {   // pad the last pair: same query, no gradient
                     qt[n] = qa;
-                    sqB2[n] = make_float2(O, 0.f);
+                    sqB2[n] = N::v2(O, T(0));
                 }
             }
         }
     }
 }
 
-template <int MODE, bool DQ, bool GEIK>
-__global__ void __launch_bounds__(kThreads, GEIK ? 5 : 9) fused_kernel(FusedArgs a)
+// Resident CTAs per SM asked of the compiler: FP32 fits leave room for the
+// sort beside them; the second-order and FP64 kernels need more registers.
+template <bool GEIK, typename T>
+constexpr int min_ctas() { return sizeof(T) == 8 ? 2 : (GEIK ? 5 : 9); }
+
+// One work item: stage, forward, backward.  ai carries the item's grid
+// (R, key records, gradient, 1/J): the kernel's own arguments, or in a
+// batched launch those of the item's shape.
+template <int MODE, bool DQ, bool GEIK, typename T, bool BATCHED>
+__device__ __forceinline__ void item_body(const FusedArgsT<T> &a, const FusedArgsT<T> &ai, const BatchArgs &b, const Item item,
+                                          const int R, const T invR, const T h, V4Of<T> *rec, V4Of<T> *qt,
+                                          V4Of<T> *qB, float4 *s_sqE, float4 *s_sqU, T &loss_acc, T &abs_acc)
 {
-    __shared__ float4 s_rec[kCentres * kKeyRecords];          // key records of the window
-    __shared__ float4 s_qt[kChunk];                           // query tile
-    __shared__ float4 s_sqB[MODE == FORWARD ? 1 : kChunk / 2];
+    using N = Num<T>;
+    using V = V4Of<T>;
+    constexpr bool BWD = MODE == BACKWARD || MODE == FIT;
+    const int t = threadIdx.x;
+    const Window w = window_of(item, R);
+    const int start = item.x, n = item.y, nc = w.nc;
+    const bool full = nc == kCentres;
+    const V orig = N::v4((T)(2 * w.cx + 1 - R) * invR, (T)(2 * w.cy + 1 - R) * invR,
+                         (T)(2 * w.cz + 1 - R) * invR, T(0));
+    // ---- 1. stage the key records (positions made window-local) and queries
+    if (t < nc) {
+        int ox, oy, oz;
+        if (full) { ox = t >> 4; oy = (t >> 2) & 3; oz = t & 3; }
+        else { oz = t % w.nz; oy = (t / w.nz) % w.ny; ox = t / (w.ny * w.nz); }
+        const V *k = ai.keys + (((size_t)(w.lox + ox) * R + (w.loy + oy)) * R + (w.loz + oz)) * kKeyRecords;
+        const T gx = (T)(2 * (w.lox + ox - w.cx)) * invR, gy = (T)(2 * (w.loy + oy - w.cy)) * invR,
+                gz = (T)(2 * (w.loz + oz - w.cz)) * invR;
+        const V g = k[0], o = k[2];
+        V *r = rec + 4 * t;
+        r[0] = N::v4(gx, gy, gz, g.w);
+        r[1] = k[1];
+        r[2] = N::v4(gx + o.x, gy + o.y, gz + o.z, o.w);
+        r[3] = k[3];
+    }
+    for (int qi = t; qi < n; qi += kThreads) qt[qi] = a.sorted[start + qi];
+    __syncthreads();
+
+    // ---- 2. forward, one (or 2 / 4) threads per query
+    const int l2 = BATCHED ? b.lanes2_max : 64, l4 = BATCHED ? b.lanes4_max : 32;
+    if (full) {
+        if (n > l2) forward_phase<MODE, DQ, GEIK, 1, true>(ai, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+        else if (n > l4) forward_phase<MODE, DQ, GEIK, 2, true>(ai, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+        else forward_phase<MODE, DQ, GEIK, 4, true>(ai, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+    } else {
+        if (n > l2) forward_phase<MODE, DQ, GEIK, 1, false>(ai, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+        else if (n > l4) forward_phase<MODE, DQ, GEIK, 2, false>(ai, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+        else forward_phase<MODE, DQ, GEIK, 4, false>(ai, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+    }
+    if (BWD) {
+        // ---- 3. backward, one thread per key
+        __syncthreads();
+        const int c = t & (kCentres - 1);
+        if (c < nc) {
+            const bool offset = t >= kCentres;
+            const V A = keyA(rec, offset, c), B = keyB(rec, offset, c);
+            T acc[19];
+            if (GEIK) {
+                float accf[19];
+                const float4 Af = make_float4((float)A.x, (float)A.y, (float)A.z, (float)A.w);
+                const float4 Bf = make_float4((float)B.x, (float)B.y, (float)B.z, (float)B.w);
+                const float4 *qtf = reinterpret_cast<const float4 *>(qt);
+                if (offset) bwd2_key_loop<true>(Af, Bf, qtf, s_sqE, s_sqU, n, accf);
+                else bwd2_key_loop<false>(Af, Bf, qtf, s_sqE, s_sqU, n, accf);
+                for (int i = 0; i < 19; ++i) acc[i] = accf[i];
+            } else {
+                if (offset) bwd_key_loop<true>(A, B, qt, qB, n, acc);
+                else bwd_key_loop<false>(A, B, qt, qB, n, acc);
+                for (int i = 8; i < 19; ++i) acc[i] = T(0);
+            }
+            int ox, oy, oz;
+            if (full) { ox = c >> 4; oy = (c >> 2) & 3; oz = c & 3; }
+            else { oz = c % w.nz; oy = (c / w.nz) % w.ny; ox = c / (w.ny * w.nz); }
+            T *gr = ai.grad + (((size_t)(w.lox + ox) * R + (w.loy + oy)) * R + (w.loz + oz)) * kSlots;
+            const T beta = -A.w * N::kLn2;
+            // value term (dO/dtheta) plus, in second-order mode, the
+            // gradient term d(u . dO/dq)/dtheta
+            const T go = acc[0] + acc[8];
+            const T gdx = acc[1] + acc[9], gdy = acc[2] + acc[10], gdz = acc[3] + acc[11];
+            const T gb = beta * (-acc[4] + acc[12]);
+            if (!offset) {
+                atomicAdd(gr + 5, go);
+                atomicAdd(gr + 6, gdx);
+                atomicAdd(gr + 7, gdy);
+                atomicAdd(gr + 8, gdz);
+                atomicAdd(gr + 3, gb);
+            } else {
+                atomicAdd(gr + 9, go);
+                atomicAdd(gr + 10, gdx);
+                atomicAdd(gr + 11, gdy);
+                atomicAdd(gr + 12, gdz);
+                atomicAdd(gr + 4, gb);
+                // dO/dDelta = w (-d' + 2 beta' (q - key)(f' - O)); d(u.G)/dDelta as above
+                const T tb = T(2) * beta;
+                atomicAdd(gr + 0, N::fma(-B.y, go, tb * (acc[5] + acc[13] + acc[16])));
+                atomicAdd(gr + 1, N::fma(-B.z, go, tb * (acc[6] + acc[14] + acc[17])));
+                atomicAdd(gr + 2, N::fma(-B.w, go, tb * (acc[7] + acc[15] + acc[18])));
+            }
+        }
+    }
+}
+
+// BATCHED: the items of many shapes in one launch; an item's shape (Item.w)
+// selects its grid (R, key records, gradient, 1/J) and the loss sums go to
+// that shape's pair in a.shape_sums after every item.
+template <int MODE, bool DQ, bool GEIK, typename T = float, bool BATCHED = false>
+__global__ void __launch_bounds__(kThreads, min_ctas<GEIK, T>()) fused_kernel(FusedArgsT<T> a, BatchArgs b)
+{
+    using V = V4Of<T>;
+    constexpr bool BWD = MODE == BACKWARD || MODE == FIT;
+    __shared__ V s_rec[kCentres * kKeyRecords];               // key records of the window
+    __shared__ V s_qt[kChunk];                                // query tile
+    __shared__ V s_sqB[BWD ? kChunk / 2 : 1];
     __shared__ float4 s_sqE[GEIK ? kChunk : 1];               // (O, gO, H, T) per query
     __shared__ float4 s_sqU[GEIK ? kChunk : 1];               // (u, 0) per query
     __shared__ int s_item;
-    __shared__ float s_red[2][kThreads / 32];
+    __shared__ T s_red[2][kThreads / 32];
 
     const int t = threadIdx.x;
     const int R = a.R;
-    const float invR = 1.f / (float)R;    // exact for power-of-two R
-    const float h = 2.f * invR;
+    const T invR = T(1) / (T)R;    // exact for power-of-two R
+    const T h = T(2) * invR;
     const int n_items = a.ctrl->n_items;
-    float loss_acc = 0.f, abs_acc = 0.f;
+    T loss_acc = T(0), abs_acc = T(0);
 
     for (;;) {
         __syncthreads();   // the previous item is consumed
@@ -546,89 +720,35 @@ __global__ void __launch_bounds__(kThreads, GEIK ? 5 : 9) fused_kernel(FusedArgs
         const int it = s_item;
         if (it >= n_items) break;
         const Item item = a.items[it];
-        const Window w = window_of(item, R);
-        const int start = item.x, n = item.y, nc = w.nc;
-        const bool full = nc == kCentres;
-        float4 *rec = s_rec, *qt = s_qt, *qB = s_sqB;
-        const float3 orig = make_float3((float)(2 * w.cx + 1 - R) * invR, (float)(2 * w.cy + 1 - R) * invR,
-                                        (float)(2 * w.cz + 1 - R) * invR);
-        // ---- 1. stage the key records (positions made window-local) and queries
-        if (t < nc) {
-            int ox, oy, oz;
-            if (full) { ox = t >> 4; oy = (t >> 2) & 3; oz = t & 3; }
-            else { oz = t % w.nz; oy = (t / w.nz) % w.ny; ox = t / (w.ny * w.nz); }
-            const float4 *k = a.keys + (((size_t)(w.lox + ox) * R + (w.loy + oy)) * R + (w.loz + oz)) * kKeyRecords;
-            const float gx = (float)(2 * (w.lox + ox - w.cx)) * invR, gy = (float)(2 * (w.loy + oy - w.cy)) * invR,
-                        gz = (float)(2 * (w.loz + oz - w.cz)) * invR;
-            const float4 g = k[0], o = k[2];
-            float4 *r = rec + 4 * t;
-            r[0] = make_float4(gx, gy, gz, g.w);
-            r[1] = k[1];
-            r[2] = make_float4(gx + o.x, gy + o.y, gz + o.z, o.w);
-            r[3] = k[3];
-        }
-        for (int qi = t; qi < n; qi += kThreads) qt[qi] = a.sorted[start + qi];
-        __syncthreads();
-
-        // ---- 2. forward, one (or 2 / 4) threads per query
-        if (full) {
-            if (n > 64) forward_phase<MODE, DQ, GEIK, 1, true>(a, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
-            else if (n > 32) forward_phase<MODE, DQ, GEIK, 2, true>(a, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
-            else forward_phase<MODE, DQ, GEIK, 4, true>(a, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
-        } else {
-            if (n > 64) forward_phase<MODE, DQ, GEIK, 1, false>(a, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
-            else if (n > 32) forward_phase<MODE, DQ, GEIK, 2, false>(a, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
-            else forward_phase<MODE, DQ, GEIK, 4, false>(a, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
-        }
-        if (MODE != FORWARD) {
-            // ---- 3. backward, one thread per key
-            __syncthreads();
-            const int c = t & (kCentres - 1);
-            if (c < nc) {
-                const bool offset = t >= kCentres;
-                const float4 A = keyA(rec, offset, c), B = keyB(rec, offset, c);
-                float acc[19];
-                if (GEIK) {
-                    if (offset) bwd2_key_loop<true>(A, B, qt, s_sqE, s_sqU, n, acc);
-                    else bwd2_key_loop<false>(A, B, qt, s_sqE, s_sqU, n, acc);
-                } else {
-                    if (offset) bwd_key_loop<true>(A, B, qt, qB, n, acc);
-                    else bwd_key_loop<false>(A, B, qt, qB, n, acc);
-                    for (int i = 8; i < 19; ++i) acc[i] = 0.f;
+        if constexpr (BATCHED) {
+            const BatchShape sh = b.shapes[item.w];
+            FusedArgsT<T> ai = a;
+            ai.R = sh.R;
+            ai.keys = a.keys + sh.c_off * kKeyRecords;
+            ai.grad = a.grad + sh.c_off * kSlots;
+            ai.inv_J = sh.inv_J;
+            const T invRb = T(1) / (T)sh.R;
+            item_body<MODE, DQ, GEIK, T, BATCHED>(a, ai, b, item, sh.R, invRb, T(2) * invRb, s_rec, s_qt, s_sqB,
+                                                  s_sqE, s_sqU, loss_acc, abs_acc);
+            if (MODE == FIT || MODE == EVAL) {
+                // this item's loss sums to its shape: one double atomic pair per warp
+                for (int o = 16; o > 0; o >>= 1) {
+                    loss_acc += __shfl_xor_sync(kFull, loss_acc, o);
+                    abs_acc += __shfl_xor_sync(kFull, abs_acc, o);
                 }
-                int ox, oy, oz;
-                    if (full) { ox = c >> 4; oy = (c >> 2) & 3; oz = c & 3; }
-                else { oz = c % w.nz; oy = (c / w.nz) % w.ny; ox = c / (w.ny * w.nz); }
-                float *gr = a.grad + (((size_t)(w.lox + ox) * R + (w.loy + oy)) * R + (w.loz + oz)) * kSlots;
-                const float beta = -A.w * kLn2;
-                // value term (dO/dtheta) plus, in second-order mode, the
-                // gradient term d(u . dO/dq)/dtheta
-                const float go = acc[0] + acc[8];
-                const float gdx = acc[1] + acc[9], gdy = acc[2] + acc[10], gdz = acc[3] + acc[11];
-                const float gb = beta * (-acc[4] + acc[12]);
-                if (!offset) {
-                    atomicAdd(gr + 5, go);
-                    atomicAdd(gr + 6, gdx);
-                    atomicAdd(gr + 7, gdy);
-                    atomicAdd(gr + 8, gdz);
-                    atomicAdd(gr + 3, gb);
-                } else {
-                    atomicAdd(gr + 9, go);
-                    atomicAdd(gr + 10, gdx);
-                    atomicAdd(gr + 11, gdy);
-                    atomicAdd(gr + 12, gdz);
-                    atomicAdd(gr + 4, gb);
-                    // dO/dDelta = w (-d' + 2 beta' (q - key)(f' - O)); d(u.G)/dDelta as above
-                    const float tb = 2.f * beta;
-                    atomicAdd(gr + 0, fmaf(-B.y, go, tb * (acc[5] + acc[13] + acc[16])));
-                    atomicAdd(gr + 1, fmaf(-B.z, go, tb * (acc[6] + acc[14] + acc[17])));
-                    atomicAdd(gr + 2, fmaf(-B.w, go, tb * (acc[7] + acc[15] + acc[18])));
+                if ((t & 31) == 0 && (loss_acc != T(0) || abs_acc != T(0))) {
+                    atomicAdd(b.shape_sums + 2 * item.w, (double)loss_acc);
+                    atomicAdd(b.shape_sums + 2 * item.w + 1, (double)abs_acc);
                 }
+                loss_acc = abs_acc = T(0);
             }
+        } else {
+            item_body<MODE, DQ, GEIK, T, BATCHED>(a, a, b, item, R, invR, h, s_rec, s_qt, s_sqB, s_sqE, s_sqU,
+                                                  loss_acc, abs_acc);
         }
     }
 
-    if (MODE == FIT) {
+    if (!BATCHED && (MODE == FIT || MODE == EVAL)) {
         // loss sums: warp shuffle, then one double atomic per CTA
         for (int o = 16; o > 0; o >>= 1) {
             loss_acc += __shfl_xor_sync(kFull, loss_acc, o);
@@ -697,7 +817,7 @@ cudaError_t launch_pack_keys(const PackArgs &a, cudaStream_t s)
     int blocks = (I + 255) / 256;
     if (blocks > sm_count() * 8) blocks = sm_count() * 8;
     launch_begin(K_PACK_KEYS, s);
-    pack_keys_kernel<<<blocks, 256, 0, s>>>(a);
+    pack_keys_kernel<float><<<blocks, 256, 0, s>>>(a);
     launch_end(K_PACK_KEYS, s);
     return cudaGetLastError();
 }
@@ -705,8 +825,8 @@ cudaError_t launch_pack_keys(const PackArgs &a, cudaStream_t s)
 cudaError_t launch_forward(const FusedArgs &a, bool with_dq, int grid, cudaStream_t s)
 {
     launch_begin(K_FORWARD, s);
-    if (with_dq) fused_kernel<FORWARD, true, false><<<grid, kThreads, 0, s>>>(a);
-    else fused_kernel<FORWARD, false, false><<<grid, kThreads, 0, s>>>(a);
+    if (with_dq) fused_kernel<FORWARD, true, false><<<grid, kThreads, 0, s>>>(a, BatchArgs{});
+    else fused_kernel<FORWARD, false, false><<<grid, kThreads, 0, s>>>(a, BatchArgs{});
     launch_end(K_FORWARD, s);
     return cudaGetLastError();
 }
@@ -714,9 +834,9 @@ cudaError_t launch_forward(const FusedArgs &a, bool with_dq, int grid, cudaStrea
 cudaError_t launch_fused_backward(const FusedArgs &a, bool with_gq, bool second_order, int grid, cudaStream_t s)
 {
     launch_begin(K_FUSED_BWD, s);
-    if (second_order) fused_kernel<BACKWARD, false, true><<<grid, kThreads, 0, s>>>(a);
-    else if (with_gq) fused_kernel<BACKWARD, true, false><<<grid, kThreads, 0, s>>>(a);
-    else fused_kernel<BACKWARD, false, false><<<grid, kThreads, 0, s>>>(a);
+    if (second_order) fused_kernel<BACKWARD, false, true><<<grid, kThreads, 0, s>>>(a, BatchArgs{});
+    else if (with_gq) fused_kernel<BACKWARD, true, false><<<grid, kThreads, 0, s>>>(a, BatchArgs{});
+    else fused_kernel<BACKWARD, false, false><<<grid, kThreads, 0, s>>>(a, BatchArgs{});
     launch_end(K_FUSED_BWD, s);
     return cudaGetLastError();
 }
@@ -724,9 +844,194 @@ cudaError_t launch_fused_backward(const FusedArgs &a, bool with_gq, bool second_
 cudaError_t launch_fused_fit(const FusedArgs &a, bool eikonal, int grid, cudaStream_t s)
 {
     launch_begin(K_FUSED_FIT, s);
-    if (eikonal) fused_kernel<FIT, false, true><<<grid, kThreads, 0, s>>>(a);
-    else fused_kernel<FIT, false, false><<<grid, kThreads, 0, s>>>(a);
+    if (eikonal) fused_kernel<FIT, false, true><<<grid, kThreads, 0, s>>>(a, BatchArgs{});
+    else fused_kernel<FIT, false, false><<<grid, kThreads, 0, s>>>(a, BatchArgs{});
     launch_end(K_FUSED_FIT, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused_eval(const FusedArgs &a, int grid, cudaStream_t s)
+{
+    launch_begin(K_EVAL, s);
+    fused_kernel<EVAL, false, false><<<grid, kThreads, 0, s>>>(a, BatchArgs{});
+    launch_end(K_EVAL, s);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void eval_finish_kernel(const Ctrl *ctrl, double inv_J, float *out)
+{
+    out[0] = (float)(ctrl->loss_sum * inv_J);
+    out[1] = (float)(ctrl->abs_sum * inv_J);
+}
+}  // namespace
+
+cudaError_t launch_eval_finish(const Ctrl *ctrl, double inv_J, float *out, cudaStream_t s)
+{
+    launch_begin(K_EVAL, s);
+    eval_finish_kernel<<<1, 1, 0, s>>>(ctrl, inv_J, out);
+    launch_end(K_EVAL, s);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ batched fit
+
+namespace {
+
+// Key records of every centre of the concatenated grids (pack_keys_kernel
+// per shape: each shape's own log_beta0).
+__global__ void __launch_bounds__(256) pack_keys_batched_kernel(BatchedPackArgs a)
+{
+    __shared__ int64_t s_off[kMaxShapes];
+    for (int i = threadIdx.x; i < a.S; i += blockDim.x) s_off[i] = a.shapes[i].c_off;
+    __syncthreads();
+    const double log2e = 1.4426950408889634;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_centres;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = a.S - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        const double lb = a.shapes[lo].log_beta0;
+        const float *th = a.params + i * kSlots;
+        float v[kSlots];
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) v[s] = __ldg(th + s);
+        float4 *k = a.keys + i * kKeyRecords;
+        k[0] = make_float4(0.f, 0.f, 0.f, (float)(-exp(lb + (double)v[3]) * log2e));
+        k[1] = make_float4(v[5], v[6], v[7], v[8]);
+        k[2] = make_float4(v[0], v[1], v[2], (float)(-exp(lb + (double)v[4]) * log2e));
+        k[3] = make_float4(v[9], v[10], v[11], v[12]);
+    }
+}
+
+// Per-shape statistics of a batched step (loss, MAE per shape, in the row of
+// the step held by the Adam clock), or of an evaluation (MSE, MAE), and the
+// sums cleared for the next step.
+__global__ void batched_stats_kernel(BatchedStatsArgs a)
+{
+    const AdamClock *clk = static_cast<const AdamClock *>(a.clk);
+    const int64_t row = clk ? clk->t - clk->t_first : 0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.S; s += gridDim.x * blockDim.x) {
+        const double inv_J = (double)a.shapes[s].inv_J;
+        const float l = (float)(a.sums[2 * s] * inv_J), ab = (float)(a.sums[2 * s + 1] * inv_J);
+        if (a.stats) {
+            a.stats[(row * a.S + s) * 2] = l;
+            a.stats[(row * a.S + s) * 2 + 1] = ab;
+        }
+        if (a.out) {
+            a.out[2 * s] = l;
+            a.out[2 * s + 1] = ab;
+        }
+        a.sums[2 * s] = 0.0;
+        a.sums[2 * s + 1] = 0.0;
+    }
+}
+
+}  // namespace
+
+int fused_batched_grid_size()
+{
+    const void *k = reinterpret_cast<const void *>(fused_kernel<FIT, false, false, float, true>);
+    return per_device_cached(k, 0, [k] {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, 0);
+        if (per_sm <= 0) per_sm = 1;
+        return sm_count() * per_sm;
+    });
+}
+
+cudaError_t launch_pack_keys_batched(const BatchedPackArgs &a, cudaStream_t s)
+{
+    int64_t blocks = (a.n_centres + 255) / 256;
+    if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
+    launch_begin(K_PACK_KEYS, s);
+    pack_keys_batched_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(a);
+    launch_end(K_PACK_KEYS, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused_batched(const FusedArgs &a, const BatchArgs &b, bool eval, int grid, cudaStream_t s)
+{
+    launch_begin(eval ? K_EVAL : K_BATCHED, s);
+    if (eval) fused_kernel<EVAL, false, false, float, true><<<grid, kThreads, 0, s>>>(a, b);
+    else fused_kernel<FIT, false, false, float, true><<<grid, kThreads, 0, s>>>(a, b);
+    launch_end(eval ? K_EVAL : K_BATCHED, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_stats(const BatchedStatsArgs &a, cudaStream_t s)
+{
+    launch_begin(K_BATCHED_STATS, s);
+    batched_stats_kernel<<<(a.S + 127) / 128, 128, 0, s>>>(a);
+    launch_end(K_BATCHED_STATS, s);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ FP64 path
+
+int fused_grid_size64()
+{
+    const void *k = reinterpret_cast<const void *>(fused_kernel<BACKWARD, true, false, double>);
+    return per_device_cached(k, 0, [k] {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, 0);
+        if (per_sm <= 0) per_sm = 1;
+        return sm_count() * per_sm;
+    });
+}
+
+namespace {
+int stream_blocks(int64_t n)
+{
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
+    return blocks < 1 ? 1 : (int)blocks;
+}
+}  // namespace
+
+cudaError_t launch_pack_keys64(const PackArgs64 &a, cudaStream_t s)
+{
+    launch_begin(K_F64, s);
+    pack_keys_kernel<double><<<stream_blocks((int64_t)a.R * a.R * a.R), 256, 0, s>>>(a);
+    launch_end(K_F64, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round_queries(const double *q64, int64_t J, int q_stride, float4 *rows32, cudaStream_t s)
+{
+    launch_begin(K_F64, s);
+    round_queries_kernel<<<stream_blocks(J), 256, 0, s>>>(q64, J, q_stride, rows32);
+    launch_end(K_F64, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_queries64(const double *q64, int64_t J, int q_stride, const int *perm, Double4 *rows64,
+                                    cudaStream_t s)
+{
+    launch_begin(K_F64, s);
+    gather_queries64_kernel<<<stream_blocks(J), 256, 0, s>>>(q64, J, q_stride, perm, rows64);
+    launch_end(K_F64, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward64(const FusedArgs64 &a, bool with_dq, int grid, cudaStream_t s)
+{
+    launch_begin(K_F64, s);
+    if (with_dq) fused_kernel<FORWARD, true, false, double><<<grid, kThreads, 0, s>>>(a, BatchArgs{});
+    else fused_kernel<FORWARD, false, false, double><<<grid, kThreads, 0, s>>>(a, BatchArgs{});
+    launch_end(K_F64, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused_backward64(const FusedArgs64 &a, bool with_gq, int grid, cudaStream_t s)
+{
+    launch_begin(K_F64, s);
+    if (with_gq) fused_kernel<BACKWARD, true, false, double><<<grid, kThreads, 0, s>>>(a, BatchArgs{});
+    else fused_kernel<BACKWARD, false, false, double><<<grid, kThreads, 0, s>>>(a, BatchArgs{});
+    launch_end(K_F64, s);
     return cudaGetLastError();
 }
 

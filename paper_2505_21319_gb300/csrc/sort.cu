@@ -342,7 +342,141 @@ cudaError_t launch_sort_k(const SortArgs &a, cudaStream_t s, int narrow_blocks)
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ batched sort
+//
+// The queries of S shapes, concatenated (shape s owns rows [q_off, q_off + J)
+// of the batch), are sorted in one pass of the same counting sort: a query's
+// bin is its shape's bin offset plus its bin on its shape's own grid, so the
+// bins of one shape are contiguous and every work item lies in one shape
+// (Item.w).  Work items hold at most a.chunk queries (a tuning knob).
+
+// Index of the last offset <= x among S ascending offsets (offs[0] = 0).
+__device__ __forceinline__ int shape_of(const int64_t *offs, int S, int64_t x)
+{
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (offs[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <bool BY_BIN>
+__device__ __forceinline__ void load_offsets(const SortArgs &a, int64_t *s_off)
+{
+    for (int i = threadIdx.x; i < a.S; i += blockDim.x) s_off[i] = BY_BIN ? a.shapes[i].bin_off : a.shapes[i].q_off;
+    __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t batched_bin(const BatchShape &sh, float x, float y, float z)
+{
+    return (uint32_t)query_bin(x, y, z, (float)sh.R * 0.5f, (float)(sh.R - 1), sh.P);
+}
+
+__global__ void __launch_bounds__(kWideThreads) bin_batched_kernel(SortArgs a)
+{
+    __shared__ int64_t s_off[kMaxShapes];
+    load_offsets<false>(a, s_off);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.J; j += stride) {
+        const BatchShape &sh = a.shapes[shape_of(s_off, a.S, j)];
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(a.q) + j);
+        a.rank[j] = atomicAdd(&a.hist[sh.bin_off + batched_bin(sh, v.x, v.y, v.z)], 1u);
+    }
+}
+
+__device__ __forceinline__ unsigned long long pack_chunk(uint32_t count, uint32_t chunk)
+{
+    unsigned long long items = (count + chunk - 1) / chunk;
+    return (items << 32) | (unsigned long long)count;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_batched_kernel(SortArgs a)
+{
+    const int64_t b0 = (int64_t)blockIdx.x * kScanSeg + (int64_t)threadIdx.x * kScanPerThread;
+    unsigned long long s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k)
+        if (b0 + k < a.nbins) s += pack_chunk(a.hist[b0 + k], (uint32_t)a.chunk);
+    unsigned long long total;
+    block_exclusive_scan(s, total);
+    if (threadIdx.x == 0) a.blocksum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_emit_batched_kernel(SortArgs a)
+{
+    __shared__ int64_t s_off[kMaxShapes];
+    load_offsets<true>(a, s_off);
+    const uint32_t chunk = (uint32_t)a.chunk;
+    const int64_t b0 = (int64_t)blockIdx.x * kScanSeg + (int64_t)threadIdx.x * kScanPerThread;
+    uint32_t cnt[kScanPerThread];
+    unsigned long long s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k) {
+        cnt[k] = b0 + k < a.nbins ? a.hist[b0 + k] : 0u;
+        s += pack_chunk(cnt[k], chunk);
+    }
+    unsigned long long total;
+    unsigned long long run = a.blocksum[blockIdx.x] + block_exclusive_scan(s, total);
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k) {
+        if (b0 + k >= a.nbins) break;
+        const uint32_t start = (uint32_t)(run & 0xffffffffull);
+        const uint32_t item0 = (uint32_t)(run >> 32);
+        a.hist[b0 + k] = start;
+        if (cnt[k]) {
+            const int sh = shape_of(s_off, a.S, b0 + k);
+            int ux, uy, uz;
+            cell_of_bin((uint32_t)(b0 + k - s_off[sh]), a.shapes[sh].P, ux, uy, uz);
+            const int packed = ux | (uy << 10) | (uz << 20);
+            const uint32_t nit = (cnt[k] + chunk - 1) / chunk;
+            for (uint32_t i = 0; i < nit; ++i) {
+                const uint32_t off = i * chunk;
+                const uint32_t len = min(chunk, cnt[k] - off);
+                a.items[item0 + i] = make_int4((int)(start + off), (int)len, packed, sh);
+            }
+        }
+        run += pack_chunk(cnt[k], chunk);
+    }
+}
+
+__global__ void __launch_bounds__(kWideThreads) scatter_batched_kernel(SortArgs a)
+{
+    __shared__ int64_t s_off[kMaxShapes];
+    load_offsets<false>(a, s_off);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.J; j += stride) {
+        const BatchShape &sh = a.shapes[shape_of(s_off, a.S, j)];
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(a.q) + j);
+        const uint32_t pos = a.hist[sh.bin_off + batched_bin(sh, v.x, v.y, v.z)] + a.rank[j];
+        a.sorted[pos] = v;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_sort_batched(const SortArgs &a, cudaStream_t s, int blocks_per_sm)
+{
+    const int g = stream_grid(a.J, kWideThreads, blocks_per_sm > 0 ? blocks_per_sm : 8);
+    const int64_t nblocks = (a.nbins + kScanSeg - 1) / kScanSeg;
+    launch_begin(K_BIN, s);
+    bin_batched_kernel<<<g, kWideThreads, 0, s>>>(a);
+    launch_end(K_BIN, s);
+    launch_begin(K_SCAN_REDUCE, s);
+    scan_reduce_batched_kernel<<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
+    launch_end(K_SCAN_REDUCE, s);
+    launch_begin(K_SCAN_TOP, s);
+    scan_top_kernel<<<1, kScanThreads, 0, s>>>(a, nblocks);
+    launch_end(K_SCAN_TOP, s);
+    launch_begin(K_SCAN_EMIT, s);
+    scan_emit_batched_kernel<<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
+    launch_end(K_SCAN_EMIT, s);
+    launch_begin(K_SCATTER, s);
+    scatter_batched_kernel<<<g, kWideThreads, 0, s>>>(a);
+    launch_end(K_SCATTER, s);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sort(const SortArgs &a, cudaStream_t s, int narrow_blocks)
 {

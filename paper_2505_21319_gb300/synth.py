@@ -247,3 +247,106 @@ def variant_params(shape: Shape | None, R: int, sets: int, deg: int, learn: int,
             phi[:, 4:20] = g.standard_normal((R ** 3, 16)) * high_scale
         p[:, off + si * nv: off + (si + 1) * nv] = phi[:, :nv]
     return p.astype(np.float32)
+
+
+# ------------------------------------------------- device-side sampling
+#
+# The same distributions drawn with torch on a device (FP64 arithmetic, a
+# torch Philox generator seeded per call: a different random stream from the
+# numpy sampler above).  For query pools too large to draw on the host in
+# reasonable time (many shapes, millions of rows each).
+
+def _torch_sdf(shape: Shape, q):
+    import torch
+    out = torch.full((q.shape[0],), float("inf"), dtype=torch.float64, device=q.device)
+    for k, c, s in zip(shape.kind, shape.centre, shape.size):
+        p = q - torch.tensor(c, dtype=torch.float64, device=q.device)
+        if k == SPHERE:
+            d = torch.linalg.norm(p, dim=1) - s[0]
+        elif k == BOX:
+            e = torch.abs(p) - torch.tensor(s, dtype=torch.float64, device=q.device)
+            d = torch.linalg.norm(torch.clamp(e, min=0.0), dim=1) + torch.clamp(e.max(dim=1).values, max=0.0)
+        else:
+            ring = torch.sqrt(p[:, 0] ** 2 + p[:, 1] ** 2) - s[0]
+            d = torch.sqrt(ring ** 2 + p[:, 2] ** 2) - s[1]
+        out = torch.minimum(out, d)
+    return out
+
+
+def _torch_prim_surface(kind, c, s, n, gen, device):
+    import torch
+    f64 = dict(dtype=torch.float64, device=device)
+    if kind == SPHERE:
+        v = torch.randn((n, 3), generator=gen, **f64)
+        v = v / torch.linalg.norm(v, dim=1, keepdim=True)
+        return torch.tensor(c, **f64) + s[0] * v
+    if kind == BOX:
+        areas = torch.tensor([s[1] * s[2], s[1] * s[2], s[0] * s[2], s[0] * s[2], s[0] * s[1], s[0] * s[1]], **f64)
+        face = torch.multinomial(areas / areas.sum(), n, replacement=True, generator=gen)
+        ext = torch.tensor(s, **f64)
+        u = (torch.rand((n, 3), generator=gen, **f64) * 2.0 - 1.0) * ext
+        axis = face // 2
+        sign = torch.where(face % 2 == 0, -1.0, 1.0).to(torch.float64)
+        u[torch.arange(n, device=device), axis] = sign * ext[axis]
+        return torch.tensor(c, **f64) + u
+    R, r = s[0], s[1]
+    parts, have = [], 0
+    while have < n:   # rejection on the area element (R + r cos v)
+        m = 2 * (n - have) + 16
+        uu = torch.rand(m, generator=gen, **f64) * 2 * np.pi
+        vv = torch.rand(m, generator=gen, **f64) * 2 * np.pi
+        keep = torch.rand(m, generator=gen, **f64) * (R + r) <= R + r * torch.cos(vv)
+        uu, vv = uu[keep], vv[keep]
+        parts.append(torch.stack([(R + r * torch.cos(vv)) * torch.cos(uu), (R + r * torch.cos(vv)) * torch.sin(uu),
+                                  r * torch.sin(vv)], 1))
+        have += parts[-1].shape[0]
+    return torch.tensor(c, **f64) + torch.cat(parts)[:n]
+
+
+def surface_points_torch(shape: Shape, n: int, gen, device):
+    """n points uniformly (by area) on the union's boundary, on a device."""
+    import torch
+    areas = torch.tensor([_prim_area(k, s) for k, s in zip(shape.kind, shape.size)], dtype=torch.float64)
+    parts, have = [], 0
+    while have < n:
+        m = 2 * (n - have) + 64
+        which = torch.multinomial(areas / areas.sum(), m, replacement=True, generator=torch.Generator().manual_seed(
+            int(torch.randint(0, 2 ** 62, (1,), generator=gen, device=device).item())))
+        counts = torch.bincount(which, minlength=len(areas)).tolist()
+        pts = torch.cat([_torch_prim_surface(shape.kind[i], shape.centre[i], shape.size[i], counts[i], gen, device)
+                         for i in range(len(areas)) if counts[i] > 0])
+        pts = pts[_torch_sdf(shape, pts) >= -1e-6]
+        parts.append(pts)
+        have += pts.shape[0]
+    out = torch.cat(parts)
+    return out[torch.randperm(out.shape[0], generator=gen, device=device)[:n]]
+
+
+def sample_batch_torch(shape: Shape, J: int, seed: int, device, sigma: float = 0.01, near_frac: float = 0.5):
+    """sample_batch's distribution drawn on ``device``: a (J, 4) float32 tensor
+    of rows (x, y, z, target SDF), the target the FP64 SDF at the
+    FP32-rounded point."""
+    import torch
+    gen = torch.Generator(device=device).manual_seed(int(seed))
+    n_near = int(round(near_frac * J))
+    n_vol = J - n_near
+    vol = torch.rand((n_vol, 3), generator=gen, dtype=torch.float64, device=device) * 2.0 - 1.0
+    parts = [vol]
+    if n_near:
+        parts.append(surface_points_torch(shape, n_near, gen, device)
+                     + sigma * torch.randn((n_near, 3), generator=gen, dtype=torch.float64, device=device))
+    q = torch.cat(parts).to(torch.float32)
+    q = q[torch.randperm(J, generator=gen, device=device)]
+    out = torch.empty((J, 4), dtype=torch.float32, device=device)
+    out[:, :3] = q
+    out[:, 3] = _torch_sdf(shape, q.to(torch.float64)).to(torch.float32)
+    return out
+
+
+def sdf_grid_torch(shape: Shape, R: int, device):
+    """The shape's SDF at the R^3 cell centres -1 + (i + 0.5) 2/R, (R, R, R)
+    float32 (x slowest), on ``device``."""
+    import torch
+    c = -1.0 + (torch.arange(R, dtype=torch.float64, device=device) + 0.5) * (2.0 / R)
+    X, Y, Z = torch.meshgrid(c, c, c, indexing="ij")
+    return _torch_sdf(shape, torch.stack([X, Y, Z], -1).reshape(-1, 3)).reshape(R, R, R).to(torch.float32)

@@ -16,9 +16,9 @@ def set_test(nodeid):
 
 
 def record(what, err, lim):
-    err = np.asarray(err, dtype=np.float64).ravel()
-    lim = np.broadcast_to(np.asarray(lim, dtype=np.float64), np.asarray(err).shape).ravel() \
-        if np.ndim(lim) else np.full(err.shape, float(lim))
+    err = np.asarray(err, dtype=np.float64)
+    lim = np.broadcast_to(np.asarray(lim, dtype=np.float64), err.shape).ravel()
+    err = err.ravel()
     if err.size == 0:
         return
     ok = np.isfinite(err)

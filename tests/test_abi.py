@@ -222,3 +222,58 @@ def test_profile_api_without_gpu(lib):
     assert lib.efunc_profile_read(b"fused_fit", ctypes.byref(ms), ctypes.byref(cnt)) == 0
     assert ms.value == 0.0 and cnt.value == 0
     assert lib.efunc_profile_read(b"nope", ctypes.byref(ms), ctypes.byref(cnt)) == -1
+
+
+def _shapes(*rj):
+    return (B.Shape * len(rj))(*[B.Shape(R, 7.0, J) for R, J in rj])
+
+
+def test_batched_helpers(lib):
+    sh = _shapes((16, 1000), (32, 5000), (64, 1 << 14))
+    assert lib.efunc_batched_param_count(sh, 3) == 13 * (16 ** 3 + 32 ** 3 + 64 ** 3)
+    assert lib.efunc_batched_query_count(sh, 3) == 1000 + 5000 + (1 << 14)
+    n3 = lib.efunc_batched_workspace_bytes(sh, 3)
+    n2 = lib.efunc_batched_workspace_bytes(sh, 2)
+    assert n3 > n2 > 0 and n3 % 256 == 0
+    for bad in (_shapes((0, 10)), _shapes((257, 10)), _shapes((8, 0)), _shapes((8, (1 << 30) + 1))):
+        assert lib.efunc_batched_param_count(bad, 1) == -1
+        assert lib.efunc_batched_workspace_bytes(bad, 1) == 0
+    assert lib.efunc_batched_param_count(sh, 0) == -1
+    assert lib.efunc_batched_param_count(sh, 1025) == -1
+    t = B.Tuning()
+    lib.efunc_default_tuning(ctypes.byref(t))
+    assert (t.chunk, t.lanes2_max, t.lanes4_max, t.sort_blocks) == (256, 64, 32, 8)
+
+
+@fake_pointers
+def test_batched_validation_enqueues_nothing(lib):
+    n0 = lib.efunc_launch_count()
+    sh = _shapes((8, 100), (4, 50))
+    ad = B.Adam(1e-3, 0.9, 0.999, 1e-8, 0.0, 0)
+    ws = lib.efunc_batched_workspace_bytes(sh, 2)
+    f = lib.efunc_fit_batched
+    args = lambda **k: dict(dict(shapes=sh, S=2, loss=0, nb=1, steps=1, tuning=None, graph=0, ws=1 << 30,
+                                 wsb=ws), **k)
+
+    def call(**k):
+        a = args(**k)
+        return f(a["shapes"], a["S"], ctypes.byref(ad), a["loss"], 16, 32, 48, 64, a["nb"], a["steps"], 0, None,
+                 a["tuning"], a["graph"], a["ws"], a["wsb"], None)
+    assert call(loss=2) == 1                       # bad loss kind
+    assert call(nb=0) == 1                         # no batches
+    assert call(nb=65) == 1
+    assert call(graph=2) == 1
+    assert call(S=0) == 1
+    assert call(shapes=_shapes((0, 10)), S=1) == 1
+    assert call(tuning=ctypes.byref(B.Tuning(16, 64, 32, 8))) == 1    # chunk below 32
+    assert call(tuning=ctypes.byref(B.Tuning(256, 32, 64, 8))) == 1   # lanes4 > lanes2
+    assert call(tuning=ctypes.byref(B.Tuning(256, 64, 32, 0))) == 1   # no sort blocks
+    assert call(wsb=ws - 256) == 3
+    assert call(ws=(1 << 30) + 64) == 3
+    assert call(steps=0) == 0
+    assert call() == 1                             # batches not in device memory
+    out = lib.efunc_eval_batched(sh, 2, 16, 32, None, None, 1 << 30, ws, None)
+    assert out == 1
+    assert lib.efunc_tune_batched(sh, 2, 0, 16, 32, 48, 64, 1, 0, ctypes.byref(B.Tuning()), None, 1 << 30, ws,
+                                  None) == 1       # no trial steps
+    assert lib.efunc_launch_count() == n0

@@ -125,6 +125,18 @@ MUTANTS = {
     "tolerance diagnostic: dO/dq sensitivity without its factor 2": (
         "*dq_sens = 2.0 * sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);",
         "*dq_sens = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);"),
+    "tolerance diagnostic: kappa_G without the weights' own rounding": (
+        "k_sum += w * (fabs(expo) + 1.0) * sqrt(dev2);",
+        "k_sum += w * fabs(expo) * sqrt(dev2);"),
+    "tolerance diagnostic: dO/dq's fabs without the constant term": (
+        "fa += w * (fabs(k.o) + fabs(k.d[0] * r[0]) + fabs(k.d[1] * r[1]) + fabs(k.d[2] * r[2]));",
+        "fa += w * (fabs(k.d[0] * r[0]) + fabs(k.d[1] * r[1]) + fabs(k.d[2] * r[2]));"),
+    "tolerance diagnostic: gabs without |O - f|": (
+        "const double ax = fabs(k.d[x]) + 2.0 * k.beta * fabs(r[x]) * fabs(O - f);",
+        "const double ax = fabs(k.d[x]) + 2.0 * k.beta * fabs(r[x]);"),
+    "tolerance diagnostic: kappa_G with the key term's 2 dropped": (
+        "const double gx = k.d[x] + 2.0 * k.beta * r[x] * (O - f) - G[x];",
+        "const double gx = k.d[x] + k.beta * r[x] * (O - f) - G[x];"),
     "tolerance diagnostic: variant fabs as |f| instead of its terms": (
         "fa += fabs(k.phi[i] * fu);",
         "fa += k.phi[i] * fu;"),

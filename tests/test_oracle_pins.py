@@ -726,6 +726,63 @@ def test_kappa_is_the_attained_first_order_sensitivity():
             assert abs(rnd - O[j]) <= eps * kappa[j] * (1 + 1e-5) + 1e-15
 
 
+def _G_direct(expo, w, g):
+    """G = sum softmax g over keys with exponents expo and extra weights w,
+    each key's term g (n, 3) held fixed: the direct dependence of dO/dq on
+    the weights (O, inside g, not recomputed)."""
+    lw = np.exp(expo - expo.max()) * w
+    return (lw[:, None] * g).sum(0) / lw.sum()
+
+
+def test_dq_error_terms_are_attained_and_bound_random_perturbations():
+    """The error terms from which the FP32 tolerance of dO/dq is derived.
+    kappa_G bounds the first-order change of G = dO/dq (Eq. func-normal)
+    under relative perturbations eps of every exponent and weight with O held
+    fixed; with two keys (R = 1) the terms g_i - G are collinear and the
+    adversarial perturbation along them attains eps kappa_G.  fabs is
+    attained by perturbing every term of every value f by eps in the sign of
+    the term (O moves by eps fabs), gabs likewise by the terms of G along
+    each axis (G_a moves by at most eps gabs), and random perturbations stay
+    below both."""
+    eps = 1e-7
+    for R, lb, seed in ((1, 1.5, 91), (3, 2.0, 92)):
+        p = synth.random_params(R, seed=seed, delta_scale=0.6, b_scale=0.6).astype(np.float64)
+        q = queries(seed + 1, 12)
+        O, _, G = oracle.forward(p, q, R, W=R, log_beta0=lb, want_dq=True)
+        kG, fab, gab = oracle.dq_error_terms(p, q, R, W=R, log_beta0=lb)
+        pos, beta, o, d = keys_of(p, R, lb)
+        rng = synth.rng(seed + 2)
+        for j in range(q.shape[0]):
+            r = q[j] - pos
+            expo = -beta * (r ** 2).sum(1)
+            f = o + (d * r).sum(1)
+            sm = np.exp(expo - expo.max())
+            sm /= sm.sum()
+            g = d + 2.0 * beta[:, None] * r * (O[j] - f)[:, None]
+            assert np.allclose(_G_direct(expo, np.ones_like(expo), g), G[j], rtol=1e-12, atol=1e-12)
+            if R == 1:
+                e = g[0] - g[1]
+                e = e / np.linalg.norm(e)
+                s = np.sign((g - G[j]) @ e)
+                worst = _G_direct(expo * (1 + eps * s * np.sign(expo)), 1 + eps * s, g)
+                assert abs(abs((worst - G[j]) @ e) / eps - kG[j]) <= 1e-5 * kG[j] + 1e-8
+            for _ in range(3):
+                rnd = _G_direct(expo * (1 + eps * rng.uniform(-1, 1, expo.size)),
+                                1 + eps * rng.uniform(-1, 1, expo.size), g)
+                assert np.linalg.norm(rnd - G[j]) <= eps * kG[j] * (1 + 1e-5) + 1e-15
+            # fabs: every term of f perturbed by eps in its own sign
+            terms = np.concatenate([o[:, None], d * r], 1)
+            f_up = (terms * (1 + eps * np.sign(terms))).sum(1)
+            assert abs(((sm * f_up).sum() - O[j]) / eps - fab[j]) <= 1e-5 * fab[j] + 1e-8
+            f_rnd = (terms * (1 + eps * rng.uniform(-1, 1, terms.shape))).sum(1)
+            assert abs((sm * f_rnd).sum() - O[j]) <= eps * fab[j] * (1 + 1e-5) + 1e-15
+            # gabs: the terms d_a and 2 beta r_a (O - f) of G_a perturbed likewise
+            ta = np.stack([d, 2.0 * beta[:, None] * r * (O[j] - f)[:, None]], 2)   # (keys, axis, term)
+            moved = (sm[:, None] * (ta * eps * np.sign(ta)).sum(2)).sum(0)
+            assert np.linalg.norm(moved) <= eps * gab[j] * (1 + 1e-9) + 1e-15
+            assert np.linalg.norm(moved) >= eps * gab[j] / np.sqrt(3) * (1 - 1e-9) - 1e-15
+
+
 def test_dq_sensitivity_is_the_norm_of_the_lse_gradient():
     """dq_sens = 2 ||sum softmax beta (q - key)||, the factor by which an
     error in O enters dO/dq, equals ||grad_q lse|| (lse = log sum

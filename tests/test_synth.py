@@ -43,3 +43,26 @@ def test_sample_batch_is_seeded_and_split():
     assert 0.45 < near.mean() < 0.7
     np.testing.assert_allclose(a[:, 3], u.sdf(a[:, :3].astype(np.float64)), atol=1e-7)
     assert not np.array_equal(a, synth.sample_batch(u, 4096, seed=8))
+
+
+def test_device_sampler_matches_the_host_distribution():
+    """sample_batch_torch draws sample_batch's distribution (another random
+    stream): half the rows uniform in the cube, half within a few sigma of
+    the surface, targets equal to the union SDF at the stored point."""
+    import torch
+    shape = synth.random_union(3)
+    J = 100000
+    a = synth.sample_batch(shape, J, seed=5)
+    b = synth.sample_batch_torch(shape, J, seed=5, device="cpu").numpy()
+    assert b.shape == (J, 4) and b.dtype == np.float32
+    np.testing.assert_allclose(b[:, 3], shape.sdf(b[:, :3].astype(np.float64)), atol=1e-7)
+    for x in (a, b):
+        assert abs((np.abs(x[:, 3]) < 0.05).mean() - 0.54) < 0.01
+        assert np.all(np.abs(x[:, :3]) <= 1.2)
+    assert abs(np.abs(a[:, 3]).mean() - np.abs(b[:, 3]).mean()) < 2e-3
+    g = synth.sdf_grid_torch(shape, 8, "cpu").numpy()
+    c = -1 + (np.arange(8) + 0.5) * 0.25
+    X, Y, Z = np.meshgrid(c, c, c, indexing="ij")
+    np.testing.assert_allclose(g.reshape(-1), shape.sdf(np.stack([X, Y, Z], -1).reshape(-1, 3)), atol=1e-7)
+    assert torch.equal(synth.sample_batch_torch(shape, 1000, seed=9, device="cpu"),
+                       synth.sample_batch_torch(shape, 1000, seed=9, device="cpu"))
