@@ -65,7 +65,8 @@ typedef enum {
     EFUNC_ERR_WORKSPACE = 3,   /* workspace NULL, misaligned or too small */
     EFUNC_ERR_NONFINITE = 4,   /* a hyper-parameter is NaN or infinite */
     EFUNC_ERR_UNSUPPORTED = 5, /* valid request outside the implemented set */
-    EFUNC_ERR_IO = 6           /* checkpoint file missing, unwritable, short or corrupt */
+    EFUNC_ERR_IO = 6,          /* checkpoint file missing, unwritable, short or corrupt */
+    EFUNC_ERR_TIMEOUT = 7      /* a bounded wait inside a kernel ran out (efunc_encoder_status) */
 } efunc_status;
 
 /* Grid description.  R in [1, 256]; W must be 2; log_beta0 is the log-scale
@@ -506,6 +507,69 @@ efunc_status efunc_tune_batched(const efunc_shape *shapes, int32_t S, int32_t lo
                                 efunc_tuning *best, double *best_ms_per_step, void *workspace,
                                 size_t workspace_bytes, efunc_stream_t stream);
 
+/* ------------------------------------------------------ warm-start encoder */
+
+/* A small BF16 3-D convolutional network that predicts a fit's starting
+ * parameter grid from the shape's SDF sampled at the 32^3 cell centres (the
+ * paper starts every fit from scratch, Sec. 3.4; it has no such encoder):
+ *   L1 3x3x3 conv 1 -> 32 + ReLU, L2 3x3x3 conv 32 -> 64 + ReLU,
+ *   L3 3x3x3 conv 64 -> 128 + ReLU, L4 1x1x1 conv 128 -> 13,
+ * zero padding, BF16 activations, FP32 accumulation; L2-L4 and their
+ * gradients run on the tensor cores (implicit GEMM, tcgen05).  It is
+ * trained on (SDF grid, fitted parameter grid) pairs with the weighted MSE
+ *   L = (1/V) sum_voxels sum_slots w_s (pred_s - target_s)^2
+ * and its FP32 master weights are updated with efunc_adam_step.
+ * Weights, one FP32 array of efunc_encoder_weight_count floats:
+ *   W1 [32][27], b1 [32], W2 [64][27][32], b2 [64], W3 [128][27][64],
+ *   b3 [128], W4 [13][128], b4 [13]
+ * with W[co][tap][ci], tap = 9 (dx + 1) + 3 (dy + 1) + (dz + 1) the offset
+ * of the input voxel read for an output voxel.
+ * Volumes: sdf [device] batch x 32^3 floats, params / target [device]
+ * batch x 32^3 x 13 floats, voxels in the order of the parameter grid
+ * (x slowest).  batch in [1, 4096].  The kernels' waits are bounded; a wait
+ * that runs out marks the workspace (efunc_encoder_status). */
+int64_t efunc_encoder_weight_count(void);
+
+/* Workspace bytes of the encoder calls for a batch (about 1.2 KB per voxel:
+ * BF16 activations and their gradients); 0 for an invalid batch. */
+size_t efunc_encoder_workspace_bytes(int32_t batch);
+
+/* params = encoder(sdf). */
+efunc_status efunc_encoder_forward(const float *weights, const float *sdf, int32_t batch, float *params,
+                                   void *workspace, size_t workspace_bytes, efunc_stream_t stream);
+
+/* One training step's forward and backward: grad [device,
+ * efunc_encoder_weight_count floats] is written with dL/dweights, *loss
+ * [device, 1 float] with L.  slot_weights [device] 13 floats or NULL (all 1). */
+efunc_status efunc_encoder_train_step(const float *weights, const float *sdf, const float *target,
+                                      const float *slot_weights, int32_t batch, float *grad, float *loss,
+                                      void *workspace, size_t workspace_bytes, efunc_stream_t stream);
+
+/* EFUNC_ERR_TIMEOUT if a wait inside an encoder kernel of the last call on
+ * this workspace ran out (its outputs are then invalid), else EFUNC_OK.
+ * Synchronises with the device. */
+efunc_status efunc_encoder_status(const void *workspace);
+
+/* The encoder's tensor-core convolution on its own (for tests): BF16
+ * activations x [batch][32^3][cin] (cin a multiple of 64, at most 256),
+ * weights w [cout][taps][cin] BF16 (taps 27 = 3x3x3 with zero padding, or
+ * 1), cout in {16, 32, 64, 128}:
+ *   out[v][co] = sum_{tap, ci} w[co][tap][ci] x[v + offset(tap)][ci]
+ * then per mode: 0 bias + ReLU -> BF16 rows of out_ld; 1 bias -> FP32 rows
+ * of out_ld, the first store_cols columns; 2 zeroed where mask (BF16 rows of
+ * out_ld) is <= 0 -> BF16 (the gradient through the ReLU of the layer
+ * below).  bias [device] cout floats or NULL.  err [device] int, set if a
+ * wait ran out. */
+efunc_status efunc_conv3d_bf16(const void *x, int32_t batch, int32_t cin, const void *w, int32_t cout, int32_t taps,
+                               const float *bias, int32_t mode, const void *mask, void *out, int32_t out_ld,
+                               int32_t store_cols, int32_t *err, efunc_stream_t stream);
+
+/* Its weight gradient: dw [cout][taps][cin] FP32 += sum_v dy[v][co]
+ * x[v + offset(tap)][ci], dy [batch][32^3][dy_ld] BF16 (dy_ld 64 or 128,
+ * cout <= dy_ld), FP32 atomics. */
+efunc_status efunc_conv3d_wgrad_bf16(const void *dy, int32_t dy_ld, int32_t cout, const void *x, int32_t cin,
+                                     int32_t batch, int32_t taps, float *dw, int32_t *err, efunc_stream_t stream);
+
 /* ---------------------------------------------------- checkpoint / resume */
 
 /* A fit's state is its parameter grid, Adam's two moments and the number of
@@ -562,8 +626,9 @@ void efunc_profile_enable(int32_t enable);
  * "variant_forward", "variant_backward", "variant_fit", "cosine_pack",
  * "cosine_forward", "cosine_backward", "cosine_fit", "eval" (efunc_eval_loss,
  * efunc_eval_batched), "f64" (every kernel of the FP64 calls), "batched"
- * (the batched fit's fused kernel) or "batched_stats" (its per-shape
- * statistics)).  Returns 0 on success, -1 for an
+ * (the batched fit's fused kernel), "batched_stats" (its per-shape
+ * statistics), "enc_conv" / "enc_wgrad" (the encoder's tensor-core
+ * convolutions and weight gradients) or "enc_aux" (its other kernels)).  Returns 0 on success, -1 for an
  * unknown name or a CUDA error. */
 int32_t efunc_profile_read(const char *name, double *total_ms, int64_t *launches);
 

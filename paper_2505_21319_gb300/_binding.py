@@ -17,7 +17,7 @@ c_size_t, c_void_p, c_char_p = ctypes.c_size_t, ctypes.c_void_p, ctypes.c_char_p
 P_float = ctypes.POINTER(ctypes.c_float)
 
 STATUS = {0: "EFUNC_OK", 1: "EFUNC_ERR_ARG", 2: "EFUNC_ERR_CUDA", 3: "EFUNC_ERR_WORKSPACE",
-          4: "EFUNC_ERR_NONFINITE", 5: "EFUNC_ERR_UNSUPPORTED", 6: "EFUNC_ERR_IO"}
+          4: "EFUNC_ERR_NONFINITE", 5: "EFUNC_ERR_UNSUPPORTED", 6: "EFUNC_ERR_IO", 7: "EFUNC_ERR_TIMEOUT"}
 LOSS_L1, LOSS_MSE = 0, 1
 
 
@@ -118,6 +118,16 @@ SIGNATURES = {
     "efunc_tune_batched": (c_int32, [ctypes.POINTER(Shape), c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                      c_int32, c_int32, ctypes.POINTER(Tuning), ctypes.POINTER(c_double), c_void_p,
                                      c_size_t, c_void_p]),
+    "efunc_encoder_weight_count": (c_int64, []),
+    "efunc_encoder_workspace_bytes": (c_size_t, [c_int32]),
+    "efunc_encoder_forward": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "efunc_encoder_train_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
+                                           c_void_p, c_size_t, c_void_p]),
+    "efunc_encoder_status": (c_int32, [c_void_p]),
+    "efunc_conv3d_bf16": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_int32, c_int32, c_void_p, c_int32,
+                                    c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
+    "efunc_conv3d_wgrad_bf16": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_int32, c_int32, c_int32, c_void_p,
+                                          c_void_p, c_void_p]),
     "efunc_profile_enable": (None, [c_int32]),
     "efunc_profile_read": (c_int32, [c_char_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     "efunc_profile_reset": (None, []),

@@ -646,6 +646,67 @@ class Batch:
                  "sort_blocks": best.sort_blocks}, ms.value)
 
 
+# ------------------------------------------------------ warm-start encoder
+
+ENC_R = 32
+
+
+def encoder_weight_count() -> int:
+    return int(B.load().efunc_encoder_weight_count())
+
+
+def encoder_init(seed: int = 0) -> torch.Tensor:
+    """He-initialised FP32 master weights of the encoder (CPU tensor; biases 0)."""
+    import numpy as np
+    g = np.random.Generator(np.random.Philox(int(seed)))
+    parts = []
+    for fan_in, n_w, n_b in ((27, 32 * 27, 32), (27 * 32, 64 * 27 * 32, 64), (27 * 64, 128 * 27 * 64, 128),
+                             (128, 13 * 128, 13)):
+        parts.append(g.standard_normal(n_w) * np.sqrt(2.0 / fan_in))
+        parts.append(np.zeros(n_b))
+    w = np.concatenate(parts).astype(np.float32)
+    assert w.size == encoder_weight_count()
+    return torch.from_numpy(w)
+
+
+class Encoder:
+    """Workspace-holding wrapper of the encoder calls for a fixed batch size."""
+
+    def __init__(self, batch: int, device="cuda"):
+        self.batch = int(batch)
+        self.device = torch.device(device)
+        n = int(B.load().efunc_encoder_workspace_bytes(self.batch))
+        if n == 0:
+            raise ValueError("invalid batch")
+        self.ws = torch.empty(n, dtype=torch.uint8, device=self.device)
+
+    def forward(self, weights, sdf):
+        """(batch, 32^3 x 13) predicted parameter grids from (batch, 32, 32, 32) SDF grids."""
+        _need(weights, "weights", encoder_weight_count())
+        _need(sdf, "sdf", self.batch * ENC_R ** 3)
+        out = torch.empty((self.batch, ENC_R ** 3 * NSLOT), dtype=torch.float32, device=self.device)
+        B.check("efunc_encoder_forward", B.load().efunc_encoder_forward(
+            _ptr(weights), _ptr(sdf), self.batch, _ptr(out), _ptr(self.ws), self.ws.numel(), _stream(self.device)))
+        return out
+
+    def train_step(self, weights, sdf, target, slot_weights=None):
+        """(grad, loss): dL/dweights and the weighted MSE of one batch."""
+        _need(weights, "weights", encoder_weight_count())
+        _need(sdf, "sdf", self.batch * ENC_R ** 3)
+        _need(target, "target", self.batch * ENC_R ** 3 * NSLOT)
+        if slot_weights is not None:
+            _need(slot_weights, "slot_weights", NSLOT)
+        grad = torch.empty_like(weights)
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        B.check("efunc_encoder_train_step", B.load().efunc_encoder_train_step(
+            _ptr(weights), _ptr(sdf), _ptr(target), _ptr(slot_weights), self.batch, _ptr(grad), _ptr(loss),
+            _ptr(self.ws), self.ws.numel(), _stream(self.device)))
+        return grad, loss
+
+    def status(self):
+        B.check("efunc_encoder_status", B.load().efunc_encoder_status(_ptr(self.ws)))
+
+
 def profile(enable: bool = True):
     B.load().efunc_profile_enable(int(enable))
 

@@ -43,7 +43,7 @@ const char *const kKernelNames[K_COUNT] = {"bin",       "scan_reduce", "scan_top
                                            "pack_keys", "forward",     "fused_backward", "fused_fit", "adam",
                                            "mean_shift", "variant_pack", "variant_forward", "variant_backward",
                                            "variant_fit", "cosine_pack", "cosine_forward", "cosine_backward",
-                                           "cosine_fit", "eval", "f64", "batched", "batched_stats"};
+                                           "cosine_fit", "eval", "f64", "batched", "batched_stats", "enc_conv", "enc_wgrad", "enc_aux"};
 
 cudaEvent_t take_event()
 {
@@ -792,6 +792,7 @@ const char *efunc_status_str(efunc_status s)
     case EFUNC_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
     case EFUNC_ERR_NONFINITE: return "non-finite hyper-parameter";
     case EFUNC_ERR_UNSUPPORTED: return "unsupported configuration";
+    case EFUNC_ERR_TIMEOUT: return "a bounded wait inside a kernel ran out";
     }
     return "unknown status";
 }
