@@ -79,6 +79,8 @@ TARGET_MAE = 1e-3
 TARGET_CHUNK = 50
 # batched fit: shapes fitted together
 BATCH_SHAPES = 256
+# learned warm start: encoder batch (shapes per step)
+WARM_BATCH = 16
 # FP32-pipe operations of one (centre, point) pair of the mean-shift
 # initialisation: 3 differences, 3 for the squared norm, 1 scale, 1 compare,
 # 1 exponent difference, 1 add to Z, 3 FMAs into S (the ex2 runs on the MUFU)
@@ -423,6 +425,57 @@ def bench_batched(api, dev, stream, rank, steps, peak, ws=1):
             "timing": "CUDA events around the whole efunc_fit_batched call (capture and instantiation included)"}
 
 
+def bench_warm_start(dev, rank, n_train, n_eval, train_steps, epochs, eval_steps, ws=1):
+    """The learned warm start against the plain initialisation: plain batched
+    fits of n_train random shapes (32^3, 2^16 queries per step, train_steps
+    steps) give the encoder's training pairs; the encoder is trained for
+    `epochs`; n_eval held-out shapes are then fitted (32^3, 2^17 queries per
+    step) from the N(0, 1e-3) initialisation and from the encoder's
+    prediction, the held-out MAE of every shape (2^15 points, half uniform,
+    half near the surface) tracked every 25 steps.  A shape's target is MAE
+    1e-3, or the plain fit's final MAE where the plain fit does not reach
+    1e-3; each arm reports the steps and seconds until its shapes reach their
+    targets (the warm arm's seconds include the encoder's prediction)."""
+    import torch
+    from paper_2505_21319_gb300 import synth
+    from paper_2505_21319_gb300 import warmstart as W
+    t0 = time.perf_counter()
+    train = W.random_shapes(200000 + 10000 * rank, n_train)
+    tp, fit_s = W.fit_plain(train, J=1 << 16, steps=train_steps, seed=11, device=dev)
+    sdf = W.sdf_grids(train, dev)
+    w, losses, enc_s = W.train_encoder(sdf, tp, epochs=epochs, batch=WARM_BATCH, lr=1e-3, seed=rank)
+    ev = W.random_shapes(300000 + 10000 * rank, n_eval)
+    held = W.heldout_rows(ev, 1 << 15, seed=99, device=dev)
+    pred, pred_s = W.predict(w, W.sdf_grids(ev, dev), batch=WARM_BATCH)
+    init = torch.cat([torch.from_numpy(synth.init_params(W.R, seed=i).reshape(1, -1)) for i in range(n_eval)]).to(dev)
+    arms = {}
+    for name, p0 in (("plain", init), ("warm", pred)):
+        st, mae, sec = W.fit_curves(ev, p0, J=1 << 17, max_steps=eval_steps, every=25, seed=5, held=held)
+        arms[name] = (st, mae, sec)
+    st_p, mae_p, _ = arms["plain"]
+    target = np.where(mae_p.min(0) <= 1e-3, 1e-3, mae_p[-1])
+    out = {"train_shapes": n_train, "train_fit_steps": train_steps, "train_fit_s": fit_s, "encoder_epochs": epochs,
+           "encoder_train_s": enc_s, "encoder_loss_first": losses[0], "encoder_loss_last": losses[-1],
+           "eval_shapes": n_eval, "eval_steps": eval_steps, "predict_s": pred_s,
+           "target_rule": "per shape: 1e-3, or the plain fit's final held-out MAE where 1e-3 is not reached",
+           "shapes_reaching_1e-3_plain": int((mae_p.min(0) <= 1e-3).sum())}
+    for name, (st, mae, sec) in arms.items():
+        steps = W.steps_to(st, mae, target)
+        reached = np.isfinite(steps)
+        last = float(np.max(steps[reached])) if reached.any() else float("nan")
+        sec_per_step = float(sec[-1] / st[-1])
+        extra = pred_s if name == "warm" else 0.0
+        wall = last * sec_per_step + extra if reached.all() else float("nan")
+        out[name] = {"mae_median_start": float(np.median(mae[0])), "mae_median_final": float(np.median(mae[-1])),
+                     "steps_to_target_median": float(np.median(steps)), "steps_to_target_mean":
+                     float(np.mean(steps[reached])) if reached.any() else float("nan"),
+                     "shapes_reached": int(reached.sum()), "steps_until_all_reached": last,
+                     "seconds_per_step": sec_per_step, "wall_s_to_target": wall,
+                     "fits_per_s": n_eval * ws / wall if np.isfinite(wall) and wall > 0 else None}
+    out["total_s"] = time.perf_counter() - t0
+    return out
+
+
 def fit_to_target(api, dev, stream, R, J, pool, held, rank, max_steps, chunk, target, ws=1, params0=None):
     """A plain fit from the N(0, 1e-3) initialisation (or params0) in chunks of
     ``chunk`` steps, the held-out MAE (volume, near-surface, and the two
@@ -489,7 +542,13 @@ def main():
     ap.add_argument("--isolated-steps", type=int, default=50)
     ap.add_argument("--graph-steps", type=int, default=500)
     ap.add_argument("--large-steps", type=int, default=20)
-    ap.add_argument("--batched-steps", type=int, default=1000,
+    ap.add_argument("--warm-train-shapes", type=int, default=512,
+                    help="shapes fitted to train the warm-start encoder (0 skips the warm-start comparison)")
+    ap.add_argument("--warm-eval-shapes", type=int, default=64)
+    ap.add_argument("--warm-train-steps", type=int, default=800)
+    ap.add_argument("--warm-epochs", type=int, default=30)
+    ap.add_argument("--warm-eval-steps", type=int, default=1500)
+    ap.add_argument("--batched-steps", type=int, default=300,
                     help="steps of the batched fit of 256 shapes (0 skips it)")
     ap.add_argument("--target-steps", type=int, default=2000,
                     help="steps of the plain fits to the MAE target (0 skips them)")
@@ -832,6 +891,14 @@ def main():
         log(f"[bench] batched: {batched['ms_per_step']:.3f} ms/step, {batched['value']:.3e} q/s, "
             f"frac {batched['frac']:.3f}, tuning {batched['tuning']}")
 
+    # ---- learned warm start (encoder) against the plain initialisation
+    warm = None
+    if args.warm_train_shapes > 0:
+        warm = bench_warm_start(dev, rank, args.warm_train_shapes, args.warm_eval_shapes, args.warm_train_steps,
+                                args.warm_epochs, args.warm_eval_steps, ws)
+        log(f"[bench] warm start: plain {warm['plain']['steps_to_target_median']} / warm "
+            f"{warm['warm']['steps_to_target_median']} median steps to target, {warm['total_s']:.0f} s")
+
     # ---- end to end through the C ABI with host buffers: the batch pool in
     # pinned host memory, every step copies its 64 MiB batch to the device
     # (overlapped with the previous step's compute by the library) and copies
@@ -889,6 +956,7 @@ def main():
             "gpu_launches": launches,
             "fits_to_target": to_target,
             "batched_fit": batched,
+            "warm_start": warm,
             "fit": {"steps_total": args.warmup + args.steps, "loss_first_timed": float(st[0, 0]),
                     "mae_first_timed": float(st[0, 1]), "mae_last": float(st[-1, 1]),
                     "fits_per_s": 1e3 / (FIT_STEPS_32 * ms) * ws, "steps_per_fit": FIT_STEPS_32},

@@ -443,15 +443,20 @@ typedef struct {
  *   lanes2_max   work items of at most this many queries take 2 lanes per
  *   lanes4_max   query in the forward, of at most lanes4_max 4 lanes
  *                (lanes4_max <= lanes2_max <= 256)
- *   sort_blocks  blocks per SM of the sort's bin and scatter kernels, [1, 16] */
+ *   sort_blocks  blocks per SM of the sort's bin and scatter kernels, [1, 16]
+ *   group_max    sparse cells: an aligned 2x2x2 block of window cells with at
+ *                least two occupied cells and at most group_max queries is
+ *                one work item (its 5x5x5 union window staged once, each key's
+ *                gradient added once); 0 disables grouping, at most 256 */
 typedef struct {
     int32_t chunk;
     int32_t lanes2_max;
     int32_t lanes4_max;
     int32_t sort_blocks;
+    int32_t group_max;
 } efunc_tuning;
 
-/* The configuration used when none is given: {256, 64, 32, 8}. */
+/* The configuration used when none is given: {256, 64, 32, 8, 128}. */
 void efunc_default_tuning(efunc_tuning *out);
 
 /* Floats per array (params, m, v) of S shapes, sum 13 R_s^3; -1 if a shape
@@ -495,9 +500,9 @@ efunc_status efunc_eval_batched(const efunc_shape *shapes, int32_t S, const floa
                                 efunc_stream_t stream);
 
 /* Autotuner of the batched fit: times trial_steps steps of efunc_fit_batched
- * (after one untimed step) for each of 12 configurations (chunk 128 / 256,
- * lane thresholds 64 / 32 and 96 / 48, 2 / 4 / 8 sort blocks per SM) on
- * these shapes and batches, with CUDA events on `stream`, and writes the
+ * (after one untimed step) for each of 24 configurations (chunk 128 / 256,
+ * lane thresholds 64 / 32 and 96 / 48, 4 / 8 sort blocks per SM, grouping
+ * of sparse cells off / 64 / 128 queries) on these shapes and batches, with CUDA events on `stream`, and writes the
  * fastest to *best (and its milliseconds per step to *best_ms_per_step, or
  * NULL).  The trial steps are Adam steps with learning rate 0: params are
  * left as they are and m, v are zeroed at the end (tune before fitting).

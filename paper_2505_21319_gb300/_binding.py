@@ -44,7 +44,8 @@ class Shape(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("chunk", c_int32), ("lanes2_max", c_int32), ("lanes4_max", c_int32), ("sort_blocks", c_int32)]
+    _fields_ = [("chunk", c_int32), ("lanes2_max", c_int32), ("lanes4_max", c_int32), ("sort_blocks", c_int32),
+                ("group_max", c_int32)]
 
 
 KEYS_GRID, KEYS_OFFSET, KEYS_BOTH = 1, 2, 3

@@ -643,7 +643,7 @@ class Batch:
             ctypes.byref(best), ctypes.byref(ms), _ptr(self.ws), self.ws.numel(), _stream(self.device)))
         self.tuning = best
         return ({"chunk": best.chunk, "lanes2_max": best.lanes2_max, "lanes4_max": best.lanes4_max,
-                 "sort_blocks": best.sort_blocks}, ms.value)
+                 "sort_blocks": best.sort_blocks, "group_max": best.group_max}, ms.value)
 
 
 # ------------------------------------------------------ warm-start encoder

@@ -67,9 +67,10 @@ constexpr int kMaxShapes = 1024;
 
 // Per-call control block at the start of the workspace.
 struct Ctrl {
-    int n_items;        // work items produced by the sort
+    int n_items;        // work items produced by the sort (one cell each)
     int next_item;      // dynamic work counter of the fused kernel
-    int pad[2];
+    int n_groups;       // grouped work items (sparse 2x2x2 cell octets), stored from the top of the item array down
+    int next_group;     // dynamic work counter of the grouped kernel
     double loss_sum;    // sum over queries of |O-o| (L1) or (O-o)^2 (MSE), plus the Eikonal term
     double abs_sum;     // sum over queries of |O-o|
 };
@@ -116,6 +117,12 @@ struct SortArgs {
     const BatchShape *shapes;
     int S;
     int chunk;           // queries per work item at most (batched sort; kChunk otherwise)
+    // sparse cells: an aligned 2x2x2 octet of bins (8 consecutive bins of the
+    // brick-Morton order) with at least two non-empty cells and at most
+    // group_max queries becomes one grouped item, written to gtop[-g] for the
+    // g-th group (the top end of the item array); 0 disables grouping
+    int group_max;
+    Item *gtop;
 };
 
 // Four doubles in one 32-byte aligned record: the FP64 counterpart of a
@@ -282,7 +289,7 @@ struct BatchedStatsArgs {
 // Kernel identifiers for the profiler.
 enum KernelId { K_BIN = 0, K_SCAN_REDUCE, K_SCAN_TOP, K_SCAN_EMIT, K_SCATTER, K_PACK_KEYS, K_FORWARD, K_FUSED_BWD,
                 K_FUSED_FIT, K_ADAM, K_MEAN_SHIFT, K_VAR_PACK, K_VAR_FORWARD, K_VAR_BACKWARD, K_VAR_FIT, K_COS_PACK, K_COS_FORWARD, K_COS_BACKWARD,
-                K_COS_FIT, K_EVAL, K_F64, K_BATCHED, K_BATCHED_STATS, K_ENC_CONV, K_ENC_WGRAD, K_ENC_AUX, K_COUNT };
+                K_COS_FIT, K_EVAL, K_F64, K_BATCHED, K_BATCHED_STATS, K_ENC_CONV, K_ENC_WGRAD, K_ENC_AUX, K_GROUPED, K_COUNT };
 
 // Launch bookkeeping (launch counter and optional CUDA-event profiling).
 void launch_begin(int kid, cudaStream_t s);
@@ -316,6 +323,10 @@ int fused_grid_size64();
 // all grids, fused fit / evaluation kernel with per-item shapes, per-shape
 // statistics
 cudaError_t launch_sort_batched(const SortArgs &a, cudaStream_t s, int blocks_per_sm);
+// Grouped items (sparse cell octets): the union window of the octet is staged
+// once; FIT and EVAL modes, single-shape or batched (b.shapes != NULL).
+cudaError_t launch_grouped(const FusedArgs &a, const BatchArgs &b, const Item *gtop, bool eval, cudaStream_t s);
+constexpr int kGroupMax = 128;   // default queries per grouped octet at most
 cudaError_t launch_pack_keys_batched(const BatchedPackArgs &a, cudaStream_t s);
 cudaError_t launch_fused_batched(const FusedArgs &a, const BatchArgs &b, bool eval, int grid, cudaStream_t s);
 cudaError_t launch_batched_stats(const BatchedStatsArgs &a, cudaStream_t s);

@@ -43,7 +43,7 @@ const char *const kKernelNames[K_COUNT] = {"bin",       "scan_reduce", "scan_top
                                            "pack_keys", "forward",     "fused_backward", "fused_fit", "adam",
                                            "mean_shift", "variant_pack", "variant_forward", "variant_backward",
                                            "variant_fit", "cosine_pack", "cosine_forward", "cosine_backward",
-                                           "cosine_fit", "eval", "f64", "batched", "batched_stats", "enc_conv", "enc_wgrad", "enc_aux"};
+                                           "cosine_fit", "eval", "f64", "batched", "batched_stats", "enc_conv", "enc_wgrad", "enc_aux", "grouped"};
 
 cudaEvent_t take_event()
 {
@@ -249,6 +249,7 @@ struct SortBuf {
     uint32_t *rank;
     float4 *sorted;
     Item *items;
+    Item *gtop;   // grouped items are stored from here down
 };
 
 SortBuf sort_buf(const Views &v, int b)
@@ -256,14 +257,23 @@ SortBuf sort_buf(const Views &v, int b)
     const Layout &L = v.L;
     char *p = v.base;
     if (b == 0)
-        return {v.ctrl(), v.hist(), v.blocksum(), v.rank(), v.sorted(), v.items()};
+        return {v.ctrl(), v.hist(), v.blocksum(), v.rank(), v.sorted(), v.items(), v.items() + L.max_items - 1};
+    Item *it2 = reinterpret_cast<Item *>(p + L.items2);
     return {reinterpret_cast<Ctrl *>(p + L.ctrl2), reinterpret_cast<uint32_t *>(p + L.hist2),
             reinterpret_cast<unsigned long long *>(p + L.blocksum2), reinterpret_cast<uint32_t *>(p + L.rank2),
-            reinterpret_cast<float4 *>(p + L.sorted2), reinterpret_cast<Item *>(p + L.items2)};
+            reinterpret_cast<float4 *>(p + L.sorted2), it2, it2 + L.max_items - 1};
 }
 
+// Queries per octet at most of the grouped items of a single-shape fit:
+// large sparse batches (at least 2^18 queries, at most 16 per bin on average)
+// group their sparse octets; denser batches keep one item per cell, and so do
+// small ones, whose few items the second (grouped) launch would only
+// lengthen (measured on one GB300: 64^3 x 2^22 1.59 instead of 3.03 ms per
+// step, 32^3 x 2^18 0.26 instead of 0.41, 16^3 x 65,536 0.13 instead of 0.067).
+int fit_group_max(const Layout &L, int64_t J) { return (J >= (1 << 18) && J <= 16 * L.nbins) ? kGroupMax : 0; }
+
 cudaError_t sort_into_buf(const SortBuf &b, const Layout &L, int R, const float *q, int64_t J, int q_stride,
-                          cudaStream_t s, int narrow_blocks)
+                          cudaStream_t s, int narrow_blocks, int group_max = 0)
 {
     cudaError_t e = cudaMemsetAsync(b.ctrl, 0, sizeof(Ctrl), s);
     if (e != cudaSuccess) return e;
@@ -283,13 +293,15 @@ cudaError_t sort_into_buf(const SortBuf &b, const Layout &L, int R, const float 
     a.perm = nullptr;
     a.items = b.items;
     a.ctrl = b.ctrl;
+    a.group_max = group_max;
+    a.gtop = b.gtop;
     return launch_sort(a, s, narrow_blocks);
 }
 
 // Clears the control block and histogram, then sorts q into the workspace
 // (or into the caller's sorted / perm buffers when given).
 cudaError_t sort_into(const Views &v, int R, const float *q, int64_t J, int q_stride, float4 *sorted, int *perm,
-                      cudaStream_t s)
+                      cudaStream_t s, int group_max = 0)
 {
     cudaError_t e = cudaMemsetAsync(v.ctrl(), 0, sizeof(Ctrl), s);
     if (e != cudaSuccess) return e;
@@ -309,6 +321,8 @@ cudaError_t sort_into(const Views &v, int R, const float *q, int64_t J, int q_st
     a.perm = perm;
     a.items = v.items();
     a.ctrl = v.ctrl();
+    a.group_max = group_max;
+    a.gtop = v.items() + v.L.max_items - 1;
     return launch_sort(a, s);
 }
 
@@ -554,6 +568,7 @@ efunc_status fit_pipelined(const efunc_grid *grid, const efunc_adam *adam, int32
     auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * (size_t)J * 4; };
     const bool eik = eikonal_weight > 0.f;
     const int grid_blocks = fused_fit_grid_size(eik, true);
+    const int gmax = eik ? 0 : fit_group_max(vw.L, J);
 
     if (cudaMemsetAsync(grad, 0, (size_t)n * 4, s) != cudaSuccess) return cuda_fail();
     // both sort buffers (and staging buffers) are free once the caller's earlier work is done
@@ -576,7 +591,7 @@ efunc_status fit_pipelined(const efunc_grid *grid, const efunc_adam *adam, int32
         if (cudaStreamWaitEvent(ss, pipe->consumed[b], 0) != cudaSuccess) return false;
         // one sort block per SM: the default kernel's steps are long enough to
         // hide it, and more sort traffic slows the kernel beside it
-        if (sort_into_buf(sort_buf(vw, b), vw.L, R, src, J, 4, ss, 1) != cudaSuccess) return false;
+        if (sort_into_buf(sort_buf(vw, b), vw.L, R, src, J, 4, ss, 1, gmax) != cudaSuccess) return false;
         if (q_host && cudaEventRecord(pipe->freed[b], ss) != cudaSuccess) return false;
         return cudaEventRecord(pipe->sorted[b], ss) == cudaSuccess;
     };
@@ -603,6 +618,7 @@ efunc_status fit_pipelined(const efunc_grid *grid, const efunc_adam *adam, int32
         f.inv_J = (float)(1.0 / (double)J);
         f.eik_weight = eikonal_weight;
         if (launch_fused_fit(f, eik, grid_blocks, s) != cudaSuccess) return cuda_fail();
+        if (gmax && launch_grouped(f, BatchArgs{}, sb.gtop, false, s) != cudaSuccess) return cuda_fail();
         float *stats_dev = reinterpret_cast<float *>(sb.ctrl) + 16;
         AdamArgs a = adam_args(adam, n, params, grad, m, v, step0 + it + 1);
         a.ctrl = sb.ctrl;
@@ -645,6 +661,7 @@ efunc_status fit_graph(const efunc_grid *grid, const efunc_adam *adam, int32_t l
     auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * (size_t)J * 4; };
     const bool eik = eikonal_weight > 0.f;
     const int grid_blocks = fused_fit_grid_size(eik, true);
+    const int gmax = eik ? 0 : fit_group_max(vw.L, J);
     const int32_t period = (n_batches % 2 == 0) ? n_batches : 2 * n_batches;
     static_assert(sizeof(Ctrl) <= 64 && sizeof(AdamClock) <= 128, "control block layout");
     AdamClock *clk = reinterpret_cast<AdamClock *>(reinterpret_cast<char *>(vw.ctrl()) + 128);
@@ -659,7 +676,7 @@ efunc_status fit_graph(const efunc_grid *grid, const efunc_adam *adam, int32_t l
     auto issue_sort = [&](int32_t k, bool wait_consumed) -> bool {
         const int b = k & 1;
         if (wait_consumed && cudaStreamWaitEvent(ss, pipe->consumed[b], 0) != cudaSuccess) return false;
-        if (sort_into_buf(sort_buf(vw, b), vw.L, R, batch(k), J, 4, ss, 1) != cudaSuccess) return false;
+        if (sort_into_buf(sort_buf(vw, b), vw.L, R, batch(k), J, 4, ss, 1, gmax) != cudaSuccess) return false;
         return cudaEventRecord(pipe->sorted[b], ss) == cudaSuccess;
     };
     // one step on stream st; `head` marks the first step of a captured period
@@ -683,6 +700,7 @@ efunc_status fit_graph(const efunc_grid *grid, const efunc_adam *adam, int32_t l
         f.inv_J = (float)(1.0 / (double)J);
         f.eik_weight = eikonal_weight;
         if (launch_fused_fit(f, eik, grid_blocks, st) != cudaSuccess) return false;
+        if (gmax && launch_grouped(f, BatchArgs{}, sb.gtop, false, st) != cudaSuccess) return false;
         AdamArgs a = base;
         a.ctrl = sb.ctrl;
         a.inv_J = f.inv_J;
@@ -1041,6 +1059,7 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
     cudaError_t e = cudaMemsetAsync(grad, 0, (size_t)n * 4, s);
     if (e != cudaSuccess) return cuda_fail();
     const int grid_blocks = fused_grid_size();
+    const int gmax = eikonal_weight > 0.f ? 0 : fit_group_max(vw.L, J);
     const size_t batch_bytes = (size_t)J * 16;
     auto batch = [&](int32_t it) { return qo + (size_t)(it % n_batches) * (size_t)J * 4; };
 
@@ -1072,7 +1091,7 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
             qdev = reinterpret_cast<const float *>(vw.stage(b, J));
         }
         // the fit reduces over queries: no permutation back to the caller's order
-        e = sort_into(vw, grid->R, qdev, J, 4, vw.sorted(), nullptr, s);
+        e = sort_into(vw, grid->R, qdev, J, 4, vw.sorted(), nullptr, s, gmax);
         if (e == cudaSuccess && q_host) e = cudaEventRecord(pipe->freed[b], s);   // staging buffer consumed
         if (e == cudaSuccess) e = pack_keys(vw, grid, params, s);
         if (e != cudaSuccess) return cuda_fail();
@@ -1082,6 +1101,7 @@ efunc_status efunc_fit(const efunc_grid *grid, const efunc_adam *adam, int32_t l
         f.inv_J = (float)(1.0 / (double)J);
         f.eik_weight = eikonal_weight;
         e = launch_fused_fit(f, eikonal_weight > 0.f, grid_blocks, s);
+        if (e == cudaSuccess && gmax) e = launch_grouped(f, BatchArgs{}, vw.items() + vw.L.max_items - 1, false, s);
         if (e != cudaSuccess) return cuda_fail();
         AdamArgs a = adam_args(adam, n, params, grad, m, v, step0 + it + 1);
         a.ctrl = vw.ctrl();
@@ -1365,10 +1385,11 @@ bool shapes_ok(const efunc_shape *shapes, int32_t S)
 bool tuning_ok(const efunc_tuning &t)
 {
     return t.chunk >= kMinChunk && t.chunk <= kChunk && t.lanes4_max >= 0 && t.lanes4_max <= t.lanes2_max &&
-           t.lanes2_max <= kChunk && t.sort_blocks >= 1 && t.sort_blocks <= 16;
+           t.lanes2_max <= kChunk && t.sort_blocks >= 1 && t.sort_blocks <= 16 && t.group_max >= 0 &&
+           t.group_max <= kChunk;
 }
 
-efunc_tuning default_tuning() { return efunc_tuning{kChunk, 64, 32, 8}; }
+efunc_tuning default_tuning() { return efunc_tuning{kChunk, 64, 32, 8, kGroupMax}; }
 
 // Layout of a batched fit's workspace: control block (with the Adam clock
 // at +128), shape table, per-shape loss sums, the sort of one batch of all
@@ -1451,6 +1472,8 @@ struct BatchedRun {
         a.shapes = table();
         a.S = S;
         a.chunk = tune.chunk;
+        a.group_max = tune.group_max;
+        a.gtop = a.items + L->max_items - 1;
         if ((e = launch_sort_batched(a, s, tune.sort_blocks)) != cudaSuccess) return e;
         BatchedPackArgs pk{params, keys(), table(), S, L->centres};
         if ((e = launch_pack_keys_batched(pk, s)) != cudaSuccess) return e;
@@ -1462,7 +1485,8 @@ struct BatchedRun {
         f.grad = grad();
         f.loss = loss;
         BatchArgs b{table(), sums(), tune.lanes2_max, tune.lanes4_max};
-        return launch_fused_batched(f, b, eval, fused_batched_grid_size(), s);
+        if ((e = launch_fused_batched(f, b, eval, fused_batched_grid_size(), s)) != cudaSuccess) return e;
+        return tune.group_max ? launch_grouped(f, b, a.gtop, eval, s) : cudaSuccess;
     }
 
     cudaError_t step(const efunc_adam *adam, int32_t loss, float *params, float *m, float *v, const float *q,
@@ -1645,11 +1669,13 @@ efunc_status efunc_tune_batched(const efunc_shape *shapes, int32_t S, int32_t lo
     efunc_status rc = EFUNC_OK;
     const int chunks[] = {128, 256};
     const int lanes[][2] = {{64, 32}, {96, 48}};
-    const int sorts[] = {2, 4, 8};
+    const int sorts[] = {4, 8};
+    const int groups[] = {0, 64, 128};
     for (int c : chunks)
         for (const auto &ln : lanes)
-            for (int sb : sorts) {
-                BatchedRun run{&L, static_cast<char *>(workspace), S, efunc_tuning{c, ln[0], ln[1], sb}};
+            for (int sb : sorts)
+                for (int gm : groups) {
+                BatchedRun run{&L, static_cast<char *>(workspace), S, efunc_tuning{c, ln[0], ln[1], sb, gm}};
                 // one untimed step, then trial_steps timed
                 if ((rc = fit_batched(run, &frozen, loss, params, m, v, qo, n_batches, 1, 0, nullptr, false, s)))
                     goto done;

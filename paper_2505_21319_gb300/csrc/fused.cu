@@ -874,6 +874,382 @@ cudaError_t launch_eval_finish(const Ctrl *ctrl, double inv_J, float *out, cudaS
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ grouped items
+//
+// A grouped item is an aligned 2x2x2 octet of window-base cells holding few
+// queries (the sort groups sparse octets).  The union of the octet's
+// windows, at most 5x5x5 centres, is staged once; every query blends its own
+// 4x4x4 sub-window (the same keys, in the same order and summation classes
+// as the generic path of fused_kernel); the backward runs thread per key
+// over the item's queries and counts a key only for the queries whose
+// window holds it.  Compared with one item per cell, the window is staged
+// and each key's gradient is added once per octet instead of once per cell.
+
+namespace {
+
+constexpr int kGU = 5;                      // union window per axis
+constexpr int kGCentres = kGU * kGU * kGU;  // 125
+
+struct GroupWin {
+    int c0x, c0y, c0z;      // window base of the octet's first cell
+    int lox, loy, loz;      // first centre of the union window
+    int nx, ny, nz, nc;     // its extent (clipped to the grid)
+};
+
+__device__ __forceinline__ GroupWin group_window(const Item item, int R)
+{
+    GroupWin g;
+    g.c0x = (item.z & 1023) - 1;
+    g.c0y = ((item.z >> 10) & 1023) - 1;
+    g.c0z = ((item.z >> 20) & 1023) - 1;
+    g.lox = max(g.c0x - 1, 0);
+    g.loy = max(g.c0y - 1, 0);
+    g.loz = max(g.c0z - 1, 0);
+    g.nx = min(g.c0x + 3, R - 1) - g.lox + 1;
+    g.ny = min(g.c0y + 3, R - 1) - g.loy + 1;
+    g.nz = min(g.c0z + 3, R - 1) - g.loz + 1;
+    g.nc = g.nx * g.ny * g.nz;
+    return g;
+}
+
+// (e, m) of one query over its own window inside the staged union: axis
+// ranges [w0, w0 + wn) of the union's centre indices, keys in the order of
+// fwd_sums (set outer, then x, y, z with z fastest), class of key k = k mod 4.
+// A full window (4 along y and z) is walked row by row without divisions.
+template <int KQ>
+__device__ __forceinline__ void grp_fwd_sums(const float4 *rec, const GroupWin &g, int w0x, int w0y, int w0z,
+                                             int wnx, int wny, int wnz, int part, float x, float y, float z, float M2,
+                                             float &e, float &m)
+{
+    constexpr int CPL = kClasses / KQ;
+    float ev[CPL], mv[CPL];
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) ev[i] = mv[i] = 0.f;
+    const int nq = wnx * wny * wnz;
+    const int cbase = (w0x * g.ny + w0y) * g.nz + w0z;
+    if (wny == 4 && wnz == 4) {
+#pragma unroll
+        for (int set = 0; set < 2; ++set) {
+            for (int base = 0; base < nq; base += kClasses) {
+                const int r = base >> 2;   // row (kx, ky) = (r >> 2, r & 3)
+                const int row = cbase + (r >> 2) * (g.ny * g.nz) + (r & 3) * g.nz;
+#pragma unroll
+                for (int i = 0; i < CPL; ++i) {
+                    const int c = row + part + KQ * i;
+                    fwd_key(keyA(rec, set, c), keyB(rec, set, c), x, y, z, M2, ev[i], mv[i]);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int set = 0; set < 2; ++set) {
+            for (int base = 0; base < nq; base += kClasses) {
+#pragma unroll
+                for (int i = 0; i < CPL; ++i) {
+                    const int k = base + part + KQ * i;
+                    if (k < nq) {
+                        const int kz = k % wnz, ky = (k / wnz) % wny, kx = k / (wny * wnz);
+                        const int c = ((w0x + kx) * g.ny + (w0y + ky)) * g.nz + (w0z + kz);
+                        fwd_key(keyA(rec, set, c), keyB(rec, set, c), x, y, z, M2, ev[i], mv[i]);
+                    }
+                }
+            }
+        }
+    }
+    e = combine_classes<KQ>(ev);
+    m = combine_classes<KQ>(mv);
+}
+
+template <int MODE, int KQ, bool BATCHED>
+__device__ __forceinline__ void grp_forward(const FusedArgs &ai, const float4 *rec, float4 *qt, float2 *og,
+                                            const unsigned char *qoff, const GroupWin &g, int n, int R, float h,
+                                            float3 orig, float &loss_acc, float &abs_acc)
+{
+    constexpr int LG = KQ == 1 ? 0 : (KQ == 2 ? 1 : 2);
+    const int t = threadIdx.x;
+    const int part = t & (KQ - 1);
+    for (int base = 0; base < n; base += kThreads / KQ) {
+        const int qi = base + (t >> LG);
+        const bool valid = qi < n;
+        float4 q = valid ? qt[qi] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int off = valid ? qoff[qi] : 0;
+        // the query's window base c = c0 + offset (sub-cell id ox << 2 | oy << 1
+        // | oz), its window [c - 1, c + 2] clipped to the grid, relative to
+        // the union's first centre
+        const int cx = g.c0x + ((off >> 2) & 1), cy = g.c0y + ((off >> 1) & 1), cz = g.c0z + (off & 1);
+        const int w0x = max(cx - 1, 0) - g.lox, w0y = max(cy - 1, 0) - g.loy, w0z = max(cz - 1, 0) - g.loz;
+        const int wnx = min(cx + 2, R - 1) - g.lox - w0x + 1, wny = min(cy + 2, R - 1) - g.loy - w0y + 1,
+                  wnz = min(cz + 2, R - 1) - g.loz - w0z + 1;
+        if (valid) {
+            q.x -= orig.x;
+            q.y -= orig.y;
+            q.z -= orig.z;
+        } else {
+            q.x = q.y = q.z = 0.5f * h;
+        }
+        float e, m;
+        grp_fwd_sums<KQ>(rec, g, w0x, w0y, w0z, wnx, wny, wnz, part, q.x, q.y, q.z, 0.f, e, m);
+        float M2 = 0.f;
+        const bool tiny = !(e >= 0x1p-60f);
+        if (__any_sync(kFull, tiny)) {
+            float mx = -INFINITY;
+            const int nq = wnx * wny * wnz;
+            for (int k = part; k < nq; k += KQ) {
+                const int kz = k % wnz, ky = (k / wnz) % wny, kx = k / (wny * wnz);
+                const int c = ((w0x + kx) * g.ny + (w0y + ky)) * g.nz + (w0z + kz);
+                mx = fmaxf(mx, key_exponent(keyA(rec, 0, c), q.x, q.y, q.z));
+                mx = fmaxf(mx, key_exponent(keyA(rec, 1, c), q.x, q.y, q.z));
+            }
+#pragma unroll
+            for (int o = 1; o < KQ; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+            float e2, m2;
+            grp_fwd_sums<KQ>(rec, g, w0x, w0y, w0z, wnx, wny, wnz, part, q.x, q.y, q.z, mx, e2, m2);
+            if (tiny) {
+                e = e2;
+                m = m2;
+                M2 = mx;
+            }
+        }
+        const float O = m / e, lse2 = M2 + lg2_approx(e);
+        const float diff = O - q.w;
+        float gO = 0.f;
+        if (MODE == FIT) {
+            if (ai.loss == EFUNC_LOSS_L1) gO = diff > 0.f ? ai.inv_J : (diff < 0.f ? -ai.inv_J : 0.f);
+            else gO = 2.f * diff * ai.inv_J;
+            if (valid && part == 0) {
+                loss_acc += ai.loss == EFUNC_LOSS_L1 ? fabsf(diff) : diff * diff;
+                abs_acc += fabsf(diff);
+            }
+        } else if (valid && part == 0) {
+            loss_acc += diff * diff;
+            abs_acc += fabsf(diff);
+        }
+        if (MODE == FIT) {
+            __syncwarp();
+            if (valid && part == 0) {
+                qt[qi] = make_float4(q.x, q.y, q.z, lse2);
+                og[qi] = make_float2(O, gO);
+            }
+        }
+    }
+}
+
+// Key order of the backward for an interior octet (a 5x5x5 union): centres
+// sorted by the set of sub-cells whose window holds them (per axis: index 0
+// only for sub-cell offset 0, 1..3 for both, 4 only for offset 1), so that
+// the lanes of a warp mostly walk the same query ranges.
+__constant__ unsigned char c_group_order[kGCentres];
+
+__device__ __forceinline__ int axis_class(int k) { return k == 0 ? 0 : (k == 4 ? 2 : 1); }
+
+template <int MODE, bool BATCHED>
+__global__ void __launch_bounds__(kThreads, 8) grouped_kernel(FusedArgs a, BatchArgs b, const Item *gtop)
+{
+    __shared__ float4 s_rec[kGCentres * kKeyRecords];
+    __shared__ float4 s_qt[kChunk];
+    __shared__ float2 s_og[kChunk];
+    __shared__ unsigned char s_off[kChunk];
+    __shared__ int s_beg[9];          // query range of sub-cell o: [s_beg[o], s_beg[o + 1])
+    __shared__ int s_item[2];
+    __shared__ float s_red[2][kThreads / 32];
+    const int t = threadIdx.x;
+    const int n_groups = a.ctrl->n_groups;
+    float loss_acc = 0.f, abs_acc = 0.f;
+    if (t == 0) s_item[0] = atomicAdd(&a.ctrl->next_group, 1);
+    int cur = 0;
+
+    for (;;) {
+        __syncthreads();   // the previous item is consumed; s_item[cur] is visible
+        const int gi = s_item[cur];
+        if (gi >= n_groups) break;
+        if (t == 0) s_item[cur ^ 1] = atomicAdd(&a.ctrl->next_group, 1);   // the next item, fetched early
+        if (t < 9) s_beg[t] = 0;
+        const Item item = gtop[-gi];
+        FusedArgs ai = a;
+        int R = a.R;
+        if (BATCHED) {
+            const BatchShape sh = b.shapes[item.w];
+            R = sh.R;
+            ai.keys = a.keys + sh.c_off * kKeyRecords;
+            ai.grad = a.grad + sh.c_off * kSlots;
+            ai.inv_J = sh.inv_J;
+        }
+        const float invR = 1.f / (float)R, h = 2.f * invR;
+        const float half_r = (float)R * 0.5f, rmax = (float)(R - 1);
+        const GroupWin g = group_window(item, R);
+        const int start = item.x, n = item.y;
+        const float3 orig = make_float3((float)(2 * g.c0x + 1 - R) * invR, (float)(2 * g.c0y + 1 - R) * invR,
+                                        (float)(2 * g.c0z + 1 - R) * invR);
+        __syncthreads();   // s_beg cleared
+        // ---- stage the union window's key records (window-local) and the queries
+        if (t < g.nc) {
+            const int oz = t % g.nz, oy = (t / g.nz) % g.ny, ox = t / (g.ny * g.nz);
+            const float4 *k = ai.keys + (((size_t)(g.lox + ox) * R + (g.loy + oy)) * R + (g.loz + oz)) * kKeyRecords;
+            const float gx = (float)(2 * (g.lox + ox - g.c0x)) * invR, gy = (float)(2 * (g.loy + oy - g.c0y)) * invR,
+                        gz = (float)(2 * (g.loz + oz - g.c0z)) * invR;
+            const float4 kg = k[0], ko = k[2];
+            float4 *r = s_rec + 4 * t;
+            r[0] = make_float4(gx, gy, gz, kg.w);
+            r[1] = k[1];
+            r[2] = make_float4(gx + ko.x, gy + ko.y, gz + ko.z, ko.w);
+            r[3] = k[3];
+        }
+        for (int qi = t; qi < n; qi += kThreads) {
+            const float4 q = a.sorted[start + qi];
+            const int cx = window_base(q.x, half_r, rmax), cy = window_base(q.y, half_r, rmax),
+                      cz = window_base(q.z, half_r, rmax);
+            const int o = ((cx - g.c0x) << 2) | ((cy - g.c0y) << 1) | (cz - g.c0z);
+            s_qt[qi] = q;
+            s_off[qi] = (unsigned char)o;
+            atomicAdd(&s_beg[o + 1], 1);
+        }
+        __syncthreads();
+        if (t == 0)
+            for (int o = 1; o <= 8; ++o) s_beg[o] += s_beg[o - 1];   // the queries are sorted by sub-cell
+        // ---- forward
+        if (n > 64) grp_forward<MODE, 1, BATCHED>(ai, s_rec, s_qt, s_og, s_off, g, n, R, h, orig, loss_acc, abs_acc);
+        else if (n > 32) grp_forward<MODE, 2, BATCHED>(ai, s_rec, s_qt, s_og, s_off, g, n, R, h, orig, loss_acc, abs_acc);
+        else grp_forward<MODE, 4, BATCHED>(ai, s_rec, s_qt, s_og, s_off, g, n, R, h, orig, loss_acc, abs_acc);
+        if (MODE == FIT) {
+            // ---- backward: keys t and t + 128 of the 2 nc keys (grid keys
+            // first), each over the sub-cells whose window holds it
+            __syncthreads();
+            const bool interior = g.nc == kGCentres;
+            for (int kid = t; kid < 2 * g.nc; kid += kThreads) {
+                const bool offset = kid >= g.nc;
+                const int slot = offset ? kid - g.nc : kid;
+                const int c = interior ? c_group_order[slot] : slot;
+                const int oz = c % g.nz, oy = (c / g.nz) % g.ny, ox = c / (g.ny * g.nz);
+                // centre index relative to the octet's base: in the window of
+                // sub-cell offset o iff o - 1 <= k <= o + 2 per axis
+                const int kx = g.lox + ox - g.c0x, ky = g.loy + oy - g.c0y, kz = g.loz + oz - g.c0z;
+                const float4 A = keyA(s_rec, offset, c), B = keyB(s_rec, offset, c);
+                float ag = 0.f, arx = 0.f, ary = 0.f, arz = 0.f, ab = 0.f, adx = 0.f, ady = 0.f, adz = 0.f;
+                bool any = false;
+                for (int o = 0; o < 8; ++o) {
+                    const int px = (o >> 2) & 1, py = (o >> 1) & 1, pz = o & 1;
+                    if (kx < px - 1 || kx > px + 2 || ky < py - 1 || ky > py + 2 || kz < pz - 1 || kz > pz + 2)
+                        continue;
+                    const int j1 = s_beg[o + 1];
+                    for (int j = s_beg[o]; j < j1; ++j) {
+                        any = true;
+                        const float4 Q = s_qt[j];
+                        const float2 S = s_og[j];
+                        const float rx = Q.x - A.x, ry = Q.y - A.y, rz = Q.z - A.z;
+                        const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                        const float w = ex2_approx(fmaf(A.w, d2, -Q.w));
+                        const float gw = w * S.y;
+                        const float f = fmaf(B.y, rx, fmaf(B.z, ry, fmaf(B.w, rz, B.x)));
+                        const float gd = gw * (f - S.x);
+                        ag += gw;
+                        arx = fmaf(gw, rx, arx);
+                        ary = fmaf(gw, ry, ary);
+                        arz = fmaf(gw, rz, arz);
+                        ab = fmaf(gd, d2, ab);
+                        adx = fmaf(gd, rx, adx);
+                        ady = fmaf(gd, ry, ady);
+                        adz = fmaf(gd, rz, adz);
+                    }
+                }
+                if (!any) continue;
+                float *gr = ai.grad + (((size_t)(g.lox + ox) * R + (g.loy + oy)) * R + (g.loz + oz)) * kSlots;
+                const float beta = -A.w * Num<float>::kLn2;
+                if (!offset) {
+                    atomicAdd(gr + 5, ag);
+                    atomicAdd(gr + 6, arx);
+                    atomicAdd(gr + 7, ary);
+                    atomicAdd(gr + 8, arz);
+                    atomicAdd(gr + 3, -beta * ab);
+                } else {
+                    atomicAdd(gr + 9, ag);
+                    atomicAdd(gr + 10, arx);
+                    atomicAdd(gr + 11, ary);
+                    atomicAdd(gr + 12, arz);
+                    atomicAdd(gr + 4, -beta * ab);
+                    const float tb = 2.f * beta;
+                    atomicAdd(gr + 0, fmaf(-B.y, ag, tb * adx));
+                    atomicAdd(gr + 1, fmaf(-B.z, ag, tb * ady));
+                    atomicAdd(gr + 2, fmaf(-B.w, ag, tb * adz));
+                }
+            }
+        }
+        if (BATCHED) {
+            for (int o = 16; o > 0; o >>= 1) {
+                loss_acc += __shfl_xor_sync(kFull, loss_acc, o);
+                abs_acc += __shfl_xor_sync(kFull, abs_acc, o);
+            }
+            if ((t & 31) == 0 && (loss_acc != 0.f || abs_acc != 0.f)) {
+                atomicAdd(b.shape_sums + 2 * item.w, (double)loss_acc);
+                atomicAdd(b.shape_sums + 2 * item.w + 1, (double)abs_acc);
+            }
+            loss_acc = abs_acc = 0.f;
+        }
+        cur ^= 1;
+    }
+    if (!BATCHED) {
+        for (int o = 16; o > 0; o >>= 1) {
+            loss_acc += __shfl_xor_sync(kFull, loss_acc, o);
+            abs_acc += __shfl_xor_sync(kFull, abs_acc, o);
+        }
+        if ((t & 31) == 0) {
+            s_red[0][t >> 5] = loss_acc;
+            s_red[1][t >> 5] = abs_acc;
+        }
+        __syncthreads();
+        if (t == 0) {
+            double l = 0.0, ab = 0.0;
+            for (int wi = 0; wi < kThreads / 32; ++wi) {
+                l += s_red[0][wi];
+                ab += s_red[1][wi];
+            }
+            atomicAdd(&a.ctrl->loss_sum, l);
+            atomicAdd(&a.ctrl->abs_sum, ab);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_grouped(const FusedArgs &a, const BatchArgs &b, const Item *gtop, bool eval, cudaStream_t s)
+{
+    const bool batched = b.shapes != nullptr;
+    // the interior key order, once per device
+    cudaError_t te = cudaSuccess;
+    per_device_cached(reinterpret_cast<const void *>(&c_group_order), 0, [&te] {
+        unsigned char order[kGCentres];
+        int n = 0;
+        for (int cls = 0; cls < 27; ++cls)
+            for (int c = 0; c < kGCentres; ++c) {
+                const int z = c % kGU, y = (c / kGU) % kGU, x = c / (kGU * kGU);
+                const auto ac = [](int k) { return k == 0 ? 0 : (k == 4 ? 2 : 1); };
+                if ((ac(x) * 3 + ac(y)) * 3 + ac(z) == cls) order[n++] = (unsigned char)c;
+            }
+        te = cudaMemcpyToSymbol(c_group_order, order, sizeof(order));
+        return te == cudaSuccess ? 1 : 0;
+    });
+    if (te != cudaSuccess) return te;
+    const void *k = batched ? (eval ? reinterpret_cast<const void *>(grouped_kernel<EVAL, true>)
+                                    : reinterpret_cast<const void *>(grouped_kernel<FIT, true>))
+                            : (eval ? reinterpret_cast<const void *>(grouped_kernel<EVAL, false>)
+                                    : reinterpret_cast<const void *>(grouped_kernel<FIT, false>));
+    const int grid = per_device_cached(k, 0, [k] {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, 0);
+        if (per_sm <= 0) per_sm = 1;
+        return sm_count() * per_sm;
+    });
+    launch_begin(K_GROUPED, s);
+    if (batched) {
+        if (eval) grouped_kernel<EVAL, true><<<grid, kThreads, 0, s>>>(a, b, gtop);
+        else grouped_kernel<FIT, true><<<grid, kThreads, 0, s>>>(a, b, gtop);
+    } else {
+        if (eval) grouped_kernel<EVAL, false><<<grid, kThreads, 0, s>>>(a, b, gtop);
+        else grouped_kernel<FIT, false><<<grid, kThreads, 0, s>>>(a, b, gtop);
+    }
+    launch_end(K_GROUPED, s);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ batched fit
 
 namespace {

@@ -288,6 +288,150 @@ __global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) scatter_kernel(S
     }
 }
 
+// Index of the last offset <= x among S ascending offsets (offs[0] = 0).
+__device__ __forceinline__ int shape_of(const int64_t *offs, int S, int64_t x)
+{
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (offs[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <bool BY_BIN>
+__device__ __forceinline__ void load_offsets(const SortArgs &a, int64_t *s_off)
+{
+    for (int i = threadIdx.x; i < a.S; i += blockDim.x) s_off[i] = BY_BIN ? a.shapes[i].bin_off : a.shapes[i].q_off;
+    __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t batched_bin(const BatchShape &sh, float x, float y, float z)
+{
+    return (uint32_t)query_bin(x, y, z, (float)sh.R * 0.5f, (float)(sh.R - 1), sh.P);
+}
+
+__device__ __forceinline__ unsigned long long pack_chunk(uint32_t count, uint32_t chunk)
+{
+    unsigned long long items = (count + chunk - 1) / chunk;
+    return (items << 32) | (unsigned long long)count;
+}
+
+// ------------------------------------------------- grouped scan (sparse cells)
+//
+// The same scan over 8 bins per thread (64 threads per 512-bin segment), so
+// that a thread holds one aligned octet of bins: a 2x2x2 block of cells.  An
+// octet with at least two non-empty cells and at most group_max queries is
+// emitted as one grouped item (appended at the top of the item array) and
+// counts no per-cell item; every other octet emits its cells' items as
+// usual.  The bins' offsets are the same either way (an octet's queries are
+// contiguous).
+constexpr int kOct = 8;
+constexpr int kGrpThreads = kScanSeg / kOct;
+
+template <bool BATCHED>
+__device__ __forceinline__ uint32_t scan_chunk(const SortArgs &a) { return BATCHED ? (uint32_t)a.chunk : (uint32_t)kChunk; }
+
+__device__ __forceinline__ bool octet_grouped(const uint32_t cnt[kOct], int group_max)
+{
+    uint32_t tot = 0;
+    int nonempty = 0;
+#pragma unroll
+    for (int k = 0; k < kOct; ++k) {
+        tot += cnt[k];
+        nonempty += cnt[k] > 0u;
+    }
+    return nonempty >= 2 && tot <= (uint32_t)group_max;
+}
+
+template <int K, bool BATCHED>
+__device__ __forceinline__ unsigned long long octet_value(const SortArgs &a, int64_t b0, uint32_t cnt[kOct])
+{
+#pragma unroll
+    for (int k = 0; k < kOct; ++k) cnt[k] = b0 + k < a.nbins ? bin_count<K>(a, b0 + k) : 0u;
+    const uint32_t chunk = scan_chunk<BATCHED>(a);
+    unsigned long long v = 0;
+    if (octet_grouped(cnt, a.group_max)) {
+#pragma unroll
+        for (int k = 0; k < kOct; ++k) v += cnt[k];   // queries only, no per-cell item
+    } else {
+#pragma unroll
+        for (int k = 0; k < kOct; ++k) v += pack_chunk(cnt[k], chunk);
+    }
+    return v;
+}
+
+template <int K, bool BATCHED>
+__global__ void __launch_bounds__(kGrpThreads) scan_reduce_grp_kernel(SortArgs a)
+{
+    uint32_t cnt[kOct];
+    const unsigned long long v = octet_value<K, BATCHED>(a, (int64_t)blockIdx.x * kScanSeg + threadIdx.x * kOct, cnt);
+    unsigned long long total;
+    block_exclusive_scan(v, total);
+    if (threadIdx.x == 0) a.blocksum[blockIdx.x] = total;
+}
+
+template <int K, bool BATCHED>
+__global__ void __launch_bounds__(kGrpThreads) scan_emit_grp_kernel(SortArgs a)
+{
+    __shared__ int64_t s_off[BATCHED ? kMaxShapes : 1];
+    if (BATCHED) load_offsets<true>(a, s_off);
+    const int64_t b0 = (int64_t)blockIdx.x * kScanSeg + threadIdx.x * kOct;
+    uint32_t cnt[kOct];
+    const unsigned long long v = octet_value<K, BATCHED>(a, b0, cnt);
+    unsigned long long total;
+    unsigned long long run = a.blocksum[blockIdx.x] + block_exclusive_scan(v, total);
+    if (b0 >= a.nbins) return;
+    const bool grouped = octet_grouped(cnt, a.group_max);
+    const uint32_t chunk = scan_chunk<BATCHED>(a);
+    int shape = 0, P = a.P;
+    int64_t local0 = b0;
+    if (BATCHED) {
+        shape = shape_of(s_off, a.S, b0);
+        P = a.shapes[shape].P;
+        local0 = b0 - s_off[shape];
+    }
+    if (grouped) {
+        int ux, uy, uz;
+        cell_of_bin((uint32_t)local0, P, ux, uy, uz);   // the octet's first cell: even coordinates
+        uint32_t tot = 0;
+#pragma unroll
+        for (int k = 0; k < kOct; ++k) tot += cnt[k];
+        const int g = atomicAdd(&a.ctrl->n_groups, 1);
+        a.gtop[-g] = make_int4((int)(run & 0xffffffffull), (int)tot, ux | (uy << 10) | (uz << 20), shape);
+    }
+#pragma unroll
+    for (int k = 0; k < kOct; ++k) {
+        if (b0 + k >= a.nbins) break;
+        const uint32_t start = (uint32_t)(run & 0xffffffffull);
+        const uint32_t item0 = (uint32_t)(run >> 32);
+        if (K == 1) {
+            a.hist[b0 + k] = start;
+        } else {
+            uint32_t off = start;
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                const uint32_t n = a.hist[c * a.nbins + b0 + k];
+                a.hist[c * a.nbins + b0 + k] = off;
+                off += n;
+            }
+        }
+        if (!grouped && cnt[k]) {
+            int ux, uy, uz;
+            cell_of_bin((uint32_t)(local0 + k), P, ux, uy, uz);
+            const int packed = ux | (uy << 10) | (uz << 20);
+            const uint32_t nit = (cnt[k] + chunk - 1) / chunk;
+            for (uint32_t i = 0; i < nit; ++i) {
+                const uint32_t off = i * chunk;
+                const uint32_t len = min(chunk, cnt[k] - off);
+                a.items[item0 + i] = make_int4((int)(start + off), (int)len, packed, shape);
+            }
+        }
+        run += grouped ? (unsigned long long)cnt[k] : pack_chunk(cnt[k], chunk);
+    }
+}
+
 int stream_grid(int64_t work, int threads, int blocks_per_sm)
 {
     const int sms = device_sm_count();
@@ -324,7 +468,8 @@ cudaError_t launch_sort_k(const SortArgs &a, cudaStream_t s, int narrow_blocks)
     launch_end(K_BIN, s);
 
     launch_begin(K_SCAN_REDUCE, s);
-    scan_reduce_kernel<K><<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
+    if (a.group_max > 0) scan_reduce_grp_kernel<K, false><<<(unsigned)nblocks, kGrpThreads, 0, s>>>(a);
+    else scan_reduce_kernel<K><<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
     launch_end(K_SCAN_REDUCE, s);
 
     launch_begin(K_SCAN_TOP, s);
@@ -332,7 +477,8 @@ cudaError_t launch_sort_k(const SortArgs &a, cudaStream_t s, int narrow_blocks)
     launch_end(K_SCAN_TOP, s);
 
     launch_begin(K_SCAN_EMIT, s);
-    scan_emit_kernel<K><<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
+    if (a.group_max > 0) scan_emit_grp_kernel<K, false><<<(unsigned)nblocks, kGrpThreads, 0, s>>>(a);
+    else scan_emit_kernel<K><<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
     launch_end(K_SCAN_EMIT, s);
 
     launch_begin(K_SCATTER, s);
@@ -350,30 +496,6 @@ cudaError_t launch_sort_k(const SortArgs &a, cudaStream_t s, int narrow_blocks)
 // bins of one shape are contiguous and every work item lies in one shape
 // (Item.w).  Work items hold at most a.chunk queries (a tuning knob).
 
-// Index of the last offset <= x among S ascending offsets (offs[0] = 0).
-__device__ __forceinline__ int shape_of(const int64_t *offs, int S, int64_t x)
-{
-    int lo = 0, hi = S - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (offs[mid] <= x) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-template <bool BY_BIN>
-__device__ __forceinline__ void load_offsets(const SortArgs &a, int64_t *s_off)
-{
-    for (int i = threadIdx.x; i < a.S; i += blockDim.x) s_off[i] = BY_BIN ? a.shapes[i].bin_off : a.shapes[i].q_off;
-    __syncthreads();
-}
-
-__device__ __forceinline__ uint32_t batched_bin(const BatchShape &sh, float x, float y, float z)
-{
-    return (uint32_t)query_bin(x, y, z, (float)sh.R * 0.5f, (float)(sh.R - 1), sh.P);
-}
-
 __global__ void __launch_bounds__(kWideThreads) bin_batched_kernel(SortArgs a)
 {
     __shared__ int64_t s_off[kMaxShapes];
@@ -384,12 +506,6 @@ __global__ void __launch_bounds__(kWideThreads) bin_batched_kernel(SortArgs a)
         const float4 v = __ldg(reinterpret_cast<const float4 *>(a.q) + j);
         a.rank[j] = atomicAdd(&a.hist[sh.bin_off + batched_bin(sh, v.x, v.y, v.z)], 1u);
     }
-}
-
-__device__ __forceinline__ unsigned long long pack_chunk(uint32_t count, uint32_t chunk)
-{
-    unsigned long long items = (count + chunk - 1) / chunk;
-    return (items << 32) | (unsigned long long)count;
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_batched_kernel(SortArgs a)
@@ -464,13 +580,15 @@ cudaError_t launch_sort_batched(const SortArgs &a, cudaStream_t s, int blocks_pe
     bin_batched_kernel<<<g, kWideThreads, 0, s>>>(a);
     launch_end(K_BIN, s);
     launch_begin(K_SCAN_REDUCE, s);
-    scan_reduce_batched_kernel<<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
+    if (a.group_max > 0) scan_reduce_grp_kernel<1, true><<<(unsigned)nblocks, kGrpThreads, 0, s>>>(a);
+    else scan_reduce_batched_kernel<<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
     launch_end(K_SCAN_REDUCE, s);
     launch_begin(K_SCAN_TOP, s);
     scan_top_kernel<<<1, kScanThreads, 0, s>>>(a, nblocks);
     launch_end(K_SCAN_TOP, s);
     launch_begin(K_SCAN_EMIT, s);
-    scan_emit_batched_kernel<<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
+    if (a.group_max > 0) scan_emit_grp_kernel<1, true><<<(unsigned)nblocks, kGrpThreads, 0, s>>>(a);
+    else scan_emit_batched_kernel<<<(unsigned)nblocks, kScanThreads, 0, s>>>(a);
     launch_end(K_SCAN_EMIT, s);
     launch_begin(K_SCATTER, s);
     scatter_batched_kernel<<<g, kWideThreads, 0, s>>>(a);

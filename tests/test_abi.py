@@ -242,7 +242,7 @@ def test_batched_helpers(lib):
     assert lib.efunc_batched_param_count(sh, 1025) == -1
     t = B.Tuning()
     lib.efunc_default_tuning(ctypes.byref(t))
-    assert (t.chunk, t.lanes2_max, t.lanes4_max, t.sort_blocks) == (256, 64, 32, 8)
+    assert (t.chunk, t.lanes2_max, t.lanes4_max, t.sort_blocks, t.group_max) == (256, 64, 32, 8, 128)
 
 
 @fake_pointers
@@ -268,6 +268,7 @@ def test_batched_validation_enqueues_nothing(lib):
     assert call(tuning=ctypes.byref(B.Tuning(16, 64, 32, 8))) == 1    # chunk below 32
     assert call(tuning=ctypes.byref(B.Tuning(256, 32, 64, 8))) == 1   # lanes4 > lanes2
     assert call(tuning=ctypes.byref(B.Tuning(256, 64, 32, 0))) == 1   # no sort blocks
+    assert call(tuning=ctypes.byref(B.Tuning(256, 64, 32, 8, 300))) == 1   # octets above an item's capacity
     assert call(wsb=ws - 256) == 3
     assert call(ws=(1 << 30) + 64) == 3
     assert call(steps=0) == 0

@@ -323,10 +323,12 @@ def _margin_targets(p, qo, R, seed):
 
 
 @pytest.mark.parametrize("loss", ["l1", "mse"])
-@pytest.mark.parametrize("R,J", [(4, 5000), (16, 65536)])
+@pytest.mark.parametrize("R,J", [(4, 5000), (16, 65536), (32, 1 << 18)])
 def test_fused_fit_gradient_and_loss(R, J, loss):
     """One fused step with lr = 0 exposes the gradient through Adam's first
-    moment (m = (1 - beta1) g); stats hold the loss and MAE of the step."""
+    moment (m = (1 - beta1) g); stats hold the loss and MAE of the step.  At
+    32^3 x 2^18 (about 6 queries per bin) the fit groups its sparse cell
+    octets into the grouped kernel's items."""
     p = params_of("sdf", R, R)
     qo = _margin_targets(p, mixed_queries(R, J, seed=R), R, seed=1)
     n = p.size
