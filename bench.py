@@ -79,8 +79,13 @@ TARGET_MAE = 1e-3
 TARGET_CHUNK = 50
 # batched fit: shapes fitted together
 BATCH_SHAPES = 256
-# learned warm start: encoder batch (shapes per step)
+# learned warm start: encoder batch (shapes per step); multiply-adds per
+# voxel of one training step's tensor-core convolutions at the real channel
+# counts: forward L2 27*32*64, L3 27*64*128, L4 128*13; the same again for
+# the weight gradients and for the input gradients
 WARM_BATCH = 16
+ENC_MACS_PER_VOXEL = 3 * (27 * 32 * 64 + 27 * 64 * 128 + 128 * 13)
+ENC_PROFILE_STEPS = 5
 # FP32-pipe operations of one (centre, point) pair of the mean-shift
 # initialisation: 3 differences, 3 for the squared norm, 1 scale, 1 compare,
 # 1 exponent difference, 1 add to Z, 3 FMAs into S (the ex2 runs on the MUFU)
@@ -444,6 +449,35 @@ def bench_warm_start(dev, rank, n_train, n_eval, train_steps, epochs, eval_steps
     tp, fit_s = W.fit_plain(train, J=1 << 16, steps=train_steps, seed=11, device=dev)
     sdf = W.sdf_grids(train, dev)
     w, losses, enc_s = W.train_encoder(sdf, tp, epochs=epochs, batch=WARM_BATCH, lr=1e-3, seed=rank)
+    # the tensor-core convolutions of a training step against the bf16 peak:
+    # algorithmic flops (real channel counts; the kernels pad L2's 32 input
+    # channels to 64) over their CUDA-event time
+    from paper_2505_21319_gb300 import api
+    enc = api.Encoder(WARM_BATCH, dev)
+    idx = torch.arange(WARM_BATCH, device=dev)
+    sd, tg = sdf[idx].contiguous(), tp[idx].contiguous()
+    for _ in range(3):
+        enc.train_step(w, sd, tg)
+    torch.cuda.synchronize(dev)
+    api.profile_reset()
+    api.profile(True)
+    for _ in range(ENC_PROFILE_STEPS):
+        enc.train_step(w, sd, tg)
+    torch.cuda.synchronize(dev)
+    api.profile(False)
+    conv_ms = sum(api.profile_read(k)[0] for k in ("enc_conv", "enc_wgrad")) / ENC_PROFILE_STEPS
+    aux_ms = api.profile_read("enc_aux")[0] / ENC_PROFILE_STEPS
+    V = WARM_BATCH * 32 ** 3
+    flops = 2.0 * V * ENC_MACS_PER_VOXEL
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        bf16_peak, peak_from = float(peaks["bf16_tflops"]), "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError):
+        bf16_peak, peak_from = 1900.0, "fallback 1.9 PFLOP/s bf16"
+    enc_roof = {"bound": "tensor", "achieved": flops / (conv_ms * 1e-3) / 1e12, "peak": bf16_peak,
+                "unit": "TFLOP/s", "frac": flops / (conv_ms * 1e-3) / 1e12 / bf16_peak, "peak_from": peak_from,
+                "flops_per_step": flops, "tc_ms_per_step": conv_ms, "other_ms_per_step": aux_ms,
+                "batch": WARM_BATCH, "kernels": "conv_fwd_kernel (forward, dgrad) + conv_wgrad_kernel"}
     ev = W.random_shapes(300000 + 10000 * rank, n_eval)
     held = W.heldout_rows(ev, 1 << 15, seed=99, device=dev)
     pred, pred_s = W.predict(w, W.sdf_grids(ev, dev), batch=WARM_BATCH)
@@ -458,7 +492,7 @@ def bench_warm_start(dev, rank, n_train, n_eval, train_steps, epochs, eval_steps
            "encoder_train_s": enc_s, "encoder_loss_first": losses[0], "encoder_loss_last": losses[-1],
            "eval_shapes": n_eval, "eval_steps": eval_steps, "predict_s": pred_s,
            "target_rule": "per shape: 1e-3, or the plain fit's final held-out MAE where 1e-3 is not reached",
-           "shapes_reaching_1e-3_plain": int((mae_p.min(0) <= 1e-3).sum())}
+           "shapes_reaching_1e-3_plain": int((mae_p.min(0) <= 1e-3).sum()), "encoder_roofline": enc_roof}
     for name, (st, mae, sec) in arms.items():
         steps = W.steps_to(st, mae, target)
         reached = np.isfinite(steps)

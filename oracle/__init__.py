@@ -52,6 +52,7 @@ def _configure(lib):
     lib.ora_forward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp, dp, dp]
     lib.ora_backward.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
     lib.ora_forward_err_terms.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
+    lib.ora_backward_err_terms.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
     lib.ora_forward_global.argtypes = [i32, f64, dp, dp, i64, i32, dp, dp]
     lib.ora_backward_grad.argtypes = [i32, i32, f64, dp, dp, i64, i32, dp, dp, dp]
     lib.ora_mean_shift.argtypes = [i32, f64, dp, i64, dp]
@@ -63,7 +64,7 @@ def _configure(lib):
     lib.ora_cosine_backward.argtypes = [i32, i32, f64, i32, dp, dp, i64, i32, dp, dp]
     lib.ora_loss_grad.argtypes = [i32, dp, dp, i64, dp, dp, dp]
     lib.ora_adam.argtypes = [i64, dp, dp, dp, dp, i64, f64, f64, f64, f64, f64, i32]
-    for fn in ("ora_forward", "ora_forward_err_terms", "ora_backward", "ora_forward_global", "ora_loss_grad", "ora_adam",
+    for fn in ("ora_forward", "ora_forward_err_terms", "ora_backward_err_terms", "ora_backward", "ora_forward_global", "ora_loss_grad", "ora_adam",
                "ora_backward_grad", "ora_mean_shift", "ora_variant_forward", "ora_variant_backward",
                "ora_cosine_forward", "ora_cosine_backward"):
         getattr(lib, fn).restype = None
@@ -211,6 +212,23 @@ def backward(params, q, gO, R: int, W: int = 2, log_beta0: float | None = None, 
     _load().ora_backward(R, W, lb, _ptr(params), _ptr(q), J, q.shape[1], _ptr(gO), _ptr(grad), _ptr(gq))
     grad = grad.reshape(R ** 3, NSLOT)
     return (grad, gq) if want_gq else grad
+
+
+def backward_error_terms(params, q, gO, R: int, W: int = 2, log_beta0: float | None = None):
+    """(abs0, abs1), (R^3, 13) each: per gradient entry of Algorithm 2 the sum
+    of its terms' magnitudes, and the same weighted by (|exponent| + 1) of
+    each term's key (the relative error of its weight).  A gradient entry
+    whose terms cancel is rounded in proportion to these, not to its value:
+    diagnostics for the FP32 tolerance of the gradients."""
+    lb = default_log_beta0(R) if log_beta0 is None else float(log_beta0)
+    params, q = _check(params, q, R)
+    gO = _f64(gO).reshape(-1)
+    if gO.size != q.shape[0]:
+        raise ValueError("gO must have J entries")
+    a0, a1 = np.zeros(R ** 3 * NSLOT), np.zeros(R ** 3 * NSLOT)
+    _load().ora_backward_err_terms(R, W, lb, _ptr(params), _ptr(q), q.shape[0], q.shape[1], _ptr(gO), _ptr(a0),
+                                   _ptr(a1))
+    return a0.reshape(R ** 3, NSLOT), a1.reshape(R ** 3, NSLOT)
 
 
 def backward_grad(params, q, gO, gG, R: int, W: int = 2, log_beta0: float | None = None):

@@ -338,6 +338,58 @@ void ora_backward(int R, int W, double log_beta0, const double *params, const do
     }
 }
 
+/* Error terms of Algorithm 2's gradients for their floating-point
+ * tolerance.  Every gradient entry is a sum over queries and keys of terms
+ * t = dL/dO_j * softmax * (a slot's factor); where the terms cancel the sum
+ * is small against them, so its rounding is bounded by the terms'
+ * magnitudes, not by the sum:
+ *   abs0[i, s] = sum |t|                         (rounding of the products and sums)
+ *   abs1[i, s] = sum |t| * (|expo| + 1)          (relative error of the weight)
+ * with every factor taken term by term in magnitude: o: 1, d: |q - p|,
+ * b: beta ||q - p||^2 |f - O|, Delta: |d| + 2 beta |q - p| |f - O|.
+ * abs0, abs1: R^3 * 13 doubles each, ACCUMULATED into. */
+void ora_backward_err_terms(int R, int W, double log_beta0, const double *params, const double *q, int64_t J,
+                            int q_stride, const double *gO, double *abs0, double *abs1)
+{
+    for (int64_t j = 0; j < J; ++j) {
+        const double *qj = q + j * q_stride;
+        double O, lse;
+        forward_one(params, R, W, log_beta0, qj, &O, &lse, NULL, NULL, NULL);
+        int lo[3], hi[3];
+        window_range(qj, R, W, lo, hi);
+        double r[3], d2, expo, f;
+        for (int a = lo[0]; a <= hi[0]; ++a)
+            for (int b = lo[1]; b <= hi[1]; ++b)
+                for (int c = lo[2]; c <= hi[2]; ++c)
+                    for (int s = 0; s < 2; ++s) {
+                        key_t_ k = make_key(params, R, log_beta0, a, b, c, s);
+                        eval_key(&k, qj, r, &d2, &expo, &f);
+                        const double gl = fabs(gO[j]) * exp(expo - lse);
+                        const double we = fabs(expo) + 1.0;
+                        const size_t base = ((size_t)((size_t)a * R + b) * R + c) * NSLOT;
+                        double t[NSLOT];
+                        int slots[8], ns = 0;
+                        const int so = s == 0 ? 5 : 9, sb = s == 0 ? 3 : 4;
+                        t[so] = gl;
+                        t[so + 1] = gl * fabs(r[0]);
+                        t[so + 2] = gl * fabs(r[1]);
+                        t[so + 3] = gl * fabs(r[2]);
+                        t[sb] = gl * k.beta * d2 * fabs(f - O);
+                        slots[ns++] = so; slots[ns++] = so + 1; slots[ns++] = so + 2; slots[ns++] = so + 3;
+                        slots[ns++] = sb;
+                        if (s == 1)
+                            for (int x = 0; x < 3; ++x) {
+                                t[x] = gl * (fabs(k.d[x]) + 2.0 * k.beta * fabs(r[x]) * fabs(f - O));
+                                slots[ns++] = x;
+                            }
+                        for (int i = 0; i < ns; ++i) {
+                            abs0[base + slots[i]] += t[slots[i]];
+                            abs1[base + slots[i]] += t[slots[i]] * we;
+                        }
+                    }
+    }
+}
+
 /* ------------------------------------------- backward through dO/dq */
 
 /* Gradient of L = sum_j [ gO_j O(q_j) + gG_j . G(q_j) ] with respect to the

@@ -137,6 +137,12 @@ MUTANTS = {
     "tolerance diagnostic: kappa_G with the key term's 2 dropped": (
         "const double gx = k.d[x] + 2.0 * k.beta * r[x] * (O - f) - G[x];",
         "const double gx = k.d[x] + k.beta * r[x] * (O - f) - G[x];"),
+    "tolerance diagnostic: gradient error terms without |f - O| in the Delta term": (
+        "t[x] = gl * (fabs(k.d[x]) + 2.0 * k.beta * fabs(r[x]) * fabs(f - O));",
+        "t[x] = gl * (fabs(k.d[x]) + 2.0 * k.beta * fabs(r[x]));"),
+    "tolerance diagnostic: gradient error terms weighted by |exponent| only": (
+        "const double we = fabs(expo) + 1.0;",
+        "const double we = fabs(expo);"),
     "tolerance diagnostic: variant fabs as |f| instead of its terms": (
         "fa += fabs(k.phi[i] * fu);",
         "fa += k.phi[i] * fu;"),

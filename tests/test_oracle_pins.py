@@ -783,6 +783,42 @@ def test_dq_error_terms_are_attained_and_bound_random_perturbations():
             assert np.linalg.norm(moved) >= eps * gab[j] / np.sqrt(3) * (1 - 1e-9) - 1e-15
 
 
+def test_backward_error_terms_bound_the_gradient_and_are_attained_by_one_query():
+    """abs0, the magnitudes of every gradient entry's terms, bounds |grad|
+    entry by entry (triangle inequality) and equals it where a single query
+    contributes terms of one sign (its o and o' entries: dL/dO times a
+    weight); abs1 weighs each term by (|exponent| + 1) >= 1 of its key."""
+    R, lb = 3, 2.0
+    p = synth.random_params(R, seed=93, delta_scale=0.6, b_scale=0.6).astype(np.float64)
+    q = queries(94, 40)
+    gO = synth.rng(95).standard_normal(q.shape[0])
+    g = oracle.backward(p, q, gO, R, W=R, log_beta0=lb)
+    a0, a1 = oracle.backward_error_terms(p, q, gO, R, W=R, log_beta0=lb)
+    assert np.all(np.abs(g) <= a0 * (1 + 1e-12) + 1e-300)
+    assert np.all(a1 >= a0 * (1 - 1e-12))
+    for j in range(3):
+        gj = oracle.backward(p, q[j:j + 1], gO[j:j + 1], R, W=R, log_beta0=lb)
+        b0, b1 = oracle.backward_error_terms(p, q[j:j + 1], gO[j:j + 1], R, W=R, log_beta0=lb)
+        for slot in (5, 9):
+            np.testing.assert_allclose(b0[:, slot], np.abs(gj[:, slot]), rtol=1e-12, atol=1e-300)
+        # the (|exponent| + 1) weight of one query's o entries: the key's own exponent
+        O, lse = oracle.forward(p, q[j:j + 1], R, W=R, log_beta0=lb)
+        pos, beta, o, d = keys_of(p, R, lb)
+        expo = -beta * ((q[j] - pos) ** 2).sum(1)
+        ng = R ** 3
+        np.testing.assert_allclose(b1[:, 5], b0[:, 5] * (np.abs(expo[:ng]) + 1), rtol=1e-12, atol=1e-300)
+        # the Delta entries: |-d + 2 beta (q - p)(f - O)| equals its bound
+        # |d| + 2 beta |q - p| |f - O| where the two parts share a sign
+        r = q[j] - pos[ng:]
+        f = o[ng:] + (d[ng:] * r).sum(1)
+        part1 = -d[ng:]
+        part2 = 2.0 * beta[ng:, None] * r * (f - O[0])[:, None]
+        same = np.sign(part1) == np.sign(part2)
+        assert same.any() and (~same).any()
+        np.testing.assert_allclose(b0[:, 0:3][same], np.abs(gj[:, 0:3][same]), rtol=1e-10, atol=1e-300)
+        assert np.all(b0[:, 0:3][~same] > np.abs(gj[:, 0:3][~same]))
+
+
 def test_dq_sensitivity_is_the_norm_of_the_lse_gradient():
     """dq_sens = 2 ||sum softmax beta (q - key)||, the factor by which an
     error in O enters dO/dq, equals ||grad_q lse|| (lse = log sum
