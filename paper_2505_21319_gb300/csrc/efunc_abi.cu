@@ -8,6 +8,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "adam_clock.cuh"
 #include "common.cuh"
 #include "sort_copies.cuh"
@@ -80,8 +82,14 @@ int drain_pending()
 
 }  // namespace
 
+// Every launch is also an NVTX range named after its kernel (a no-op unless
+// a tool such as ncu --nvtx is attached), so that profiles can select the
+// sort, the key pack, the fused kernels and Adam by name.
+static_assert(sizeof(kKernelNames) / sizeof(kKernelNames[0]) == K_COUNT, "one name per kernel id");
+
 void launch_begin(int kid, cudaStream_t s)
 {
+    nvtxRangePushA(kKernelNames[kid]);
     if (g_in_capture) {
         ++g_captured;
         return;
@@ -96,6 +104,7 @@ void launch_begin(int kid, cudaStream_t s)
 
 void launch_end(int kid, cudaStream_t s)
 {
+    nvtxRangePop();
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on || g_in_capture || g_pending.empty() || g_pending.back().kid != kid || g_pending.back().stop)
         return;

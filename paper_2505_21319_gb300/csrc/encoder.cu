@@ -637,27 +637,21 @@ cudaError_t enc_conv(const bf16 *x, int batch, int cin, const bf16 *w, int N, in
     a.mask = mask;
     a.out = out;
     a.err = err;
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
+    switch (N) {   // the kernels' dynamic shared-memory limits, before the launch
+    case 16: e = set_smem(conv_fwd_kernel<16>, conv_smem_bytes<16>()); break;
+    case 32: e = set_smem(conv_fwd_kernel<32>, conv_smem_bytes<32>()); break;
+    case 64: e = set_smem(conv_fwd_kernel<64>, conv_smem_bytes<64>()); break;
+    case 128: e = set_smem(conv_fwd_kernel<128>, conv_smem_bytes<128>()); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
     launch_begin(K_ENC_CONV, s);
     switch (N) {
-    case 16:
-        if ((e = set_smem(conv_fwd_kernel<16>, conv_smem_bytes<16>())) != cudaSuccess) return e;
-        conv_fwd_kernel<16><<<a.n_tiles, 128, conv_smem_bytes<16>(), s>>>(ma, mb, a);
-        break;
-    case 32:
-        if ((e = set_smem(conv_fwd_kernel<32>, conv_smem_bytes<32>())) != cudaSuccess) return e;
-        conv_fwd_kernel<32><<<a.n_tiles, 128, conv_smem_bytes<32>(), s>>>(ma, mb, a);
-        break;
-    case 64:
-        if ((e = set_smem(conv_fwd_kernel<64>, conv_smem_bytes<64>())) != cudaSuccess) return e;
-        conv_fwd_kernel<64><<<a.n_tiles, 128, conv_smem_bytes<64>(), s>>>(ma, mb, a);
-        break;
-    case 128:
-        if ((e = set_smem(conv_fwd_kernel<128>, conv_smem_bytes<128>())) != cudaSuccess) return e;
-        conv_fwd_kernel<128><<<a.n_tiles, 128, conv_smem_bytes<128>(), s>>>(ma, mb, a);
-        break;
-    default:
-        return cudaErrorInvalidValue;
+    case 16: conv_fwd_kernel<16><<<a.n_tiles, 128, conv_smem_bytes<16>(), s>>>(ma, mb, a); break;
+    case 32: conv_fwd_kernel<32><<<a.n_tiles, 128, conv_smem_bytes<32>(), s>>>(ma, mb, a); break;
+    case 64: conv_fwd_kernel<64><<<a.n_tiles, 128, conv_smem_bytes<64>(), s>>>(ma, mb, a); break;
+    default: conv_fwd_kernel<128><<<a.n_tiles, 128, conv_smem_bytes<128>(), s>>>(ma, mb, a); break;
     }
     launch_end(K_ENC_CONV, s);
     return cudaGetLastError();
@@ -679,10 +673,21 @@ cudaError_t enc_wgrad(const bf16 *dy, int dy_ld, int cout, const bf16 *x, int ci
     a.cin = cin;
     a.dw = dw;
     a.err = err;
-    // split the voxel tiles so that the grid fills the GPU about twice
-    const int cells = taps * a.cin_chunks;
-    int split = (2 * device_sm_count() + cells - 1) / cells;
-    split = max(1, min(split, a.n_tiles));
+    // split the voxel tiles so that the grid fills the GPU at least twice
+    // (one CTA per SM fits) with the last wave as full as possible
+    const int cells = taps * a.cin_chunks, sms = device_sm_count();
+    const int split0 = max(1, min((2 * sms + cells - 1) / cells, a.n_tiles));
+    int split = split0;
+    double best = 0.0;
+    for (int sp = split0; sp <= min(4 * split0, a.n_tiles); ++sp) {
+        const int per = (a.n_tiles + sp - 1) / sp, eff = (a.n_tiles + per - 1) / per;
+        const int ctas = cells * eff, waves = (ctas + sms - 1) / sms;
+        const double fill = (double)ctas / ((double)waves * sms);
+        if (fill > best + 1e-9) {
+            best = fill;
+            split = eff;
+        }
+    }
     a.tiles_per_cta = (a.n_tiles + split - 1) / split;
     split = (a.n_tiles + a.tiles_per_cta - 1) / a.tiles_per_cta;
     cudaError_t e = set_smem(conv_wgrad_kernel, kWgradSmem);
