@@ -31,6 +31,8 @@
 // runs the same kernels (same staging, windows, summation classes and
 // branches) with exp2 / log2 in double, so that finite differences of the
 // FP64 results check the very code the FP32 path runs.
+#include <type_traits>
+
 #include "adam_clock.cuh"
 #include "common.cuh"
 
@@ -479,18 +481,257 @@ __device__ __forceinline__ void bwd2_key_loop(const float4 A, const float4 B, co
     acc[13] = px; acc[14] = py; acc[15] = pz; acc[16] = qx; acc[17] = qy; acc[18] = qz;
 }
 
+// ------------------------------------------ packed FP32 (f32x2) forms
+//
+// The SMs of this GPU issue two FP32 operations per f32x2 instruction (each
+// half rounds exactly as the scalar instruction; the FMA pipe's rate is the
+// same, the issue slots are halved).  The FP32 kernels are issue bound, so
+// their forward blends two keys per instruction (summation classes j and
+// j + 2 of one query) and their backward two queries per instruction (one
+// key).  Every operation is written with its rounding (_rn, no contraction).
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long r, x, y;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 ex2_2(float2 a) { return make_float2(ex2_approx(a.x), ex2_approx(a.y)); }
+
+// Paired key tile (FP32): pair p = 2 r + j of set s (0 grid keys, 1 offset
+// keys) interleaves keys 4 r + j and 4 r + j + 2 of the window, classes j
+// and j + 2:
+//   P[0] = (x, x', y, y')   P[1] = (z, z', -beta log2 e, ...')
+//   P[2] = (o, o', dx, dx') P[3] = (dy, dy', dz, dz')
+// at rec2 + 4 (32 s + p), positions window-local.  Keys from the window's
+// last centre up to a multiple of 4 are neutral (position 1e18, scale -1,
+// values 0): their weight is exactly 0 and they add exact zeros.
+constexpr int kPairs = kCentres / 2;
+
+__device__ __forceinline__ const float4 *pair_of(const float4 *rec2, int set, int p)
+{
+    return rec2 + 4 * (kPairs * set + p);
+}
+
+__device__ __forceinline__ float *pair_slot(float4 *rec2, int set, int k)
+{
+    return reinterpret_cast<float *>(rec2 + 4 * (kPairs * set + 2 * (k >> 2) + (k & 1))) + ((k >> 1) & 1);
+}
+
+__device__ __forceinline__ void stage_pair_key(float4 *rec2, int set, int k, float4 A, float4 B)
+{
+    float *f = pair_slot(rec2, set, k);
+    f[0] = A.x; f[2] = A.y; f[4] = A.z; f[6] = A.w;
+    f[8] = B.x; f[10] = B.y; f[12] = B.z; f[14] = B.w;
+}
+
+__device__ __forceinline__ float4 pair_keyA(const float4 *rec2, int set, int k)
+{
+    const float *f = pair_slot(const_cast<float4 *>(rec2), set, k);
+    return make_float4(f[0], f[2], f[4], f[6]);
+}
+
+// Per-lane sums -> (e or m) of the query in the fixed order ((c0 + c1) +
+// (c2 + c3)) of combine_classes.  KQ = 1: v[0] = (c0, c2), v[1] = (c1, c3);
+// KQ = 2: lane `part` holds (c_part, c_part+2); KQ = 4: lanes `part` and
+// `part ^ 2` blend the same pair, lane `part` keeps class `part`.
+template <int KQ>
+__device__ __forceinline__ float combine_x2(const float2 *v, int part)
+{
+    if (KQ == 1) return (v[0].x + v[1].x) + (v[0].y + v[1].y);
+    if (KQ == 2) {
+        const float lo = v[0].x + __shfl_xor_sync(kFull, v[0].x, 1);
+        const float hi = v[0].y + __shfl_xor_sync(kFull, v[0].y, 1);
+        return lo + hi;
+    }
+    const float c = (part & 2) ? v[0].y : v[0].x;
+    const float s1 = c + __shfl_xor_sync(kFull, c, 1);
+    return s1 + __shfl_xor_sync(kFull, s1, 2);
+}
+
+// Two keys of one pair for a query at (x, y, z) (duplicated in both halves):
+// the generic key form of fwd_key, exponent shifted by nm = -M2.
+__device__ __forceinline__ void fwd_pair(const float4 *P, float2 xd, float2 yd, float2 zd, float2 nm, float2 &ev,
+                                         float2 &mv)
+{
+    const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3];
+    const float2 rx = sub2(xd, lo2(P0)), ry = sub2(yd, hi2(P0)), rz = sub2(zd, lo2(P1));
+    const float2 d2 = fma2(rx, rx, fma2(ry, ry, mul2(rz, rz)));
+    const float2 l = ex2_2(fma2(hi2(P1), d2, nm));
+    const float2 f = fma2(hi2(P2), rx, fma2(lo2(P3), ry, fma2(hi2(P3), rz, lo2(P2))));
+    ev = add2(ev, l);
+    mv = fma2(l, f, mv);
+}
+
+// (e, m) of one query over a window of nc keys per set from the paired tile
+// (any window shape; the shifted recomputation after an underflow).
+template <int KQ>
+__device__ __forceinline__ void fwd_sums_x2(const float4 *rec2, int nc, int part, float x, float y, float z,
+                                            float nM2, float &e, float &m)
+{
+    constexpr int NP = KQ == 1 ? 2 : 1;   // pairs per lane and row
+    const int j0 = KQ == 1 ? 0 : (part & 1);
+    float2 ev[NP], mv[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) ev[i] = mv[i] = make_float2(0.f, 0.f);
+    const float2 xd = dup2(x), yd = dup2(y), zd = dup2(z), nm = dup2(nM2);
+    const int rows = (nc + 3) >> 2;
+#pragma unroll
+    for (int set = 0; set < 2; ++set)
+        for (int r = 0; r < rows; ++r)
+#pragma unroll
+            for (int i = 0; i < NP; ++i) fwd_pair(pair_of(rec2, set, 2 * r + j0 + i), xd, yd, zd, nm, ev[i], mv[i]);
+    e = combine_x2<KQ>(ev, part);
+    m = combine_x2<KQ>(mv, part);
+}
+
+// Full window (nc = 64): grid keys on the lattice, d2 = (rx^2 + ry^2) + rz^2
+// formed per row and pair without their positions (as fwd_sums_full); offset
+// keys in the generic form.
+template <int KQ>
+__device__ __forceinline__ void fwd_sums_full_x2(const float4 *rec2, int part, float h, float x, float y, float z,
+                                                 float &e, float &m)
+{
+    constexpr int NP = KQ == 1 ? 2 : 1;
+    const int j0 = KQ == 1 ? 0 : (part & 1);
+    float2 ev[NP], mv[NP], rz[NP], ry[4], y2[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        ry[a] = dup2(__fsub_rn(y, (float)(a - 1) * h));
+        y2[a] = mul2(ry[a], ry[a]);
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        const int j = j0 + i;
+        rz[i] = make_float2(__fsub_rn(z, (float)(j - 1) * h), __fsub_rn(z, (float)(j + 1) * h));
+        ev[i] = mv[i] = make_float2(0.f, 0.f);
+    }
+#pragma unroll 1
+    for (int ox = 0; ox < 4; ++ox) {
+        const float2 rx = dup2(__fsub_rn(x, (float)(ox - 1) * h));
+#pragma unroll
+        for (int oy = 0; oy < 4; ++oy) {
+            const float2 xy = fma2(rx, rx, y2[oy]);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const float4 *P = pair_of(rec2, 0, 2 * (4 * ox + oy) + j0 + i);
+                const float4 P1 = P[1], P2 = P[2], P3 = P[3];
+                const float2 l = ex2_2(mul2(hi2(P1), fma2(rz[i], rz[i], xy)));
+                const float2 f = fma2(hi2(P2), rx, fma2(lo2(P3), ry[oy], fma2(hi2(P3), rz[i], lo2(P2))));
+                ev[i] = add2(ev[i], l);
+                mv[i] = fma2(l, f, mv[i]);
+            }
+        }
+    }
+    const float2 xd = dup2(x), yd = dup2(y), zd = dup2(z), nm = dup2(-0.f);
+#pragma unroll 1
+    for (int r0 = 0; r0 < kCentres / 4; r0 += 4)
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+            for (int i = 0; i < NP; ++i)
+                fwd_pair(pair_of(rec2, 1, 2 * (r0 + rr) + j0 + i), xd, yd, zd, nm, ev[i], mv[i]);
+    e = combine_x2<KQ>(ev, part);
+    m = combine_x2<KQ>(mv, part);
+}
+
+// Forward of one query from the paired tile (as forward_query).
+template <int KQ, bool FULL>
+__device__ __forceinline__ FwdOut<float> forward_query_x2(const float4 *rec2, int nc, int part, float h, float4 q)
+{
+    float e, m;
+    if (FULL) fwd_sums_full_x2<KQ>(rec2, part, h, q.x, q.y, q.z, e, m);
+    else fwd_sums_x2<KQ>(rec2, nc, part, q.x, q.y, q.z, -0.f, e, m);
+    float M2 = 0.f;
+    const bool tiny = !(e >= 0x1p-60f);
+    if (__any_sync(kFull, tiny)) {
+        float mx = -INFINITY;
+        for (int k = part; k < nc; k += KQ) {
+            mx = fmaxf(mx, key_exponent(pair_keyA(rec2, 0, k), q.x, q.y, q.z));
+            mx = fmaxf(mx, key_exponent(pair_keyA(rec2, 1, k), q.x, q.y, q.z));
+        }
+#pragma unroll
+        for (int o = 1; o < KQ; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+        float e2, m2;
+        fwd_sums_x2<KQ>(rec2, nc, part, q.x, q.y, q.z, -mx, e2, m2);
+        if (tiny) {
+            e = e2;
+            m = m2;
+            M2 = mx;
+        }
+    }
+    return {m / e, M2 + lg2_approx(e)};
+}
+
+// Paired query rows of the backward: pair jp = queries 2 jp, 2 jp + 1 at
+// sq2 + 3 jp,
+//   [0] = (x, x', y, y')  [1] = (z, z', -lse2, -lse2')  [2] = (-O, -O', gO, gO')
+// (window-local positions); an odd count is padded with a copy of the last
+// query carrying dL/dO = 0.
+__device__ __forceinline__ void store_pair_query(float4 *sq2, int qi, float4 q, float lse2, float O, float gO)
+{
+    float *f = reinterpret_cast<float *>(sq2 + 3 * (qi >> 1)) + (qi & 1);
+    f[0] = q.x; f[2] = q.y; f[4] = q.z; f[6] = -lse2; f[8] = -O; f[10] = gO;
+}
+
+// Thread-per-key loop of the backward, two queries per instruction: the sums
+// of bwd_key_loop over the even and the odd queries, added at the end.
+template <bool OFFSET>
+__device__ __forceinline__ void bwd_key_loop_x2(const float4 A, const float4 B, const float4 *__restrict__ sq2,
+                                                int pairs, float acc[8])
+{
+    const float2 ax = dup2(A.x), ay = dup2(A.y), az = dup2(A.z), nbl = dup2(A.w);
+    const float2 bo = dup2(B.x), bx = dup2(B.y), by = dup2(B.z), bz = dup2(B.w);
+    const float2 z2 = make_float2(0.f, 0.f);
+    float2 ag = z2, arx = z2, ary = z2, arz = z2, ab = z2, adx = z2, ady = z2, adz = z2;
+#pragma unroll 2
+    for (int jp = 0; jp < pairs; ++jp) {
+        const float4 Q0 = sq2[3 * jp], Q1 = sq2[3 * jp + 1], S = sq2[3 * jp + 2];
+        const float2 rx = sub2(lo2(Q0), ax), ry = sub2(hi2(Q0), ay), rz = sub2(lo2(Q1), az);
+        const float2 d2 = fma2(rx, rx, fma2(ry, ry, mul2(rz, rz)));
+        const float2 w = ex2_2(fma2(nbl, d2, hi2(Q1)));
+        const float2 g = mul2(w, hi2(S));
+        const float2 f = fma2(bx, rx, fma2(by, ry, fma2(bz, rz, bo)));
+        const float2 gd = mul2(g, add2(f, lo2(S)));
+        ag = add2(ag, g);
+        arx = fma2(g, rx, arx);
+        ary = fma2(g, ry, ary);
+        arz = fma2(g, rz, arz);
+        ab = fma2(gd, d2, ab);
+        if (OFFSET) {
+            adx = fma2(gd, rx, adx);
+            ady = fma2(gd, ry, ady);
+            adz = fma2(gd, rz, adz);
+        }
+    }
+    acc[0] = ag.x + ag.y; acc[1] = arx.x + arx.y; acc[2] = ary.x + ary.y; acc[3] = arz.x + arz.y;
+    acc[4] = ab.x + ab.y; acc[5] = adx.x + adx.y; acc[6] = ady.x + ady.y; acc[7] = adz.x + adz.y;
+}
+
 // ------------------------------------------------------------- kernel
 
 // Forward over the item's queries.  qt holds the raw query tile (x, y, z,
 // target); a query's row is rewritten in place with (local position, lse2)
 // by the lane that owns it, after every lane of its group has read it.
 template <int MODE, bool DQ, bool GEIK, int KQ, bool FULL, typename T>
-__device__ __forceinline__ void forward_phase(const FusedArgsT<T> &a, const V4Of<T> *rec, V4Of<T> *qt,
-                                              V4Of<T> *sqB, float4 *sqE, float4 *sqU, int start, int n, int nc,
-                                              V4Of<T> orig, T h, T &loss_acc, T &abs_acc)
+__device__ __forceinline__ void forward_phase(const FusedArgsT<T> &a, const V4Of<T> *rec, const float4 *rec2,
+                                              V4Of<T> *qt, V4Of<T> *sqB, float4 *sq2, float4 *sqE, float4 *sqU,
+                                              int start, int n, int nc, V4Of<T> orig, T h, T &loss_acc, T &abs_acc)
 {
     using N = Num<T>;
     using V = V4Of<T>;
+    constexpr bool PAIRS = std::is_same<T, float>::value;   // packed FP32 forward
+    constexpr bool PAIRQ = PAIRS && !GEIK;                 // packed FP32 backward
     constexpr int LG = KQ == 1 ? 0 : (KQ == 2 ? 1 : 2);
     const int t = threadIdx.x;
     const int part = t & (KQ - 1);
@@ -510,7 +751,9 @@ __device__ __forceinline__ void forward_phase(const FusedArgsT<T> &a, const V4Of
             // lanes without a query evaluate the window centre (never stored)
             q = N::v4(T(0.5) * h, T(0.5) * h, T(0.5) * h, T(0));
         }
-        const FwdOut<T> r = forward_query<KQ, FULL>(rec, nc, part, h, q);
+        FwdOut<T> r;
+        if constexpr (PAIRS) r = forward_query_x2<KQ, FULL>(rec2, nc, part, h, q);
+        else r = forward_query<KQ, FULL>(rec, nc, part, h, q);
         const T O = r.O, lse2 = r.lse2;
 
         T gO = T(0);
@@ -570,7 +813,12 @@ __device__ __forceinline__ void forward_phase(const FusedArgsT<T> &a, const V4Of
                 sqU[qi] = make_float4(u0, u1, u2, 0.f);
             }
         }
-        if (MODE == BACKWARD || MODE == FIT) {
+        if constexpr (PAIRQ && (MODE == BACKWARD || MODE == FIT)) {
+            if (valid && part == 0) {
+                store_pair_query(sq2, qi, q, lse2, O, gO);
+                if (qi == n - 1 && (n & 1)) store_pair_query(sq2, n, q, lse2, O, 0.f);
+            }
+        } else if (MODE == BACKWARD || MODE == FIT) {
             __syncwarp();   // every lane of the group has read its row of qt
             if (valid && part == 0) {
                 const V qa = N::v4(q.x, q.y, q.z, lse2);
@@ -586,42 +834,57 @@ __device__ __forceinline__ void forward_phase(const FusedArgsT<T> &a, const V4Of
     }
 }
 
-// Resident CTAs per SM asked of the compiler: FP32 fits leave room for the
-// sort beside them; the second-order and FP64 kernels need more registers.
+// Resident CTAs per SM asked of the compiler: the FP32 kernels run 8 CTAs
+// of 64 registers (7 beside a block of the next batch's sort in the
+// pipelined fit); the second-order and FP64 kernels need more registers.
 template <bool GEIK, typename T>
-constexpr int min_ctas() { return sizeof(T) == 8 ? 2 : (GEIK ? 5 : 9); }
+constexpr int min_ctas() { return sizeof(T) == 8 ? 2 : (GEIK ? 5 : 8); }
 
 // One work item: stage, forward, backward.  ai carries the item's grid
 // (R, key records, gradient, 1/J): the kernel's own arguments, or in a
 // batched launch those of the item's shape.
 template <int MODE, bool DQ, bool GEIK, typename T, bool BATCHED>
 __device__ __forceinline__ void item_body(const FusedArgsT<T> &a, const FusedArgsT<T> &ai, const BatchArgs &b, const Item item,
-                                          const int R, const T invR, const T h, V4Of<T> *rec, V4Of<T> *qt,
-                                          V4Of<T> *qB, float4 *s_sqE, float4 *s_sqU, T &loss_acc, T &abs_acc)
+                                          const int R, const T invR, const T h, V4Of<T> *rec, float4 *rec2,
+                                          float4 *keyT, V4Of<T> *qt, V4Of<T> *qB, float4 *sq2, float4 *s_sqE,
+                                          float4 *s_sqU, T &loss_acc, T &abs_acc)
 {
     using N = Num<T>;
     using V = V4Of<T>;
     constexpr bool BWD = MODE == BACKWARD || MODE == FIT;
+    constexpr bool PAIRS = std::is_same<T, float>::value;   // paired key tile, packed forward
+    constexpr bool NEED_REC = !PAIRS || DQ || GEIK;        // the per-key tile (dO/dq sums, FP64)
+    constexpr bool PAIRQ = PAIRS && !GEIK;                 // paired query rows, packed backward
     const int t = threadIdx.x;
     const Window w = window_of(item, R);
     const int start = item.x, n = item.y, nc = w.nc;
     const bool full = nc == kCentres;
     const V orig = N::v4((T)(2 * w.cx + 1 - R) * invR, (T)(2 * w.cy + 1 - R) * invR,
                          (T)(2 * w.cz + 1 - R) * invR, T(0));
-    // ---- 1. stage the key records (positions made window-local) and queries
-    if (t < nc) {
+    // ---- 1. stage the key records (positions made window-local) and
+    // queries: thread t stages key t (set t / 64 of centre t mod 64)
+    const int kc = t & (kCentres - 1), kset = t / kCentres;
+    if (kc < nc) {
         int ox, oy, oz;
-        if (full) { ox = t >> 4; oy = (t >> 2) & 3; oz = t & 3; }
-        else { oz = t % w.nz; oy = (t / w.nz) % w.ny; ox = t / (w.ny * w.nz); }
+        if (full) { ox = kc >> 4; oy = (kc >> 2) & 3; oz = kc & 3; }
+        else { oz = kc % w.nz; oy = (kc / w.nz) % w.ny; ox = kc / (w.ny * w.nz); }
         const V *k = ai.keys + (((size_t)(w.lox + ox) * R + (w.loy + oy)) * R + (w.loz + oz)) * kKeyRecords;
         const T gx = (T)(2 * (w.lox + ox - w.cx)) * invR, gy = (T)(2 * (w.loy + oy - w.cy)) * invR,
                 gz = (T)(2 * (w.loz + oz - w.cz)) * invR;
-        const V g = k[0], o = k[2];
-        V *r = rec + 4 * t;
-        r[0] = N::v4(gx, gy, gz, g.w);
-        r[1] = k[1];
-        r[2] = N::v4(gx + o.x, gy + o.y, gz + o.z, o.w);
-        r[3] = k[3];
+        const V p = k[2 * kset], B = k[2 * kset + 1];
+        const V A = kset ? N::v4(gx + p.x, gy + p.y, gz + p.z, p.w) : N::v4(gx, gy, gz, p.w);
+        if constexpr (NEED_REC) {
+            rec[4 * kc + 2 * kset] = A;
+            rec[4 * kc + 2 * kset + 1] = B;
+        }
+        if constexpr (PAIRS) {
+            stage_pair_key(rec2, kset, kc, A, B);
+            keyT[2 * t] = A;
+            keyT[2 * t + 1] = B;
+        }
+    } else if (PAIRS && kc < ((nc + 3) & ~3)) {
+        // neutral keys up to a multiple of 4
+        stage_pair_key(rec2, kset, kc, make_float4(1e18f, 1e18f, 1e18f, -1.f), make_float4(0.f, 0.f, 0.f, 0.f));
     }
     for (int qi = t; qi < n; qi += kThreads) qt[qi] = a.sorted[start + qi];
     __syncthreads();
@@ -629,13 +892,13 @@ __device__ __forceinline__ void item_body(const FusedArgsT<T> &a, const FusedArg
     // ---- 2. forward, one (or 2 / 4) threads per query
     const int l2 = BATCHED ? b.lanes2_max : 64, l4 = BATCHED ? b.lanes4_max : 32;
     if (full) {
-        if (n > l2) forward_phase<MODE, DQ, GEIK, 1, true>(ai, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
-        else if (n > l4) forward_phase<MODE, DQ, GEIK, 2, true>(ai, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
-        else forward_phase<MODE, DQ, GEIK, 4, true>(ai, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+        if (n > l2) forward_phase<MODE, DQ, GEIK, 1, true>(ai, rec, rec2, qt, qB, sq2, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+        else if (n > l4) forward_phase<MODE, DQ, GEIK, 2, true>(ai, rec, rec2, qt, qB, sq2, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+        else forward_phase<MODE, DQ, GEIK, 4, true>(ai, rec, rec2, qt, qB, sq2, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
     } else {
-        if (n > l2) forward_phase<MODE, DQ, GEIK, 1, false>(ai, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
-        else if (n > l4) forward_phase<MODE, DQ, GEIK, 2, false>(ai, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
-        else forward_phase<MODE, DQ, GEIK, 4, false>(ai, rec, qt, qB, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+        if (n > l2) forward_phase<MODE, DQ, GEIK, 1, false>(ai, rec, rec2, qt, qB, sq2, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+        else if (n > l4) forward_phase<MODE, DQ, GEIK, 2, false>(ai, rec, rec2, qt, qB, sq2, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
+        else forward_phase<MODE, DQ, GEIK, 4, false>(ai, rec, rec2, qt, qB, sq2, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
     }
     if (BWD) {
         // ---- 3. backward, one thread per key
@@ -643,9 +906,22 @@ __device__ __forceinline__ void item_body(const FusedArgsT<T> &a, const FusedArg
         const int c = t & (kCentres - 1);
         if (c < nc) {
             const bool offset = t >= kCentres;
-            const V A = keyA(rec, offset, c), B = keyB(rec, offset, c);
+            V A, B;
+            if constexpr (PAIRS) {
+                A = keyT[2 * t];   // staged by this thread
+                B = keyT[2 * t + 1];
+            } else {
+                A = keyA(rec, offset, c);
+                B = keyB(rec, offset, c);
+            }
             T acc[19];
-            if (GEIK) {
+            if constexpr (PAIRQ) {
+                float accf[8];
+                if (offset) bwd_key_loop_x2<true>(A, B, sq2, (n + 1) >> 1, accf);
+                else bwd_key_loop_x2<false>(A, B, sq2, (n + 1) >> 1, accf);
+                for (int i = 0; i < 8; ++i) acc[i] = accf[i];
+                for (int i = 8; i < 19; ++i) acc[i] = T(0);
+            } else if (GEIK) {
                 float accf[19];
                 const float4 Af = make_float4((float)A.x, (float)A.y, (float)A.z, (float)A.w);
                 const float4 Bf = make_float4((float)B.x, (float)B.y, (float)B.z, (float)B.w);
@@ -698,9 +974,15 @@ __global__ void __launch_bounds__(kThreads, min_ctas<GEIK, T>()) fused_kernel(Fu
 {
     using V = V4Of<T>;
     constexpr bool BWD = MODE == BACKWARD || MODE == FIT;
-    __shared__ V s_rec[kCentres * kKeyRecords];               // key records of the window
-    __shared__ V s_qt[kChunk];                                // query tile
-    __shared__ V s_sqB[BWD ? kChunk / 2 : 1];
+    constexpr bool PAIRS = std::is_same<T, float>::value;
+    constexpr bool NEED_REC = !PAIRS || DQ || GEIK;
+    constexpr bool PAIRQ = PAIRS && !GEIK && BWD;
+    __shared__ V s_rec[NEED_REC ? kCentres * kKeyRecords : 1];      // key records of the window
+    __shared__ float4 s_rec2[PAIRS ? 2 * kPairs * 4 : 1];           // the same keys, paired (FP32)
+    __shared__ float4 s_keyT[PAIRS ? 2 * kThreads : 1];             // (A, B) of thread t's key (FP32)
+    __shared__ V s_qt[kChunk];                                      // query tile
+    __shared__ V s_sqB[BWD && !PAIRQ ? kChunk / 2 : 1];
+    __shared__ float4 s_sq2[PAIRQ ? 3 * kChunk / 2 : 1];            // paired query rows (FP32 backward)
     __shared__ float4 s_sqE[GEIK ? kChunk : 1];               // (O, gO, H, T) per query
     __shared__ float4 s_sqU[GEIK ? kChunk : 1];               // (u, 0) per query
     __shared__ int s_item;
@@ -728,8 +1010,8 @@ __global__ void __launch_bounds__(kThreads, min_ctas<GEIK, T>()) fused_kernel(Fu
             ai.grad = a.grad + sh.c_off * kSlots;
             ai.inv_J = sh.inv_J;
             const T invRb = T(1) / (T)sh.R;
-            item_body<MODE, DQ, GEIK, T, BATCHED>(a, ai, b, item, sh.R, invRb, T(2) * invRb, s_rec, s_qt, s_sqB,
-                                                  s_sqE, s_sqU, loss_acc, abs_acc);
+            item_body<MODE, DQ, GEIK, T, BATCHED>(a, ai, b, item, sh.R, invRb, T(2) * invRb, s_rec, s_rec2, s_keyT,
+                                                  s_qt, s_sqB, s_sq2, s_sqE, s_sqU, loss_acc, abs_acc);
             if (MODE == FIT || MODE == EVAL) {
                 // this item's loss sums to its shape: one double atomic pair per warp
                 for (int o = 16; o > 0; o >>= 1) {
@@ -743,8 +1025,8 @@ __global__ void __launch_bounds__(kThreads, min_ctas<GEIK, T>()) fused_kernel(Fu
                 loss_acc = abs_acc = T(0);
             }
         } else {
-            item_body<MODE, DQ, GEIK, T, BATCHED>(a, a, b, item, R, invR, h, s_rec, s_qt, s_sqB, s_sqE, s_sqU,
-                                                  loss_acc, abs_acc);
+            item_body<MODE, DQ, GEIK, T, BATCHED>(a, a, b, item, R, invR, h, s_rec, s_rec2, s_keyT, s_qt, s_sqB,
+                                                  s_sq2, s_sqE, s_sqU, loss_acc, abs_acc);
         }
     }
 
@@ -880,10 +1162,14 @@ cudaError_t launch_eval_finish(const Ctrl *ctrl, double inv_J, float *out, cudaS
 // queries (the sort groups sparse octets).  The union of the octet's
 // windows, at most 5x5x5 centres, is staged once; every query blends its own
 // 4x4x4 sub-window (the same keys, in the same order and summation classes
-// as the generic path of fused_kernel); the backward runs thread per key
-// over the item's queries and counts a key only for the queries whose
-// window holds it.  Compared with one item per cell, the window is staged
-// and each key's gradient is added once per octet instead of once per cell.
+// as the generic path of fused_kernel).  The backward walks the octet's
+// sub-cells in turn: for each, all 128 threads take the 128 keys of its
+// window over its queries (two per instruction), so that no lane idles on
+// another lane's queries, and add their sums to a shared gradient tile of
+// the union; the tile then goes to the gradient with one atomic per non-zero
+// entry, consecutive threads on consecutive floats of a z-row.  Compared
+// with one item per cell, the window is staged and each key's gradient is
+// added once per octet instead of once per cell.
 
 namespace {
 
@@ -895,6 +1181,16 @@ struct GroupWin {
     int lox, loy, loz;      // first centre of the union window
     int nx, ny, nz, nc;     // its extent (clipped to the grid)
 };
+
+// t / n for 1 <= n <= 5 and 0 <= t < 13107, exact: (t * ceil(2^16 / n)) >> 16
+// (the error t (ceil(2^16 / n) - 2^16 / n) / 2^16 stays below 1 / n).
+__device__ __forceinline__ int small_div(int t, int n) { return (t * ((65536 + n - 1) / n)) >> 16; }
+
+// Union key tile of a grouped item: four arrays of kGCentres records
+// (grid A, grid B, offset A, offset B), so that lanes reading different
+// centres fall on consecutive 16-byte bank groups.
+__device__ __forceinline__ float4 gA(const float4 *rec, int set, int c) { return rec[2 * set * kGCentres + c]; }
+__device__ __forceinline__ float4 gB(const float4 *rec, int set, int c) { return rec[(2 * set + 1) * kGCentres + c]; }
 
 __device__ __forceinline__ GroupWin group_window(const Item item, int R)
 {
@@ -936,21 +1232,38 @@ __device__ __forceinline__ void grp_fwd_sums(const float4 *rec, const GroupWin &
 #pragma unroll
                 for (int i = 0; i < CPL; ++i) {
                     const int c = row + part + KQ * i;
-                    fwd_key(keyA(rec, set, c), keyB(rec, set, c), x, y, z, M2, ev[i], mv[i]);
+                    fwd_key(gA(rec, set, c), gB(rec, set, c), x, y, z, M2, ev[i], mv[i]);
                 }
             }
         }
     } else {
+        // clipped window: walk the keys k = part, part + KQ, ... with their
+        // union index c, carrying z into y and y into x
 #pragma unroll
         for (int set = 0; set < 2; ++set) {
+            int kz = part, ky = 0, c = cbase + part;
+            while (kz >= wnz) {
+                kz -= wnz;
+                c += g.nz - wnz;
+                if (++ky == wny) {
+                    ky = 0;
+                    c += (g.ny - wny) * g.nz;
+                }
+            }
             for (int base = 0; base < nq; base += kClasses) {
 #pragma unroll
                 for (int i = 0; i < CPL; ++i) {
                     const int k = base + part + KQ * i;
-                    if (k < nq) {
-                        const int kz = k % wnz, ky = (k / wnz) % wny, kx = k / (wny * wnz);
-                        const int c = ((w0x + kx) * g.ny + (w0y + ky)) * g.nz + (w0z + kz);
-                        fwd_key(keyA(rec, set, c), keyB(rec, set, c), x, y, z, M2, ev[i], mv[i]);
+                    if (k < nq) fwd_key(gA(rec, set, c), gB(rec, set, c), x, y, z, M2, ev[i], mv[i]);
+                    kz += KQ;
+                    c += KQ;
+                    while (kz >= wnz) {
+                        kz -= wnz;
+                        c += g.nz - wnz;
+                        if (++ky == wny) {
+                            ky = 0;
+                            c += (g.ny - wny) * g.nz;
+                        }
                     }
                 }
             }
@@ -961,9 +1274,10 @@ __device__ __forceinline__ void grp_fwd_sums(const float4 *rec, const GroupWin &
 }
 
 template <int MODE, int KQ, bool BATCHED>
-__device__ __forceinline__ void grp_forward(const FusedArgs &ai, const float4 *rec, float4 *qt, float2 *og,
-                                            const unsigned char *qoff, const GroupWin &g, int n, int R, float h,
-                                            float3 orig, float &loss_acc, float &abs_acc)
+__device__ __forceinline__ void grp_forward(const FusedArgs &ai, const float4 *rec, const float4 *qt, float4 *sq2,
+                                            const unsigned char *qoff, const int *beg, const int *pbeg,
+                                            const GroupWin &g, int n, int R, float h, float3 orig, float &loss_acc,
+                                            float &abs_acc)
 {
     constexpr int LG = KQ == 1 ? 0 : (KQ == 2 ? 1 : 2);
     const int t = threadIdx.x;
@@ -997,8 +1311,8 @@ __device__ __forceinline__ void grp_forward(const FusedArgs &ai, const float4 *r
             for (int k = part; k < nq; k += KQ) {
                 const int kz = k % wnz, ky = (k / wnz) % wny, kx = k / (wny * wnz);
                 const int c = ((w0x + kx) * g.ny + (w0y + ky)) * g.nz + (w0z + kz);
-                mx = fmaxf(mx, key_exponent(keyA(rec, 0, c), q.x, q.y, q.z));
-                mx = fmaxf(mx, key_exponent(keyA(rec, 1, c), q.x, q.y, q.z));
+                mx = fmaxf(mx, key_exponent(gA(rec, 0, c), q.x, q.y, q.z));
+                mx = fmaxf(mx, key_exponent(gA(rec, 1, c), q.x, q.y, q.z));
             }
 #pragma unroll
             for (int o = 1; o < KQ; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
@@ -1024,37 +1338,32 @@ __device__ __forceinline__ void grp_forward(const FusedArgs &ai, const float4 *r
             loss_acc += diff * diff;
             abs_acc += fabsf(diff);
         }
-        if (MODE == FIT) {
-            __syncwarp();
-            if (valid && part == 0) {
-                qt[qi] = make_float4(q.x, q.y, q.z, lse2);
-                og[qi] = make_float2(O, gO);
-            }
+        if (MODE == FIT && valid && part == 0) {
+            // paired rows of the query's sub-cell, an odd last one padded
+            const int r = qi - beg[off], p = 2 * pbeg[off] + r;
+            store_pair_query(sq2, p, q, lse2, O, gO);
+            if (qi == beg[off + 1] - 1 && (r & 1) == 0) store_pair_query(sq2, p + 1, q, lse2, O, 0.f);
         }
     }
 }
-
-// Key order of the backward for an interior octet (a 5x5x5 union): centres
-// sorted by the set of sub-cells whose window holds them (per axis: index 0
-// only for sub-cell offset 0, 1..3 for both, 4 only for offset 1), so that
-// the lanes of a warp mostly walk the same query ranges.
-__constant__ unsigned char c_group_order[kGCentres];
-
-__device__ __forceinline__ int axis_class(int k) { return k == 0 ? 0 : (k == 4 ? 2 : 1); }
 
 template <int MODE, bool BATCHED>
 __global__ void __launch_bounds__(kThreads, 8) grouped_kernel(FusedArgs a, BatchArgs b, const Item *gtop)
 {
     __shared__ float4 s_rec[kGCentres * kKeyRecords];
     __shared__ float4 s_qt[kChunk];
-    __shared__ float2 s_og[kChunk];
+    __shared__ float4 s_sq2[MODE == FIT ? 3 * (kChunk / 2 + 8) : 1];   // paired rows, per sub-cell
+    __shared__ float s_grad[MODE == FIT ? kGCentres * kSlots : 1];     // the union's gradient tile
     __shared__ unsigned char s_off[kChunk];
     __shared__ int s_beg[9];          // query range of sub-cell o: [s_beg[o], s_beg[o + 1])
+    __shared__ int s_pbeg[9];         // its pairs from s_pbeg[o]
     __shared__ int s_item[2];
     __shared__ float s_red[2][kThreads / 32];
     const int t = threadIdx.x;
     const int n_groups = a.ctrl->n_groups;
     float loss_acc = 0.f, abs_acc = 0.f;
+    if (MODE == FIT)
+        for (int i = t; i < kGCentres * kSlots; i += kThreads) s_grad[i] = 0.f;
     if (t == 0) s_item[0] = atomicAdd(&a.ctrl->next_group, 1);
     int cur = 0;
 
@@ -1062,7 +1371,8 @@ __global__ void __launch_bounds__(kThreads, 8) grouped_kernel(FusedArgs a, Batch
         __syncthreads();   // the previous item is consumed; s_item[cur] is visible
         const int gi = s_item[cur];
         if (gi >= n_groups) break;
-        if (t == 0) s_item[cur ^ 1] = atomicAdd(&a.ctrl->next_group, 1);   // the next item, fetched early
+        int next = 0;
+        if (t == 0) next = atomicAdd(&a.ctrl->next_group, 1);   // the next item, published at the end
         if (t < 9) s_beg[t] = 0;
         const Item item = gtop[-gi];
         FusedArgs ai = a;
@@ -1083,16 +1393,16 @@ __global__ void __launch_bounds__(kThreads, 8) grouped_kernel(FusedArgs a, Batch
         __syncthreads();   // s_beg cleared
         // ---- stage the union window's key records (window-local) and the queries
         if (t < g.nc) {
-            const int oz = t % g.nz, oy = (t / g.nz) % g.ny, ox = t / (g.ny * g.nz);
+            const int rowi = small_div(t, g.nz), oz = t - rowi * g.nz;
+            const int ox = small_div(rowi, g.ny), oy = rowi - ox * g.ny;
             const float4 *k = ai.keys + (((size_t)(g.lox + ox) * R + (g.loy + oy)) * R + (g.loz + oz)) * kKeyRecords;
             const float gx = (float)(2 * (g.lox + ox - g.c0x)) * invR, gy = (float)(2 * (g.loy + oy - g.c0y)) * invR,
                         gz = (float)(2 * (g.loz + oz - g.c0z)) * invR;
             const float4 kg = k[0], ko = k[2];
-            float4 *r = s_rec + 4 * t;
-            r[0] = make_float4(gx, gy, gz, kg.w);
-            r[1] = k[1];
-            r[2] = make_float4(gx + ko.x, gy + ko.y, gz + ko.z, ko.w);
-            r[3] = k[3];
+            s_rec[t] = make_float4(gx, gy, gz, kg.w);
+            s_rec[kGCentres + t] = k[1];
+            s_rec[2 * kGCentres + t] = make_float4(gx + ko.x, gy + ko.y, gz + ko.z, ko.w);
+            s_rec[3 * kGCentres + t] = k[3];
         }
         for (int qi = t; qi < n; qi += kThreads) {
             const float4 q = a.sorted[start + qi];
@@ -1104,72 +1414,76 @@ __global__ void __launch_bounds__(kThreads, 8) grouped_kernel(FusedArgs a, Batch
             atomicAdd(&s_beg[o + 1], 1);
         }
         __syncthreads();
-        if (t == 0)
-            for (int o = 1; o <= 8; ++o) s_beg[o] += s_beg[o - 1];   // the queries are sorted by sub-cell
+        if (t == 0) {
+            // the queries are sorted by sub-cell; pair ranges padded to even counts
+            s_pbeg[0] = 0;
+            for (int o = 1; o <= 8; ++o) {
+                s_pbeg[o] = s_pbeg[o - 1] + ((s_beg[o] + 1) >> 1);
+                s_beg[o] += s_beg[o - 1];
+            }
+        }
+        __syncthreads();
         // ---- forward
-        if (n > 64) grp_forward<MODE, 1, BATCHED>(ai, s_rec, s_qt, s_og, s_off, g, n, R, h, orig, loss_acc, abs_acc);
-        else if (n > 32) grp_forward<MODE, 2, BATCHED>(ai, s_rec, s_qt, s_og, s_off, g, n, R, h, orig, loss_acc, abs_acc);
-        else grp_forward<MODE, 4, BATCHED>(ai, s_rec, s_qt, s_og, s_off, g, n, R, h, orig, loss_acc, abs_acc);
+        if (n > 64) grp_forward<MODE, 1, BATCHED>(ai, s_rec, s_qt, s_sq2, s_off, s_beg, s_pbeg, g, n, R, h, orig, loss_acc, abs_acc);
+        else if (n > 32) grp_forward<MODE, 2, BATCHED>(ai, s_rec, s_qt, s_sq2, s_off, s_beg, s_pbeg, g, n, R, h, orig, loss_acc, abs_acc);
+        else grp_forward<MODE, 4, BATCHED>(ai, s_rec, s_qt, s_sq2, s_off, s_beg, s_pbeg, g, n, R, h, orig, loss_acc, abs_acc);
         if (MODE == FIT) {
-            // ---- backward: keys t and t + 128 of the 2 nc keys (grid keys
-            // first), each over the sub-cells whose window holds it
-            __syncthreads();
-            const bool interior = g.nc == kGCentres;
-            for (int kid = t; kid < 2 * g.nc; kid += kThreads) {
-                const bool offset = kid >= g.nc;
-                const int slot = offset ? kid - g.nc : kid;
-                const int c = interior ? c_group_order[slot] : slot;
-                const int oz = c % g.nz, oy = (c / g.nz) % g.ny, ox = c / (g.ny * g.nz);
-                // centre index relative to the octet's base: in the window of
-                // sub-cell offset o iff o - 1 <= k <= o + 2 per axis
-                const int kx = g.lox + ox - g.c0x, ky = g.loy + oy - g.c0y, kz = g.loz + oz - g.c0z;
-                const float4 A = keyA(s_rec, offset, c), B = keyB(s_rec, offset, c);
-                float ag = 0.f, arx = 0.f, ary = 0.f, arz = 0.f, ab = 0.f, adx = 0.f, ady = 0.f, adz = 0.f;
-                bool any = false;
-                for (int o = 0; o < 8; ++o) {
-                    const int px = (o >> 2) & 1, py = (o >> 1) & 1, pz = o & 1;
-                    if (kx < px - 1 || kx > px + 2 || ky < py - 1 || ky > py + 2 || kz < pz - 1 || kz > pz + 2)
-                        continue;
-                    const int j1 = s_beg[o + 1];
-                    for (int j = s_beg[o]; j < j1; ++j) {
-                        any = true;
-                        const float4 Q = s_qt[j];
-                        const float2 S = s_og[j];
-                        const float rx = Q.x - A.x, ry = Q.y - A.y, rz = Q.z - A.z;
-                        const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                        const float w = ex2_approx(fmaf(A.w, d2, -Q.w));
-                        const float gw = w * S.y;
-                        const float f = fmaf(B.y, rx, fmaf(B.z, ry, fmaf(B.w, rz, B.x)));
-                        const float gd = gw * (f - S.x);
-                        ag += gw;
-                        arx = fmaf(gw, rx, arx);
-                        ary = fmaf(gw, ry, ary);
-                        arz = fmaf(gw, rz, arz);
-                        ab = fmaf(gd, d2, ab);
-                        adx = fmaf(gd, rx, adx);
-                        ady = fmaf(gd, ry, ady);
-                        adz = fmaf(gd, rz, adz);
-                    }
-                }
-                if (!any) continue;
-                float *gr = ai.grad + (((size_t)(g.lox + ox) * R + (g.loy + oy)) * R + (g.loz + oz)) * kSlots;
+            // ---- backward, sub-cell by sub-cell: thread t takes key t of the
+            // sub-cell's window (set t / 64) over the sub-cell's query pairs
+            // and adds its sums to the union's gradient tile
+            const int kc = t & (kCentres - 1), kset = t / kCentres;
+            __syncthreads();   // the paired rows are written
+            for (int o = 0; o < 8; ++o) {
+                const int npairs = s_pbeg[o + 1] - s_pbeg[o];
+                if (npairs == 0) continue;   // uniform
+                const int cx = g.c0x + ((o >> 2) & 1), cy = g.c0y + ((o >> 1) & 1), cz = g.c0z + (o & 1);
+                const int w0x = max(cx - 1, 0), w0y = max(cy - 1, 0), w0z = max(cz - 1, 0);
+                const int wnx = min(cx + 2, R - 1) - w0x + 1, wny = min(cy + 2, R - 1) - w0y + 1,
+                          wnz = min(cz + 2, R - 1) - w0z + 1;
+                if (kc < wnx * wny * wnz) {
+                const int kr = small_div(kc, wnz), kz = kc - kr * wnz;
+                const int kx = small_div(kr, wny), ky = kr - kx * wny;
+                const int u = ((w0x - g.lox + kx) * g.ny + (w0y - g.loy + ky)) * g.nz + (w0z - g.loz + kz);
+                const float4 A = gA(s_rec, kset, u), B = gB(s_rec, kset, u);
+                float acc[8];
+                if (kset) bwd_key_loop_x2<true>(A, B, s_sq2 + 3 * s_pbeg[o], npairs, acc);
+                else bwd_key_loop_x2<false>(A, B, s_sq2 + 3 * s_pbeg[o], npairs, acc);
+                float *gt = s_grad + u * kSlots;
                 const float beta = -A.w * Num<float>::kLn2;
-                if (!offset) {
-                    atomicAdd(gr + 5, ag);
-                    atomicAdd(gr + 6, arx);
-                    atomicAdd(gr + 7, ary);
-                    atomicAdd(gr + 8, arz);
-                    atomicAdd(gr + 3, -beta * ab);
+                if (!kset) {
+                    gt[5] += acc[0];
+                    gt[6] += acc[1];
+                    gt[7] += acc[2];
+                    gt[8] += acc[3];
+                    gt[3] += -beta * acc[4];
                 } else {
-                    atomicAdd(gr + 9, ag);
-                    atomicAdd(gr + 10, arx);
-                    atomicAdd(gr + 11, ary);
-                    atomicAdd(gr + 12, arz);
-                    atomicAdd(gr + 4, -beta * ab);
+                    gt[9] += acc[0];
+                    gt[10] += acc[1];
+                    gt[11] += acc[2];
+                    gt[12] += acc[3];
+                    gt[4] += -beta * acc[4];
                     const float tb = 2.f * beta;
-                    atomicAdd(gr + 0, fmaf(-B.y, ag, tb * adx));
-                    atomicAdd(gr + 1, fmaf(-B.z, ag, tb * ady));
-                    atomicAdd(gr + 2, fmaf(-B.w, ag, tb * adz));
+                    gt[0] += fmaf(-B.y, acc[0], tb * acc[5]);
+                    gt[1] += fmaf(-B.z, acc[0], tb * acc[6]);
+                    gt[2] += fmaf(-B.w, acc[0], tb * acc[7]);
+                }
+                }
+                __syncthreads();   // this sub-cell's adds are done
+            }
+            // ---- the tile to the gradient: rows of nz centres along z are
+            // contiguous in the grid, so consecutive threads add consecutive
+            // floats; the tile is cleared for the next item
+            const int row = g.nz * kSlots, lane = t & 31;
+            for (int r = t >> 5; r < g.nx * g.ny; r += kThreads / 32) {
+                const int ox = small_div(r, g.ny), oy = r - ox * g.ny;
+                float *dst = ai.grad + (((size_t)(g.lox + ox) * R + (g.loy + oy)) * R + g.loz) * kSlots;
+                float *src = s_grad + r * row;
+                for (int f = lane; f < row; f += 32) {
+                    const float v = src[f];
+                    if (v != 0.f) {
+                        atomicAdd(dst + f, v);
+                        src[f] = 0.f;
+                    }
                 }
             }
         }
@@ -1184,6 +1498,7 @@ __global__ void __launch_bounds__(kThreads, 8) grouped_kernel(FusedArgs a, Batch
             }
             loss_acc = abs_acc = 0.f;
         }
+        if (t == 0) s_item[cur ^ 1] = next;
         cur ^= 1;
     }
     if (!BATCHED) {
@@ -1213,21 +1528,6 @@ __global__ void __launch_bounds__(kThreads, 8) grouped_kernel(FusedArgs a, Batch
 cudaError_t launch_grouped(const FusedArgs &a, const BatchArgs &b, const Item *gtop, bool eval, cudaStream_t s)
 {
     const bool batched = b.shapes != nullptr;
-    // the interior key order, once per device
-    cudaError_t te = cudaSuccess;
-    per_device_cached(reinterpret_cast<const void *>(&c_group_order), 0, [&te] {
-        unsigned char order[kGCentres];
-        int n = 0;
-        for (int cls = 0; cls < 27; ++cls)
-            for (int c = 0; c < kGCentres; ++c) {
-                const int z = c % kGU, y = (c / kGU) % kGU, x = c / (kGU * kGU);
-                const auto ac = [](int k) { return k == 0 ? 0 : (k == 4 ? 2 : 1); };
-                if ((ac(x) * 3 + ac(y)) * 3 + ac(z) == cls) order[n++] = (unsigned char)c;
-            }
-        te = cudaMemcpyToSymbol(c_group_order, order, sizeof(order));
-        return te == cudaSuccess ? 1 : 0;
-    });
-    if (te != cudaSuccess) return te;
     const void *k = batched ? (eval ? reinterpret_cast<const void *>(grouped_kernel<EVAL, true>)
                                     : reinterpret_cast<const void *>(grouped_kernel<FIT, true>))
                             : (eval ? reinterpret_cast<const void *>(grouped_kernel<EVAL, false>)
