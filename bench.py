@@ -113,6 +113,17 @@ def fused_traffic():
     return int(tb.group(1))
 
 
+def json_safe(x):
+    """x with every non-finite float replaced by None (strict JSON)."""
+    if isinstance(x, dict):
+        return {k: json_safe(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [json_safe(v) for v in x]
+    if isinstance(x, float) and not math.isfinite(x):
+        return None
+    return x
+
+
 def max_over_ranks(x: float, device=None) -> float:
     """Max of a per-rank scalar over all ranks (identity without a process group)."""
     import torch
@@ -493,19 +504,28 @@ def bench_warm_start(dev, rank, n_train, n_eval, train_steps, epochs, eval_steps
            "eval_shapes": n_eval, "eval_steps": eval_steps, "predict_s": pred_s,
            "target_rule": "per shape: 1e-3, or the plain fit's final held-out MAE where 1e-3 is not reached",
            "shapes_reaching_1e-3_plain": int((mae_p.min(0) <= 1e-3).sum()), "encoder_roofline": enc_roof}
+    def finite(x):
+        return float(x) if np.isfinite(x) else None   # JSON has no inf / nan
+
     for name, (st, mae, sec) in arms.items():
         steps = W.steps_to(st, mae, target)
         reached = np.isfinite(steps)
-        last = float(np.max(steps[reached])) if reached.any() else float("nan")
         sec_per_step = float(sec[-1] / st[-1])
         extra = pred_s if name == "warm" else 0.0
-        wall = last * sec_per_step + extra if reached.all() else float("nan")
+        # steps until half / 90 % / all of the shapes reached their targets
+        # (inf where that many never did within eval_steps)
+        q = {k: float(np.quantile(steps, f, method="higher")) for k, f in (("p50", 0.5), ("p90", 0.9), ("all", 1.0))}
         out[name] = {"mae_median_start": float(np.median(mae[0])), "mae_median_final": float(np.median(mae[-1])),
-                     "steps_to_target_median": float(np.median(steps)), "steps_to_target_mean":
-                     float(np.mean(steps[reached])) if reached.any() else float("nan"),
-                     "shapes_reached": int(reached.sum()), "steps_until_all_reached": last,
-                     "seconds_per_step": sec_per_step, "wall_s_to_target": wall,
-                     "fits_per_s": n_eval * ws / wall if np.isfinite(wall) and wall > 0 else None}
+                     "mae_median_at_step": {str(int(s_)): float(np.median(mae[i])) for i, s_ in enumerate(st)
+                                            if int(s_) in (100, 250, 500, 1000, 1500)},
+                     "shapes_reached": int(reached.sum()), "steps_to_target": {k: finite(v) for k, v in q.items()},
+                     "seconds_per_step": sec_per_step,
+                     "wall_s_to_target": {k: finite(v * sec_per_step + extra) for k, v in q.items()},
+                     "fits_per_s_half": (0.5 * n_eval * ws / (q["p50"] * sec_per_step + extra))
+                     if np.isfinite(q["p50"]) else None}
+    sp, sw = out["plain"]["steps_to_target"]["p50"], out["warm"]["steps_to_target"]["p50"]
+    out["median_step_ratio"] = sp / sw if sp and sw else None
+    out["fits_per_s_note"] = "fits_per_s_half: half of the shapes at their targets over the seconds that took"
     out["total_s"] = time.perf_counter() - t0
     return out
 
@@ -930,8 +950,8 @@ def main():
     if args.warm_train_shapes > 0:
         warm = bench_warm_start(dev, rank, args.warm_train_shapes, args.warm_eval_shapes, args.warm_train_steps,
                                 args.warm_epochs, args.warm_eval_steps, ws)
-        log(f"[bench] warm start: plain {warm['plain']['steps_to_target_median']} / warm "
-            f"{warm['warm']['steps_to_target_median']} median steps to target, {warm['total_s']:.0f} s")
+        log(f"[bench] warm start: plain {warm['plain']['steps_to_target']['p50']} / warm "
+            f"{warm['warm']['steps_to_target']['p50']} median steps to target, {warm['total_s']:.0f} s")
 
     # ---- end to end through the C ABI with host buffers: the batch pool in
     # pinned host memory, every step copies its 64 MiB batch to the device
@@ -995,7 +1015,7 @@ def main():
                     "mae_first_timed": float(st[0, 1]), "mae_last": float(st[-1, 1]),
                     "fits_per_s": 1e3 / (FIT_STEPS_32 * ms) * ws, "steps_per_fit": FIT_STEPS_32},
         }
-        print(json.dumps(line), flush=True)
+        print(json.dumps(json_safe(line), allow_nan=False), flush=True)
     if ws > 1:
         dist.destroy_process_group()
     return 0

@@ -643,6 +643,21 @@ void efunc_profile_reset(void);
 /* Kernels launched by this library since it was loaded. */
 int64_t efunc_launch_count(void);
 
+/* Bounds-check build (the sources compiled with -DEFUNC_DEBUG_BOUNDS into
+ * lib/libefunc_debug.so): the kernels test the indices of their hot gathers
+ * and scatters - staged key records and gradient rows inside the grid, each
+ * staged query inside its work item's cell or octet, paired-row slots
+ * inside their buffer, the sort's bins and sorted positions - and on a
+ * failing test record its code in a device flag and skip the access (no
+ * trap, no abort).  Waits for the current device, writes the first code
+ * recorded there since the last call to *code (0: none; 1 staged key outside
+ * the grid, 2 staged query outside its item's cell, 3 union key outside the
+ * grid, 4 staged query outside its octet, 5 paired-row slot past its buffer,
+ * 6 bin past the bin count, 7 sorted position past J, 8 work item with a bad
+ * range) and clears it.  The normal build writes 0 and returns
+ * EFUNC_ERR_UNSUPPORTED; code NULL is EFUNC_ERR_ARG. */
+efunc_status efunc_debug_bounds(int32_t *code);
+
 /* The cudaError_t of the CUDA call behind the calling thread's most recent
  * EFUNC_ERR_CUDA (0 before any).  The library clears the runtime's pending
  * error when it reports one, so a failure never resurfaces in a later call. */

@@ -133,10 +133,16 @@ SIGNATURES = {
     "efunc_profile_read": (c_int32, [c_char_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     "efunc_profile_reset": (None, []),
     "efunc_launch_count": (c_int64, []),
+    "efunc_debug_bounds": (c_int32, [ctypes.POINTER(c_int32)]),
 }
 
 _lock = threading.Lock()
 _lib = None
+
+
+def debug_bounds_requested() -> bool:
+    """EFUNC_DEBUG_BOUNDS=1 selects the bounds-checking build of the library."""
+    return os.environ.get("EFUNC_DEBUG_BOUNDS", "0") not in ("", "0")
 
 
 def load(build: bool = True) -> ctypes.CDLL:
@@ -144,11 +150,13 @@ def load(build: bool = True) -> ctypes.CDLL:
     global _lib
     with _lock:
         if _lib is None:
-            if build and not _build.up_to_date():
-                _build.build()
-            if not os.path.exists(_build.LIB):
-                raise RuntimeError(f"CUDA library {_build.LIB} is missing and could not be built")
-            lib = ctypes.CDLL(_build.LIB)
+            debug = debug_bounds_requested()
+            path = _build.lib_path(debug)
+            if build and not _build.up_to_date(debug):
+                _build.build(debug=debug)
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing and could not be built")
+            lib = ctypes.CDLL(path)
             for name, (res, args) in SIGNATURES.items():
                 fn = getattr(lib, name)
                 fn.restype = res

@@ -725,3 +725,15 @@ def profile_reset():
 
 def launch_count() -> int:
     return int(B.load().efunc_launch_count())
+
+
+def debug_bounds() -> int | None:
+    """The first bounds-check code the kernels recorded on the current device
+    since the last call (0: none), cleared; None unless the bounds-check build
+    is loaded (EFUNC_DEBUG_BOUNDS=1)."""
+    code = ctypes.c_int32(0)
+    st = B.load().efunc_debug_bounds(ctypes.byref(code))
+    if st == 5:   # EFUNC_ERR_UNSUPPORTED: the normal build
+        return None
+    B.check("efunc_debug_bounds", st)
+    return int(code.value)

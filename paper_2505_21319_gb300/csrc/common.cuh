@@ -380,6 +380,29 @@ __device__ __forceinline__ void cell_of_bin(uint32_t bin, int P, int &ux, int &u
     uz = bz * 4 + lz;
 }
 
+// Bounds-check build (-DEFUNC_DEBUG_BOUNDS): the hot gathers and scatters
+// test their indices with bounds_ok(condition, code); a failing test records
+// its code in a device flag of the translation unit (the first one wins) and
+// the caller skips the access.  In the normal build the test is the constant
+// true and compiles away.  Codes: 1 staged key outside the grid, 2 staged
+// query outside its item's cell, 3 union key outside the grid, 4 staged
+// query outside its octet, 5 paired-row slot past its buffer, 6 bin past the
+// bin count, 7 sorted position past J, 8 work item with a bad range.
+#ifdef EFUNC_DEBUG_BOUNDS
+static __device__ int g_bounds_code;
+__device__ __forceinline__ bool bounds_ok(bool ok, int code)
+{
+    if (!ok) atomicCAS(&g_bounds_code, 0, code);
+    return ok;
+}
+#else
+__device__ __forceinline__ bool bounds_ok(bool, int) { return true; }
+#endif
+// first code recorded by fused.cu / sort.cu on the current device, cleared
+// (0 without a failure or in the normal build, -1 on a CUDA error)
+int bounds_code_fused();
+int bounds_code_sort();
+
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;

@@ -1737,6 +1737,22 @@ int32_t efunc_profile_read(const char *name, double *total_ms, int64_t *launches
     return -1;
 }
 
+efunc_status efunc_debug_bounds(int32_t *code)
+{
+    if (!code) return EFUNC_ERR_ARG;
+    *code = 0;
+#ifdef EFUNC_DEBUG_BOUNDS
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int a = bounds_code_fused(), b = bounds_code_sort();
+    if (a < 0 || b < 0) return cuda_fail(cudaGetLastError());
+    *code = a != 0 ? a : b;
+    return EFUNC_OK;
+#else
+    return EFUNC_ERR_UNSUPPORTED;
+#endif
+}
+
 void efunc_profile_reset(void)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);

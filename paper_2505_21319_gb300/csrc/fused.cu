@@ -856,6 +856,7 @@ __device__ __forceinline__ void item_body(const FusedArgsT<T> &a, const FusedArg
     constexpr bool NEED_REC = !PAIRS || DQ || GEIK;        // the per-key tile (dO/dq sums, FP64)
     constexpr bool PAIRQ = PAIRS && !GEIK;                 // paired query rows, packed backward
     const int t = threadIdx.x;
+    if (!bounds_ok(item.x >= 0 && item.y >= 1 && item.y <= kChunk, 8)) return;   // uniform in the CTA
     const Window w = window_of(item, R);
     const int start = item.x, n = item.y, nc = w.nc;
     const bool full = nc == kCentres;
@@ -868,7 +869,10 @@ __device__ __forceinline__ void item_body(const FusedArgsT<T> &a, const FusedArg
         int ox, oy, oz;
         if (full) { ox = kc >> 4; oy = (kc >> 2) & 3; oz = kc & 3; }
         else { oz = kc % w.nz; oy = (kc / w.nz) % w.ny; ox = kc / (w.ny * w.nz); }
-        const V *k = ai.keys + (((size_t)(w.lox + ox) * R + (w.loy + oy)) * R + (w.loz + oz)) * kKeyRecords;
+        int ix = w.lox + ox, iy = w.loy + oy, iz = w.loz + oz;
+        if (!bounds_ok((unsigned)ix < (unsigned)R && (unsigned)iy < (unsigned)R && (unsigned)iz < (unsigned)R, 1))
+            ix = iy = iz = 0;   // read centre 0 instead
+        const V *k = ai.keys + (((size_t)ix * R + iy) * R + iz) * kKeyRecords;
         const T gx = (T)(2 * (w.lox + ox - w.cx)) * invR, gy = (T)(2 * (w.loy + oy - w.cy)) * invR,
                 gz = (T)(2 * (w.loz + oz - w.cz)) * invR;
         const V p = k[2 * kset], B = k[2 * kset + 1];
@@ -886,7 +890,17 @@ __device__ __forceinline__ void item_body(const FusedArgsT<T> &a, const FusedArg
         // neutral keys up to a multiple of 4
         stage_pair_key(rec2, kset, kc, make_float4(1e18f, 1e18f, 1e18f, -1.f), make_float4(0.f, 0.f, 0.f, 0.f));
     }
-    for (int qi = t; qi < n; qi += kThreads) qt[qi] = a.sorted[start + qi];
+    for (int qi = t; qi < n; qi += kThreads) {
+        qt[qi] = a.sorted[start + qi];
+#ifdef EFUNC_DEBUG_BOUNDS
+        if constexpr (std::is_same<T, float>::value) {
+            const float half_r = (float)R * 0.5f, rmax = (float)(R - 1);
+            const float4 q = qt[qi];
+            bounds_ok(window_base(q.x, half_r, rmax) == w.cx && window_base(q.y, half_r, rmax) == w.cy &&
+                          window_base(q.z, half_r, rmax) == w.cz, 2);
+        }
+#endif
+    }
     __syncthreads();
 
     // ---- 2. forward, one (or 2 / 4) threads per query
@@ -937,6 +951,8 @@ __device__ __forceinline__ void item_body(const FusedArgsT<T> &a, const FusedArg
             int ox, oy, oz;
             if (full) { ox = c >> 4; oy = (c >> 2) & 3; oz = c & 3; }
             else { oz = c % w.nz; oy = (c / w.nz) % w.ny; ox = c / (w.ny * w.nz); }
+            const bool in_grid = bounds_ok((unsigned)(w.lox + ox) < (unsigned)R && (unsigned)(w.loy + oy) < (unsigned)R &&
+                                               (unsigned)(w.loz + oz) < (unsigned)R, 1);
             T *gr = ai.grad + (((size_t)(w.lox + ox) * R + (w.loy + oy)) * R + (w.loz + oz)) * kSlots;
             const T beta = -A.w * N::kLn2;
             // value term (dO/dtheta) plus, in second-order mode, the
@@ -944,7 +960,9 @@ __device__ __forceinline__ void item_body(const FusedArgsT<T> &a, const FusedArg
             const T go = acc[0] + acc[8];
             const T gdx = acc[1] + acc[9], gdy = acc[2] + acc[10], gdz = acc[3] + acc[11];
             const T gb = beta * (-acc[4] + acc[12]);
-            if (!offset) {
+            if (!in_grid) {
+                // skipped (bounds-check build)
+            } else if (!offset) {
                 atomicAdd(gr + 5, go);
                 atomicAdd(gr + 6, gdx);
                 atomicAdd(gr + 7, gdy);
@@ -1274,7 +1292,8 @@ __device__ __forceinline__ void grp_fwd_sums(const float4 *rec, const GroupWin &
 }
 
 template <int MODE, int KQ, bool BATCHED>
-__device__ __forceinline__ void grp_forward(const FusedArgs &ai, const float4 *rec, const float4 *qt, float4 *sq2,
+__device__ __forceinline__ void grp_forward(const int loss, const float inv_J, const float4 *rec, const float4 *qt,
+                                            float4 *sq2,
                                             const unsigned char *qoff, const int *beg, const int *pbeg,
                                             const GroupWin &g, int n, int R, float h, float3 orig, float &loss_acc,
                                             float &abs_acc)
@@ -1328,10 +1347,10 @@ __device__ __forceinline__ void grp_forward(const FusedArgs &ai, const float4 *r
         const float diff = O - q.w;
         float gO = 0.f;
         if (MODE == FIT) {
-            if (ai.loss == EFUNC_LOSS_L1) gO = diff > 0.f ? ai.inv_J : (diff < 0.f ? -ai.inv_J : 0.f);
-            else gO = 2.f * diff * ai.inv_J;
+            if (loss == EFUNC_LOSS_L1) gO = diff > 0.f ? inv_J : (diff < 0.f ? -inv_J : 0.f);
+            else gO = 2.f * diff * inv_J;
             if (valid && part == 0) {
-                loss_acc += ai.loss == EFUNC_LOSS_L1 ? fabsf(diff) : diff * diff;
+                loss_acc += loss == EFUNC_LOSS_L1 ? fabsf(diff) : diff * diff;
                 abs_acc += fabsf(diff);
             }
         } else if (valid && part == 0) {
@@ -1341,14 +1360,16 @@ __device__ __forceinline__ void grp_forward(const FusedArgs &ai, const float4 *r
         if (MODE == FIT && valid && part == 0) {
             // paired rows of the query's sub-cell, an odd last one padded
             const int r = qi - beg[off], p = 2 * pbeg[off] + r;
-            store_pair_query(sq2, p, q, lse2, O, gO);
-            if (qi == beg[off + 1] - 1 && (r & 1) == 0) store_pair_query(sq2, p + 1, q, lse2, O, 0.f);
+            if (bounds_ok(p + 1 < 2 * (kChunk / 2 + 8), 5)) {
+                store_pair_query(sq2, p, q, lse2, O, gO);
+                if (qi == beg[off + 1] - 1 && (r & 1) == 0) store_pair_query(sq2, p + 1, q, lse2, O, 0.f);
+            }
         }
     }
 }
 
 template <int MODE, bool BATCHED>
-__global__ void __launch_bounds__(kThreads, 8) grouped_kernel(FusedArgs a, BatchArgs b, const Item *gtop)
+__global__ void __launch_bounds__(kThreads, 7) grouped_kernel(FusedArgs a, BatchArgs b, const Item *gtop)
 {
     __shared__ float4 s_rec[kGCentres * kKeyRecords];
     __shared__ float4 s_qt[kChunk];
@@ -1375,19 +1396,21 @@ __global__ void __launch_bounds__(kThreads, 8) grouped_kernel(FusedArgs a, Batch
         if (t == 0) next = atomicAdd(&a.ctrl->next_group, 1);   // the next item, published at the end
         if (t < 9) s_beg[t] = 0;
         const Item item = gtop[-gi];
-        FusedArgs ai = a;
+        const float4 *keys = a.keys;
+        float *grad = a.grad;
+        float inv_J = a.inv_J;
         int R = a.R;
         if (BATCHED) {
             const BatchShape sh = b.shapes[item.w];
             R = sh.R;
-            ai.keys = a.keys + sh.c_off * kKeyRecords;
-            ai.grad = a.grad + sh.c_off * kSlots;
-            ai.inv_J = sh.inv_J;
+            keys = a.keys + sh.c_off * kKeyRecords;
+            grad = a.grad + sh.c_off * kSlots;
+            inv_J = sh.inv_J;
         }
         const float invR = 1.f / (float)R, h = 2.f * invR;
         const float half_r = (float)R * 0.5f, rmax = (float)(R - 1);
         const GroupWin g = group_window(item, R);
-        const int start = item.x, n = item.y;
+        const int start = item.x, n = bounds_ok(item.x >= 0 && item.y >= 1 && item.y <= kChunk, 8) ? item.y : 0;
         const float3 orig = make_float3((float)(2 * g.c0x + 1 - R) * invR, (float)(2 * g.c0y + 1 - R) * invR,
                                         (float)(2 * g.c0z + 1 - R) * invR);
         __syncthreads();   // s_beg cleared
@@ -1395,7 +1418,10 @@ __global__ void __launch_bounds__(kThreads, 8) grouped_kernel(FusedArgs a, Batch
         if (t < g.nc) {
             const int rowi = small_div(t, g.nz), oz = t - rowi * g.nz;
             const int ox = small_div(rowi, g.ny), oy = rowi - ox * g.ny;
-            const float4 *k = ai.keys + (((size_t)(g.lox + ox) * R + (g.loy + oy)) * R + (g.loz + oz)) * kKeyRecords;
+            int ix = g.lox + ox, iy = g.loy + oy, iz = g.loz + oz;
+            if (!bounds_ok((unsigned)ix < (unsigned)R && (unsigned)iy < (unsigned)R && (unsigned)iz < (unsigned)R, 3))
+                ix = iy = iz = 0;   // read centre 0 instead
+            const float4 *k = keys + (((size_t)ix * R + iy) * R + iz) * kKeyRecords;
             const float gx = (float)(2 * (g.lox + ox - g.c0x)) * invR, gy = (float)(2 * (g.loy + oy - g.c0y)) * invR,
                         gz = (float)(2 * (g.loz + oz - g.c0z)) * invR;
             const float4 kg = k[0], ko = k[2];
@@ -1408,7 +1434,9 @@ __global__ void __launch_bounds__(kThreads, 8) grouped_kernel(FusedArgs a, Batch
             const float4 q = a.sorted[start + qi];
             const int cx = window_base(q.x, half_r, rmax), cy = window_base(q.y, half_r, rmax),
                       cz = window_base(q.z, half_r, rmax);
-            const int o = ((cx - g.c0x) << 2) | ((cy - g.c0y) << 1) | (cz - g.c0z);
+            int o = ((cx - g.c0x) << 2) | ((cy - g.c0y) << 1) | (cz - g.c0z);
+            if (!bounds_ok((unsigned)(cx - g.c0x) < 2u && (unsigned)(cy - g.c0y) < 2u && (unsigned)(cz - g.c0z) < 2u, 4))
+                o = 0;
             s_qt[qi] = q;
             s_off[qi] = (unsigned char)o;
             atomicAdd(&s_beg[o + 1], 1);
@@ -1424,9 +1452,9 @@ __global__ void __launch_bounds__(kThreads, 8) grouped_kernel(FusedArgs a, Batch
         }
         __syncthreads();
         // ---- forward
-        if (n > 64) grp_forward<MODE, 1, BATCHED>(ai, s_rec, s_qt, s_sq2, s_off, s_beg, s_pbeg, g, n, R, h, orig, loss_acc, abs_acc);
-        else if (n > 32) grp_forward<MODE, 2, BATCHED>(ai, s_rec, s_qt, s_sq2, s_off, s_beg, s_pbeg, g, n, R, h, orig, loss_acc, abs_acc);
-        else grp_forward<MODE, 4, BATCHED>(ai, s_rec, s_qt, s_sq2, s_off, s_beg, s_pbeg, g, n, R, h, orig, loss_acc, abs_acc);
+        if (n > 64) grp_forward<MODE, 1, BATCHED>(a.loss, inv_J, s_rec, s_qt, s_sq2, s_off, s_beg, s_pbeg, g, n, R, h, orig, loss_acc, abs_acc);
+        else if (n > 32) grp_forward<MODE, 2, BATCHED>(a.loss, inv_J, s_rec, s_qt, s_sq2, s_off, s_beg, s_pbeg, g, n, R, h, orig, loss_acc, abs_acc);
+        else grp_forward<MODE, 4, BATCHED>(a.loss, inv_J, s_rec, s_qt, s_sq2, s_off, s_beg, s_pbeg, g, n, R, h, orig, loss_acc, abs_acc);
         if (MODE == FIT) {
             // ---- backward, sub-cell by sub-cell: thread t takes key t of the
             // sub-cell's window (set t / 64) over the sub-cell's query pairs
@@ -1476,9 +1504,11 @@ __global__ void __launch_bounds__(kThreads, 8) grouped_kernel(FusedArgs a, Batch
             const int row = g.nz * kSlots, lane = t & 31;
             for (int r = t >> 5; r < g.nx * g.ny; r += kThreads / 32) {
                 const int ox = small_div(r, g.ny), oy = r - ox * g.ny;
-                float *dst = ai.grad + (((size_t)(g.lox + ox) * R + (g.loy + oy)) * R + g.loz) * kSlots;
+                float *dst = grad + (((size_t)(g.lox + ox) * R + (g.loy + oy)) * R + g.loz) * kSlots;
                 float *src = s_grad + r * row;
-                for (int f = lane; f < row; f += 32) {
+                const bool in_grid = bounds_ok((unsigned)(g.lox + ox) < (unsigned)R && (unsigned)(g.loy + oy) < (unsigned)R &&
+                                                   (unsigned)g.loz + (unsigned)g.nz <= (unsigned)R, 3);
+                for (int f = lane; f < row && in_grid; f += 32) {
                     const float v = src[f];
                     if (v != 0.f) {
                         atomicAdd(dst + f, v);
@@ -1524,6 +1554,19 @@ __global__ void __launch_bounds__(kThreads, 8) grouped_kernel(FusedArgs a, Batch
 }
 
 }  // namespace
+
+
+int bounds_code_fused()
+{
+#ifdef EFUNC_DEBUG_BOUNDS
+    int c = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&c, g_bounds_code, sizeof c) != cudaSuccess) return -1;
+    if (c != 0 && cudaMemcpyToSymbol(g_bounds_code, &z, sizeof z) != cudaSuccess) return -1;
+    return c;
+#else
+    return 0;
+#endif
+}
 
 cudaError_t launch_grouped(const FusedArgs &a, const BatchArgs &b, const Item *gtop, bool eval, cudaStream_t s)
 {

@@ -268,10 +268,15 @@ __global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) scatter_kernel(S
         for (int u = 0; u < kUnroll; ++u) {
             const uint32_t rk = pos[u];   // (copy, rank in the copy)
             const uint32_t bin = query_bin(v[u].x, v[u].y, v[u].z, half_r, rmax, a.P);
+            if (!bounds_ok(bin < a.nbins, 6)) {
+                pos[u] = 0xffffffffu;   // skipped below
+                continue;
+            }
             pos[u] = K == 1 ? a.hist[bin] + rk : a.hist[(int64_t)(rk >> kRankBits) * a.nbins + bin] + (rk & kRankMask);
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
+            if (!bounds_ok(pos[u] < a.J, 7)) continue;
             a.sorted[pos[u]] = v[u];
             if (a.perm) a.perm[pos[u]] = (int)(j + u * stride);
         }
@@ -280,9 +285,11 @@ __global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) scatter_kernel(S
         float x, y, z, w;
         load_query(a.q, j, a.q_stride, VEC4, x, y, z, w);
         const uint32_t bin = query_bin(x, y, z, half_r, rmax, a.P);
+        if (!bounds_ok(bin < a.nbins, 6)) continue;
         const uint32_t rk = a.rank[j];
         const uint32_t pos =
             K == 1 ? a.hist[bin] + rk : a.hist[(int64_t)(rk >> kRankBits) * a.nbins + bin] + (rk & kRankMask);
+        if (!bounds_ok(pos < a.J, 7)) continue;
         a.sorted[pos] = make_float4(x, y, z, w);
         if (a.perm) a.perm[pos] = (int)j;
     }
@@ -600,6 +607,19 @@ cudaError_t launch_sort(const SortArgs &a, cudaStream_t s, int narrow_blocks)
 {
     return hist_copies(a.nbins) == 1 ? launch_sort_k<1>(a, s, narrow_blocks)
                                      : launch_sort_k<kCoarseCopies>(a, s, narrow_blocks);
+}
+
+
+int bounds_code_sort()
+{
+#ifdef EFUNC_DEBUG_BOUNDS
+    int c = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&c, g_bounds_code, sizeof c) != cudaSuccess) return -1;
+    if (c != 0 && cudaMemcpyToSymbol(g_bounds_code, &z, sizeof z) != cudaSuccess) return -1;
+    return c;
+#else
+    return 0;
+#endif
 }
 
 }  // namespace efunc
