@@ -48,7 +48,7 @@ assert api.debug_bounds() == 0
 for R, J in ((8, 5003), (16, 65536), (32, 1 << 18)):
     p = torch.from_numpy(synth.random_params(R, seed=R)).to(dev)
     qo = torch.from_numpy(synth.sample_batch(synth.random_union(R), J, seed=R)).to(dev)
-    O = api.efunc_forward(p, qo[:, :3])
+    O = api.efunc_forward(p, qo[:, :3].contiguous())
     g = api.efunc_backward(p, qo, torch.full((J,), 1.0 / J, device=dev))
     m, v = torch.zeros_like(p), torch.zeros_like(p)
     api.efunc_fit(p, m, v, qo, steps=3)                       # in line or pipelined, grouped at 32^3 x 2^18
@@ -82,5 +82,5 @@ def test_every_index_check_passes_on_the_hot_path():
     dev = torch.device("cuda:0")
     p = torch.from_numpy(synth.random_params(8, seed=8)).to(dev)
     qo = torch.from_numpy(synth.sample_batch(synth.random_union(8), 5003, seed=8)).to(dev)
-    O = api.efunc_forward(p, qo[:, :3]).cpu().numpy()
+    O = api.efunc_forward(p, qo[:, :3].contiguous()).cpu().numpy()
     np.testing.assert_array_equal(O, np.array(res["8"]["O"], dtype=np.float32))
