@@ -629,12 +629,14 @@ void efunc_profile_enable(int32_t enable);
  * "bin", "scan_reduce", "scan_top", "scan_emit", "scatter", "pack_keys",
  * "forward", "fused_backward", "fused_fit", "adam", "mean_shift", "variant_pack",
  * "variant_forward", "variant_backward", "variant_fit", "cosine_pack",
- * "cosine_forward", "cosine_backward", "cosine_fit", "eval" (efunc_eval_loss,
- * efunc_eval_batched), "f64" (every kernel of the FP64 calls), "batched"
- * (the batched fit's fused kernel), "batched_stats" (its per-shape
- * statistics), "enc_conv" / "enc_wgrad" (the encoder's tensor-core
- * convolutions and weight gradients) or "enc_aux" (its other kernels)).  Returns 0 on success, -1 for an
- * unknown name or a CUDA error. */
+ * "cosine_forward", "cosine_backward", "cosine_fit", "eval" (the fused
+ * kernel of efunc_eval_loss and efunc_eval_batched), "eval_finish" (the
+ * one-thread kernel that turns their sums into means), "f64" (every kernel
+ * of the FP64 calls), "batched" (the batched fit's fused kernel),
+ * "batched_stats" (its per-shape statistics), "enc_conv" / "enc_wgrad" (the
+ * encoder's tensor-core convolutions and weight gradients), "enc_aux" (its
+ * other kernels) or "grouped" (the grouped-item kernel)).  Returns 0 on
+ * success, -1 for an unknown name or a CUDA error. */
 int32_t efunc_profile_read(const char *name, double *total_ms, int64_t *launches);
 
 /* Clears the per-kernel totals (pending events are discarded). */

@@ -289,7 +289,8 @@ struct BatchedStatsArgs {
 // Kernel identifiers for the profiler.
 enum KernelId { K_BIN = 0, K_SCAN_REDUCE, K_SCAN_TOP, K_SCAN_EMIT, K_SCATTER, K_PACK_KEYS, K_FORWARD, K_FUSED_BWD,
                 K_FUSED_FIT, K_ADAM, K_MEAN_SHIFT, K_VAR_PACK, K_VAR_FORWARD, K_VAR_BACKWARD, K_VAR_FIT, K_COS_PACK, K_COS_FORWARD, K_COS_BACKWARD,
-                K_COS_FIT, K_EVAL, K_F64, K_BATCHED, K_BATCHED_STATS, K_ENC_CONV, K_ENC_WGRAD, K_ENC_AUX, K_GROUPED, K_COUNT };
+                K_COS_FIT, K_EVAL, K_F64, K_BATCHED, K_BATCHED_STATS, K_ENC_CONV, K_ENC_WGRAD, K_ENC_AUX, K_GROUPED,
+                K_EVAL_FINISH, K_COUNT };
 
 // Launch bookkeeping (launch counter and optional CUDA-event profiling).
 void launch_begin(int kid, cudaStream_t s);

@@ -45,7 +45,8 @@ const char *const kKernelNames[K_COUNT] = {"bin",       "scan_reduce", "scan_top
                                            "pack_keys", "forward",     "fused_backward", "fused_fit", "adam",
                                            "mean_shift", "variant_pack", "variant_forward", "variant_backward",
                                            "variant_fit", "cosine_pack", "cosine_forward", "cosine_backward",
-                                           "cosine_fit", "eval", "f64", "batched", "batched_stats", "enc_conv", "enc_wgrad", "enc_aux", "grouped"};
+                                           "cosine_fit", "eval", "f64", "batched", "batched_stats", "enc_conv", "enc_wgrad", "enc_aux", "grouped",
+                                           "eval_finish"};
 
 cudaEvent_t take_event()
 {

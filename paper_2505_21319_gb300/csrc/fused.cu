@@ -528,11 +528,26 @@ __device__ __forceinline__ float *pair_slot(float4 *rec2, int set, int k)
     return reinterpret_cast<float *>(rec2 + 4 * (kPairs * set + 2 * (k >> 2) + (k & 1))) + ((k >> 1) & 1);
 }
 
-__device__ __forceinline__ void stage_pair_key(float4 *rec2, int set, int k, float4 A, float4 B)
+// Stages key k (this lane) and key k ^ 2 (lane ^ 2: the other class of the
+// same pair) into their pair's four rows: the lane of class j writes P[0],
+// P[1], its partner P[2], P[3], each after one swap of half a key record, so
+// that the tile is written with conflict-free 16-byte stores.  Every lane of
+// the warp calls it; store = the pair is part of the tile.
+__device__ __forceinline__ void stage_pair_keys(float4 *rec2, int set, int k, bool store, float4 A, float4 B)
 {
-    float *f = pair_slot(rec2, set, k);
-    f[0] = A.x; f[2] = A.y; f[4] = A.z; f[6] = A.w;
-    f[8] = B.x; f[10] = B.y; f[12] = B.z; f[14] = B.w;
+    const bool hi = (k >> 1) & 1;   // class j + 2 of its pair
+    const float4 s = hi ? A : B;
+    const float4 r = make_float4(__shfl_xor_sync(kFull, s.x, 2), __shfl_xor_sync(kFull, s.y, 2),
+                                 __shfl_xor_sync(kFull, s.z, 2), __shfl_xor_sync(kFull, s.w, 2));
+    if (!store) return;
+    float4 *P = rec2 + 4 * (kPairs * set + 2 * (k >> 2) + (k & 1));
+    if (!hi) {
+        P[0] = make_float4(A.x, r.x, A.y, r.y);
+        P[1] = make_float4(A.z, r.z, A.w, r.w);
+    } else {
+        P[2] = make_float4(r.x, B.x, r.y, B.y);
+        P[3] = make_float4(r.z, B.z, r.w, B.w);
+    }
 }
 
 __device__ __forceinline__ float4 pair_keyA(const float4 *rec2, int set, int k)
@@ -645,12 +660,96 @@ __device__ __forceinline__ void fwd_sums_full_x2(const float4 *rec2, int part, f
     m = combine_x2<KQ>(mv, part);
 }
 
+__device__ __forceinline__ void fwd_pair_2q(const float4 *P, float2 xa, float2 ya, float2 za, float2 xb, float2 yb,
+                                            float2 zb, float2 nm, float2 &eva, float2 &mva, float2 &evb, float2 &mvb)
+{
+    const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3];
+    {
+        const float2 rx = sub2(xa, lo2(P0)), ry = sub2(ya, hi2(P0)), rz = sub2(za, lo2(P1));
+        const float2 d2 = fma2(rx, rx, fma2(ry, ry, mul2(rz, rz)));
+        const float2 l = ex2_2(fma2(hi2(P1), d2, nm));
+        const float2 f = fma2(hi2(P2), rx, fma2(lo2(P3), ry, fma2(hi2(P3), rz, lo2(P2))));
+        eva = add2(eva, l);
+        mva = fma2(l, f, mva);
+    }
+    {
+        const float2 rx = sub2(xb, lo2(P0)), ry = sub2(yb, hi2(P0)), rz = sub2(zb, lo2(P1));
+        const float2 d2 = fma2(rx, rx, fma2(ry, ry, mul2(rz, rz)));
+        const float2 l = ex2_2(fma2(hi2(P1), d2, nm));
+        const float2 f = fma2(hi2(P2), rx, fma2(lo2(P3), ry, fma2(hi2(P3), rz, lo2(P2))));
+        evb = add2(evb, l);
+        mvb = fma2(l, f, mvb);
+    }
+}
+
+// Full window, own query q of thread t (a for even, b for odd t): grid keys
+// on the lattice for the own query over all classes (as fwd_sums_full_x2<1>),
+// then the offset keys for both queries of the thread pair over the classes
+// j0, j0 + 2 of this thread, the class sums handed over by shuffles so that
+// every class is summed in row order as in the other lane counts.
+__device__ __forceinline__ void fwd_sums_full_o2q(const float4 *rec2, float h, float4 qa, float4 qb, float4 q, float &e,
+                                                  float &m)
+{
+    const int j0 = threadIdx.x & 1;
+    float2 ev[2], mv[2], rz[2], ry[4], y2[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        ry[a] = dup2(__fsub_rn(q.y, (float)(a - 1) * h));
+        y2[a] = mul2(ry[a], ry[a]);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        rz[i] = make_float2(__fsub_rn(q.z, (float)(i - 1) * h), __fsub_rn(q.z, (float)(i + 1) * h));
+        ev[i] = mv[i] = make_float2(0.f, 0.f);
+    }
+#pragma unroll 1
+    for (int ox = 0; ox < 4; ++ox) {
+        const float2 rx = dup2(__fsub_rn(q.x, (float)(ox - 1) * h));
+#pragma unroll
+        for (int oy = 0; oy < 4; ++oy) {
+            const float2 xy = fma2(rx, rx, y2[oy]);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const float4 *P = pair_of(rec2, 0, 2 * (4 * ox + oy) + i);
+                const float4 P1 = P[1], P2 = P[2], P3 = P[3];
+                const float2 l = ex2_2(mul2(hi2(P1), fma2(rz[i], rz[i], xy)));
+                const float2 f = fma2(hi2(P2), rx, fma2(lo2(P3), ry[oy], fma2(hi2(P3), rz[i], lo2(P2))));
+                ev[i] = add2(ev[i], l);
+                mv[i] = fma2(l, f, mv[i]);
+            }
+        }
+    }
+    // hand the partner the classes it continues for this thread's query
+    const float2 mine_e = j0 ? ev[1] : ev[0], mine_m = j0 ? mv[1] : mv[0];
+    const float2 send_e = j0 ? ev[0] : ev[1], send_m = j0 ? mv[0] : mv[1];
+    const float2 got_e = make_float2(__shfl_xor_sync(kFull, send_e.x, 1), __shfl_xor_sync(kFull, send_e.y, 1));
+    const float2 got_m = make_float2(__shfl_xor_sync(kFull, send_m.x, 1), __shfl_xor_sync(kFull, send_m.y, 1));
+    float2 eva = j0 ? got_e : mine_e, mva = j0 ? got_m : mine_m;
+    float2 evb = j0 ? mine_e : got_e, mvb = j0 ? mine_m : got_m;
+    const float2 xa = dup2(qa.x), ya = dup2(qa.y), za = dup2(qa.z);
+    const float2 xb = dup2(qb.x), yb = dup2(qb.y), zb = dup2(qb.z), nm = dup2(-0.f);
+#pragma unroll 1
+    for (int r0 = 0; r0 < kCentres / 4; r0 += 4)
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr)
+            fwd_pair_2q(pair_of(rec2, 1, 2 * (r0 + rr) + j0), xa, ya, za, xb, yb, zb, nm, eva, mva, evb, mvb);
+    // back: the own query's classes of the partner
+    const float2 se = j0 ? eva : evb, sm = j0 ? mva : mvb;
+    const float2 me = j0 ? evb : eva, mm = j0 ? mvb : mva;
+    const float re0 = __shfl_xor_sync(kFull, se.x, 1), re1 = __shfl_xor_sync(kFull, se.y, 1);
+    const float rm0 = __shfl_xor_sync(kFull, sm.x, 1), rm1 = __shfl_xor_sync(kFull, sm.y, 1);
+    e = (me.x + re0) + (me.y + re1);
+    m = (mm.x + rm0) + (mm.y + rm1);
+}
+
 // Forward of one query from the paired tile (as forward_query).
 template <int KQ, bool FULL>
-__device__ __forceinline__ FwdOut<float> forward_query_x2(const float4 *rec2, int nc, int part, float h, float4 q)
+__device__ __forceinline__ FwdOut<float> forward_query_x2(const float4 *rec2, int nc, int part, float h, float4 q,
+                                                          float4 qa, float4 qb)
 {
     float e, m;
-    if (FULL) fwd_sums_full_x2<KQ>(rec2, part, h, q.x, q.y, q.z, e, m);
+    if (FULL && KQ == 1) fwd_sums_full_o2q(rec2, h, qa, qb, q, e, m);
+    else if (FULL) fwd_sums_full_x2<KQ>(rec2, part, h, q.x, q.y, q.z, e, m);
     else fwd_sums_x2<KQ>(rec2, nc, part, q.x, q.y, q.z, -0.f, e, m);
     float M2 = 0.f;
     const bool tiny = !(e >= 0x1p-60f);
@@ -737,23 +836,37 @@ __device__ __forceinline__ void forward_phase(const FusedArgsT<T> &a, const V4Of
     const int part = t & (KQ - 1);
     constexpr int per_round = kThreads / KQ;
     for (int base = 0; base < n; base += per_round) {
+        // a warp without a query in this round leaves its issue slots to the other CTAs
+        if (base + ((t & ~31) >> LG) >= n) continue;
         const int qi = base + (t >> LG);
         const bool valid = qi < n;
         int j_user = 0;
         if (MODE != FIT && MODE != EVAL) j_user = valid ? __ldg(a.perm + start + qi) : 0;   // issued before the long compute
+        auto local_query = [&](int i) {
+            V v = N::v4(T(0.5) * h, T(0.5) * h, T(0.5) * h, T(0));
+            if (i < n) {
+                v = qt[i];
+                v.x -= orig.x;
+                v.y -= orig.y;
+                v.z -= orig.z;
+            }
+            return v;
+        };
         V q;
-        if (valid) {
-            q = qt[qi];
-            q.x -= orig.x;   // window-local coordinates
-            q.y -= orig.y;
-            q.z -= orig.z;
-        } else {
-            // lanes without a query evaluate the window centre (never stored)
-            q = N::v4(T(0.5) * h, T(0.5) * h, T(0.5) * h, T(0));
-        }
         FwdOut<T> r;
-        if constexpr (PAIRS) r = forward_query_x2<KQ, FULL>(rec2, nc, part, h, q);
-        else r = forward_query<KQ, FULL>(rec, nc, part, h, q);
+        if constexpr (PAIRS) {
+            if constexpr (KQ == 1 && FULL) {
+                const V qa = local_query(qi & ~1), qb = local_query(qi | 1);
+                q = (t & 1) ? qb : qa;
+                r = forward_query_x2<KQ, FULL>(rec2, nc, part, h, q, qa, qb);
+            } else {
+                q = local_query(valid ? qi : n);
+                r = forward_query_x2<KQ, FULL>(rec2, nc, part, h, q, q, q);
+            }
+        } else {
+            q = local_query(valid ? qi : n);
+            r = forward_query<KQ, FULL>(rec, nc, part, h, q);
+        }
         const T O = r.O, lse2 = r.lse2;
 
         T gO = T(0);
@@ -865,6 +978,8 @@ __device__ __forceinline__ void item_body(const FusedArgsT<T> &a, const FusedArg
     // ---- 1. stage the key records (positions made window-local) and
     // queries: thread t stages key t (set t / 64 of centre t mod 64)
     const int kc = t & (kCentres - 1), kset = t / kCentres;
+    // keys past the window's last centre (up to a multiple of 4) are neutral
+    V A = N::v4(T(1e18), T(1e18), T(1e18), T(-1)), B = N::v4(T(0), T(0), T(0), T(0));
     if (kc < nc) {
         int ox, oy, oz;
         if (full) { ox = kc >> 4; oy = (kc >> 2) & 3; oz = kc & 3; }
@@ -875,21 +990,19 @@ __device__ __forceinline__ void item_body(const FusedArgsT<T> &a, const FusedArg
         const V *k = ai.keys + (((size_t)ix * R + iy) * R + iz) * kKeyRecords;
         const T gx = (T)(2 * (w.lox + ox - w.cx)) * invR, gy = (T)(2 * (w.loy + oy - w.cy)) * invR,
                 gz = (T)(2 * (w.loz + oz - w.cz)) * invR;
-        const V p = k[2 * kset], B = k[2 * kset + 1];
-        const V A = kset ? N::v4(gx + p.x, gy + p.y, gz + p.z, p.w) : N::v4(gx, gy, gz, p.w);
+        const V p = k[2 * kset];
+        B = k[2 * kset + 1];
+        A = kset ? N::v4(gx + p.x, gy + p.y, gz + p.z, p.w) : N::v4(gx, gy, gz, p.w);
         if constexpr (NEED_REC) {
             rec[4 * kc + 2 * kset] = A;
             rec[4 * kc + 2 * kset + 1] = B;
         }
         if constexpr (PAIRS) {
-            stage_pair_key(rec2, kset, kc, A, B);
             keyT[2 * t] = A;
             keyT[2 * t + 1] = B;
         }
-    } else if (PAIRS && kc < ((nc + 3) & ~3)) {
-        // neutral keys up to a multiple of 4
-        stage_pair_key(rec2, kset, kc, make_float4(1e18f, 1e18f, 1e18f, -1.f), make_float4(0.f, 0.f, 0.f, 0.f));
     }
+    if constexpr (PAIRS) stage_pair_keys(rec2, kset, kc, kc < ((nc + 3) & ~3), A, B);
     for (int qi = t; qi < n; qi += kThreads) {
         qt[qi] = a.sorted[start + qi];
 #ifdef EFUNC_DEBUG_BOUNDS
@@ -915,10 +1028,13 @@ __device__ __forceinline__ void item_body(const FusedArgsT<T> &a, const FusedArg
         else forward_phase<MODE, DQ, GEIK, 4, false>(ai, rec, rec2, qt, qB, sq2, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
     }
     if (BWD) {
-        // ---- 3. backward, one thread per key
+        // ---- 3. backward, one thread per key (the window is formed again
+        // from the item instead of being held through the forward)
         __syncthreads();
         const int c = t & (kCentres - 1);
-        if (c < nc) {
+        const Window w = window_of(item, R);
+        const bool full = w.nc == kCentres;
+        if (c < w.nc) {
             const bool offset = t >= kCentres;
             V A, B;
             if constexpr (PAIRS) {
@@ -1168,9 +1284,9 @@ __global__ void eval_finish_kernel(const Ctrl *ctrl, double inv_J, float *out)
 
 cudaError_t launch_eval_finish(const Ctrl *ctrl, double inv_J, float *out, cudaStream_t s)
 {
-    launch_begin(K_EVAL, s);
+    launch_begin(K_EVAL_FINISH, s);
     eval_finish_kernel<<<1, 1, 0, s>>>(ctrl, inv_J, out);
-    launch_end(K_EVAL, s);
+    launch_end(K_EVAL_FINISH, s);
     return cudaGetLastError();
 }
 
