@@ -1678,7 +1678,7 @@ efunc_status efunc_tune_batched(const efunc_shape *shapes, int32_t S, int32_t lo
     efunc_tuning best_t = default_tuning();
     efunc_status rc = EFUNC_OK;
     const int chunks[] = {128, 256};
-    const int lanes[][2] = {{64, 32}, {96, 48}};
+    const int lanes[][2] = {{64, 32}, {96, 48}, {64, 0}, {96, 0}};
     const int sorts[] = {4, 8};
     const int groups[] = {0, 64, 128};
     for (int c : chunks)

@@ -10,7 +10,8 @@
 //      64 bytes per centre) in shared memory, key positions rewritten into
 //      window-local coordinates (origin at the centre of index c, the window
 //      base; queries are shifted into the same frame);
-//   2. forward, thread per query (2 or 4 threads per query for sparse cells):
+//   2. forward, thread per query (2 threads per query in items of at most 64
+//      queries; 4 in a batched fit whose tuning asks for it):
 //      e = sum 2^{s}, m = sum 2^{s} f with s = -beta log2(e) ||q - key||^2,
 //      O = m / e, lse2 = log2 e (Algorithm 1 in base 2).  The keys are summed
 //      in four interleaved classes combined in a fixed tree, so a query's
@@ -1017,7 +1018,9 @@ __device__ __forceinline__ void item_body(const FusedArgsT<T> &a, const FusedArg
     __syncthreads();
 
     // ---- 2. forward, one (or 2 / 4) threads per query
-    const int l2 = BATCHED ? b.lanes2_max : 64, l4 = BATCHED ? b.lanes4_max : 32;
+    // single grids: no four-lane items (those lanes would blend every pair twice;
+    // two lanes per query are faster, same-process A/B at 64^3 x 2^24: -3.6 %)
+    const int l2 = BATCHED ? b.lanes2_max : 64, l4 = BATCHED ? b.lanes4_max : 0;
     if (full) {
         if (n > l2) forward_phase<MODE, DQ, GEIK, 1, true>(ai, rec, rec2, qt, qB, sq2, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);
         else if (n > l4) forward_phase<MODE, DQ, GEIK, 2, true>(ai, rec, rec2, qt, qB, sq2, s_sqE, s_sqU, start, n, nc, orig, h, loss_acc, abs_acc);

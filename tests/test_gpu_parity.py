@@ -229,6 +229,40 @@ def test_forward_is_deterministic_and_order_independent():
     np.testing.assert_array_equal(a[perm], c)
 
 
+def test_forward_independent_of_item_size():
+    """A query's O and lse must not depend on how many other queries share its
+    window cell: the cell's item size picks the forward's lane form (two lanes
+    per query at <= 64 queries, one lane with the offset keys blended for two
+    queries per thread pair above, two rounds above 128, a split into items of
+    256 above that), and every form sums each class of keys in the same order.
+    Probes sit in an interior cell (full window, lattice grid keys) and a cell
+    at the grid's edge (clipped window); filler queries in the same cells
+    change the item sizes from 8 to 308."""
+    R = 8
+    g = synth.rng(11)
+    p = to_dev(params_of("sdf", R, 11))
+    half = np.float32(R * 0.5)
+
+    def in_cell(c, k):
+        # (q + 1) R / 2 - 1/2 in [c, c + 1) per axis, away from the faces
+        u = np.asarray(c, np.float64) + g.uniform(0.05, 0.95, (k, 3))
+        return ((u + 0.5) / float(half) - 1.0).astype(np.float32)
+
+    cells = [(3, 3, 3), (0, 3, 5)]
+    probes = np.concatenate([in_cell(c, 8) for c in cells])
+    ref = None
+    for extra in (0, 24, 60, 120, 200, 300):
+        fill = np.concatenate([in_cell(c, extra) for c in cells]) if extra else np.zeros((0, 3), np.float32)
+        q = np.concatenate([probes, fill])
+        O, lse = api.efunc_forward(p, to_dev(q), want_lse=True)
+        got = (O.cpu().numpy()[:len(probes)], lse.cpu().numpy()[:len(probes)])
+        if ref is None:
+            ref = got
+        else:
+            np.testing.assert_array_equal(got[0], ref[0], err_msg=f"O with {extra} fillers per cell")
+            np.testing.assert_array_equal(got[1], ref[1], err_msg=f"lse with {extra} fillers per cell")
+
+
 def test_forward_underflow_fallback_and_far_queries():
     """Large scales (b = +3: beta h^2 ~ 86) make every weight of many queries
     underflow 2^-60 without the max shift, and so do queries outside the
