@@ -317,7 +317,7 @@ efunc_status efunc_fit_graph(const efunc_grid *grid, const efunc_adam *adam, int
  * keeps it until the process exits).
  *   - Limit: requests whose efunc_eval_workspace_bytes(grid, J) exceeds
  *     32 MiB return EFUNC_ERR_WORKSPACE with nothing enqueued.  That admits
- *     up to 1,268,480 queries at R = 32, 1,372,896 at R = 16 and 435,648 at
+ *     up to 1,245,200 queries at R = 32, 1,372,896 at R = 16 and 435,648 at
  *     R = 64; larger requests need efunc_forward with a caller workspace.
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device current); make that first call before
