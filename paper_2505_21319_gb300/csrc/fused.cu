@@ -1132,10 +1132,9 @@ __global__ void __launch_bounds__(kThreads, min_ctas<GEIK, T>()) fused_kernel(Fu
     const int n_items = a.ctrl->n_items;
     T loss_acc = T(0), abs_acc = T(0);
 
+    if (t == 0) s_item = atomicAdd(&a.ctrl->next_item, 1);
     for (;;) {
-        __syncthreads();   // the previous item is consumed
-        if (t == 0) s_item = atomicAdd(&a.ctrl->next_item, 1);
-        __syncthreads();
+        __syncthreads();   // s_item published; the previous item is consumed
         const int it = s_item;
         if (it >= n_items) break;
         const Item item = a.items[it];
@@ -1165,6 +1164,10 @@ __global__ void __launch_bounds__(kThreads, min_ctas<GEIK, T>()) fused_kernel(Fu
             item_body<MODE, DQ, GEIK, T, BATCHED>(a, a, b, item, R, invR, h, s_rec, s_rec2, s_keyT, s_qt, s_sqB,
                                                   s_sq2, s_sqE, s_sqU, loss_acc, abs_acc);
         }
+        // thread 0 has done its share of the item: claim the next one while
+        // the other warps finish theirs (every thread read s_item before the
+        // staging barrier of this item)
+        if (t == 0) s_item = atomicAdd(&a.ctrl->next_item, 1);
     }
 
     if (!BATCHED && (MODE == FIT || MODE == EVAL)) {
