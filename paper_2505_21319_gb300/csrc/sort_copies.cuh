@@ -1,8 +1,9 @@
 // Histogram copies of the cell sort.  A bin holds tens to thousands of
 // queries of a 2^22 batch (most near the surface), and the histogram atomics
 // of one bin, issued from every SM, queue at one L2 address.  On grids of at
-// most kCopiesBins bins (R <= 47) the histogram has kCoarseCopies copies
-// (measured at 32^3 x 2^22: the in-line bin kernel 0.096 -> 0.063 ms),
+// most kCopiesBins bins (R <= 47) the histogram has room for kCoarseCopies
+// copies (measured at 32^3 x 2^22: the in-line bin kernel 0.096 -> 0.063 ms;
+// the narrow sort beside a fit kernel uses them on coarse grids only),
 // copy-major (entry
 // copy * nbins + bin: the copies of a bin lie a whole histogram apart, in
 // different L2 lines and slices), and a query takes its rank in one copy;
