@@ -94,21 +94,32 @@ WORKLOAD = "C2 plain fit: 32^3x13 FP32 grid, 2^22 queries/step (50% uniform, 50%
            "union of 8 random primitives, L1 loss, Adam lr 1e-3"
 
 
-def fused_traffic():
-    """DRAM bytes per fused launch from the committed ncu summary, or None when
-    the kernel's sources changed since that capture."""
+def kernel_source_hash() -> str:
+    """SHA-256 of the fused kernel's sources with comments and blank lines
+    removed, so that the hash follows the code, not its prose."""
     import hashlib
     import re
     h = hashlib.sha256()
     for f in ("paper_2505_21319_gb300/csrc/fused.cu", "paper_2505_21319_gb300/csrc/common.cuh"):
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        src = open(os.path.join(ROOT, f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        lines = [ln.rstrip() for ln in src.splitlines() if ln.strip()]
+        h.update("\n".join(lines).encode())
+    return h.hexdigest()
+
+
+def fused_traffic():
+    """DRAM bytes per fused launch from the committed ncu summary, or None when
+    the kernel's code changed since that capture."""
+    import re
     try:
         txt = open(os.path.join(ROOT, "profiles", "fused_fit_32cubed_2p22.md")).read()
     except OSError:
         return None
     sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
     tb = re.search(r"traffic_bytes_per_launch:\s*(\d+)", txt)
-    if not sha or not tb or sha.group(1) != h.hexdigest():
+    if not sha or not tb or sha.group(1) != kernel_source_hash():
         return None
     return int(tb.group(1))
 

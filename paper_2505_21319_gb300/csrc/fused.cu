@@ -661,6 +661,9 @@ __device__ __forceinline__ void fwd_sums_full_x2(const float4 *rec2, int part, f
     m = combine_x2<KQ>(mv, part);
 }
 
+// fwd_pair for two queries a and b from one load of the pair: the forward
+// is bound by these broadcast 16-byte shared loads (two wavefronts each), so
+// the threads of a pair in one-lane-per-query items share them (below).
 __device__ __forceinline__ void fwd_pair_2q(const float4 *P, float2 xa, float2 ya, float2 za, float2 xb, float2 yb,
                                             float2 zb, float2 nm, float2 &eva, float2 &mva, float2 &evb, float2 &mvb)
 {
@@ -743,7 +746,9 @@ __device__ __forceinline__ void fwd_sums_full_o2q(const float4 *rec2, float h, f
     m = (mm.x + rm0) + (mm.y + rm1);
 }
 
-// Forward of one query from the paired tile (as forward_query).
+// Forward of one query from the paired tile (as forward_query).  qa and qb
+// are the two queries of this thread's pair (even and odd thread), used by
+// full windows with one lane per query; q is this thread's own.
 template <int KQ, bool FULL>
 __device__ __forceinline__ FwdOut<float> forward_query_x2(const float4 *rec2, int nc, int part, float h, float4 q,
                                                           float4 qa, float4 qb)

@@ -50,3 +50,20 @@ def test_eikonal_counts_add_the_second_order_terms():
     plain = bench.algorithmic_ops(q, R)
     assert plain == 64 * bench.OPS_PER_CENTRE_FULL + bench.OPS_PER_QUERY_FULL_SETUP + 8 * bench.OPS_PER_CENTRE
     assert bench.eikonal_algorithmic_ops(q, R) == plain + nc.sum() * bench.EIK_EXTRA_PER_CENTRE
+
+
+def test_kernel_source_hash_follows_code_not_comments(tmp_path, monkeypatch):
+    """The DRAM traffic of the committed ncu summary is reported only while the
+    fused kernel's code hashes to the summary's value: comment and blank-line
+    edits keep the hash, any code edit changes it."""
+    csrc = tmp_path / "paper_2505_21319_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    code = "int f(int x)\n{\n    return x + 1;   // one more\n}\n"
+    (csrc / "fused.cu").write_text(code)
+    (csrc / "common.cuh").write_text("/* header */\n#pragma once\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    (csrc / "fused.cu").write_text("// leading note\n" + code.replace("// one more", "/* one\n more */") + "\n\n")
+    assert bench.kernel_source_hash() == h0
+    (csrc / "fused.cu").write_text(code.replace("x + 1", "x + 2"))
+    assert bench.kernel_source_hash() != h0
