@@ -278,3 +278,19 @@ def test_batched_validation_enqueues_nothing(lib):
     assert lib.efunc_tune_batched(sh, 2, 0, 16, 32, 48, 64, 1, 0, ctypes.byref(B.Tuning()), None, 1 << 30, ws,
                                   None) == 1       # no trial steps
     assert lib.efunc_launch_count() == n0
+
+
+def test_noalloc_capacities_in_the_header(lib):
+    """The capacities the header states for efunc_forward_noalloc follow from
+    the forward's workspace layout and the fixed 32 MiB array: each is the
+    largest J whose efunc_eval_workspace_bytes fits (host arithmetic only)."""
+    src = open(HEADER).read()
+    m = re.search(r"up to ([\d,]+) queries at R = 32, ([\d,]+) at R = 16 and ([\d,]+) at\s*\*\s*R = 64", src)
+    assert m, "capacity sentence not found in efunc.h"
+    stated = {32: int(m.group(1).replace(",", "")), 16: int(m.group(2).replace(",", "")),
+              64: int(m.group(3).replace(",", ""))}
+    cap = 32 << 20
+    for R, J in stated.items():
+        g = B.Grid(R, 2, float(lib.efunc_default_log_beta0(R)))
+        assert 0 < lib.efunc_eval_workspace_bytes(ctypes.byref(g), J) <= cap, R
+        assert lib.efunc_eval_workspace_bytes(ctypes.byref(g), J + 1) > cap, R
