@@ -617,6 +617,8 @@ def main():
                     help="steps of the batched fit of 256 shapes (0 skips it)")
     ap.add_argument("--target-steps", type=int, default=2000,
                     help="steps of the plain fits to the MAE target (0 skips them)")
+    ap.add_argument("--dense-reps", type=int, default=5,
+                    help="efunc_forward calls over a 256^3 lattice of points (0 skips the dense query)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-seconds", type=float, default=150.0,
                     help="--impl reference: seconds of oracle work over warm-up and timed steps")
@@ -819,6 +821,31 @@ def main():
                    "ops_per_pair": MEAN_SHIFT_OPS_PER_PAIR}
         del scratch, pts
 
+    # ---- dense query (inference): efunc_forward over a 256^3 lattice of points
+    # filling the domain, on the fitted grid (sort, key pack, forward, outputs
+    # in the lattice's order).  The paper's timing discussion after Table
+    # tab:memory_time quotes about 5 s for such a 256^3 query with global
+    # support on unstated hardware: context, not a comparable figure.
+    dense = None
+    if args.dense_reps > 0:
+        n_ax = 256
+        ax = (torch.arange(n_ax, device=dev, dtype=torch.float32) + 0.5) * (2.0 / n_ax) - 1.0
+        lat = torch.stack(torch.meshgrid(ax, ax, ax, indexing="ij"), dim=-1).reshape(-1, 3).contiguous()
+        api.efunc_forward(params, lat)
+        torch.cuda.synchronize(dev)
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        for _ in range(args.dense_reps):
+            api.efunc_forward(params, lat)
+        d1.record(stream)
+        torch.cuda.synchronize(dev)
+        dms = d0.elapsed_time(d1) / args.dense_reps
+        dense = {"points": int(lat.shape[0]), "R": R, "ms": dms, "pts_per_s": lat.shape[0] / (dms * 1e-3),
+                 "timing": "CUDA events around efunc_forward calls (sort, key pack, forward, outputs in lattice order)",
+                 "paper": "about 5 s for a 256^3 dense query with global support, hardware not stated (context)"}
+        del lat
+
     # ---- ablation variants of Table tab:ablation: the same fit (sort, pack,
     # fused forward + L1 + backward, Adam) with each configuration's layout
     variants = None
@@ -1012,6 +1039,7 @@ def main():
             "e2e": e2e,
             "eikonal_fit": eik,
             "mean_shift_init": ms_init,
+            "dense_query_256cubed": dense,
             "variants": variants,
             "cosine_series": cosine,
             "graph_fit": graph_fit,
