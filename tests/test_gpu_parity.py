@@ -163,7 +163,7 @@ def to_dev(a):
 
 # ------------------------------------------------------------------ sort
 
-@pytest.mark.parametrize("R,J", [(1, 100), (4, 3001), (16, 70001), (32, 1 << 18)])
+@pytest.mark.parametrize("R,J", [(1, 100), (4, 3001), (16, 70001), (32, 1 << 18), (40, 1 << 18), (48, 1 << 18)])
 def test_cell_sort_groups_queries_by_window(R, J):
     qo = mixed_queries(R, J, seed=R)
     qs, perm = api.efunc_cell_sort(to_dev(qo), R)
